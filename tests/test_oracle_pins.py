@@ -1,0 +1,496 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics.
+
+Each test pins one part of the oracle to something other than itself: values
+printed in Table II, textbook complex-power flows, closed forms at flat start,
+the series-loss identity, invariances of the flow equations, complex-step and
+finite-difference derivatives of an independently written textbook c(x), dense
+brute force for the condensed matrix, and the C library for sin/cos.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2405_14032_b300 import synth
+from tests import helpers as H
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def cfg1():
+    inst = synth.config_instance("cfg1")
+    pt = synth.make_point(1, inst)
+    o = oracle.Oracle(inst)
+    return inst, pt, o
+
+
+def _parse_rounded(s):
+    return float(s[:-1]) * (1e3 if s.endswith("k") else 1e6)
+
+
+# ---------------------------------------------------------------------------
+# Layout counts (Table II)
+# ---------------------------------------------------------------------------
+def test_table2_counts_match_paper():
+    """nvars and ncons of Table II (rounded as printed) come out of the oracle's
+    layout for networks of those sizes; the reference row must be counted
+    (case118 x 168 gives 268k only with it)."""
+    rows = [ln.split() for ln in open(os.path.join(HERE, "golden", "table2_counts.txt"))
+            if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 6
+    for case, N, L, G, T, nv, nc in rows:
+        N, L, G, T = int(N), int(L), int(G), int(T)
+        net = H.network(N, np.zeros(L, np.int32), np.ones(L, np.int32), np.full(L, 0.01), np.full(L, 0.1),
+                        np.zeros(L), gen_bus=np.zeros(G, np.int32), load_bus=[0])
+        o = oracle.Oracle(H.instance(net, T, pd=np.zeros(T), qd=np.zeros(T)))
+        unit = 1e3 if nv.endswith("k") else 1e6
+        assert round(o.n / unit) == _parse_rounded(nv) / unit, (case, T, o.n)
+        unit = 1e3 if nc.endswith("k") else 1e6
+        assert round(o.m / unit) == _parse_rounded(nc) / unit, (case, T, o.m)
+        if case == "case118" and T == 168:
+            assert round((o.m - T) / 1e3) != 268  # without the reference row it would read 267k
+
+
+def test_cfg_sizes():
+    o = oracle.Oracle(synth.config_instance("cfg1"))
+    assert (o.n, o.m, o.nnz_jac, o.nnz_hess) == (944, 1410, 5248, 2560)
+
+
+# ---------------------------------------------------------------------------
+# Flows
+# ---------------------------------------------------------------------------
+def _two_bus(tap=1.0, shift=0.0, r=0.02, x=0.08, b=0.03):
+    net = H.network(2, [0], [1], [r], [x], [b], gen_bus=[0], load_bus=[1], tap=[tap], shift=[shift])
+    return H.instance(net, 1, pd=[0.0], qd=[0.0])
+
+
+def _flows_from_complex_power(r, x, b, tap, shift, vf, vt, thf, tht):
+    """Textbook branch flows from complex power S = V conj(I)."""
+    y = 1.0 / complex(r, x)
+    Vf = vf * np.exp(1j * thf)
+    Vt = vt * np.exp(1j * tht)
+    a = tap * np.exp(1j * shift)
+    If = (y + 1j * b / 2) / abs(a) ** 2 * Vf - y / np.conj(a) * Vt
+    It = -y / a * Vf + (y + 1j * b / 2) * Vt
+    Sf = Vf * np.conj(If)
+    St = Vt * np.conj(It)
+    return Sf.real, Sf.imag, St.real, St.imag
+
+
+@pytest.mark.parametrize("tap,shift", [(1.0, 0.0), (1.05, 0.0), (0.97, 0.1), (1.0, -0.2)])
+def test_two_bus_closed_form(tap, shift):
+    inst = _two_bus(tap, shift)
+    o = oracle.Oracle(inst)
+    sl = H.var_slices(inst.net, 1)
+    x = np.zeros(o.n)
+    vf, vt, thf, tht = 1.03, 0.98, 0.12, -0.07
+    x[sl["va"]] = [thf, tht]
+    x[sl["vm"]] = [vf, vt]
+    c = o.eval(x, np.zeros(o.m), 1.0)["c"]
+    ro = H.row_offsets(inst.net, 1)
+    Pf, Qf, Pt, Qt = (-c[ro[k]] for k in (1, 2, 3, 4))  # arc variables are 0
+    ePf, eQf, ePt, eQt = _flows_from_complex_power(0.02, 0.08, 0.03, tap, shift, vf, vt, thf, tht)
+    for got, exp in ((Pf, ePf), (Qf, eQf), (Pt, ePt), (Qt, eQt)):
+        assert abs(got - exp) <= 1e-13 * (1 + abs(exp)), (got, exp)
+
+
+def test_flat_start(cfg1):
+    """vm = 1, va = 0, tau = 1, phi = 0: P_fr = gff + gft = 0 and
+    Q_fr = -bff - bft = -b/2 (charging only)."""
+    inst, pt, o = cfg1
+    net = inst.net
+    sl = H.var_slices(net, inst.T)
+    x = np.zeros(o.n)
+    x[sl["vm"]] = 1.0
+    c = o.eval(x, pt.lam, 1.0)["c"]
+    ro = H.row_offsets(net, inst.T)
+    L = net.n_branch
+    for k, expect in ((1, 0.0), (2, net.br_b / 2), (3, 0.0), (4, net.br_b / 2)):
+        got = c[ro[k]:ro[k + 1]].reshape(inst.T, L)  # p - P = 0 - P
+        np.testing.assert_allclose(got, np.broadcast_to(expect, got.shape), rtol=0, atol=1e-13)
+
+
+def test_series_loss_identity(cfg1):
+    """tau = 1: P_fr + P_to = g |V_f - V_t|^2 and
+    Q_fr + Q_to = -b |V_f - V_t|^2 - (b_c/2)(vf^2 + vt^2), y = g + jb."""
+    inst, pt, o = cfg1
+    net, T, L = inst.net, inst.T, inst.net.n_branch
+    sl = H.var_slices(net, T)
+    x = pt.x.copy()
+    x[sl["p"]] = 0.0
+    x[sl["q"]] = 0.0
+    c = o.eval(x, pt.lam, 1.0)["c"]
+    ro = H.row_offsets(net, T)
+    Pf, Qf, Pt, Qt = (-c[ro[k]:ro[k + 1]].reshape(T, L) for k in (1, 2, 3, 4))
+    va = x[sl["va"]].reshape(T, -1)
+    vm = x[sl["vm"]].reshape(T, -1)
+    f, t = net.br_f, net.br_t
+    y = 1.0 / (net.br_r + 1j * net.br_x)
+    dV2 = np.abs(vm[:, f] * np.exp(1j * va[:, f]) - vm[:, t] * np.exp(1j * va[:, t])) ** 2
+    np.testing.assert_allclose(Pf + Pt, y.real * dV2, rtol=1e-11, atol=1e-13)
+    np.testing.assert_allclose(Qf + Qt, -y.imag * dV2 - net.br_b / 2 * (vm[:, f] ** 2 + vm[:, t] ** 2),
+                               rtol=1e-11, atol=1e-13)
+
+
+def test_paper_mutual_term_form(cfg1):
+    """Without its self term, the to-end flow is the form printed in Eq. (1d, 1e):
+    v_m v_n [G cos(th_n - th_m) + B sin(th_n - th_m)] and
+    v_m v_n [G sin(th_n - th_m) - B cos(th_n - th_m)] with G = gtf, B = btf."""
+    inst, pt, o = cfg1
+    net, T, L = inst.net, inst.T, inst.net.n_branch
+    sl = H.var_slices(net, T)
+    x = pt.x.copy()
+    x[sl["p"]] = 0.0
+    x[sl["q"]] = 0.0
+    c = o.eval(x, pt.lam, 1.0)["c"]
+    ro = H.row_offsets(net, T)
+    Pt = -c[ro[3]:ro[4]].reshape(T, L)
+    Qt = -c[ro[4]:ro[5]].reshape(T, L)
+    gff, bff, gft, bft, gtf, btf, gtt, btt = o.branch_terms()
+    va = x[sl["va"]].reshape(T, -1)
+    vm = x[sl["vm"]].reshape(T, -1)
+    f, t = net.br_f, net.br_t
+    d = va[:, t] - va[:, f]
+    u = vm[:, f] * vm[:, t]
+    np.testing.assert_allclose(Pt - gtt * vm[:, t] ** 2, u * (gtf * np.cos(d) + btf * np.sin(d)), rtol=1e-12,
+                               atol=1e-12)
+    np.testing.assert_allclose(Qt + btt * vm[:, t] ** 2, u * (gtf * np.sin(d) - btf * np.cos(d)), rtol=1e-12,
+                               atol=1e-12)
+
+
+def test_pi_model_terms_textbook():
+    """tau = 1, phi = 0: Y_ff = Y_tt = y + j b/2, Y_ft = Y_tf = -y (exactly)."""
+    inst = synth.config_instance("cfg1")
+    o = oracle.Oracle(inst)
+    gff, bff, gft, bft, gtf, btf, gtt, btt = o.branch_terms()
+    y = 1.0 / (inst.net.br_r + 1j * inst.net.br_x)
+    np.testing.assert_allclose(gff + 1j * bff, y + 0.5j * inst.net.br_b, rtol=1e-15)
+    np.testing.assert_array_equal(gff, gtt)
+    np.testing.assert_array_equal(bff, btt)
+    np.testing.assert_array_equal(gft, -gff)
+    np.testing.assert_array_equal(gtf, gft)
+    np.testing.assert_array_equal(bft, btf)
+
+
+def test_rotation_invariance_and_homogeneity(cfg1):
+    """Flows depend on angle differences only, so d/dth_f + d/dth_t = 0 on the
+    flow rows and c is unchanged by a common angle shift; flows are degree-2
+    homogeneous in (vf, vt): vf dE/dvf + vt dE/dvt = 2E."""
+    inst, pt, o = cfg1
+    net, T, L = inst.net, inst.T, inst.net.n_branch
+    sl = H.var_slices(net, T)
+    r = o.eval(pt.x, pt.lam, 1.0)
+    jr, jc = o.jac_pattern()
+    ro = H.row_offsets(net, T)
+    rp = o.jac_rowptr()
+    x2 = pt.x.copy()
+    x2[sl["va"]] += 0.37
+    c2 = o.eval(x2, pt.lam, 1.0)["c"]
+    flow = slice(ro[1], ro[5])
+    np.testing.assert_allclose(c2[flow], r["c"][flow], rtol=0, atol=5e-14 * 60)
+    for k in (1, 2, 3, 4):
+        for i in range(ro[k], ro[k + 1]):
+            s = rp[i]
+            jv = r["jv"][s:s + 5]
+            assert jv[1] + jv[2] == 0.0
+            tt, l = divmod(i - ro[k], L)
+            vf = pt.x[sl["vm"]][tt * net.n_bus + net.br_f[l]]
+            vt = pt.x[sl["vm"]][tt * net.n_bus + net.br_t[l]]
+            arc = pt.x[jc[s]]
+            E = arc - r["c"][i]
+            # J = -dE/dv, so vf J_vf + vt J_vt = -2E
+            assert abs(vf * jv[3] + vt * jv[4] + 2 * E) <= 1e-13 * (1 + abs(E) + abs(vf * jv[3]) + abs(vt * jv[4]))
+
+
+def test_balance_constructed_feasible():
+    """A point made feasible by hand (arc variables set to the textbook flows,
+    one load per bus set to close the balance) has zero flow and balance
+    residuals up to rounding."""
+    net0 = synth.make_network(11, 40, 64, 9, 0)
+    N, T = net0.n_bus, 3
+    net = H.network(N, net0.br_f, net0.br_t, net0.br_r, net0.br_x, net0.br_b, gen_bus=net0.gen_bus,
+                    load_bus=np.arange(N), gs=np.linspace(0, 0.05, N), bs=np.linspace(0.3, 0, N),
+                    ref=net0.ref_bus)
+    inst = H.instance(net, T, pd=np.zeros(T * N), qd=np.zeros(T * N))
+    o = oracle.Oracle(inst)
+    pt = synth.make_point(12, inst)
+    x = pt.x.copy()
+    sl = H.var_slices(net, T)
+    ro = H.row_offsets(net, T)
+    L = net.n_branch
+    c0 = o.cons_textbook(x)
+    # arc p, q := flows (c = arc - E  =>  E = arc - c)
+    for k, (var, off) in enumerate((("p", 0), ("q", 0), ("p", L), ("q", L)), start=1):
+        E = (x[sl[var]].reshape(T, 2 * L)[:, off:off + L] - c0[ro[k]:ro[k + 1]].reshape(T, L))
+        blk = x[sl[var]].reshape(T, 2 * L)
+        blk[:, off:off + L] = E
+        x[sl[var]] = blk.ravel()
+    va = x[sl["va"]].reshape(T, N)
+    vm = x[sl["vm"]].reshape(T, N)
+    p = x[sl["p"]].reshape(T, 2 * L)
+    q = x[sl["q"]].reshape(T, 2 * L)
+    pg = x[sl["pg"]].reshape(T, -1)
+    qg = x[sl["qg"]].reshape(T, -1)
+    arc_bus = np.concatenate([net.br_f, net.br_t])
+    pd = np.zeros((T, N))
+    qd = np.zeros((T, N))
+    for n in range(N):
+        gens = np.nonzero(net.gen_bus == n)[0]
+        arcs = np.nonzero(arc_bus == n)[0]
+        pd[:, n] = pg[:, gens].sum(1) - p[:, arcs].sum(1) - net.bus_gs[n] * vm[:, n] ** 2
+        qd[:, n] = qg[:, gens].sum(1) - q[:, arcs].sum(1) + net.bus_bs[n] * vm[:, n] ** 2
+    inst2 = H.instance(net, T, pd=pd, qd=qd)
+    o2 = oracle.Oracle(inst2)
+    c = o2.eval(x, pt.lam, 1.0)["c"]
+    scale = 1 + np.abs(x).max() * 20
+    assert np.abs(c[ro[1]:ro[5]]).max() <= 1e-14 * scale
+    assert np.abs(c[ro[8]:ro[10]]).max() <= 1e-14 * scale
+    assert np.array_equal(va, va)  # angles untouched
+
+
+# ---------------------------------------------------------------------------
+# Derivatives: complex step and finite differences of the textbook c(x)
+# ---------------------------------------------------------------------------
+def _dense_J(o, r):
+    jr, jc = o.jac_pattern()
+    return H.dense_jac(jr, jc, r["jv"], o.m, o.n), jr, jc
+
+
+def test_jacobian_complex_step(cfg1):
+    inst, pt, o = cfg1
+    r = o.eval(pt.x, pt.lam, 1.0)
+    J, jr, jc = _dense_J(o, r)
+    mask = np.zeros_like(J, dtype=bool)
+    mask[jr, jc] = True
+    worst = 0.0
+    for j in range(o.n):
+        e = np.zeros(o.n)
+        e[j] = 1.0
+        col = o.cons_cstep(pt.x, e)
+        assert np.all(col[~mask[:, j]] == 0.0), j  # nothing outside the pattern
+        err = np.abs(col - J[:, j]) / (1.0 + np.abs(J[:, j]))
+        worst = max(worst, err.max())
+    assert worst <= 2e-14, worst
+
+
+def test_jacobian_finite_difference(cfg1):
+    inst, pt, o = cfg1
+    r = o.eval(pt.x, pt.lam, 1.0)
+    J, _, _ = _dense_J(o, r)
+    h = 1e-6
+    rng = np.random.default_rng(0)
+    for j in rng.choice(o.n, 80, replace=False):
+        xp, xm = pt.x.copy(), pt.x.copy()
+        xp[j] += h
+        xm[j] -= h
+        fd = (o.cons_textbook(xp) - o.cons_textbook(xm)) / (2 * h)
+        np.testing.assert_allclose(fd, J[:, j], rtol=1e-7, atol=1e-7)
+
+
+def test_constraints_match_textbook(cfg1):
+    """The rounding-order evaluation equals the textbook expression (C-library
+    sin/cos, no fma) to a few ulps of the terms."""
+    inst, pt, o = cfg1
+    c = o.eval(pt.x, pt.lam, 1.0)["c"]
+    ct = o.cons_textbook(pt.x)
+    assert np.abs(c - ct).max() <= 64 * np.spacing(60.0)
+
+
+def test_objective_and_gradient(cfg1):
+    inst, pt, o = cfg1
+    r = o.eval(pt.x, pt.lam, 1.0)
+    assert abs(r["f"] - o.obj_textbook(pt.x)) <= 1e-13 * abs(r["f"])
+    sl = H.var_slices(inst.net, inst.T)
+    pg = pt.x[sl["pg"]].reshape(inst.T, -1)
+    np.testing.assert_allclose(r["g"][sl["pg"]].reshape(inst.T, -1), 2 * inst.net.gen_c2 * pg + inst.net.gen_c1,
+                               rtol=1e-15)
+    g = r["g"].copy()
+    g[sl["pg"]] = 0
+    assert np.all(g == 0)
+
+
+def test_hessian_complex_step_and_symmetry(cfg1):
+    """Column j of W equals Im(grad L(x + i h e_j)) / h, and the complex-step
+    matrix is symmetric (the J formulas are a true gradient)."""
+    inst, pt, o = cfg1
+    r = o.eval(pt.x, pt.lam, pt.sigma)
+    hr, hc = o.hess_pattern()
+    assert np.all(hr >= hc)
+    W = H.dense_sym(hr, hc, r["hv"], o.n)
+    Wcs = np.empty((o.n, o.n))
+    for j in range(o.n):
+        e = np.zeros(o.n)
+        e[j] = 1.0
+        Wcs[:, j] = o.gradlag_cstep(pt.x, pt.lam, pt.sigma, e)
+    scale = 1.0 + np.abs(W)
+    assert (np.abs(Wcs - W) / scale).max() <= 2e-14
+    assert (np.abs(Wcs - Wcs.T) / scale).max() <= 2e-14
+    # outside the pattern, nothing
+    mask = np.zeros((o.n, o.n), bool)
+    mask[hr, hc] = True
+    mask |= mask.T
+    assert np.all(Wcs[~mask] == 0.0)
+
+
+def test_hessian_finite_difference(cfg1):
+    inst, pt, o = cfg1
+    r = o.eval(pt.x, pt.lam, pt.sigma)
+    hr, hc = o.hess_pattern()
+    W = H.dense_sym(hr, hc, r["hv"], o.n)
+    h = 1e-6
+    rng = np.random.default_rng(1)
+    for j in rng.choice(o.n, 60, replace=False):
+        xp, xm = pt.x.copy(), pt.x.copy()
+        xp[j] += h
+        xm[j] -= h
+        fd = (o.gradlag(xp, pt.lam, pt.sigma) - o.gradlag(xm, pt.lam, pt.sigma)) / (2 * h)
+        np.testing.assert_allclose(fd, W[:, j], rtol=1e-6, atol=1e-6)
+
+
+# ---------------------------------------------------------------------------
+# Condensed matrix
+# ---------------------------------------------------------------------------
+def test_kkt_dense_brute_force(cfg1):
+    """M = W + diag(Sigma_x + delta_w) + J^T D J (dense numpy) and its pattern
+    is diag U pattern(W) U {pairs within a J row}."""
+    inst, pt, o = cfg1
+    r = o.eval(pt.x, pt.lam, pt.sigma)
+    J, jr, jc = _dense_J(o, r)
+    hr, hc = o.hess_pattern()
+    W = H.dense_sym(hr, hc, r["hv"], o.n)
+    Md = W + np.diag(pt.sigma_x + pt.delta_w) + J.T @ (pt.dvec[:, None] * J)
+    mag = np.abs(W) + np.diag(pt.sigma_x + pt.delta_w) + np.abs(J).T @ (pt.dvec[:, None] * np.abs(J))
+    rowptr, cols, vals = o.kkt_csr(pt.x, pt.lam, pt.sigma, pt.sigma_x, pt.dvec, pt.delta_w)
+    rows = np.repeat(np.arange(o.n), np.diff(rowptr))
+    assert np.all(cols <= rows)
+    for i in range(o.n):  # sorted, unique, diagonal last
+        seg = cols[rowptr[i]:rowptr[i + 1]]
+        assert np.all(np.diff(seg) > 0) and seg[-1] == i
+    # pattern from the definition
+    pat = set(zip(range(o.n), range(o.n)))
+    pat |= set(zip(hr.tolist(), hc.tolist()))
+    rp = o.jac_rowptr()
+    for i in range(o.m):
+        cs = jc[rp[i]:rp[i + 1]]
+        for a in cs:
+            for b in cs:
+                if a >= b:
+                    pat.add((int(a), int(b)))
+    assert pat == set(zip(rows.tolist(), cols.tolist()))
+    err = np.abs(vals - Md[rows, cols])
+    assert np.all(err <= 4e-16 * 8 * mag[rows, cols] + 1e-300)
+
+
+def test_kkt_matrix_free_product(cfg1):
+    inst, pt, o = cfg1
+    r = o.eval(pt.x, pt.lam, pt.sigma)
+    J, _, _ = _dense_J(o, r)
+    hr, hc = o.hess_pattern()
+    rowptr, cols, vals = o.kkt_csr(pt.x, pt.lam, pt.sigma, pt.sigma_x, pt.dvec, pt.delta_w)
+    Ms = H.csr_to_dense_sym(rowptr, cols, vals, o.n)
+    v = np.random.default_rng(2).standard_normal(o.n)
+    Wv = o.hvp(pt.x, pt.lam, pt.sigma, v)
+    mv = Wv + (pt.sigma_x + pt.delta_w) * v + o.vjp(pt.x, pt.dvec * o.jvp(pt.x, v))[0]
+    mag = np.abs(Ms) @ np.abs(v)
+    assert np.all(np.abs(Ms @ v - mv) <= 1e-13 * mag)
+
+
+# ---------------------------------------------------------------------------
+# Matrix-free products
+# ---------------------------------------------------------------------------
+def test_vjp_jvp_hvp(cfg1):
+    inst, pt, o = cfg1
+    r = o.eval(pt.x, pt.lam, pt.sigma)
+    J, _, _ = _dense_J(o, r)
+    hr, hc = o.hess_pattern()
+    W = H.dense_sym(hr, hc, r["hv"], o.n)
+    rng = np.random.default_rng(3)
+    y = rng.standard_normal(o.m)
+    v = rng.standard_normal(o.n)
+    gx, gpd, gqd = o.vjp(pt.x, y)
+    jv = o.jvp(pt.x, v)
+    hv = o.hvp(pt.x, pt.lam, pt.sigma, v)
+    assert np.all(np.abs(gx - J.T @ y) <= 1e-14 * (np.abs(J).T @ np.abs(y)) + 1e-300)
+    assert np.all(np.abs(jv - J @ v) <= 1e-14 * (np.abs(J) @ np.abs(v)) + 1e-300)
+    assert np.all(np.abs(hv - W @ v) <= 1e-14 * (np.abs(W) @ np.abs(v)) + 1e-300)
+    # dot-product test <y, J v> = <J^T y, v>
+    assert abs(y @ jv - gx @ v) <= 1e-13 * (np.abs(y) @ (np.abs(J) @ np.abs(v)))
+    # load adjoint: dc/dPd = -1 at the P-balance row of the load's bus
+    T, N, D = inst.T, inst.net.n_bus, inst.net.n_load
+    ro = H.row_offsets(inst.net, T)
+    for t in range(T):
+        for d in range(D):
+            assert gpd[t * D + d] == -y[ro[8] + t * N + inst.net.load_bus[d]]
+            assert gqd[t * D + d] == -y[ro[9] + t * N + inst.net.load_bus[d]]
+
+
+def test_load_adjoint_complex_step():
+    """(dc/dPd)^T y by finite change of the loads through the textbook c."""
+    inst = synth.make_instance(21, 12, 20, 3, 7, 2)
+    o = oracle.Oracle(inst)
+    pt = synth.make_point(21, inst)
+    y = np.random.default_rng(4).standard_normal(o.m)
+    _, gpd, _ = o.vjp(pt.x, y)
+    base = o.cons_textbook(pt.x)
+    pd = inst.pd.copy()
+    pd[1, 3] += 0.5
+    o2 = oracle.Oracle(synth.Instance(net=inst.net, T=2, pd=pd, qd=inst.qd))
+    dc = (o2.cons_textbook(pt.x) - base) / 0.5
+    assert abs(dc @ y - gpd[1 * 7 + 3]) <= 1e-12
+
+
+def test_hvp_finite_difference(cfg1):
+    inst, pt, o = cfg1
+    v = np.random.default_rng(5).standard_normal(o.n)
+    h = 1e-6
+    fd = (o.gradlag(pt.x + h * v, pt.lam, pt.sigma) - o.gradlag(pt.x - h * v, pt.lam, pt.sigma)) / (2 * h)
+    np.testing.assert_allclose(o.hvp(pt.x, pt.lam, pt.sigma, v), fd, rtol=1e-6, atol=1e-6)
+
+
+def test_windowed_outputs_agree_with_full():
+    inst = synth.make_instance(31, 25, 40, 5, 10, 6)
+    o = oracle.Oracle(inst)
+    pt = synth.make_point(31, inst)
+    full = o.eval(pt.x, pt.lam, pt.sigma)
+    rows, rowlen, cols, vals = o.kkt(pt.x, pt.lam, pt.sigma, pt.sigma_x, pt.dvec, pt.delta_w)
+    rowptr = np.concatenate([[0], np.cumsum(rowlen)])
+    for t0, t1 in ((0, 2), (2, 5), (5, 6)):
+        w = o.eval(pt.x, pt.lam, pt.sigma, t0, t1)
+        for k in ("g", "c", "jv", "hv"):
+            ok = ~np.isnan(w[k])
+            assert ok.any()
+            assert np.array_equal(w[k][ok], full[k][ok])
+        wr, wl, wc, wv = o.kkt(pt.x, pt.lam, pt.sigma, pt.sigma_x, pt.dvec, pt.delta_w, t0, t1)
+        pos = np.concatenate([np.arange(rowptr[r], rowptr[r + 1]) for r in wr])
+        assert np.array_equal(cols[pos], wc) and np.array_equal(vals[pos], wv)
+        gx, _, _ = o.vjp(pt.x, pt.lam, t0, t1)
+        gxf, _, _ = o.vjp(pt.x, pt.lam)
+        ok = ~np.isnan(gx)
+        assert np.array_equal(gx[ok], gxf[ok])
+
+
+# ---------------------------------------------------------------------------
+# sin / cos
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("lo,hi", [(-math.pi / 4, math.pi / 4), (-3.0, 3.0), (-1e5, 1e5)])
+def test_sincos_against_c_library(lo, hi):
+    x = np.random.default_rng(6).uniform(lo, hi, 200000)
+    s, c = oracle.sincos(x)
+    es = np.abs(s - np.sin(x)) / np.spacing(np.abs(np.sin(x)) + 1e-300)
+    ec = np.abs(c - np.cos(x)) / np.spacing(np.abs(np.cos(x)) + 1e-300)
+    near_zero = (np.abs(np.sin(x)) < 1e-3) | (np.abs(np.cos(x)) < 1e-3)
+    assert es[~near_zero].max() <= 2 and ec[~near_zero].max() <= 2
+    assert np.all(np.abs(s - np.sin(x)) <= 4e-16) and np.all(np.abs(c - np.cos(x)) <= 4e-16)
+    assert np.abs(s * s + c * c - 1).max() <= 5e-16
+
+
+def test_sincos_special_values():
+    s, c = oracle.sincos(np.array([0.0, -0.0, math.pi / 6, math.pi / 2, 1e-300]))
+    # the sign of a zero result is not specified (values compare equal)
+    assert s[0] == 0.0 and c[0] == 1.0 and s[1] == 0.0 and c[1] == 1.0
+    assert abs(s[2] - 0.5) <= 2 * np.spacing(0.5)
+    assert abs(c[3]) <= 1e-16 and s[3] == 1.0
+    assert s[4] == 1e-300
