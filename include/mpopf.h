@@ -1,0 +1,186 @@
+/*
+ * mpopf.h -- C ABI of libmpopf: the data-parallel hot path inside each
+ * interior-point iteration of the multi-period AC OPF method of
+ * arXiv 2405.14032 (Shin, Rao, Schanen, Maldonado, Anitescu), on one NVIDIA
+ * B300 (sm_103a).
+ *
+ * The library evaluates the NLP callbacks of the multi-period AC OPF model
+ * (Eq. 1, in the standard form of Eq. 3) and assembles the condensed KKT matrix
+ * M = W + delta_w I + Sigma_x + J^T D J of the lifted-KKT interior-point method
+ * (Sec. III-B).  All values are IEEE binary64.
+ *
+ * Conventions (every entry point):
+ *   - Device pointers are CUDA device memory owned by the caller unless stated
+ *     otherwise; outputs are written, never read.  Pointers must be 8-byte
+ *     aligned.  Host pointers are plain host memory (pinned memory makes the
+ *     copies of mpopf_sweep_host asynchronous).
+ *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy default
+ *     stream.  Work is enqueued asynchronously on it; nothing synchronises
+ *     unless stated.  Calls on one handle must not overlap in time (they share
+ *     the handle's scratch buffer).
+ *   - Return value: MPOPF_OK (0) or a negative code; mpopf_last_error() gives a
+ *     message (thread-local).  No call allocates device memory except
+ *     mpopf_setup (and, once, mpopf_sweep_host for its staging buffers).
+ *   - Outputs are deterministic: identical inputs give bitwise-identical
+ *     outputs (no atomics on values).  There is no CPU fallback: without a
+ *     CUDA device every call returns MPOPF_ERR_CUDA.
+ *
+ * Model layout (0-based; N buses, L branches, G generators, D loads, T periods;
+ * arc a = l is the from end of branch l, arc a = L + l its to end):
+ *   variables x [n], n = T (2N + 2G + 4L), kind-major then period then component:
+ *     va[t][i] at t N + i;  vm at T N + t N + i;  pg at 2TN + t G + g;
+ *     qg at 2TN + TG + t G + g;  p[t][a] at 2TN + 2TG + 2tL + a;
+ *     q[t][a] at 2TN + 2TG + 2TL + 2tL + a.
+ *   constraint rows [m], m = T (1 + 7L + 2N) + G (T - 1):
+ *     K0  reference angle       t                      va[t][ref]              = 0
+ *     K1  from-end P flow      T + 0TL + tL + l        p[t][l]   - P_fr        = 0
+ *     K2  from-end Q flow      T + 1TL + tL + l        q[t][l]   - Q_fr        = 0
+ *     K3  to-end P flow        T + 2TL + tL + l        p[t][L+l] - P_to        = 0
+ *     K4  to-end Q flow        T + 3TL + tL + l        q[t][L+l] - Q_to        = 0
+ *     K5  angle difference     T + 4TL + tL + l        va_f - va_t  in [angmin, angmax]
+ *     K6  thermal, from end    T + 5TL + tL + l        p^2 + q^2 - smax^2 <= 0
+ *     K7  thermal, to end      T + 6TL + tL + l        (arc L + l)
+ *     K8  P balance            T + 7TL + tN + n        sum pg - sum p_a - gs vm^2 - sum Pd = 0
+ *     K9  Q balance            T + 7TL + TN + tN + n   sum qg - sum q_a + bs vm^2 - sum Qd = 0
+ *     K10 P ramp (t >= 1)      T + 7TL + 2TN + (t-1)G + g   pg[t] - pg[t-1] in [-ramp, ramp]
+ *   Flows are the pi-model of a branch with series admittance 1/(r + jx),
+ *   charging b, tap tau and shift phi (Eq. 1d, 1e print the mutual term only).
+ *   Objective (Eq. 1a): f = sum_{t,g} c2 pg^2 + c1 pg + c0.
+ *
+ * Patterns (fixed at setup, Sec. III-A "pre-analyzed sparsity patterns"):
+ *   J (COO): rows ascending; within a row the J order
+ *     K0 [va_ref]; K1..K4 [arc, va_f, va_t, vm_f, vm_t]; K5 [va_f, va_t];
+ *     K6/K7 [p_a, q_a]; K8 [vm_n, pg of the bus ascending, p_a of the bus
+ *     ascending]; K9 the same with qg, q_a; K10 [pg_t, pg_{t-1}].
+ *   W = sigma grad^2 f + sum_i lambda_i grad^2 c_i (Eq. 4), lower COO
+ *     (row >= col), duplicates allowed (a consumer sums them), groups in order:
+ *     objective (t, g) [pg,pg]; branch (t, l) 10 entries over (va_f, va_t,
+ *     vm_f, vm_t) pairs (0,0),(1,0),(1,1),(2,0),(2,1),(2,2),(3,0),(3,1),(3,2),
+ *     (3,3); thermal (t, l) [p_from, q_from, p_to, q_to] diagonals; shunt
+ *     (t, n) [vm,vm] P part then Q part.
+ *   M (CSR, lower incl. the full diagonal): pattern = diag U pattern(W) U
+ *     {pairs of columns sharing a J row}; columns ascending in each row.
+ *   Sign convention: the caller passes lambda as it appears in W; the paper's
+ *     p_x = grad f - J^T y implies lambda = -y.
+ */
+#ifndef MPOPF_H
+#define MPOPF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  MPOPF_OK = 0,
+  MPOPF_ERR_ARG = -1,   /* bad argument (NULL pointer, index out of range, ...) */
+  MPOPF_ERR_SIZE = -2,  /* sizes overflow the index types (n, m must be < 2^31) */
+  MPOPF_ERR_CUDA = -3,  /* CUDA error (no device, launch failure, ...) */
+  MPOPF_ERR_ALLOC = -4  /* device allocation failed */
+};
+
+/* Output selection bits for mpopf_eval. */
+enum {
+  MPOPF_OUT_OBJ = 1,
+  MPOPF_OUT_GRAD = 2,
+  MPOPF_OUT_CONS = 4,
+  MPOPF_OUT_JAC = 8,
+  MPOPF_OUT_HESS = 16,
+  MPOPF_OUT_KKT = 32,
+  MPOPF_OUT_ALL = 63
+};
+
+/* Network data (Eq. 1 and its nomenclature), host arrays owned by the caller;
+ * mpopf_setup copies them.  Per-unit values.  Requirements: n_bus >= 1,
+ * 0 <= ref_bus < n_bus, branch ends in range and distinct (self-loops are
+ * rejected), tap != 0, r^2 + x^2 > 0, generator and load buses in range. */
+typedef struct {
+  int32_t n_bus, n_branch, n_gen, n_load, ref_bus;
+  const double *bus_gs, *bus_bs, *bus_vmin, *bus_vmax;          /* [N] */
+  const int32_t *br_f, *br_t;                                   /* [L] */
+  const double *br_r, *br_x, *br_b, *br_tap, *br_shift;        /* [L] */
+  const double *br_smax, *br_angmin, *br_angmax;                /* [L] */
+  const int32_t *gen_bus;                                       /* [G] */
+  const double *gen_c2, *gen_c1, *gen_c0;                       /* [G] */
+  const double *gen_pmin, *gen_pmax, *gen_qmin, *gen_qmax, *gen_ramp; /* [G] */
+  const int32_t *load_bus;                                      /* [D] */
+} mpopf_network;
+
+/* Sizes and patterns.  Every pointer is DEVICE memory owned by the handle and
+ * valid until mpopf_destroy. */
+typedef struct {
+  int64_t n, m, nnz_jac, nnz_hess, nnz_kkt;
+  int32_t n_bus, n_branch, n_gen, n_load, n_periods;
+  const int32_t *jac_row, *jac_col;    /* [nnz_jac] */
+  const int32_t *hess_row, *hess_col;  /* [nnz_hess], row >= col */
+  const int64_t *kkt_rowptr;           /* [n + 1] */
+  const int32_t *kkt_col;              /* [nnz_kkt], ascending, col <= row */
+  const double *xl, *xu;               /* [n] variable bounds (Eq. 1g-1i), +-INFINITY if none */
+  const double *gl, *gu;               /* [m] row bounds (Eq. 1f, 1j, 1k; equalities 0) */
+} mpopf_pattern;
+
+typedef struct mpopf_handle mpopf_handle;
+
+/* Setup (once): validates the network, builds the layout and every pattern
+ * (Sec. III-A: sparsity analysed once per pattern, then expanded over the
+ * data), uploads network data and the loads pd/qd (host [T][D], row-major; may
+ * be NULL when D = 0), and allocates the handle's scratch.  Synchronous.
+ * On success *out is a new handle and *pat (may be NULL) its patterns. */
+int mpopf_setup(const mpopf_network *net, int32_t n_periods, const double *pd, const double *qd,
+                mpopf_handle **out, mpopf_pattern *pat);
+
+/* Pattern of an existing handle. */
+int mpopf_get_pattern(const mpopf_handle *h, mpopf_pattern *pat);
+
+/* Replace the per-period loads (Eq. 1b, 1c right-hand sides) from DEVICE
+ * arrays d_pd, d_qd [T][D]; stream-ordered copy into the handle. */
+int mpopf_set_loads(mpopf_handle *h, const double *d_pd, const double *d_qd, void *stream);
+
+/* Evaluation at x [n] (device).  Each output pointer may be NULL (skipped);
+ * `outputs` selects with MPOPF_OUT_* bits which non-NULL outputs to compute.
+ *   f       [1]          objective (Eq. 1a); deterministic tree reduction
+ *   grad    [n]          gradient of f
+ *   c       [m]          constraint values
+ *   jv      [nnz_jac]    J values in the COO order of the pattern
+ *   hv      [nnz_hess]   W values (needs lam [m], sigma)
+ *   kv      [nnz_kkt]    M = W + diag(sigma_x + delta_w) + J^T diag(dvec) J
+ *                        (Sec. III-B condensed matrix; needs lam, sigma,
+ *                        sigma_x [n], dvec [m], delta_w)
+ * Reads x, lam, sigma_x, dvec once; computes each product once.  */
+int mpopf_eval(mpopf_handle *h, unsigned outputs, const double *x, const double *lam, double sigma,
+               const double *sigma_x, const double *dvec, double delta_w, double *f, double *grad, double *c,
+               double *jv, double *hv, double *kv, void *stream);
+
+/* The individual callbacks (each = mpopf_eval with one output bit). */
+int mpopf_eval_obj(mpopf_handle *h, const double *x, double *f, void *stream);
+int mpopf_eval_grad(mpopf_handle *h, const double *x, double *grad, void *stream);
+int mpopf_eval_cons(mpopf_handle *h, const double *x, double *c, void *stream);
+int mpopf_eval_jac(mpopf_handle *h, const double *x, double *jv, void *stream);
+int mpopf_eval_hess(mpopf_handle *h, const double *x, const double *lam, double sigma, double *hv, void *stream);
+int mpopf_assemble_kkt(mpopf_handle *h, const double *x, const double *lam, double sigma, const double *sigma_x,
+                       const double *dvec, double delta_w, double *kv, void *stream);
+
+/* Full sweep: all six outputs in one pass (= mpopf_eval with MPOPF_OUT_ALL). */
+int mpopf_sweep(mpopf_handle *h, const double *x, const double *lam, double sigma, const double *sigma_x,
+                const double *dvec, double delta_w, double *f, double *grad, double *c, double *jv, double *hv,
+                double *kv, void *stream);
+
+/* Full sweep from HOST buffers: copies x, lam, sigma_x, dvec to the device,
+ * runs mpopf_sweep and copies all six outputs back to the host buffers, then
+ * synchronises `stream`.  Staging buffers are allocated on the first call and
+ * kept by the handle. */
+int mpopf_sweep_host(mpopf_handle *h, const double *x, const double *lam, double sigma, const double *sigma_x,
+                     const double *dvec, double delta_w, double *f, double *grad, double *c, double *jv,
+                     double *hv, double *kv, void *stream);
+
+/* Number of kernel launches one mpopf_eval call with these output bits makes. */
+int mpopf_launch_count(const mpopf_handle *h, unsigned outputs);
+
+void mpopf_destroy(mpopf_handle *h);
+const char *mpopf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MPOPF_H */

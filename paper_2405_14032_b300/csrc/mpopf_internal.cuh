@@ -1,0 +1,90 @@
+// Internal layout shared by the setup and the evaluation kernels of libmpopf.
+#pragma once
+#include <cstdint>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "mpopf.h"
+
+namespace mpopf {
+
+// Per-branch constants (structure of arrays, [BC_COUNT][L]).
+enum {
+  BC_GFF, BC_BFF, BC_GFT, BC_BFT, BC_GTF, BC_BTF, BC_GTT, BC_BTT,  // pi-model terms
+  BC_G2FF, BC_B2FF, BC_G2TT, BC_B2TT,                              // 2 x self terms
+  BC_SMAX2,                                                        // smax^2
+  BC_COUNT
+};
+
+// Everything a kernel needs, passed by value.
+struct Dev {
+  int32_t N, L, G, D, T, ref;
+  int64_t n, m;
+  // variable block starts (va at 0)
+  int64_t x_vm, x_pg, x_qg, x_p, x_q;
+  // constraint block starts (K0 at 0, K_k (1..7) at T + (k-1) T L)
+  int64_t c_k8, c_k9, c_k10;
+  // J value starts (K0 at 0, K_k (1..4) at T + 5 (k-1) T L)
+  int64_t j_k5, j_k6, j_k7, j_k8, j_k9, j_k10, jk8_per;
+  // W value starts (objective at 0)
+  int64_t h_br, h_th, h_sh;
+  // M: region start of each variable kind and per-period block sizes
+  int64_t m_va, m_vm, m_pg, m_qg, m_p, m_q;
+  int64_t mb_va, mb_vm, mb_pg0, mb_pg1, mb_qg, mb_p, mb_q;
+  int64_t nnz_jac, nnz_hess, nnz_kkt;
+  // network
+  const int32_t *br_f, *br_t;
+  const double *bc;         // [BC_COUNT][L]
+  const uint8_t *br_sym;    // 1 if gtf == gft and btf == bft bitwise
+  const double *bus_m2gs, *bus_p2bs, *bus_mgs, *bus_bs;
+  const int32_t *bgen_ptr, *bgen_idx;    // generators of a bus, ascending
+  const int32_t *barc_ptr, *barc_idx;    // arcs of a bus, ascending arc index
+  const int32_t *bload_ptr, *bload_idx;  // loads of a bus, ascending
+  const int32_t *inc_ptr, *inc_code;     // incident branches by branch index: code = 2 l + end (0 from, 1 to)
+  const int32_t *nbr_ptr, *nbr_bus, *nbr_grp;  // distinct neighbours ascending; nbr_grp[k]..[k+1] into grp_code
+  const int32_t *grp_code;               // branches joining the bus to a neighbour, ascending: 2 l + end
+  const int32_t *bus_nd, *bus_ndlt;      // distinct neighbours; those with a smaller index
+  const int32_t *gen_bus, *gen_rank;     // rank = position among the generators of its bus
+  const double *gen_c2, *gen_c1, *gen_c0, *gen_c2x2;
+  const int32_t *arc_rank;               // position among the arcs of its bus
+  const int32_t *jk8_off;                // offset of the K8 (and K9) J row of bus n inside a period block
+  // M row offsets inside a period block
+  const int32_t *mo_va, *mo_vm, *mo_pg0, *mo_pg1, *mo_qg, *mo_p, *mo_q;
+  // loads [T][D]
+  const double *pd, *qd;
+  // scratch: per branch-period the 6 distinct values of the branch element's
+  // bus-variable block of M, [T][L][6]; objective partial sums
+  double *S;
+  double *fpart;
+  int32_t fpart_n;
+};
+
+inline constexpr int kBlock = 256;
+
+// Kernel launchers (mpopf_kernels.cu).
+cudaError_t launch_eval(const Dev &d, unsigned outputs, const double *x, const double *lam, double sigma,
+                        const double *sx, const double *dv, double dw, double *f, double *grad, double *c,
+                        double *jv, double *hv, double *kv, cudaStream_t s);
+int eval_launch_count(const Dev &d, unsigned outputs);
+// Pattern expansion (mpopf_setup.cu).
+cudaError_t launch_patterns(const Dev &d, int32_t *jrow, int32_t *jcol, int32_t *hrow, int32_t *hcol,
+                            int64_t *krowptr, int32_t *kcol, double *xl, double *xu, double *gl, double *gu,
+                            const double *vmin, const double *vmax, const double *pmin, const double *pmax,
+                            const double *qmin, const double *qmax, const double *angmin, const double *angmax,
+                            const double *ramp, cudaStream_t s);
+
+void set_error(const std::string &msg);
+
+}  // namespace mpopf
+
+// The handle (opaque to callers).
+struct mpopf_handle {
+  mpopf::Dev d;
+  mpopf_pattern pat;
+  void *blocks[96];  // device allocations owned by the handle
+  int nblocks;
+  // staging for mpopf_sweep_host (allocated on first use)
+  double *stage;
+  size_t stage_bytes;
+};

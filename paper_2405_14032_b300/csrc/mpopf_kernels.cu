@@ -1,0 +1,622 @@
+// Evaluation kernels of libmpopf (sm_103a, FP64).
+//
+// One thread per component x period instance (the SIMD abstraction of Eq. 2):
+//   k_branch  (t, l): flows, rows K1..K7, their J entries, the branch block of W,
+//                     the thermal W entries, the four M rows of the branch's
+//                     arcs, and the six distinct values of the branch element's
+//                     bus-variable block of M (to the scratch buffer S);
+//   k_bus     (t, n): balance rows K8/K9, the reference row, shunt W entries,
+//                     and the va/vm rows of M, summing the incident branches'
+//                     values from S in a fixed order (no atomics);
+//   k_gen     (t, g): objective terms, gradient, objective W entry, ramp rows
+//                     and the pg/qg rows of M;
+//   k_fsum           : the objective's fixed-order tree reduction.
+// Every value follows one fixed sequence of binary64 operations (explicit fma
+// where the definition has one; the build disables contraction), so results
+// are bitwise reproducible from run to run.
+#include "mpopf_internal.cuh"
+
+namespace mpopf {
+namespace {
+
+// ---------------------------------------------------------------------------
+// sin and cos of the angle difference: Cody & Waite reduction by pi/2 in three
+// parts (Software Manual for the Elementary Functions, 1980), then the Taylor
+// series of sin (through r^17) and cos (through r^18), Horner in r^2, with
+// coefficients RN((-1)^k / k!).  |x| <= RN(pi/4) needs no reduction.  Outside
+// |x| < 2^30 (and for NaN/Inf) the CUDA library is used.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void sincos_cw(double x, double *sn, double *cs) {
+  const unsigned long long ax = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffULL;
+  if (ax >= 0x41D0000000000000ULL) {  // |x| >= 2^30, Inf, NaN
+    sincos(x, sn, cs);
+    return;
+  }
+  double r = x;
+  int q = 0;
+  if (ax > 0x3FE921FB54442D18ULL) {  // |x| > RN(pi/4)
+    const double k = rint(x * 0x1.45f306dc9c883p-1);
+    r = fma(-k, 0x1.921fb54442d18p+0, x);
+    r = fma(-k, 0x1.1a62633145c07p-54, r);
+    r = fma(-k, -0x1.f1976b7ed8fbcp-110, r);
+    q = (int)(__double2ll_rz(k) & 3);
+  }
+  const double r2 = r * r;
+  double p = 1.0 / 355687428096000.0;
+  p = fma(p, r2, -1.0 / 1307674368000.0);
+  p = fma(p, r2, 1.0 / 6227020800.0);
+  p = fma(p, r2, -1.0 / 39916800.0);
+  p = fma(p, r2, 1.0 / 362880.0);
+  p = fma(p, r2, -1.0 / 5040.0);
+  p = fma(p, r2, 1.0 / 120.0);
+  p = fma(p, r2, -1.0 / 6.0);
+  const double r3 = r2 * r;
+  const double s = fma(r3, p, r);
+  double c = -1.0 / 6402373705728000.0;
+  c = fma(c, r2, 1.0 / 20922789888000.0);
+  c = fma(c, r2, -1.0 / 87178291200.0);
+  c = fma(c, r2, 1.0 / 479001600.0);
+  c = fma(c, r2, -1.0 / 3628800.0);
+  c = fma(c, r2, 1.0 / 40320.0);
+  c = fma(c, r2, -1.0 / 720.0);
+  c = fma(c, r2, 1.0 / 24.0);
+  c = fma(c, r2, -1.0 / 2.0);
+  const double co = fma(r2, c, 1.0);
+  if (q == 0) { *sn = s; *cs = co; }
+  else if (q == 1) { *sn = co; *cs = -s; }
+  else if (q == 2) { *sn = -s; *cs = -co; }
+  else { *sn = -co; *cs = s; }
+}
+
+template <unsigned MASK>
+__device__ __forceinline__ unsigned eff(unsigned rt) { return MASK ? MASK : rt; }
+
+// ---------------------------------------------------------------------------
+// Branch x period.
+// ---------------------------------------------------------------------------
+template <unsigned MASK>
+__global__ void __launch_bounds__(kBlock) k_branch(Dev d, unsigned rt, const double *__restrict__ x,
+                                                   const double *__restrict__ lam, const double *__restrict__ sx,
+                                                   const double *__restrict__ dv, double dw,
+                                                   double *__restrict__ grad, double *__restrict__ c,
+                                                   double *__restrict__ jv, double *__restrict__ hv,
+                                                   double *__restrict__ kv) {
+  const unsigned mk = eff<MASK>(rt);
+  const int32_t L = d.L;
+  const int32_t tl = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+  if (tl >= d.T * L) return;
+  const int32_t t = tl / L, l = tl - t * L;
+  const int64_t TL = (int64_t)d.T * L;
+  const int64_t tN = (int64_t)t * d.N;
+  const int64_t pb = d.x_p + 2 * (int64_t)t * L, qb = d.x_q + 2 * (int64_t)t * L;
+  if (mk & MPOPF_OUT_GRAD) {
+    grad[pb + l] = 0.0;
+    grad[pb + L + l] = 0.0;
+    grad[qb + l] = 0.0;
+    grad[qb + L + l] = 0.0;
+  }
+  if (!(mk & (MPOPF_OUT_CONS | MPOPF_OUT_JAC | MPOPF_OUT_HESS | MPOPF_OUT_KKT))) return;
+
+  const int32_t f = __ldg(d.br_f + l), to = __ldg(d.br_t + l);
+  const double thf = __ldg(x + tN + f), tht = __ldg(x + tN + to);
+  const double vf = __ldg(x + d.x_vm + tN + f), vt = __ldg(x + d.x_vm + tN + to);
+  const double *bc = d.bc;
+  const double gft = __ldg(bc + (int64_t)BC_GFT * L + l), bft = __ldg(bc + (int64_t)BC_BFT * L + l);
+  const double gtf = __ldg(bc + (int64_t)BC_GTF * L + l), btf = __ldg(bc + (int64_t)BC_BTF * L + l);
+
+  // Flow terms.
+  const double dth = thf - tht;
+  double sn, cs;
+  sincos_cw(dth, &sn, &cs);
+  const double bS = bft * sn, bC = bft * cs;
+  const double A1 = fma(gft, cs, bS);
+  const double A2 = fma(gft, sn, -bC);
+  double A3, A4;
+  if (__ldg(d.br_sym + l)) {  // btf == bft: the products are the same
+    A3 = fma(gtf, cs, -bS);
+    A4 = fma(-gtf, sn, -bC);
+  } else {
+    A3 = fma(gtf, cs, -(btf * sn));
+    A4 = fma(-gtf, sn, -(btf * cs));
+  }
+  const double vtA1 = vt * A1, vtA2 = vt * A2, vfA3 = vf * A3, vfA4 = vf * A4;
+  const double uA1 = vf * vtA1, uA2 = vf * vtA2, uA3 = vt * vfA3, uA4 = vt * vfA4;
+
+  const double pf = __ldg(x + pb + l), pt = __ldg(x + pb + L + l);
+  const double qf = __ldg(x + qb + l), qt = __ldg(x + qb + L + l);
+  const int64_t rk1 = d.T + tl;  // row of K1; K_k at rk1 + (k-1) T L
+
+  if (mk & MPOPF_OUT_CONS) {
+    const double gff = __ldg(bc + (int64_t)BC_GFF * L + l), bff = __ldg(bc + (int64_t)BC_BFF * L + l);
+    const double gtt = __ldg(bc + (int64_t)BC_GTT * L + l), btt = __ldg(bc + (int64_t)BC_BTT * L + l);
+    const double smax2 = __ldg(bc + (int64_t)BC_SMAX2 * L + l);
+    const double vf2 = vf * vf, vt2 = vt * vt;
+    c[rk1] = pf - fma(gff, vf2, uA1);
+    c[rk1 + TL] = qf - fma(-bff, vf2, uA2);
+    c[rk1 + 2 * TL] = pt - fma(gtt, vt2, uA3);
+    c[rk1 + 3 * TL] = qt - fma(-btt, vt2, uA4);
+    c[rk1 + 4 * TL] = dth;
+    c[rk1 + 5 * TL] = fma(pf, pf, fma(qf, qf, -smax2));
+    c[rk1 + 6 * TL] = fma(pt, pt, fma(qt, qt, -smax2));
+  }
+  if (!(mk & (MPOPF_OUT_JAC | MPOPF_OUT_HESS | MPOPF_OUT_KKT))) return;
+
+  const double g2ff = __ldg(bc + (int64_t)BC_G2FF * L + l), b2ff = __ldg(bc + (int64_t)BC_B2FF * L + l);
+  const double g2tt = __ldg(bc + (int64_t)BC_G2TT * L + l), b2tt = __ldg(bc + (int64_t)BC_B2TT * L + l);
+  // J entries of the flow rows over (va_f, va_t, vm_f, vm_t): [a, -a, b, c].
+  const double a1 = uA2, b1 = -fma(g2ff, vf, vtA1), c1 = -(vf * A1);
+  const double a2 = -uA1, b2 = -fma(-b2ff, vf, vtA2), c2 = -(vf * A2);
+  const double a3 = -uA4, b3 = -(vt * A3), c3 = -fma(g2tt, vt, vfA3);
+  const double a4 = uA3, b4 = -(vt * A4), c4 = -fma(-b2tt, vt, vfA4);
+  const double jp6 = 2.0 * pf, jq6 = 2.0 * qf, jp7 = 2.0 * pt, jq7 = 2.0 * qt;
+
+  if (mk & MPOPF_OUT_JAC) {
+    double *j1 = jv + d.T + (int64_t)tl * 5;
+    const int64_t s5 = 5 * TL;
+    j1[0] = 1.0; j1[1] = a1; j1[2] = -a1; j1[3] = b1; j1[4] = c1;
+    j1[s5 + 0] = 1.0; j1[s5 + 1] = a2; j1[s5 + 2] = -a2; j1[s5 + 3] = b2; j1[s5 + 4] = c2;
+    j1[2 * s5 + 0] = 1.0; j1[2 * s5 + 1] = a3; j1[2 * s5 + 2] = -a3; j1[2 * s5 + 3] = b3; j1[2 * s5 + 4] = c3;
+    j1[3 * s5 + 0] = 1.0; j1[3 * s5 + 1] = a4; j1[3 * s5 + 2] = -a4; j1[3 * s5 + 3] = b4; j1[3 * s5 + 4] = c4;
+    double *j5 = jv + d.j_k5 + (int64_t)tl * 2;
+    j5[0] = 1.0; j5[1] = -1.0;
+    double *j6 = jv + d.j_k6 + (int64_t)tl * 2;
+    j6[0] = jp6; j6[1] = jq6;
+    double *j7 = jv + d.j_k7 + (int64_t)tl * 2;
+    j7[0] = jp7; j7[1] = jq7;
+  }
+  if (!(mk & (MPOPF_OUT_HESS | MPOPF_OUT_KKT))) return;
+
+  // W: branch block (sum over the four flow rows) and thermal entries.
+  const double l1 = __ldg(lam + rk1), l2 = __ldg(lam + rk1 + TL), l3 = __ldg(lam + rk1 + 2 * TL);
+  const double l4 = __ldg(lam + rk1 + 3 * TL), l6 = __ldg(lam + rk1 + 5 * TL), l7 = __ldg(lam + rk1 + 6 * TL);
+  const double Asum = fma(l4, A4, fma(l3, A3, fma(l2, A2, l1 * A1)));
+  const double Bsum = fma(l4, A3, fma(-l3, A4, fma(-l2, A1, l1 * A2)));
+  const double Wdd = vf * (vt * Asum);
+  const double Wdvf = vt * Bsum, Wdvt = vf * Bsum;
+  const double Wvfvf = fma(l2, b2ff, -(l1 * g2ff));
+  const double Wvtvt = fma(l4, b2tt, -(l3 * g2tt));
+  const double h6 = 2.0 * l6, h7 = 2.0 * l7;
+  if (mk & MPOPF_OUT_HESS) {
+    double *hb = hv + d.h_br + (int64_t)tl * 10;
+    hb[0] = Wdd; hb[1] = -Wdd; hb[2] = Wdd; hb[3] = Wdvf; hb[4] = -Wdvf;
+    hb[5] = Wvfvf; hb[6] = Wdvt; hb[7] = -Wdvt; hb[8] = -Asum; hb[9] = Wvtvt;
+    double *ht = hv + d.h_th + (int64_t)tl * 4;
+    ht[0] = h6; ht[1] = h6; ht[2] = h7; ht[3] = h7;
+  }
+  if (!(mk & MPOPF_OUT_KKT)) return;
+
+  // Condensed matrix: the branch element's local block.
+  const double D1 = __ldg(dv + rk1), D2 = __ldg(dv + rk1 + TL), D3 = __ldg(dv + rk1 + 2 * TL);
+  const double D4 = __ldg(dv + rk1 + 3 * TL), D5 = __ldg(dv + rk1 + 4 * TL), D6 = __ldg(dv + rk1 + 5 * TL);
+  const double D7 = __ldg(dv + rk1 + 6 * TL);
+  const double w11 = D1 * a1, w31 = D1 * b1, w41 = D1 * c1;
+  const double w12 = D2 * a2, w32 = D2 * b2, w42 = D2 * c2;
+  const double w13 = D3 * a3, w33 = D3 * b3, w43 = D3 * c3;
+  const double w14 = D4 * a4, w34 = D4 * b4, w44 = D4 * c4;
+  double Sdd = fma(w14, a4, fma(w13, a3, fma(w12, a2, fma(w11, a1, Wdd))));
+  Sdd = Sdd + D5;
+  const double Svfd = fma(w34, a4, fma(w33, a3, fma(w32, a2, fma(w31, a1, Wdvf))));
+  const double Svtd = fma(w44, a4, fma(w43, a3, fma(w42, a2, fma(w41, a1, Wdvt))));
+  const double Svfvf = fma(w34, b4, fma(w33, b3, fma(w32, b2, fma(w31, b1, Wvfvf))));
+  const double Svtvf = fma(w44, b4, fma(w43, b3, fma(w42, b2, fma(w41, b1, -Asum))));
+  const double Svtvt = fma(w44, c4, fma(w43, c3, fma(w42, c2, fma(w41, c1, Wvtvt))));
+  {
+    double2 *sp = reinterpret_cast<double2 *>(d.S + (int64_t)tl * 6);
+    sp[0] = make_double2(Sdd, Svfd);
+    sp[1] = make_double2(Svtd, Svfvf);
+    sp[2] = make_double2(Svtvf, Svtvt);
+  }
+  // Arc-variable diagonals and the (q, p) pair of each end.
+  const double t6p = D6 * jp6, t6q = D6 * jq6, t7p = D7 * jp7, t7q = D7 * jq7;
+  const double Lpp_f = fma(t6p, jp6, h6 + D1);
+  const double Lqq_f = fma(t6q, jq6, h6 + D2);
+  const double Lqp_f = t6q * jp6;
+  const double Lpp_t = fma(t7p, jp7, h7 + D3);
+  const double Lqq_t = fma(t7q, jq7, h7 + D4);
+  const double Lqp_t = t7q * jp7;
+  // Bus elements at both ends: their (arc, vm) and (arc, arc) entries.
+  const int64_t r8f = d.c_k8 + tN + f, r8t = d.c_k8 + tN + to;
+  const double D8f = __ldg(dv + r8f), D9f = __ldg(dv + r8f + (d.c_k9 - d.c_k8));
+  const double D8t = __ldg(dv + r8t), D9t = __ldg(dv + r8t + (d.c_k9 - d.c_k8));
+  const double w8f = D8f * (__ldg(d.bus_m2gs + f) * vf), w9f = D9f * (__ldg(d.bus_p2bs + f) * vf);
+  const double w8t = D8t * (__ldg(d.bus_m2gs + to) * vt), w9t = D9t * (__ldg(d.bus_p2bs + to) * vt);
+  const double sxpf = __ldg(sx + pb + l), sxpt = __ldg(sx + pb + L + l);
+  const double sxqf = __ldg(sx + qb + l), sxqt = __ldg(sx + qb + L + l);
+  const bool flo = f < to;
+  const int32_t kf = __ldg(d.bgen_ptr + f + 1) - __ldg(d.bgen_ptr + f);
+  const int32_t kt = __ldg(d.bgen_ptr + to + 1) - __ldg(d.bgen_ptr + to);
+  const int32_t rf = __ldg(d.arc_rank + l), rt2 = __ldg(d.arc_rank + L + l);
+  // Writes one arc row: [va lo, va hi, vm lo, vm hi], ngen x gval, [qp], nrank x aval, diag.
+  auto arc_row = [&](double *row, double vaf, double vat, double vmf, double vmt, int32_t ngen, double gval,
+                     bool has_qp, double qp, int32_t nrank, double aval, double diag) {
+    row[0] = flo ? vaf : vat;
+    row[1] = flo ? vat : vaf;
+    row[2] = flo ? vmf : vmt;
+    row[3] = flo ? vmt : vmf;
+    int k = 4;
+    for (int32_t e = 0; e < ngen; ++e) row[k++] = gval;
+    if (has_qp) row[k++] = qp;
+    for (int32_t e = 0; e < nrank; ++e) row[k++] = aval;
+    row[k] = diag;
+  };
+  const int64_t mp = d.m_p + (int64_t)t * d.mb_p, mq = d.m_q + (int64_t)t * d.mb_q;
+  arc_row(kv + mp + __ldg(d.mo_p + l), w11, -w11, w31 - w8f, w41, kf, -D8f, false, 0.0, rf, D8f,
+          ((sxpf + dw) + Lpp_f) + D8f);
+  arc_row(kv + mq + __ldg(d.mo_q + l), w12, -w12, w32 - w9f, w42, kf, -D9f, true, Lqp_f, rf, D9f,
+          ((sxqf + dw) + Lqq_f) + D9f);
+  arc_row(kv + mp + __ldg(d.mo_p + L + l), w13, -w13, w33, w43 - w8t, kt, -D8t, false, 0.0, rt2, D8t,
+          ((sxpt + dw) + Lpp_t) + D8t);
+  arc_row(kv + mq + __ldg(d.mo_q + L + l), w14, -w14, w34, w44 - w9t, kt, -D9t, true, Lqp_t, rt2, D9t,
+          ((sxqt + dw) + Lqq_t) + D9t);
+}
+
+// ---------------------------------------------------------------------------
+// Bus x period.
+// ---------------------------------------------------------------------------
+template <unsigned MASK>
+__global__ void __launch_bounds__(kBlock) k_bus(Dev d, unsigned rt, const double *__restrict__ x,
+                                                const double *__restrict__ lam, const double *__restrict__ sx,
+                                                const double *__restrict__ dv, double dw, double *__restrict__ grad,
+                                                double *__restrict__ c, double *__restrict__ jv,
+                                                double *__restrict__ hv, double *__restrict__ kv) {
+  const unsigned mk = eff<MASK>(rt);
+  const int32_t N = d.N;
+  const int32_t tn = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+  if (tn >= d.T * N) return;
+  const int32_t t = tn / N, n = tn - t * N;
+  const int64_t tN = (int64_t)t * N;
+  const int64_t L = d.L, G = d.G;
+  if (mk & MPOPF_OUT_GRAD) {
+    grad[tn] = 0.0;
+    grad[d.x_vm + tn] = 0.0;
+  }
+  if (n == d.ref) {
+    if (mk & MPOPF_OUT_CONS) c[t] = __ldg(x + tN + n);
+    if (mk & MPOPF_OUT_JAC) jv[t] = 1.0;
+  }
+  if (!(mk & (MPOPF_OUT_CONS | MPOPF_OUT_JAC | MPOPF_OUT_HESS | MPOPF_OUT_KKT))) return;
+  const double vm = __ldg(x + d.x_vm + tn);
+  const int32_t g0 = __ldg(d.bgen_ptr + n), g1 = __ldg(d.bgen_ptr + n + 1);
+  const int32_t a0 = __ldg(d.barc_ptr + n), a1 = __ldg(d.barc_ptr + n + 1);
+  const double m2gs = __ldg(d.bus_m2gs + n), p2bs = __ldg(d.bus_p2bs + n);
+  if (mk & MPOPF_OUT_CONS) {
+    const double vm2 = vm * vm;
+    double aP = 0.0, aQ = 0.0;
+    const int64_t pgb = d.x_pg + (int64_t)t * G, qgb = d.x_qg + (int64_t)t * G;
+    for (int32_t e = g0; e < g1; ++e) {
+      const int32_t g = __ldg(d.bgen_idx + e);
+      aP = aP + __ldg(x + pgb + g);
+      aQ = aQ + __ldg(x + qgb + g);
+    }
+    const int64_t pab = d.x_p + 2 * (int64_t)t * L, qab = d.x_q + 2 * (int64_t)t * L;
+    for (int32_t e = a0; e < a1; ++e) {
+      const int32_t a = __ldg(d.barc_idx + e);
+      aP = aP - __ldg(x + pab + a);
+      aQ = aQ - __ldg(x + qab + a);
+    }
+    aP = fma(__ldg(d.bus_mgs + n), vm2, aP);
+    aQ = fma(__ldg(d.bus_bs + n), vm2, aQ);
+    const int64_t ldb = (int64_t)t * d.D;
+    for (int32_t e = __ldg(d.bload_ptr + n); e < __ldg(d.bload_ptr + n + 1); ++e) {
+      const int32_t k = __ldg(d.bload_idx + e);
+      aP = aP - __ldg(d.pd + ldb + k);
+      aQ = aQ - __ldg(d.qd + ldb + k);
+    }
+    c[d.c_k8 + tn] = aP;
+    c[d.c_k9 + tn] = aQ;
+  }
+  const double J8 = m2gs * vm, J9 = p2bs * vm;
+  if (mk & MPOPF_OUT_JAC) {
+    double *r8 = jv + d.j_k8 + (int64_t)t * d.jk8_per + __ldg(d.jk8_off + n);
+    double *r9 = r8 + (d.j_k9 - d.j_k8);
+    r8[0] = J8;
+    r9[0] = J9;
+    int k = 1;
+    for (int32_t e = g0; e < g1; ++e, ++k) { r8[k] = 1.0; r9[k] = 1.0; }
+    for (int32_t e = a0; e < a1; ++e, ++k) { r8[k] = -1.0; r9[k] = -1.0; }
+  }
+  if (!(mk & (MPOPF_OUT_HESS | MPOPF_OUT_KKT))) return;
+  const double WP = __ldg(lam + d.c_k8 + tn) * m2gs, WQ = __ldg(lam + d.c_k9 + tn) * p2bs;
+  if (mk & MPOPF_OUT_HESS) {
+    hv[d.h_sh + 2 * (int64_t)tn] = WP;
+    hv[d.h_sh + 2 * (int64_t)tn + 1] = WQ;
+  }
+  if (!(mk & MPOPF_OUT_KKT)) return;
+
+  const int32_t nd = __ldg(d.bus_nd + n), ndlt = __ldg(d.bus_ndlt + n);
+  double *va_row = kv + d.m_va + (int64_t)t * d.mb_va + __ldg(d.mo_va + n);
+  double *vm_row = kv + d.m_vm + (int64_t)t * d.mb_vm + __ldg(d.mo_vm + n);
+  const double *S = d.S + (int64_t)t * L * 6;
+  // Entries shared with each distinct neighbour (sum over joining branches in
+  // branch order).
+  int32_t k = 0;
+  for (int32_t q = __ldg(d.nbr_ptr + n); q < __ldg(d.nbr_ptr + n + 1); ++q, ++k) {
+    const int32_t nb = __ldg(d.nbr_bus + q);
+    double cdd = 0.0, cvd = 0.0, cvv = 0.0;
+    bool first = true;
+    for (int32_t e = __ldg(d.nbr_grp + q); e < __ldg(d.nbr_grp + q + 1); ++e) {
+      const int32_t code = __ldg(d.grp_code + e);
+      const double *s = S + (int64_t)(code >> 1) * 6;
+      const double vd = (code & 1) ? __ldg(s + 2) : -__ldg(s + 1);  // (vm_n, va_nb)
+      if (first) {
+        cdd = -__ldg(s + 0);
+        cvd = vd;
+        cvv = __ldg(s + 4);
+        first = false;
+      } else {
+        cdd = cdd - __ldg(s + 0);
+        cvd = cvd + vd;
+        cvv = cvv + __ldg(s + 4);
+      }
+    }
+    if (nb < n) {
+      va_row[k] = cdd;
+      vm_row[nd + 1 + k] = cvv;
+    }
+    vm_row[k < ndlt ? k : k + 1] = cvd;
+  }
+  // Diagonal entries: diagonal term, reference element, incident branches in
+  // branch order, bus element.
+  double Ddd = __ldg(sx + tn) + dw;
+  if (n == d.ref) Ddd = Ddd + __ldg(dv + t);
+  double Dvv = __ldg(sx + d.x_vm + tn) + dw;
+  double Dvd = 0.0;
+  bool first = true;
+  for (int32_t e = __ldg(d.inc_ptr + n); e < __ldg(d.inc_ptr + n + 1); ++e) {
+    const int32_t code = __ldg(d.inc_code + e);
+    const double *s = S + (int64_t)(code >> 1) * 6;
+    const bool at_to = code & 1;
+    const double vd = at_to ? -__ldg(s + 2) : __ldg(s + 1);
+    Ddd = Ddd + __ldg(s + 0);
+    Dvv = Dvv + (at_to ? __ldg(s + 5) : __ldg(s + 3));
+    if (first) { Dvd = vd; first = false; }
+    else Dvd = Dvd + vd;
+  }
+  const double D8 = __ldg(dv + d.c_k8 + tn), D9 = __ldg(dv + d.c_k9 + tn);
+  const double w8 = D8 * J8, w9 = D9 * J9;
+  const double Lbus = fma(w9, J9, fma(w8, J8, WP + WQ));
+  Dvv = Dvv + Lbus;
+  va_row[ndlt] = Ddd;
+  if (nd > 0) vm_row[ndlt] = Dvd;
+  vm_row[(nd > 0 ? nd + 1 : 0) + ndlt] = Dvv;
+}
+
+// ---------------------------------------------------------------------------
+// Generator x period.
+// ---------------------------------------------------------------------------
+template <unsigned MASK>
+__global__ void __launch_bounds__(kBlock) k_gen(Dev d, unsigned rt, const double *__restrict__ x,
+                                                double sigma, const double *__restrict__ sx,
+                                                const double *__restrict__ dv, double dw, double *__restrict__ grad,
+                                                double *__restrict__ c, double *__restrict__ jv,
+                                                double *__restrict__ hv, double *__restrict__ kv) {
+  const unsigned mk = eff<MASK>(rt);
+  const int32_t G = d.G;
+  const int32_t tg = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+  const bool live = tg < d.T * G;
+  const int32_t t = live ? tg / G : 0, g = live ? tg - t * G : 0;
+  double pg = 0.0;
+  if (live) pg = __ldg(x + d.x_pg + tg);
+  if (mk & MPOPF_OUT_OBJ) {
+    __shared__ double red[kBlock];
+    red[threadIdx.x] = live ? fma(fma(__ldg(d.gen_c2 + g), pg, __ldg(d.gen_c1 + g)), pg, __ldg(d.gen_c0 + g)) : 0.0;
+    __syncthreads();
+    for (int s = kBlock / 2; s > 0; s >>= 1) {
+      if ((int)threadIdx.x < s) red[threadIdx.x] = red[threadIdx.x] + red[threadIdx.x + s];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) d.fpart[blockIdx.x] = red[0];
+  }
+  if (!live) return;
+  const double c2x2 = __ldg(d.gen_c2x2 + g);
+  if (mk & MPOPF_OUT_GRAD) {
+    grad[d.x_pg + tg] = fma(c2x2, pg, __ldg(d.gen_c1 + g));
+    grad[d.x_qg + tg] = 0.0;
+  }
+  const double Wobj = sigma * c2x2;
+  if (mk & MPOPF_OUT_HESS) hv[tg] = Wobj;
+  const int64_t rr = d.c_k10 + (int64_t)(t - 1) * G + g;  // ramp row (t, g)
+  if (t >= 1) {
+    if (mk & MPOPF_OUT_CONS) c[rr] = pg - __ldg(x + d.x_pg + tg - G);
+    if (mk & MPOPF_OUT_JAC) {
+      jv[d.j_k10 + 2 * ((int64_t)(t - 1) * G + g)] = 1.0;
+      jv[d.j_k10 + 2 * ((int64_t)(t - 1) * G + g) + 1] = -1.0;
+    }
+  }
+  if (!(mk & MPOPF_OUT_KKT)) return;
+  const int32_t nb = __ldg(d.gen_bus + g), rank = __ldg(d.gen_rank + g);
+  const int64_t tn = (int64_t)t * d.N + nb;
+  const double vm = __ldg(x + d.x_vm + tn);
+  const double D8 = __ldg(dv + d.c_k8 + tn), D9 = __ldg(dv + d.c_k9 + tn);
+  const double w8 = D8 * (__ldg(d.bus_m2gs + nb) * vm), w9 = D9 * (__ldg(d.bus_p2bs + nb) * vm);
+  double *pr = kv + d.m_pg + (t == 0 ? (int64_t)__ldg(d.mo_pg0 + g)
+                                     : d.mb_pg0 + (int64_t)(t - 1) * d.mb_pg1 + __ldg(d.mo_pg1 + g));
+  pr[0] = w8;
+  int k = 1;
+  double diag = ((__ldg(sx + d.x_pg + tg) + dw) + Wobj) + D8;
+  if (t >= 1) {
+    const double D10 = __ldg(dv + rr);
+    pr[k++] = -D10;
+    diag = diag + D10;
+  }
+  if (t + 1 < d.T) diag = diag + __ldg(dv + rr + G);
+  for (int32_t e = 0; e < rank; ++e) pr[k++] = D8;
+  pr[k] = diag;
+  double *qr = kv + d.m_qg + (int64_t)t * d.mb_qg + __ldg(d.mo_qg + g);
+  qr[0] = w9;
+  for (int32_t e = 0; e < rank; ++e) qr[1 + e] = D9;
+  qr[1 + rank] = (__ldg(sx + d.x_qg + tg) + dw) + D9;
+}
+
+// Objective: fixed-order reduction of the per-block partial sums.
+__global__ void __launch_bounds__(1024) k_fsum(const double *__restrict__ part, int32_t count,
+                                               double *__restrict__ f) {
+  __shared__ double red[1024];
+  double a = 0.0;
+  for (int32_t i = threadIdx.x; i < count; i += 1024) a = a + part[i];
+  red[threadIdx.x] = a;
+  __syncthreads();
+  for (int s = 512; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) red[threadIdx.x] = red[threadIdx.x] + red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *f = red[0];
+}
+
+unsigned grid_for(int64_t count) { return (unsigned)((count + kBlock - 1) / kBlock); }
+
+template <unsigned MASK>
+void launch_all(const Dev &d, unsigned rt, const double *x, const double *lam, double sigma, const double *sx,
+                const double *dv, double dw, double *f, double *grad, double *c, double *jv, double *hv, double *kv,
+                cudaStream_t s) {
+  const unsigned mk = MASK ? MASK : rt;
+  const unsigned rest = MPOPF_OUT_GRAD | MPOPF_OUT_CONS | MPOPF_OUT_JAC | MPOPF_OUT_HESS | MPOPF_OUT_KKT;
+  if ((mk & rest) && d.L > 0)
+    k_branch<MASK><<<grid_for((int64_t)d.T * d.L), kBlock, 0, s>>>(d, rt, x, lam, sx, dv, dw, grad, c, jv, hv, kv);
+  if (mk & rest)
+    k_bus<MASK><<<grid_for((int64_t)d.T * d.N), kBlock, 0, s>>>(d, rt, x, lam, sx, dv, dw, grad, c, jv, hv, kv);
+  if (mk && d.G > 0)
+    k_gen<MASK><<<grid_for((int64_t)d.T * d.G), kBlock, 0, s>>>(d, rt, x, sigma, sx, dv, dw, grad, c, jv, hv, kv);
+  if (mk & MPOPF_OUT_OBJ) k_fsum<<<1, 1024, 0, s>>>(d.fpart, d.G > 0 ? d.fpart_n : 0, f);
+}
+
+}  // namespace
+
+int eval_launch_count(const Dev &d, unsigned mk) {
+  const unsigned rest = MPOPF_OUT_GRAD | MPOPF_OUT_CONS | MPOPF_OUT_JAC | MPOPF_OUT_HESS | MPOPF_OUT_KKT;
+  int k = 0;
+  if ((mk & rest) && d.L > 0) ++k;
+  if (mk & rest) ++k;
+  if (mk && d.G > 0) ++k;
+  if (mk & MPOPF_OUT_OBJ) ++k;
+  return k;
+}
+
+cudaError_t launch_eval(const Dev &d, unsigned mk, const double *x, const double *lam, double sigma,
+                        const double *sx, const double *dv, double dw, double *f, double *grad, double *c,
+                        double *jv, double *hv, double *kv, cudaStream_t s) {
+  switch (mk) {
+    case MPOPF_OUT_OBJ: launch_all<MPOPF_OUT_OBJ>(d, mk, x, lam, sigma, sx, dv, dw, f, grad, c, jv, hv, kv, s); break;
+    case MPOPF_OUT_GRAD: launch_all<MPOPF_OUT_GRAD>(d, mk, x, lam, sigma, sx, dv, dw, f, grad, c, jv, hv, kv, s); break;
+    case MPOPF_OUT_CONS: launch_all<MPOPF_OUT_CONS>(d, mk, x, lam, sigma, sx, dv, dw, f, grad, c, jv, hv, kv, s); break;
+    case MPOPF_OUT_JAC: launch_all<MPOPF_OUT_JAC>(d, mk, x, lam, sigma, sx, dv, dw, f, grad, c, jv, hv, kv, s); break;
+    case MPOPF_OUT_HESS: launch_all<MPOPF_OUT_HESS>(d, mk, x, lam, sigma, sx, dv, dw, f, grad, c, jv, hv, kv, s); break;
+    case MPOPF_OUT_KKT: launch_all<MPOPF_OUT_KKT>(d, mk, x, lam, sigma, sx, dv, dw, f, grad, c, jv, hv, kv, s); break;
+    case MPOPF_OUT_ALL: launch_all<MPOPF_OUT_ALL>(d, mk, x, lam, sigma, sx, dv, dw, f, grad, c, jv, hv, kv, s); break;
+    default: launch_all<0>(d, mk, x, lam, sigma, sx, dv, dw, f, grad, c, jv, hv, kv, s); break;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace mpopf
+
+using namespace mpopf;
+
+namespace {
+int fail(int code, const std::string &msg) {
+  set_error(msg);
+  return code;
+}
+}  // namespace
+
+extern "C" {
+
+int mpopf_launch_count(const mpopf_handle *h, unsigned outputs) {
+  if (!h) return fail(MPOPF_ERR_ARG, "mpopf_launch_count: NULL handle");
+  return eval_launch_count(h->d, outputs & MPOPF_OUT_ALL);
+}
+
+int mpopf_eval(mpopf_handle *h, unsigned outputs, const double *x, const double *lam, double sigma,
+               const double *sigma_x, const double *dvec, double delta_w, double *f, double *grad, double *c,
+               double *jv, double *hv, double *kv, void *stream) {
+  if (!h) return fail(MPOPF_ERR_ARG, "mpopf_eval: NULL handle");
+  unsigned mk = outputs & MPOPF_OUT_ALL;
+  if (!f) mk &= ~MPOPF_OUT_OBJ;
+  if (!grad) mk &= ~MPOPF_OUT_GRAD;
+  if (!c) mk &= ~MPOPF_OUT_CONS;
+  if (!jv) mk &= ~MPOPF_OUT_JAC;
+  if (!hv) mk &= ~MPOPF_OUT_HESS;
+  if (!kv) mk &= ~MPOPF_OUT_KKT;
+  if (mk == 0) return MPOPF_OK;
+  if (!x) return fail(MPOPF_ERR_ARG, "mpopf_eval: NULL x");
+  if ((mk & (MPOPF_OUT_HESS | MPOPF_OUT_KKT)) && !lam) return fail(MPOPF_ERR_ARG, "mpopf_eval: NULL lam");
+  if ((mk & MPOPF_OUT_KKT) && (!sigma_x || !dvec)) return fail(MPOPF_ERR_ARG, "mpopf_eval: NULL sigma_x or dvec");
+  const cudaError_t e = launch_eval(h->d, mk, x, lam, sigma, sigma_x, dvec, delta_w, f, grad, c, jv, hv, kv,
+                                    static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return fail(MPOPF_ERR_CUDA, std::string("mpopf_eval: ") + cudaGetErrorString(e));
+  return MPOPF_OK;
+}
+
+int mpopf_eval_obj(mpopf_handle *h, const double *x, double *f, void *stream) {
+  return mpopf_eval(h, MPOPF_OUT_OBJ, x, nullptr, 0.0, nullptr, nullptr, 0.0, f, nullptr, nullptr, nullptr, nullptr,
+                    nullptr, stream);
+}
+int mpopf_eval_grad(mpopf_handle *h, const double *x, double *grad, void *stream) {
+  return mpopf_eval(h, MPOPF_OUT_GRAD, x, nullptr, 0.0, nullptr, nullptr, 0.0, nullptr, grad, nullptr, nullptr,
+                    nullptr, nullptr, stream);
+}
+int mpopf_eval_cons(mpopf_handle *h, const double *x, double *c, void *stream) {
+  return mpopf_eval(h, MPOPF_OUT_CONS, x, nullptr, 0.0, nullptr, nullptr, 0.0, nullptr, nullptr, c, nullptr, nullptr,
+                    nullptr, stream);
+}
+int mpopf_eval_jac(mpopf_handle *h, const double *x, double *jv, void *stream) {
+  return mpopf_eval(h, MPOPF_OUT_JAC, x, nullptr, 0.0, nullptr, nullptr, 0.0, nullptr, nullptr, nullptr, jv, nullptr,
+                    nullptr, stream);
+}
+int mpopf_eval_hess(mpopf_handle *h, const double *x, const double *lam, double sigma, double *hv, void *stream) {
+  return mpopf_eval(h, MPOPF_OUT_HESS, x, lam, sigma, nullptr, nullptr, 0.0, nullptr, nullptr, nullptr, nullptr, hv,
+                    nullptr, stream);
+}
+int mpopf_assemble_kkt(mpopf_handle *h, const double *x, const double *lam, double sigma, const double *sigma_x,
+                       const double *dvec, double delta_w, double *kv, void *stream) {
+  return mpopf_eval(h, MPOPF_OUT_KKT, x, lam, sigma, sigma_x, dvec, delta_w, nullptr, nullptr, nullptr, nullptr,
+                    nullptr, kv, stream);
+}
+int mpopf_sweep(mpopf_handle *h, const double *x, const double *lam, double sigma, const double *sigma_x,
+                const double *dvec, double delta_w, double *f, double *grad, double *c, double *jv, double *hv,
+                double *kv, void *stream) {
+  if (!f || !grad || !c || !jv || !hv || !kv) return fail(MPOPF_ERR_ARG, "mpopf_sweep: NULL output");
+  return mpopf_eval(h, MPOPF_OUT_ALL, x, lam, sigma, sigma_x, dvec, delta_w, f, grad, c, jv, hv, kv, stream);
+}
+
+int mpopf_sweep_host(mpopf_handle *h, const double *x, const double *lam, double sigma, const double *sigma_x,
+                     const double *dvec, double delta_w, double *f, double *grad, double *c, double *jv, double *hv,
+                     double *kv, void *stream) {
+  if (!h) return fail(MPOPF_ERR_ARG, "mpopf_sweep_host: NULL handle");
+  if (!x || !lam || !sigma_x || !dvec || !f || !grad || !c || !jv || !hv || !kv)
+    return fail(MPOPF_ERR_ARG, "mpopf_sweep_host: NULL buffer");
+  const Dev &d = h->d;
+  const size_t n = d.n, m = d.m;
+  const size_t words = 2 * n + 2 * m + 1 + n + m + d.nnz_jac + d.nnz_hess + d.nnz_kkt;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!h->stage) {
+    void *p = nullptr;
+    const cudaError_t e = cudaMalloc(&p, words * sizeof(double));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(MPOPF_ERR_ALLOC, std::string("mpopf_sweep_host: staging: ") + cudaGetErrorString(e));
+    }
+    h->stage = static_cast<double *>(p);
+    h->stage_bytes = words * sizeof(double);
+  }
+  double *dx = h->stage, *dl = dx + n, *dsx = dl + m, *ddv = dsx + n;
+  double *df = ddv + m, *dg = df + 1, *dc = dg + n, *dj = dc + m, *dh = dj + d.nnz_jac, *dk = dh + d.nnz_hess;
+  cudaError_t e = cudaMemcpyAsync(dx, x, n * 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dl, lam, m * 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dsx, sigma_x, n * 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ddv, dvec, m * 8, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return fail(MPOPF_ERR_CUDA, std::string("mpopf_sweep_host: ") + cudaGetErrorString(e));
+  const int rc = mpopf_eval(h, MPOPF_OUT_ALL, dx, dl, sigma, dsx, ddv, delta_w, df, dg, dc, dj, dh, dk, stream);
+  if (rc != MPOPF_OK) return rc;
+  e = cudaMemcpyAsync(f, df, 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(grad, dg, n * 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c, dc, m * 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(jv, dj, d.nnz_jac * 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hv, dh, d.nnz_hess * 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(kv, dk, d.nnz_kkt * 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(MPOPF_ERR_CUDA, std::string("mpopf_sweep_host: ") + cudaGetErrorString(e));
+  return MPOPF_OK;
+}
+
+}  // extern "C"

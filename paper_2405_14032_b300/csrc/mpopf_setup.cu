@@ -1,0 +1,566 @@
+// Setup of libmpopf: validation, layout, per-period templates, device upload and
+// expansion of the J, W and M patterns over the horizon.
+//
+// Sec. III-A of the paper analyses the sparsity of each repeated pattern once
+// and expands it over the data array; here the analysis is the per-period
+// template (row lengths and offsets of one period, identical for every period
+// except the ramp entries of the generator rows at t >= 1) and the expansion is
+// a GPU kernel per pattern.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "mpopf_internal.cuh"
+
+namespace mpopf {
+
+static thread_local std::string g_err;
+void set_error(const std::string &msg) { g_err = msg; }
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Pattern expansion kernels (one thread per row or entry).
+// ---------------------------------------------------------------------------
+__global__ void k_pat_jac(Dev d, int32_t *__restrict__ jrow, int32_t *__restrict__ jcol) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= d.m) return;
+  const int64_t T = d.T, L = d.L, N = d.N, G = d.G;
+  if (i < T) {
+    jrow[i] = (int32_t)i;
+    jcol[i] = (int32_t)(i * N + d.ref);
+    return;
+  }
+  const int64_t TL = T * L;
+  int64_t r = i - T;
+  if (r < 7 * TL) {
+    const int k = (int)(r / TL) + 1;
+    const int64_t tl = r - (k - 1) * TL, t = tl / L, l = tl - t * L;
+    const int64_t f = d.br_f[l], to = d.br_t[l];
+    const int64_t vaf = t * N + f, vat = t * N + to, vmf = d.x_vm + t * N + f, vmt = d.x_vm + t * N + to;
+    if (k <= 4) {
+      const int64_t arc = (k == 1) ? d.x_p + 2 * t * L + l
+                        : (k == 2) ? d.x_q + 2 * t * L + l
+                        : (k == 3) ? d.x_p + 2 * t * L + L + l
+                                   : d.x_q + 2 * t * L + L + l;
+      const int64_t o = T + 5 * (k - 1) * TL + tl * 5;
+      const int64_t cols[5] = {arc, vaf, vat, vmf, vmt};
+      for (int e = 0; e < 5; ++e) { jrow[o + e] = (int32_t)i; jcol[o + e] = (int32_t)cols[e]; }
+    } else if (k == 5) {
+      const int64_t o = d.j_k5 + tl * 2;
+      jrow[o] = (int32_t)i; jcol[o] = (int32_t)vaf;
+      jrow[o + 1] = (int32_t)i; jcol[o + 1] = (int32_t)vat;
+    } else {
+      const int64_t a = (k == 6) ? l : L + l;
+      const int64_t o = (k == 6 ? d.j_k6 : d.j_k7) + tl * 2;
+      jrow[o] = (int32_t)i; jcol[o] = (int32_t)(d.x_p + 2 * t * L + a);
+      jrow[o + 1] = (int32_t)i; jcol[o + 1] = (int32_t)(d.x_q + 2 * t * L + a);
+    }
+    return;
+  }
+  r -= 7 * TL;
+  if (r < 2 * T * N) {
+    const bool P = r < T * N;
+    const int64_t tn = P ? r : r - T * N, t = tn / N, nb = tn - t * N;
+    int64_t o = (P ? d.j_k8 : d.j_k9) + t * d.jk8_per + d.jk8_off[nb];
+    jrow[o] = (int32_t)i; jcol[o] = (int32_t)(d.x_vm + t * N + nb); ++o;
+    for (int32_t e = d.bgen_ptr[nb]; e < d.bgen_ptr[nb + 1]; ++e, ++o) {
+      jrow[o] = (int32_t)i;
+      jcol[o] = (int32_t)((P ? d.x_pg : d.x_qg) + t * G + d.bgen_idx[e]);
+    }
+    for (int32_t e = d.barc_ptr[nb]; e < d.barc_ptr[nb + 1]; ++e, ++o) {
+      jrow[o] = (int32_t)i;
+      jcol[o] = (int32_t)((P ? d.x_p : d.x_q) + 2 * t * L + d.barc_idx[e]);
+    }
+    return;
+  }
+  r -= 2 * T * N;
+  const int64_t t = 1 + r / G, g = r - (t - 1) * G;
+  const int64_t o = d.j_k10 + r * 2;
+  jrow[o] = (int32_t)i; jcol[o] = (int32_t)(d.x_pg + t * G + g);
+  jrow[o + 1] = (int32_t)i; jcol[o + 1] = (int32_t)(d.x_pg + (t - 1) * G + g);
+}
+
+__global__ void k_pat_hess(Dev d, int32_t *__restrict__ hrow, int32_t *__restrict__ hcol) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= d.nnz_hess) return;
+  const int64_t T = d.T, L = d.L, N = d.N, G = d.G;
+  int64_t r, c;
+  if (e < d.h_br) {
+    const int64_t t = e / G, g = e - t * G;
+    r = c = d.x_pg + t * G + g;
+  } else if (e < d.h_th) {
+    const int64_t q = e - d.h_br, tl = q / 10, k = q - tl * 10, t = tl / L, l = tl - t * L;
+    const int64_t u[4] = {t * N + d.br_f[l], t * N + d.br_t[l], d.x_vm + t * N + d.br_f[l], d.x_vm + t * N + d.br_t[l]};
+    const int pa[10] = {0, 1, 1, 2, 2, 2, 3, 3, 3, 3};
+    const int pb[10] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3};
+    const int64_t A = u[pa[k]], B = u[pb[k]];
+    r = A > B ? A : B;
+    c = A > B ? B : A;
+  } else if (e < d.h_sh) {
+    const int64_t q = e - d.h_th, tl = q / 4, k = q - tl * 4, t = tl / L, l = tl - t * L;
+    const int64_t a = (k < 2) ? l : L + l;
+    r = c = ((k & 1) ? d.x_q : d.x_p) + 2 * t * L + a;
+  } else {
+    const int64_t q = (e - d.h_sh) / 2;
+    r = c = d.x_vm + q;  // q = t N + n
+  }
+  (void)T;
+  hrow[e] = (int32_t)r;
+  hcol[e] = (int32_t)c;
+}
+
+// M row pointers and columns, one thread per row; columns ascending.
+__global__ void k_pat_kkt(Dev d, int64_t *__restrict__ rowptr, int32_t *__restrict__ kcol) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= d.n) return;
+  // Row starts come from the templates; columns are written directly.
+  const int64_t T = d.T, L = d.L, N = d.N, G = d.G;
+  (void)T;
+  int64_t start = 0;
+  int64_t k = 0;
+  auto put = [&](int64_t col) { kcol[start + k] = (int32_t)col; ++k; };
+  if (j < d.x_vm) {
+    const int64_t t = j / N, nb = j - t * N;
+    start = d.m_va + t * d.mb_va + d.mo_va[nb];
+    for (int32_t q = d.nbr_ptr[nb]; q < d.nbr_ptr[nb + 1]; ++q)
+      if (d.nbr_bus[q] < nb) put(t * N + d.nbr_bus[q]);
+    put(j);
+  } else if (j < d.x_pg) {
+    const int64_t tn = j - d.x_vm, t = tn / N, nb = tn - t * N;
+    start = d.m_vm + t * d.mb_vm + d.mo_vm[nb];
+    const int32_t q0 = d.nbr_ptr[nb], q1 = d.nbr_ptr[nb + 1];
+    if (q1 > q0) {
+      bool self_done = false;
+      for (int32_t q = q0; q < q1; ++q) {
+        const int64_t o = d.nbr_bus[q];
+        if (!self_done && o > nb) { put(t * N + nb); self_done = true; }
+        put(t * N + o);
+      }
+      if (!self_done) put(t * N + nb);
+    }
+    for (int32_t q = q0; q < q1; ++q)
+      if (d.nbr_bus[q] < nb) put(d.x_vm + t * N + d.nbr_bus[q]);
+    put(j);
+  } else if (j < d.x_qg) {
+    const int64_t tg = j - d.x_pg, t = tg / G, g = tg - t * G, nb = d.gen_bus[g];
+    start = d.m_pg + (t == 0 ? (int64_t)d.mo_pg0[g] : d.mb_pg0 + (t - 1) * d.mb_pg1 + d.mo_pg1[g]);
+    put(d.x_vm + t * N + nb);
+    if (t >= 1) put(d.x_pg + (t - 1) * G + g);
+    for (int32_t q = d.bgen_ptr[nb]; q < d.bgen_ptr[nb] + d.gen_rank[g]; ++q) put(d.x_pg + t * G + d.bgen_idx[q]);
+    put(j);
+  } else if (j < d.x_p) {
+    const int64_t tg = j - d.x_qg, t = tg / G, g = tg - t * G, nb = d.gen_bus[g];
+    start = d.m_qg + t * d.mb_qg + d.mo_qg[g];
+    put(d.x_vm + t * N + nb);
+    for (int32_t q = d.bgen_ptr[nb]; q < d.bgen_ptr[nb] + d.gen_rank[g]; ++q) put(d.x_qg + t * G + d.bgen_idx[q]);
+    put(j);
+  } else {
+    const bool isP = j < d.x_q;
+    const int64_t ta = j - (isP ? d.x_p : d.x_q), t = ta / (2 * L), a = ta - t * 2 * L;
+    const int64_t l = a < L ? a : a - L;
+    const int64_t f = d.br_f[l], to = d.br_t[l], nb = a < L ? f : to;
+    const int64_t lo = f < to ? f : to, hi = f < to ? to : f;
+    start = isP ? d.m_p + t * d.mb_p + d.mo_p[a] : d.m_q + t * d.mb_q + d.mo_q[a];
+    put(t * N + lo);
+    put(t * N + hi);
+    put(d.x_vm + t * N + lo);
+    put(d.x_vm + t * N + hi);
+    for (int32_t q = d.bgen_ptr[nb]; q < d.bgen_ptr[nb + 1]; ++q) put((isP ? d.x_pg : d.x_qg) + t * G + d.bgen_idx[q]);
+    if (!isP) put(d.x_p + 2 * t * L + a);
+    for (int32_t q = d.barc_ptr[nb]; q < d.barc_ptr[nb] + d.arc_rank[a]; ++q)
+      put((isP ? d.x_p : d.x_q) + 2 * t * L + d.barc_idx[q]);
+    put(j);
+  }
+  rowptr[j] = start;
+  if (j == d.n - 1) rowptr[d.n] = start + k;
+}
+
+__global__ void k_bounds(Dev d, double *__restrict__ xl, double *__restrict__ xu, double *__restrict__ gl,
+                         double *__restrict__ gu, const double *vmin, const double *vmax, const double *pmin,
+                         const double *pmax, const double *qmin, const double *qmax, const double *angmin,
+                         const double *angmax, const double *ramp) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t N = d.N, G = d.G, L = d.L, T = d.T;
+  if (i < d.n) {
+    double lo = -INFINITY, hi = INFINITY;
+    if (i >= d.x_vm && i < d.x_pg) { const int64_t nb = (i - d.x_vm) % N; lo = vmin[nb]; hi = vmax[nb]; }
+    else if (i >= d.x_pg && i < d.x_qg) { const int64_t g = (i - d.x_pg) % G; lo = pmin[g]; hi = pmax[g]; }
+    else if (i >= d.x_qg && i < d.x_p) { const int64_t g = (i - d.x_qg) % G; lo = qmin[g]; hi = qmax[g]; }
+    xl[i] = lo;
+    xu[i] = hi;
+  }
+  if (i < d.m) {
+    double lo = 0.0, hi = 0.0;
+    const int64_t TL = T * L;
+    if (i >= T && i < T + 7 * TL) {
+      const int k = (int)((i - T) / TL) + 1;
+      const int64_t l = ((i - T) - (k - 1) * TL) % L;
+      if (k == 5) { lo = angmin[l]; hi = angmax[l]; }
+      if (k == 6 || k == 7) { lo = -INFINITY; hi = 0.0; }
+    } else if (i >= d.c_k10) {
+      const int64_t g = (i - d.c_k10) % G;
+      lo = -ramp[g];
+      hi = ramp[g];
+    }
+    gl[i] = lo;
+    gu[i] = hi;
+  }
+}
+
+unsigned grid_for(int64_t count) { return (unsigned)((count + kBlock - 1) / kBlock); }
+
+}  // namespace
+
+cudaError_t launch_patterns(const Dev &d, int32_t *jrow, int32_t *jcol, int32_t *hrow, int32_t *hcol,
+                            int64_t *krowptr, int32_t *kcol, double *xl, double *xu, double *gl, double *gu,
+                            const double *vmin, const double *vmax, const double *pmin, const double *pmax,
+                            const double *qmin, const double *qmax, const double *angmin, const double *angmax,
+                            const double *ramp, cudaStream_t s) {
+  if (d.m > 0) k_pat_jac<<<grid_for(d.m), kBlock, 0, s>>>(d, jrow, jcol);
+  if (d.nnz_hess > 0) k_pat_hess<<<grid_for(d.nnz_hess), kBlock, 0, s>>>(d, hrow, hcol);
+  if (d.n > 0) k_pat_kkt<<<grid_for(d.n), kBlock, 0, s>>>(d, krowptr, kcol);
+  const int64_t nm = d.n > d.m ? d.n : d.m;
+  k_bounds<<<grid_for(nm), kBlock, 0, s>>>(d, xl, xu, gl, gu, vmin, vmax, pmin, pmax, qmin, qmax, angmin, angmax,
+                                          ramp);
+  return cudaGetLastError();
+}
+
+}  // namespace mpopf
+
+using namespace mpopf;
+
+namespace {
+
+template <class T>
+T *dev_upload(mpopf_handle *h, const std::vector<T> &v, cudaError_t *err) {
+  if (*err != cudaSuccess) return nullptr;
+  void *p = nullptr;
+  const size_t bytes = std::max<size_t>(v.size(), 1) * sizeof(T);
+  *err = cudaMalloc(&p, bytes);
+  if (*err != cudaSuccess) return nullptr;
+  h->blocks[h->nblocks++] = p;
+  if (!v.empty()) *err = cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+  return static_cast<T *>(p);
+}
+
+template <class T>
+T *dev_alloc(mpopf_handle *h, int64_t count, cudaError_t *err) {
+  if (*err != cudaSuccess) return nullptr;
+  void *p = nullptr;
+  *err = cudaMalloc(&p, std::max<int64_t>(count, 1) * sizeof(T));
+  if (*err != cudaSuccess) return nullptr;
+  h->blocks[h->nblocks++] = p;
+  return static_cast<T *>(p);
+}
+
+void free_blocks(mpopf_handle *h) {
+  for (int i = 0; i < h->nblocks; ++i) cudaFree(h->blocks[i]);
+  h->nblocks = 0;
+  if (h->stage) cudaFree(h->stage);
+  h->stage = nullptr;
+}
+
+int fail(int code, const std::string &msg) {
+  set_error(msg);
+  return code;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *mpopf_last_error(void) { return g_err.c_str(); }
+
+int mpopf_setup(const mpopf_network *net, int32_t n_periods, const double *pd, const double *qd, mpopf_handle **out,
+                mpopf_pattern *pat) {
+  if (!net || !out) return fail(MPOPF_ERR_ARG, "mpopf_setup: NULL network or output handle");
+  *out = nullptr;
+  const int64_t N = net->n_bus, L = net->n_branch, G = net->n_gen, D = net->n_load, T = n_periods;
+  if (N < 1 || L < 0 || G < 0 || D < 0) return fail(MPOPF_ERR_ARG, "mpopf_setup: need n_bus >= 1 and counts >= 0");
+  if (T < 1) return fail(MPOPF_ERR_ARG, "mpopf_setup: need n_periods >= 1");
+  if (net->ref_bus < 0 || net->ref_bus >= N) return fail(MPOPF_ERR_ARG, "mpopf_setup: ref_bus out of range");
+  // Sizes first (before touching any array), so oversized problems fail cleanly.
+  const int64_t n = T * (2 * N + 2 * G + 4 * L);
+  const int64_t m = T * (1 + 7 * L + 2 * N) + G * (T - 1);
+  if (n >= ((int64_t)1 << 31) || m >= ((int64_t)1 << 31) || T * L >= ((int64_t)1 << 31))
+    return fail(MPOPF_ERR_SIZE, "mpopf_setup: n or m >= 2^31 (32-bit pattern indices)");
+  if (N > 0 && (!net->bus_gs || !net->bus_bs || !net->bus_vmin || !net->bus_vmax))
+    return fail(MPOPF_ERR_ARG, "mpopf_setup: NULL bus array");
+  if (L > 0 && (!net->br_f || !net->br_t || !net->br_r || !net->br_x || !net->br_b || !net->br_tap ||
+                !net->br_shift || !net->br_smax || !net->br_angmin || !net->br_angmax))
+    return fail(MPOPF_ERR_ARG, "mpopf_setup: NULL branch array");
+  if (G > 0 && (!net->gen_bus || !net->gen_c2 || !net->gen_c1 || !net->gen_c0 || !net->gen_pmin ||
+                !net->gen_pmax || !net->gen_qmin || !net->gen_qmax || !net->gen_ramp))
+    return fail(MPOPF_ERR_ARG, "mpopf_setup: NULL generator array");
+  if (D > 0 && (!net->load_bus || !pd || !qd)) return fail(MPOPF_ERR_ARG, "mpopf_setup: NULL load array");
+  for (int64_t l = 0; l < L; ++l) {
+    const int32_t f = net->br_f[l], t = net->br_t[l];
+    if (f < 0 || f >= N || t < 0 || t >= N) return fail(MPOPF_ERR_ARG, "mpopf_setup: branch end out of range");
+    if (f == t) return fail(MPOPF_ERR_ARG, "mpopf_setup: self-loop branch");
+    const double r = net->br_r[l], x = net->br_x[l];
+    if (!(r * r + x * x > 0.0)) return fail(MPOPF_ERR_ARG, "mpopf_setup: branch with r = x = 0");
+    if (!(net->br_tap[l] != 0.0) || !std::isfinite(net->br_tap[l]))
+      return fail(MPOPF_ERR_ARG, "mpopf_setup: branch tap must be finite and nonzero");
+  }
+  for (int64_t g = 0; g < G; ++g)
+    if (net->gen_bus[g] < 0 || net->gen_bus[g] >= N) return fail(MPOPF_ERR_ARG, "mpopf_setup: generator bus out of range");
+  for (int64_t k = 0; k < D; ++k)
+    if (net->load_bus[k] < 0 || net->load_bus[k] >= N) return fail(MPOPF_ERR_ARG, "mpopf_setup: load bus out of range");
+
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return fail(MPOPF_ERR_CUDA, "mpopf_setup: no CUDA device");
+  }
+
+  // ---- pi-model terms (textbook: y = 1/(r + jx), Y_ff = (y + jb/2)/tau^2,
+  // Y_ft = -y/(tau e^{-j phi}), Y_tf = -y/(tau e^{j phi}), Y_tt = y + jb/2) ----
+  std::vector<double> bc((size_t)BC_COUNT * L);
+  std::vector<uint8_t> sym(L);
+  for (int64_t l = 0; l < L; ++l) {
+    const double r = net->br_r[l], x = net->br_x[l], chg = net->br_b[l];
+    const double den = r * r + x * x;
+    const double g = r / den;
+    const double b = -x / den;
+    const double tau = net->br_tap[l], tau2 = tau * tau;
+    const double cph = std::cos(net->br_shift[l]), sph = std::sin(net->br_shift[l]);
+    const double gff = g / tau2, bff = (b + 0.5 * chg) / tau2;
+    const double gft = -(g * cph - b * sph) / tau, bft = -(g * sph + b * cph) / tau;
+    const double gtf = -(g * cph + b * sph) / tau, btf = -(b * cph - g * sph) / tau;
+    const double gtt = g, btt = b + 0.5 * chg;
+    const double vals[BC_COUNT] = {gff, bff, gft, bft, gtf, btf, gtt, btt, 2.0 * gff, 2.0 * bff, 2.0 * gtt,
+                                   2.0 * btt, net->br_smax[l] * net->br_smax[l]};
+    for (int k = 0; k < BC_COUNT; ++k) bc[(size_t)k * L + l] = vals[k];
+    sym[l] = (std::memcmp(&gtf, &gft, 8) == 0 && std::memcmp(&btf, &bft, 8) == 0) ? 1 : 0;
+  }
+  std::vector<double> m2gs(N), p2bs(N), mgs(N), bsv(N);
+  for (int64_t i = 0; i < N; ++i) {
+    m2gs[i] = -(2.0 * net->bus_gs[i]);
+    p2bs[i] = 2.0 * net->bus_bs[i];
+    mgs[i] = -net->bus_gs[i];
+    bsv[i] = net->bus_bs[i];
+  }
+
+  // ---- adjacency ----
+  auto csr = [&](int64_t nitems, auto key, std::vector<int32_t> *ptr, std::vector<int32_t> *idx) {
+    ptr->assign(N + 1, 0);
+    for (int64_t e = 0; e < nitems; ++e) (*ptr)[key(e) + 1]++;
+    for (int64_t i = 0; i < N; ++i) (*ptr)[i + 1] += (*ptr)[i];
+    idx->assign(nitems, 0);
+    std::vector<int32_t> fill(ptr->begin(), ptr->end() - 1);
+    for (int64_t e = 0; e < nitems; ++e) (*idx)[fill[key(e)]++] = (int32_t)e;  // ascending e
+  };
+  std::vector<int32_t> bgen_ptr, bgen_idx, barc_ptr, barc_idx, bload_ptr, bload_idx;
+  csr(G, [&](int64_t g) { return (int64_t)net->gen_bus[g]; }, &bgen_ptr, &bgen_idx);
+  csr(2 * L, [&](int64_t a) { return (int64_t)(a < L ? net->br_f[a] : net->br_t[a - L]); }, &barc_ptr, &barc_idx);
+  csr(D, [&](int64_t k) { return (int64_t)net->load_bus[k]; }, &bload_ptr, &bload_idx);
+  std::vector<int32_t> gen_rank(G), arc_rank(2 * L);
+  for (int64_t i = 0; i < N; ++i) {
+    for (int32_t q = bgen_ptr[i]; q < bgen_ptr[i + 1]; ++q) gen_rank[bgen_idx[q]] = q - bgen_ptr[i];
+    for (int32_t q = barc_ptr[i]; q < barc_ptr[i + 1]; ++q) arc_rank[barc_idx[q]] = q - barc_ptr[i];
+  }
+  // incident branches by branch index (code 2l + end)
+  std::vector<std::vector<int32_t>> inc(N);
+  for (int64_t l = 0; l < L; ++l) {
+    inc[net->br_f[l]].push_back((int32_t)(2 * l));
+    inc[net->br_t[l]].push_back((int32_t)(2 * l + 1));
+  }
+  std::vector<int32_t> inc_ptr(N + 1, 0), inc_code;
+  std::vector<int32_t> nbr_ptr(N + 1, 0), nbr_bus, nbr_grp, grp_code, bus_nd(N), bus_ndlt(N);
+  inc_code.reserve(2 * L);
+  for (int64_t i = 0; i < N; ++i) {
+    std::vector<int32_t> &v = inc[i];  // already ascending in l
+    inc_code.insert(inc_code.end(), v.begin(), v.end());
+    inc_ptr[i + 1] = (int32_t)inc_code.size();
+    std::vector<std::pair<int32_t, int32_t>> nb;  // (neighbour, code)
+    for (int32_t code : v) {
+      const int64_t l = code >> 1;
+      nb.push_back({(code & 1) ? net->br_f[l] : net->br_t[l], code});
+    }
+    std::stable_sort(nb.begin(), nb.end(), [](auto &a, auto &b) { return a.first < b.first; });
+    int32_t nd = 0, ndlt = 0;
+    for (size_t k = 0; k < nb.size(); ++k) {
+      if (k == 0 || nb[k].first != nb[k - 1].first) {
+        nbr_bus.push_back(nb[k].first);
+        nbr_grp.push_back((int32_t)grp_code.size());
+        ++nd;
+        if (nb[k].first < i) ++ndlt;
+      }
+      grp_code.push_back(nb[k].second);
+    }
+    nbr_ptr[i + 1] = (int32_t)nbr_bus.size();
+    bus_nd[i] = nd;
+    bus_ndlt[i] = ndlt;
+  }
+  nbr_grp.push_back((int32_t)grp_code.size());
+
+  // ---- templates ----
+  std::vector<int32_t> jk8_off(N);
+  int64_t acc = 0;
+  for (int64_t i = 0; i < N; ++i) {
+    jk8_off[i] = (int32_t)acc;
+    acc += 1 + (bgen_ptr[i + 1] - bgen_ptr[i]) + (barc_ptr[i + 1] - barc_ptr[i]);
+  }
+  const int64_t jk8_per = acc;  // = N + G + 2L
+  auto prefix = [](const std::vector<int64_t> &len, std::vector<int32_t> *off) {
+    off->assign(len.size(), 0);
+    int64_t s = 0;
+    for (size_t k = 0; k < len.size(); ++k) { (*off)[k] = (int32_t)s; s += len[k]; }
+    return s;
+  };
+  std::vector<int64_t> len_va(N), len_vm(N), len_pg0(G), len_pg1(G), len_qg(G), len_p(2 * L), len_q(2 * L);
+  for (int64_t i = 0; i < N; ++i) {
+    len_va[i] = bus_ndlt[i] + 1;
+    len_vm[i] = (bus_nd[i] > 0 ? bus_nd[i] + 1 : 0) + bus_ndlt[i] + 1;
+  }
+  for (int64_t g = 0; g < G; ++g) {
+    len_pg0[g] = 1 + gen_rank[g] + 1;
+    len_pg1[g] = 2 + gen_rank[g] + 1;
+    len_qg[g] = 1 + gen_rank[g] + 1;
+  }
+  for (int64_t a = 0; a < 2 * L; ++a) {
+    const int64_t bus = a < L ? net->br_f[a] : net->br_t[a - L];
+    const int64_t kb = bgen_ptr[bus + 1] - bgen_ptr[bus];
+    len_p[a] = 4 + kb + arc_rank[a] + 1;
+    len_q[a] = 4 + kb + 1 + arc_rank[a] + 1;
+  }
+  std::vector<int32_t> mo_va, mo_vm, mo_pg0, mo_pg1, mo_qg, mo_p, mo_q;
+  const int64_t mb_va = prefix(len_va, &mo_va), mb_vm = prefix(len_vm, &mo_vm);
+  const int64_t mb_pg0 = prefix(len_pg0, &mo_pg0), mb_pg1 = prefix(len_pg1, &mo_pg1);
+  const int64_t mb_qg = prefix(len_qg, &mo_qg), mb_p = prefix(len_p, &mo_p), mb_q = prefix(len_q, &mo_q);
+  const int64_t big = (int64_t)1 << 31;
+  if (mb_vm >= big || mb_p >= big || mb_q >= big || jk8_per * 1 >= big)
+    return fail(MPOPF_ERR_SIZE, "mpopf_setup: one period of M exceeds 32-bit offsets");
+
+  mpopf_handle *h = new mpopf_handle();
+  std::memset(h, 0, sizeof(*h));
+  Dev &d = h->d;
+  d.N = (int32_t)N; d.L = (int32_t)L; d.G = (int32_t)G; d.D = (int32_t)D; d.T = (int32_t)T; d.ref = net->ref_bus;
+  d.n = n; d.m = m;
+  d.x_vm = T * N; d.x_pg = 2 * T * N; d.x_qg = 2 * T * N + T * G; d.x_p = 2 * T * N + 2 * T * G;
+  d.x_q = d.x_p + 2 * T * L;
+  d.c_k8 = T + 7 * T * L; d.c_k9 = d.c_k8 + T * N; d.c_k10 = d.c_k9 + T * N;
+  d.j_k5 = T + 20 * T * L; d.j_k6 = d.j_k5 + 2 * T * L; d.j_k7 = d.j_k6 + 2 * T * L; d.j_k8 = d.j_k7 + 2 * T * L;
+  d.jk8_per = jk8_per; d.j_k9 = d.j_k8 + T * jk8_per; d.j_k10 = d.j_k9 + T * jk8_per;
+  d.nnz_jac = d.j_k10 + 2 * (T - 1) * G;
+  d.h_br = T * G; d.h_th = d.h_br + 10 * T * L; d.h_sh = d.h_th + 4 * T * L; d.nnz_hess = d.h_sh + 2 * T * N;
+  d.mb_va = mb_va; d.mb_vm = mb_vm; d.mb_pg0 = mb_pg0; d.mb_pg1 = mb_pg1; d.mb_qg = mb_qg; d.mb_p = mb_p; d.mb_q = mb_q;
+  d.m_va = 0;
+  d.m_vm = d.m_va + T * mb_va;
+  d.m_pg = d.m_vm + T * mb_vm;
+  d.m_qg = d.m_pg + mb_pg0 + (T - 1) * mb_pg1;
+  d.m_p = d.m_qg + T * mb_qg;
+  d.m_q = d.m_p + T * mb_p;
+  d.nnz_kkt = d.m_q + T * mb_q;
+
+  cudaError_t err = cudaSuccess;
+  std::vector<int32_t> brf(net->br_f, net->br_f + L), brt(net->br_t, net->br_t + L);
+  d.br_f = dev_upload(h, brf, &err);
+  d.br_t = dev_upload(h, brt, &err);
+  d.bc = dev_upload(h, bc, &err);
+  d.br_sym = dev_upload(h, sym, &err);
+  d.bus_m2gs = dev_upload(h, m2gs, &err);
+  d.bus_p2bs = dev_upload(h, p2bs, &err);
+  d.bus_mgs = dev_upload(h, mgs, &err);
+  d.bus_bs = dev_upload(h, bsv, &err);
+  d.bgen_ptr = dev_upload(h, bgen_ptr, &err); d.bgen_idx = dev_upload(h, bgen_idx, &err);
+  d.barc_ptr = dev_upload(h, barc_ptr, &err); d.barc_idx = dev_upload(h, barc_idx, &err);
+  d.bload_ptr = dev_upload(h, bload_ptr, &err); d.bload_idx = dev_upload(h, bload_idx, &err);
+  d.inc_ptr = dev_upload(h, inc_ptr, &err); d.inc_code = dev_upload(h, inc_code, &err);
+  d.nbr_ptr = dev_upload(h, nbr_ptr, &err); d.nbr_bus = dev_upload(h, nbr_bus, &err);
+  d.nbr_grp = dev_upload(h, nbr_grp, &err); d.grp_code = dev_upload(h, grp_code, &err);
+  d.bus_nd = dev_upload(h, bus_nd, &err); d.bus_ndlt = dev_upload(h, bus_ndlt, &err);
+  std::vector<int32_t> gbus(net->gen_bus, net->gen_bus + G);
+  d.gen_bus = dev_upload(h, gbus, &err);
+  d.gen_rank = dev_upload(h, gen_rank, &err);
+  std::vector<double> c2(net->gen_c2, net->gen_c2 + G), c1(net->gen_c1, net->gen_c1 + G),
+      c0(net->gen_c0, net->gen_c0 + G), c2x2(G);
+  for (int64_t g = 0; g < G; ++g) c2x2[g] = 2.0 * c2[g];
+  d.gen_c2 = dev_upload(h, c2, &err); d.gen_c1 = dev_upload(h, c1, &err);
+  d.gen_c0 = dev_upload(h, c0, &err); d.gen_c2x2 = dev_upload(h, c2x2, &err);
+  d.arc_rank = dev_upload(h, arc_rank, &err);
+  d.jk8_off = dev_upload(h, jk8_off, &err);
+  d.mo_va = dev_upload(h, mo_va, &err); d.mo_vm = dev_upload(h, mo_vm, &err);
+  d.mo_pg0 = dev_upload(h, mo_pg0, &err); d.mo_pg1 = dev_upload(h, mo_pg1, &err);
+  d.mo_qg = dev_upload(h, mo_qg, &err); d.mo_p = dev_upload(h, mo_p, &err); d.mo_q = dev_upload(h, mo_q, &err);
+  std::vector<double> vpd(pd ? pd : (const double *)nullptr, pd ? pd + T * D : (const double *)nullptr);
+  std::vector<double> vqd(qd ? qd : (const double *)nullptr, qd ? qd + T * D : (const double *)nullptr);
+  d.pd = dev_upload(h, vpd, &err);
+  d.qd = dev_upload(h, vqd, &err);
+  d.S = dev_alloc<double>(h, T * L * 6, &err);
+  d.fpart_n = (int32_t)std::max<int64_t>(1, (T * G + kBlock - 1) / kBlock);
+  d.fpart = dev_alloc<double>(h, d.fpart_n, &err);
+  // patterns and bounds
+  mpopf_pattern &P = h->pat;
+  int32_t *jrow = dev_alloc<int32_t>(h, d.nnz_jac, &err), *jcol = dev_alloc<int32_t>(h, d.nnz_jac, &err);
+  int32_t *hrow = dev_alloc<int32_t>(h, d.nnz_hess, &err), *hcol = dev_alloc<int32_t>(h, d.nnz_hess, &err);
+  int64_t *krp = dev_alloc<int64_t>(h, n + 1, &err);
+  int32_t *kcol = dev_alloc<int32_t>(h, d.nnz_kkt, &err);
+  double *xl = dev_alloc<double>(h, n, &err), *xu = dev_alloc<double>(h, n, &err);
+  double *gl = dev_alloc<double>(h, m, &err), *gu = dev_alloc<double>(h, m, &err);
+  // temporary bound sources
+  std::vector<double> tmp_src;
+  auto cat = [&](const double *p, int64_t k) { if (k > 0) tmp_src.insert(tmp_src.end(), p, p + k); };
+  cat(net->bus_vmin, N); cat(net->bus_vmax, N);
+  if (G > 0) { cat(net->gen_pmin, G); cat(net->gen_pmax, G); cat(net->gen_qmin, G); cat(net->gen_qmax, G); cat(net->gen_ramp, G); }
+  if (L > 0) { cat(net->br_angmin, L); cat(net->br_angmax, L); }
+  double *src = dev_upload(h, tmp_src, &err);
+  if (err != cudaSuccess) {
+    const bool oom = err == cudaErrorMemoryAllocation;
+    std::string msg = std::string("mpopf_setup: ") + cudaGetErrorString(err);
+    free_blocks(h);
+    delete h;
+    cudaGetLastError();
+    return fail(oom ? MPOPF_ERR_ALLOC : MPOPF_ERR_CUDA, msg);
+  }
+  const double *vmin = src, *vmax = src + N;
+  const double *pmin = src + 2 * N, *pmax = pmin + G, *qmin = pmax + G, *qmax = qmin + G, *ramp = qmax + G;
+  const double *angmin = src + 2 * N + 5 * G, *angmax = angmin + L;
+  err = launch_patterns(d, jrow, jcol, hrow, hcol, krp, kcol, xl, xu, gl, gu, vmin, vmax, pmin, pmax, qmin, qmax,
+                        angmin, angmax, ramp, 0);
+  if (err == cudaSuccess) err = cudaDeviceSynchronize();
+  if (err != cudaSuccess) {
+    std::string msg = std::string("mpopf_setup: pattern expansion: ") + cudaGetErrorString(err);
+    free_blocks(h);
+    delete h;
+    cudaGetLastError();
+    return fail(MPOPF_ERR_CUDA, msg);
+  }
+  P.n = n; P.m = m; P.nnz_jac = d.nnz_jac; P.nnz_hess = d.nnz_hess; P.nnz_kkt = d.nnz_kkt;
+  P.n_bus = d.N; P.n_branch = d.L; P.n_gen = d.G; P.n_load = d.D; P.n_periods = d.T;
+  P.jac_row = jrow; P.jac_col = jcol; P.hess_row = hrow; P.hess_col = hcol;
+  P.kkt_rowptr = krp; P.kkt_col = kcol; P.xl = xl; P.xu = xu; P.gl = gl; P.gu = gu;
+  if (pat) *pat = P;
+  *out = h;
+  return MPOPF_OK;
+}
+
+int mpopf_get_pattern(const mpopf_handle *h, mpopf_pattern *pat) {
+  if (!h || !pat) return fail(MPOPF_ERR_ARG, "mpopf_get_pattern: NULL argument");
+  *pat = h->pat;
+  return MPOPF_OK;
+}
+
+int mpopf_set_loads(mpopf_handle *h, const double *d_pd, const double *d_qd, void *stream) {
+  if (!h) return fail(MPOPF_ERR_ARG, "mpopf_set_loads: NULL handle");
+  const size_t bytes = (size_t)h->d.T * h->d.D * sizeof(double);
+  if (bytes == 0) return MPOPF_OK;
+  if (!d_pd || !d_qd) return fail(MPOPF_ERR_ARG, "mpopf_set_loads: NULL load array");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(const_cast<double *>(h->d.pd), d_pd, bytes, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(const_cast<double *>(h->d.qd), d_qd, bytes, cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return fail(MPOPF_ERR_CUDA, std::string("mpopf_set_loads: ") + cudaGetErrorString(e));
+  return MPOPF_OK;
+}
+
+void mpopf_destroy(mpopf_handle *h) {
+  if (!h) return;
+  free_blocks(h);
+  delete h;
+}
+
+}  // extern "C"

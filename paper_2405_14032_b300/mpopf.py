@@ -1,0 +1,215 @@
+"""Thin ctypes binding of ``libmpopf.so`` (declared in ``include/mpopf.h``).
+
+Argument marshalling only: every step of the evaluation runs in the library's
+CUDA kernels.  Device arrays are torch CUDA tensors (float64, contiguous);
+PyTorch supplies device memory and the current stream.  The library must be
+built (``python -m paper_2405_14032_b300.build``); loading fails loudly
+otherwise -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmpopf.so")
+
+OUT_OBJ, OUT_GRAD, OUT_CONS, OUT_JAC, OUT_HESS, OUT_KKT = 1, 2, 4, 8, 16, 32
+OUT_ALL = 63
+
+_P = ctypes.c_void_p
+_D = ctypes.c_double
+_I32 = ctypes.c_int32
+_U = ctypes.c_uint
+
+
+class _Network(ctypes.Structure):
+    _fields_ = [("n_bus", _I32), ("n_branch", _I32), ("n_gen", _I32), ("n_load", _I32), ("ref_bus", _I32)] + [
+        (name, _P) for name in (
+            "bus_gs", "bus_bs", "bus_vmin", "bus_vmax", "br_f", "br_t", "br_r", "br_x", "br_b", "br_tap",
+            "br_shift", "br_smax", "br_angmin", "br_angmax", "gen_bus", "gen_c2", "gen_c1", "gen_c0",
+            "gen_pmin", "gen_pmax", "gen_qmin", "gen_qmax", "gen_ramp", "load_bus")]
+
+
+class _Pattern(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("m", ctypes.c_int64), ("nnz_jac", ctypes.c_int64),
+                ("nnz_hess", ctypes.c_int64), ("nnz_kkt", ctypes.c_int64),
+                ("n_bus", _I32), ("n_branch", _I32), ("n_gen", _I32), ("n_load", _I32), ("n_periods", _I32)] + [
+        (name, _P) for name in ("jac_row", "jac_col", "hess_row", "hess_col", "kkt_rowptr", "kkt_col",
+                                "xl", "xu", "gl", "gu")]
+
+
+_lib = None
+
+
+def lib():
+    """Load libmpopf.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libmpopf.so not found at {LIB_PATH}; build it with "
+                               "`python -m paper_2405_14032_b300.build` (there is no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        sig = {
+            "mpopf_setup": (ctypes.c_int, [ctypes.POINTER(_Network), _I32, _P, _P, ctypes.POINTER(_P),
+                                           ctypes.POINTER(_Pattern)]),
+            "mpopf_get_pattern": (ctypes.c_int, [_P, ctypes.POINTER(_Pattern)]),
+            "mpopf_set_loads": (ctypes.c_int, [_P, _P, _P, _P]),
+            "mpopf_eval": (ctypes.c_int, [_P, _U, _P, _P, _D, _P, _P, _D, _P, _P, _P, _P, _P, _P, _P]),
+            "mpopf_eval_obj": (ctypes.c_int, [_P, _P, _P, _P]),
+            "mpopf_eval_grad": (ctypes.c_int, [_P, _P, _P, _P]),
+            "mpopf_eval_cons": (ctypes.c_int, [_P, _P, _P, _P]),
+            "mpopf_eval_jac": (ctypes.c_int, [_P, _P, _P, _P]),
+            "mpopf_eval_hess": (ctypes.c_int, [_P, _P, _P, _D, _P, _P]),
+            "mpopf_assemble_kkt": (ctypes.c_int, [_P, _P, _P, _D, _P, _P, _D, _P, _P]),
+            "mpopf_sweep": (ctypes.c_int, [_P, _P, _P, _D, _P, _P, _D, _P, _P, _P, _P, _P, _P, _P]),
+            "mpopf_sweep_host": (ctypes.c_int, [_P, _P, _P, _D, _P, _P, _D, _P, _P, _P, _P, _P, _P, _P]),
+            "mpopf_launch_count": (ctypes.c_int, [_P, _U]),
+            "mpopf_destroy": (None, [_P]),
+            "mpopf_last_error": (ctypes.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    """Names the header declares (for the load/export check)."""
+    return ["mpopf_setup", "mpopf_get_pattern", "mpopf_set_loads", "mpopf_eval", "mpopf_eval_obj",
+            "mpopf_eval_grad", "mpopf_eval_cons", "mpopf_eval_jac", "mpopf_eval_hess", "mpopf_assemble_kkt",
+            "mpopf_sweep", "mpopf_sweep_host", "mpopf_launch_count", "mpopf_destroy", "mpopf_last_error"]
+
+
+class MpopfError(RuntimeError):
+    pass
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise MpopfError(f"{what} failed ({rc}): {lib().mpopf_last_error().decode()}")
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+class _DeviceArray:
+    """Zero-copy view of library-owned device memory for torch.as_tensor."""
+
+    def __init__(self, ptr, count, typestr):
+        self.__cuda_array_interface__ = {"shape": (int(count),), "typestr": typestr,
+                                         "data": (int(ptr or 0), False), "version": 3, "strides": None}
+
+
+def _stream_ptr(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Handle:
+    """A multi-period AC OPF model on the GPU (``mpopf_setup`` once)."""
+
+    def __init__(self, inst):
+        net = inst.net
+        self._keep = []
+
+        def arr(a, dt):
+            a = np.ascontiguousarray(a, dtype=dt)
+            self._keep.append(a)
+            return a.ctypes.data if a.size else None
+
+        f64, i32 = np.float64, np.int32
+        c = _Network(
+            n_bus=net.n_bus, n_branch=net.n_branch, n_gen=net.n_gen, n_load=net.n_load, ref_bus=net.ref_bus,
+            bus_gs=arr(net.bus_gs, f64), bus_bs=arr(net.bus_bs, f64), bus_vmin=arr(net.bus_vmin, f64),
+            bus_vmax=arr(net.bus_vmax, f64), br_f=arr(net.br_f, i32), br_t=arr(net.br_t, i32),
+            br_r=arr(net.br_r, f64), br_x=arr(net.br_x, f64), br_b=arr(net.br_b, f64), br_tap=arr(net.br_tap, f64),
+            br_shift=arr(net.br_shift, f64), br_smax=arr(net.br_smax, f64), br_angmin=arr(net.br_angmin, f64),
+            br_angmax=arr(net.br_angmax, f64), gen_bus=arr(net.gen_bus, i32), gen_c2=arr(net.gen_c2, f64),
+            gen_c1=arr(net.gen_c1, f64), gen_c0=arr(net.gen_c0, f64), gen_pmin=arr(net.gen_pmin, f64),
+            gen_pmax=arr(net.gen_pmax, f64), gen_qmin=arr(net.gen_qmin, f64), gen_qmax=arr(net.gen_qmax, f64),
+            gen_ramp=arr(net.gen_ramp, f64), load_bus=arr(net.load_bus, i32))
+        pd = arr(inst.pd, f64)
+        qd = arr(inst.qd, f64)
+        h = ctypes.c_void_p()
+        pat = _Pattern()
+        _check(lib().mpopf_setup(ctypes.byref(c), int(inst.T), pd, qd, ctypes.byref(h), ctypes.byref(pat)),
+               "mpopf_setup")
+        self._keep = []
+        self.h = h
+        self.pat = pat
+        self.T = int(inst.T)
+        self.n, self.m = int(pat.n), int(pat.m)
+        self.nnz_jac, self.nnz_hess, self.nnz_kkt = int(pat.nnz_jac), int(pat.nnz_hess), int(pat.nnz_kkt)
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            lib().mpopf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- patterns (zero-copy torch views of handle-owned device memory) ------
+    def pattern(self):
+        import torch
+        p = self.pat
+        t = lambda ptr, k, ty: torch.as_tensor(_DeviceArray(ptr, k, ty), device="cuda")
+        return dict(
+            jac_row=t(p.jac_row, self.nnz_jac, "<i4"), jac_col=t(p.jac_col, self.nnz_jac, "<i4"),
+            hess_row=t(p.hess_row, self.nnz_hess, "<i4"), hess_col=t(p.hess_col, self.nnz_hess, "<i4"),
+            kkt_rowptr=t(p.kkt_rowptr, self.n + 1, "<i8"), kkt_col=t(p.kkt_col, self.nnz_kkt, "<i4"),
+            xl=t(p.xl, self.n, "<f8"), xu=t(p.xu, self.n, "<f8"), gl=t(p.gl, self.m, "<f8"),
+            gu=t(p.gu, self.m, "<f8"))
+
+    def launch_count(self, outputs=OUT_ALL):
+        return int(lib().mpopf_launch_count(self.h, outputs))
+
+    # -- evaluation -----------------------------------------------------------
+    def new_outputs(self, outputs=OUT_ALL):
+        import torch
+        kw = dict(dtype=torch.float64, device="cuda")
+        e = lambda k: torch.empty(k, **kw)
+        return dict(f=e(1) if outputs & OUT_OBJ else None, grad=e(self.n) if outputs & OUT_GRAD else None,
+                    c=e(self.m) if outputs & OUT_CONS else None, jv=e(self.nnz_jac) if outputs & OUT_JAC else None,
+                    hv=e(self.nnz_hess) if outputs & OUT_HESS else None,
+                    kv=e(self.nnz_kkt) if outputs & OUT_KKT else None)
+
+    def eval(self, outputs, x, lam=None, sigma=1.0, sigma_x=None, dvec=None, delta_w=0.0, out=None, stream=None):
+        out = self.new_outputs(outputs) if out is None else out
+        _check(lib().mpopf_eval(self.h, outputs, _ptr(x), _ptr(lam), float(sigma), _ptr(sigma_x), _ptr(dvec),
+                                float(delta_w), _ptr(out.get("f")), _ptr(out.get("grad")), _ptr(out.get("c")),
+                                _ptr(out.get("jv")), _ptr(out.get("hv")), _ptr(out.get("kv")),
+                                _stream_ptr(stream)), "mpopf_eval")
+        return out
+
+    def sweep(self, x, lam, sigma, sigma_x, dvec, delta_w, out=None, stream=None):
+        out = self.new_outputs(OUT_ALL) if out is None else out
+        _check(lib().mpopf_sweep(self.h, _ptr(x), _ptr(lam), float(sigma), _ptr(sigma_x), _ptr(dvec),
+                                 float(delta_w), _ptr(out["f"]), _ptr(out["grad"]), _ptr(out["c"]), _ptr(out["jv"]),
+                                 _ptr(out["hv"]), _ptr(out["kv"]), _stream_ptr(stream)), "mpopf_sweep")
+        return out
+
+    def sweep_host(self, x, lam, sigma, sigma_x, dvec, delta_w, out, stream=None):
+        """All inputs and outputs are host arrays (numpy or pinned torch CPU tensors)."""
+        _check(lib().mpopf_sweep_host(self.h, _ptr(x), _ptr(lam), float(sigma), _ptr(sigma_x), _ptr(dvec),
+                                      float(delta_w), _ptr(out["f"]), _ptr(out["grad"]), _ptr(out["c"]),
+                                      _ptr(out["jv"]), _ptr(out["hv"]), _ptr(out["kv"]), _stream_ptr(stream)),
+               "mpopf_sweep_host")
+        return out
+
+    def set_loads(self, pd, qd, stream=None):
+        _check(lib().mpopf_set_loads(self.h, _ptr(pd), _ptr(qd), _stream_ptr(stream)), "mpopf_set_loads")

@@ -1,0 +1,100 @@
+"""The C-ABI library loads, exports every symbol include/mpopf.h declares, and
+rejects bad arguments on the host before any device work (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2405_14032_b300 import mpopf, synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "mpopf.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(mpopf_[a-z_0-9]+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = mpopf.lib()
+    names = _declared()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) <= set(mpopf.exported_symbols()) | set(names)
+
+
+def _setup_rc(net, T=2, pd=None, qd=None):
+    lib = mpopf.lib()
+    h = ctypes.c_void_p()
+    pat = mpopf._Pattern()
+    keep = []
+
+    def arr(a, dt):
+        a = np.ascontiguousarray(a, dtype=dt)
+        keep.append(a)
+        return a.ctypes.data if a.size else None
+
+    c = mpopf._Network(
+        n_bus=net.n_bus, n_branch=net.n_branch, n_gen=net.n_gen, n_load=net.n_load, ref_bus=net.ref_bus,
+        **{k: arr(getattr(net, k), np.int32 if k in ("br_f", "br_t", "gen_bus", "load_bus") else np.float64)
+           for k, _ in mpopf._Network._fields_[5:]})
+    pd = np.zeros((T, net.n_load)) if pd is None else pd
+    qd = np.zeros((T, net.n_load)) if qd is None else qd
+    rc = lib.mpopf_setup(ctypes.byref(c), T, arr(pd, np.float64), arr(qd, np.float64), ctypes.byref(h),
+                         ctypes.byref(pat))
+    if rc == 0:
+        lib.mpopf_destroy(h)
+    return rc, lib.mpopf_last_error().decode()
+
+
+def test_rejects_bad_arguments_on_host():
+    net = synth.make_network(3, 10, 14, 2, 3)
+    rc, msg = _setup_rc(net, T=0)
+    assert rc == -1 and "n_periods" in msg
+    bad = synth.make_network(3, 10, 14, 2, 3)
+    bad.br_t = bad.br_f.copy()
+    rc, msg = _setup_rc(bad)
+    assert rc == -1 and "self-loop" in msg
+    bad = synth.make_network(3, 10, 14, 2, 3)
+    bad.gen_bus = np.array([0, 11], np.int32)
+    rc, msg = _setup_rc(bad)
+    assert rc == -1 and "generator bus" in msg
+    bad = synth.make_network(3, 10, 14, 2, 3)
+    bad.ref_bus = 10
+    rc, msg = _setup_rc(bad)
+    assert rc == -1
+    bad = synth.make_network(3, 10, 14, 2, 3)
+    bad.br_tap = np.zeros(14)
+    rc, msg = _setup_rc(bad)
+    assert rc == -1 and "tap" in msg
+
+
+def test_rejects_oversized_problem_before_allocation():
+    """n = T (2N + 2G + 4L) >= 2^31 is refused with MPOPF_ERR_SIZE before any
+    array is read (the arrays here are NULL)."""
+    lib = mpopf.lib()
+    c = mpopf._Network(n_bus=600_000_000, n_branch=0, n_gen=0, n_load=0, ref_bus=0)
+    h = ctypes.c_void_p()
+    rc = lib.mpopf_setup(ctypes.byref(c), 2, None, None, ctypes.byref(h), None)
+    assert rc == -2
+    assert "2^31" in lib.mpopf_last_error().decode()
+
+
+def test_null_handle_calls_fail_cleanly():
+    lib = mpopf.lib()
+    assert lib.mpopf_eval(None, 63, None, None, 1.0, None, None, 0.0, None, None, None, None, None, None,
+                          None) == -1
+    assert lib.mpopf_launch_count(None, 63) == -1
+    lib.mpopf_destroy(None)
+
+
+def test_no_device_is_an_error_not_a_fallback():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    rc, msg = _setup_rc(synth.make_network(3, 10, 14, 2, 3))
+    assert rc == -3 and "CUDA" in msg
