@@ -1,0 +1,356 @@
+#!/usr/bin/env python
+"""Benchmark of the per-iteration hot path of the multi-period AC OPF method
+(arXiv 2405.14032): one full derivative sweep = f, grad f, c, J (COO), W (lower
+COO) and the condensed KKT matrix M = W + diag(Sigma_x + delta_w) + J^T D J
+(lower CSR), all FP64, on the 10,000-bus / 16,000-branch / 2,000-generator /
+6,000-load network with T = 168 hourly periods (seeded synthetic data).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One JSON line on rank 0.  Under torchrun (N > 1) every rank evaluates its own
+copy of the instance (independent problems, no data-path collective; weak
+scaling); the timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "full derivative sweeps/s + HBM GB/s (10k-bus T=168); batched & adjoint vs plain"
+UNIT = "sweeps/s"
+WORKLOAD = dict(n_bus=10000, n_branch=16000, n_gen=2000, n_load=6000, seed=3)
+# FP64 operations of one branch x period instance of the full sweep (k_branch,
+# ALL outputs): angle difference 1, sin/cos 19, flow terms 14, constraint values
+# 14, Jacobian 12, W block and thermal 18, condensed-matrix contributions 75.
+FP64_OPS_PER_BRANCH_PERIOD = 153
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--periods", type=int, default=168, help="horizon T (168 is the benchmark workload)")
+    ap.add_argument("--e2e-steps", type=int, default=8)
+    return ap.parse_args()
+
+
+def algorithmic_bytes(n, m, nnz_jac, nnz_hess, nnz_kkt, D, T):
+    """Each array touched once: reads x, Sigma_x (n), lambda, D (m), loads
+    (2 D T); writes grad (n), c (m), J, W, M values."""
+    return 8 * (2 * n + 2 * m + 2 * D * T) + 8 * (n + m + nnz_jac + nnz_hess + nnz_kkt)
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+def kernel_source_hash():
+    src = os.path.join(ROOT, "paper_2405_14032_b300", "csrc", "mpopf_kernels.cu")
+    with open(src, "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def ncu_traffic():
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, or None when the kernel source changed since the capture."""
+    p = os.path.join(ROOT, "profiles", "k_branch_traffic.json")
+    try:
+        with open(p) as fh:
+            rec = json.load(fh)
+    except OSError:
+        return None
+    if rec.get("kernel_source_sha256_16") != kernel_source_hash():
+        return None
+    return rec.get("dram_bytes_per_launch_full_workload")
+
+
+# ---------------------------------------------------------------------------
+# Clocks (NVML, read-only) sampled during the timed region.
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    REASONS = {
+        "gpu_idle": 0x1, "applications_clocks_setting": 0x2, "sw_power_cap": 0x4, "hw_slowdown": 0x8,
+        "sync_boost": 0x10, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40,
+        "hw_power_brake_slowdown": 0x80, "display_clock_setting": 0x100,
+    }
+
+    def __init__(self, index, period_s=0.01):
+        self.index, self.period = index, period_s
+        self.samples, self.reasons = [], 0
+        self.max_mhz = None
+        self._stop = threading.Event()
+        self._t = None
+        self.ok = False
+
+    def start(self):
+        try:
+            import pynvml
+            pynvml.nvmlInit()
+            self._nv = pynvml
+            self._h = pynvml.nvmlDeviceGetHandleByIndex(self.index)
+            self.max_mhz = pynvml.nvmlDeviceGetMaxClockInfo(self._h, pynvml.NVML_CLOCK_SM)
+            self.ok = True
+        except Exception:
+            return self
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def _run(self):
+        nv = self._nv
+        while not self._stop.is_set():
+            try:
+                self.samples.append(nv.nvmlDeviceGetClockInfo(self._h, nv.NVML_CLOCK_SM))
+                self.reasons |= nv.nvmlDeviceGetCurrentClocksEventReasons(self._h)
+            except Exception:
+                pass
+            time.sleep(self.period)
+
+    def stop(self):
+        self._stop.set()
+        if self._t:
+            self._t.join()
+        if not self.ok:
+            return None
+        return {"sm_mhz": statistics.median(self.samples) if self.samples else None,
+                "sm_max_mhz": self.max_mhz, "samples": len(self.samples),
+                "reasons": [k for k, v in self.REASONS.items() if self.reasons & v],
+                "source": "NVML, read-only, every 10 ms during the timed region"}
+
+
+# ---------------------------------------------------------------------------
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def max_over_ranks(value, world, device=None):
+    """Max of a float over the ranks of the default process group (identity
+    for one rank).  Timing only; no data-path collective."""
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def fp64_gemm_peak(torch, n=8192, reps=3):
+    """Measured FP64 FMA rate (ops/s, one fused multiply-add = one op) of a
+    cuBLAS FP64 GEMM on this GPU, best of `reps`."""
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    torch.matmul(a, b)
+    best = 0.0
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        best = max(best, n ** 3 / (e0.elapsed_time(e1) * 1e-3))
+    del a, b
+    torch.cuda.empty_cache()
+    return best
+
+
+def cpu_baseline(inst, pt, budget_s=15.0):
+    """The CPU oracle as it stands on a bounded sample of the same workload:
+    all callbacks and the condensed-matrix rows of whole periods, one period
+    at a time, until about `budget_s` of CPU work; single thread."""
+    import oracle
+    o = oracle.Oracle(inst)
+    out = dict(f=np.empty(1), g=np.empty(o.n), c=np.empty(o.m), jv=np.empty(o.nnz_jac), hv=np.empty(o.nnz_hess))
+    done, t0 = 0, time.perf_counter()
+    while True:
+        t = done % inst.T
+        o.eval(pt.x, pt.lam, pt.sigma, t, t + 1, out=out)
+        o.kkt(pt.x, pt.lam, pt.sigma, pt.sigma_x, pt.dvec, pt.delta_w, t, t + 1)
+        done += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or done >= inst.T:
+            break
+    per_sweep = el / done * inst.T
+    return {"value": 1.0 / per_sweep, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{done} of {inst.T} periods (all callbacks + M rows of each period), "
+                      f"{el:.1f} s, extrapolated to the full horizon"}
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args, world, rank):
+    """The reference arm: the CPU oracle on this workload, timed on the host
+    cores; each step evaluates every callback and the M rows of one period
+    (a bounded sample), steps rotate over the periods."""
+    if rank != 0:
+        return 0
+    from paper_2405_14032_b300 import synth
+    import oracle
+    inst = synth.make_instance(WORKLOAD["seed"], WORKLOAD["n_bus"], WORKLOAD["n_branch"], WORKLOAD["n_gen"],
+                               WORKLOAD["n_load"], args.periods)
+    pt = synth.make_point(WORKLOAD["seed"], inst)
+    o = oracle.Oracle(inst)
+    out = dict(f=np.empty(1), g=np.empty(o.n), c=np.empty(o.m), jv=np.empty(o.nnz_jac), hv=np.empty(o.nnz_hess))
+
+    def step(k):
+        t = k % inst.T
+        o.eval(pt.x, pt.lam, pt.sigma, t, t + 1, out=out)
+        o.kkt(pt.x, pt.lam, pt.sigma, pt.sigma_x, pt.dvec, pt.delta_w, t, t + 1)
+
+    for k in range(args.warmup):
+        step(k)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        step(args.warmup + k)
+    el = time.perf_counter() - t0
+    sweeps = args.steps / inst.T
+    value = sweeps / el
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "mpopf_sweep_10k_bus_T168", **{k: v for k, v in WORKLOAD.items()},
+                       "n_periods": inst.T},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "per step: all callbacks + M rows of one period of the horizon"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    from paper_2405_14032_b300 import mpopf, synth
+
+    T = args.periods
+    inst = synth.make_instance(WORKLOAD["seed"], WORKLOAD["n_bus"], WORKLOAD["n_branch"], WORKLOAD["n_gen"],
+                               WORKLOAD["n_load"], T)
+    pt = synth.make_point(WORKLOAD["seed"], inst)
+    h = mpopf.Handle(inst)
+    n, m = h.n, h.m
+    D = inst.net.n_load
+    todev = lambda a: torch.as_tensor(a, dtype=torch.float64, device=dev)
+    # two perturbed iterates, alternated step by step
+    xs = [todev(pt.x), todev(synth.perturb(WORKLOAD["seed"], pt.x, 0))]
+    lam, sx, dv = todev(pt.lam), todev(pt.sigma_x), todev(pt.dvec)
+    out = h.new_outputs()
+    launches = h.launch_count()
+    alg = algorithmic_bytes(n, m, h.nnz_jac, h.nnz_hess, h.nnz_kkt, D, T)
+
+    fp64_peak = fp64_gemm_peak(torch) if rank == 0 else None
+
+    for k in range(args.warmup):
+        h.sweep(xs[k % 2], lam, pt.sigma, sx, dv, pt.delta_w, out=out)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local).start()
+    h.profile_start(args.steps * launches)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for k in range(args.steps):
+        h.sweep(xs[k % 2], lam, pt.sigma, sx, dv, pt.delta_w, out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    prof = h.profile_stop()
+    if world > 1:
+        torch.distributed.barrier()
+    ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(ms, world, dev)
+    ms_step = ms / args.steps
+    value = world * args.steps / (ms * 1e-3)
+
+    # dominant kernel and its roofline
+    top = max(prof, key=lambda k: prof[k][0])
+    top_ms = prof[top][0] / max(prof[top][1], 1)
+    roof = None
+    if top == "branch" and fp64_peak:
+        ops = FP64_OPS_PER_BRANCH_PERIOD * T * inst.net.n_branch
+        achieved = ops / (top_ms * 1e-3) / 1e9
+        peak = fp64_peak / 1e9
+        roof = {"bound": "alu", "kernel": "k_branch (branch x period)", "achieved": achieved, "peak": peak,
+                "unit": "Gop/s (FP64 fma/add/mul)", "frac": achieved / peak,
+                "traffic": ncu_traffic(), "ops_per_launch": ops, "avg_launch_ms": top_ms,
+                "peak_source": "measured: cuBLAS FP64 GEMM in this run (FMA count / time)"}
+    peaks = measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs")
+    gbs = alg / (ms_step * 1e-3) / 1e9
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"mpopf_sweep_10k_bus_T{T}", **WORKLOAD, "n_periods": T,
+                       "n": n, "m": m, "nnz_jac": h.nnz_jac, "nnz_hess": h.nnz_hess, "nnz_kkt": h.nnz_kkt,
+                       "parallelism": f"replicas{world}" if world > 1 else "single",
+                       "l2": "inputs + outputs 2.7 GB per step > 126 MB L2; no flush",
+                       "iterates": "two perturbed iterates alternated"},
+            "hbm": {"algorithmic_bytes_per_sweep": alg, "gbs": gbs, "peak_gbs": hbm_peak,
+                    "frac": gbs / hbm_peak if hbm_peak else None, "peak_source": "MEASURED_PEAKS.json"},
+            "roofline": roof,
+            "kernels_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+            "clocks": clk,
+            "gpu_launches": launches * args.steps}
+
+    # end to end through the C-ABI with host buffers
+    if rank == 0:
+        pin = lambda k: torch.empty(k, dtype=torch.float64, pin_memory=True).numpy()
+        hx, hl, hs, hd = pin(n), pin(m), pin(n), pin(m)
+        hx[:], hl[:], hs[:], hd[:] = pt.x, pt.lam, pt.sigma_x, pt.dvec
+        hout = dict(f=pin(1), grad=pin(n), c=pin(m), jv=pin(h.nnz_jac), hv=pin(h.nnz_hess), kv=pin(h.nnz_kkt))
+        stream = torch.cuda.current_stream()
+        h.sweep_host(hx, hl, pt.sigma, hs, hd, pt.delta_w, hout, stream=stream)
+        ke = max(1, args.e2e_steps)
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            h.sweep_host(hx, hl, pt.sigma, hs, hd, pt.delta_w, hout, stream=stream)
+        el = time.perf_counter() - t0
+        line["e2e"] = {"value": ke / el, "unit": UNIT, "h2d_bytes_per_step": 8 * (2 * n + 2 * m),
+                       "d2h_bytes_per_step": 8 * (1 + n + m + h.nnz_jac + h.nnz_hess + h.nnz_kkt),
+                       "steps": ke, "api": "mpopf_sweep_host (pinned host buffers, all inputs in, all outputs out)"}
+        if world == 1:
+            line["cpu_baseline"] = cpu_baseline(inst, pt)
+        print(json.dumps(line), flush=True)
+    h.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+    return run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

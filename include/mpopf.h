@@ -177,6 +177,17 @@ int mpopf_sweep_host(mpopf_handle *h, const double *x, const double *lam, double
 /* Number of kernel launches one mpopf_eval call with these output bits makes. */
 int mpopf_launch_count(const mpopf_handle *h, unsigned outputs);
 
+/* Per-kernel timing (instrumentation for benchmarks, not part of the paper's
+ * method).  mpopf_profile_start creates 2 * max_launches CUDA events; every
+ * later kernel launch of mpopf_eval (up to max_launches) is bracketed by an
+ * event pair on its stream.  mpopf_profile_stop synchronises on those events,
+ * writes the summed milliseconds and launch counts per kernel kind
+ * (ms_sum[4], launches[4]: 0 branch x period, 1 bus x period,
+ * 2 generator x period, 3 objective reduction; either may be NULL) and
+ * releases the events. */
+int mpopf_profile_start(mpopf_handle *h, int32_t max_launches);
+int mpopf_profile_stop(mpopf_handle *h, double *ms_sum, int32_t *launches);
+
 void mpopf_destroy(mpopf_handle *h);
 const char *mpopf_last_error(void);
 

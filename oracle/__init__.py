@@ -131,15 +131,19 @@ class Oracle:
         return rp
 
     # -- callbacks --------------------------------------------------------
-    def eval(self, x, lam, sigma, t0=0, t1=None, want=("f", "g", "c", "jv", "hv")):
-        """Outputs restricted to periods [t0, t1); entries outside stay NaN."""
+    def eval(self, x, lam, sigma, t0=0, t1=None, want=("f", "g", "c", "jv", "hv"), out=None):
+        """Outputs restricted to periods [t0, t1); entries outside stay NaN
+        (or keep whatever `out`, a dict of preallocated arrays, held)."""
         t1 = self.T if t1 is None else t1
         x, lam = _f64(x), _f64(lam)
-        f = np.full(1, np.nan) if "f" in want else None
-        g = np.full(self.n, np.nan) if "g" in want else None
-        c = np.full(self.m, np.nan) if "c" in want else None
-        jv = np.full(self.nnz_jac, np.nan) if "jv" in want else None
-        hv = np.full(self.nnz_hess, np.nan) if "hv" in want else None
+        if out is not None:
+            f, g, c, jv, hv = (out.get(k) for k in ("f", "g", "c", "jv", "hv"))
+        else:
+            f = np.full(1, np.nan) if "f" in want else None
+            g = np.full(self.n, np.nan) if "g" in want else None
+            c = np.full(self.m, np.nan) if "c" in want else None
+            jv = np.full(self.nnz_jac, np.nan) if "jv" in want else None
+            hv = np.full(self.nnz_hess, np.nan) if "hv" in want else None
         _lib.orc_eval(self.h, t0, t1, _ptr(x), _ptr(lam), float(sigma),
                       _ptr(f), _ptr(g), _ptr(c), _ptr(jv), _ptr(hv))
         return dict(f=None if f is None else float(f[0]), g=g, c=c, jv=jv, hv=hv)

@@ -146,6 +146,7 @@ struct Model {
   // incidence lists, ascending
   std::vector<std::vector<int64_t>> bus_gens, bus_arcs, bus_loads;
   int64_t n, m;
+  std::vector<int64_t> jrp;  // start of each row's J entries in the COO arrays [m + 1]
 };
 
 // Variables: kind-major, then period, then component.
@@ -185,6 +186,35 @@ void row_decode(const Model& M, int64_t i, int* kind, int64_t* t, int64_t* comp)
   if (i < 2 * M.T * M.N) { *kind = 8 + (int)(i / (M.T * M.N)); i %= (M.T * M.N); *t = i / M.N; *comp = i % M.N; return; }
   i -= 2 * M.T * M.N;
   *kind = 10; *t = 1 + i / M.G; *comp = i % M.G;
+}
+
+// Number of J entries of row i (its J order, see row_eval).
+int64_t row_len(const Model& M, int64_t i) {
+  int kind; int64_t t, comp;
+  row_decode(M, i, &kind, &t, &comp);
+  if (kind == 0) return 1;
+  if (kind >= 1 && kind <= 4) return 5;
+  if (kind >= 5 && kind <= 7) return 2;
+  if (kind == 8 || kind == 9) return 1 + (int64_t)M.bus_gens[comp].size() + (int64_t)M.bus_arcs[comp].size();
+  return 2;
+}
+
+// Rows of periods [t0, t1) as ascending index ranges [first, last).
+std::vector<std::pair<int64_t, int64_t>> window_rows(const Model& M, int64_t t0, int64_t t1) {
+  std::vector<std::pair<int64_t, int64_t>> r;
+  r.push_back({r_k0(M, t0), r_k0(M, t1)});
+  for (int k = 1; k <= 7; ++k) r.push_back({r_br(M, k, t0, 0), r_br(M, k, t1, 0)});
+  r.push_back({r_k8(M, t0, 0), r_k8(M, t1, 0)});
+  r.push_back({r_k9(M, t0, 0), r_k9(M, t1, 0)});
+  const int64_t a = std::max<int64_t>(t0, 1), b = std::max<int64_t>(t1, 1);
+  r.push_back({r_k10(M, a, 0), r_k10(M, b, 0)});
+  return r;
+}
+
+// Variables of periods [t0, t1) as ascending index ranges.
+std::vector<std::pair<int64_t, int64_t>> window_vars(const Model& M, int64_t t0, int64_t t1) {
+  return {{v_va(M, t0, 0), v_va(M, t1, 0)}, {v_vm(M, t0, 0), v_vm(M, t1, 0)}, {v_pg(M, t0, 0), v_pg(M, t1, 0)},
+          {v_qg(M, t0, 0), v_qg(M, t1, 0)}, {v_p(M, t0, 0), v_p(M, t1, 0)}, {v_q(M, t0, 0), v_q(M, t1, 0)}};
 }
 
 // pi-model terms of a branch (textbook: series admittance y = 1/(r + jx),
@@ -482,6 +512,8 @@ void* orc_new(const int64_t* dims /* N, L, G, D, ref, T */,
   for (int64_t d = 0; d < D; ++d) M->bus_loads[M->lbus[d]].push_back(d);
   M->n = T * (2 * N + 2 * G + 4 * L);
   M->m = T * (1 + 7 * L + 2 * N) + G * (T - 1);
+  M->jrp.assign(M->m + 1, 0);
+  for (int64_t i = 0; i < M->m; ++i) M->jrp[i + 1] = M->jrp[i] + row_len(*M, i);
   return M;
 }
 
@@ -490,17 +522,7 @@ void orc_free(void* h) { delete static_cast<Model*>(h); }
 // n, m, nnz of J, nnz of W (H).
 void orc_sizes(void* h, int64_t* out) {
   const Model& M = *static_cast<Model*>(h);
-  int64_t nnzj = 0;
-  std::vector<int64_t> cols; std::vector<double> vals; double cv;
-  std::vector<double> x(M.n, 1.0);
-  for (int64_t i = 0; i < M.m; ++i) {
-    int kind; int64_t t, comp;
-    row_decode(M, i, &kind, &t, &comp);
-    if (kind >= 1 && kind <= 4) { nnzj += 5; continue; }
-    row_eval<double>(M, x.data(), i, &cols, &vals, &cv);
-    nnzj += (int64_t)cols.size();
-  }
-  out[0] = M.n; out[1] = M.m; out[2] = nnzj;
+  out[0] = M.n; out[1] = M.m; out[2] = M.jrp[M.m];
   out[3] = M.T * (M.G + 10 * M.L + 4 * M.L + 2 * M.N);
 }
 
@@ -560,16 +582,7 @@ void orc_hess_pattern(void* h, int32_t* rows, int32_t* cols) {
 // Offsets of the J entries of each row (int64 [m + 1]) — positions in the COO arrays.
 void orc_jac_rowptr(void* h, int64_t* rp) {
   const Model& M = *static_cast<Model*>(h);
-  std::vector<double> x(M.n, 1.0);
-  std::vector<int64_t> c; std::vector<double> v; double cv;
-  rp[0] = 0;
-  for (int64_t i = 0; i < M.m; ++i) {
-    int kind; int64_t t, comp;
-    row_decode(M, i, &kind, &t, &comp);
-    int64_t len = 5;
-    if (!(kind >= 1 && kind <= 4)) { row_eval<double>(M, x.data(), i, &c, &v, &cv); len = (int64_t)c.size(); }
-    rp[i + 1] = rp[i] + len;
-  }
+  for (int64_t i = 0; i <= M.m; ++i) rp[i] = M.jrp[i];
 }
 
 // Objective, gradient, constraints, J values and W values restricted to the
@@ -590,25 +603,21 @@ void orc_eval(void* h, int64_t t0, int64_t t1, const double* x, const double* la
     *fobj = acc;
   }
   if (grad) {
-    for (int64_t j = 0; j < M.n; ++j) {
-      int kind; int64_t t, comp;
-      var_decode(M, j, &kind, &t, &comp);
-      if (t < t0 || t >= t1) continue;
-      grad[j] = kind == 2 ? std::fma(2.0 * M.c2[comp], x[j], M.c1[comp]) : 0.0;
-    }
+    for (const auto& rg : window_vars(M, t0, t1))
+      for (int64_t j = rg.first; j < rg.second; ++j) {
+        int kind; int64_t t, comp;
+        var_decode(M, j, &kind, &t, &comp);
+        grad[j] = kind == 2 ? std::fma(2.0 * M.c2[comp], x[j], M.c1[comp]) : 0.0;
+      }
   }
   if (c || jv) {
-    std::vector<int64_t> rp(M.m + 1);
-    if (jv) orc_jac_rowptr(h, rp.data());
     std::vector<int64_t> cols; std::vector<double> vals; double cv;
-    for (int64_t i = 0; i < M.m; ++i) {
-      int kind; int64_t t, comp;
-      row_decode(M, i, &kind, &t, &comp);
-      if (t < t0 || t >= t1) continue;
-      row_eval<double>(M, x, i, &cols, &vals, &cv);
-      if (c) c[i] = cv;
-      if (jv) for (size_t e = 0; e < vals.size(); ++e) jv[rp[i] + e] = vals[e];
-    }
+    for (const auto& rg : window_rows(M, t0, t1))
+      for (int64_t i = rg.first; i < rg.second; ++i) {
+        row_eval<double>(M, x, i, &cols, &vals, &cv);
+        if (c) c[i] = cv;
+        if (jv) for (size_t e = 0; e < vals.size(); ++e) jv[M.jrp[i] + e] = vals[e];
+      }
   }
   if (hv) {
     std::vector<HEnt> e;
@@ -637,26 +646,56 @@ void orc_eval(void* h, int64_t t0, int64_t t1, const double* x, const double* la
 // Condensed matrix rows for the variables of periods [t0, t1), in global row
 // order.  Returns the number of entries; fills rows_out (global row index of
 // each window row), rowlen, and (when cols/vals are not NULL) the sorted
-// columns and values of each row.
-int64_t orc_kkt(void* h, int64_t t0, int64_t t1, const double* x, const double* lam, double sigma,
-                const double* sigx, const double* dvec, double delta_w,
-                int64_t* rows_out, int64_t* rowlen, int32_t* cols, double* vals) {
-  const Model& M = *static_cast<Model*>(h);
-  std::map<std::pair<int64_t, int64_t>, double> Mv;
-  // Window rows: every variable whose period is in [t0, t1), ascending.
+// columns and values of each row.  A call with cols == NULL computes and keeps
+// the result; the next call with the same arguments and cols != NULL copies it.
+}  // extern "C"
+
+namespace {
+struct KktCache {
+  const void* key[8] = {nullptr};
+  double dkey[2] = {0, 0};
+  std::vector<int64_t> rows, rowlen;
+  std::vector<int32_t> cols;
+  std::vector<double> vals;
+};
+thread_local KktCache g_kkt;
+
+// Local block of one element: (key, value) pairs, each key once, values
+// accumulated in the stated order.
+struct Local {
+  std::vector<std::pair<std::pair<int64_t, int64_t>, double>> e;
+  double& at(int64_t r, int64_t c) {
+    for (auto& kv : e)
+      if (kv.first.first == r && kv.first.second == c) return kv.second;
+    e.push_back({{r, c}, 0.0});
+    return e.back().second;
+  }
+};
+
+void kkt_compute(const Model& M, int64_t t0, int64_t t1, const double* x, const double* lam, double sigma,
+                 const double* sigx, const double* dvec, double delta_w, KktCache* out) {
+  // Contributions in the order they are added: diagonal terms first, then
+  // every element's local values in element order.  A stable sort by key
+  // keeps that order within each key; each key is then summed left to right.
+  std::vector<std::pair<std::pair<int64_t, int64_t>, double>> contrib;
   std::vector<int64_t> wrows;
-  for (int64_t j = 0; j < M.n; ++j)
-    if (var_in_window(M, j, t0, t1)) wrows.push_back(j);
-  // Diagonal term first.
-  for (int64_t j : wrows) Mv[{j, j}] = sigx[j] + delta_w;
+  for (const auto& rg : window_vars(M, t0, t1))
+    for (int64_t j = rg.first; j < rg.second; ++j) {
+      wrows.push_back(j);
+      contrib.push_back({{j, j}, sigx[j] + delta_w});
+    }
   std::vector<HEnt> we;
   std::vector<int64_t> erows, cols_i;
   std::vector<double> vals_i;
   double cv;
+  Local loc;
   for_elements(M, t0, t1, [&](int kind, int64_t t, int64_t comp) {
-    std::map<std::pair<int64_t, int64_t>, double> loc;
+    loc.e.clear();
     elem_w(M, x, lam, sigma, kind, t, comp, &we);
-    for (const HEnt& e : we) loc[{e.r, e.c}] += e.v;
+    for (const HEnt& e : we) {
+      double& slot = loc.at(e.r, e.c);
+      slot = slot + e.v;
+    }
     elem_rows(M, kind, t, comp, &erows);
     for (int64_t i : erows) {
       row_eval<double>(M, x, i, &cols_i, &vals_i, &cv);
@@ -664,32 +703,56 @@ int64_t orc_kkt(void* h, int64_t t0, int64_t t1, const double* x, const double* 
       for (size_t p = 0; p < cols_i.size(); ++p) {
         const double w = Di * vals_i[p];
         for (size_t q = 0; q <= p; ++q) {
-          const std::pair<int64_t, int64_t> key{std::max(cols_i[p], cols_i[q]), std::min(cols_i[p], cols_i[q])};
-          double& slot = loc[key];
+          double& slot = loc.at(std::max(cols_i[p], cols_i[q]), std::min(cols_i[p], cols_i[q]));
           slot = std::fma(w, vals_i[q], slot);
         }
       }
     }
-    for (const auto& kv : loc) {
-      if (!var_in_window(M, kv.first.first, t0, t1)) continue;
-      Mv[kv.first] += kv.second;
-    }
+    for (const auto& kv : loc.e)
+      if (var_in_window(M, kv.first.first, t0, t1)) contrib.push_back(kv);
   });
-  // Emit rows in global order.
-  int64_t total = 0;
-  size_t wi = 0;
-  int64_t cur = -1, len = 0;
-  auto flush = [&]() {
-    if (cur >= 0) { rows_out[wi] = cur; rowlen[wi] = len; ++wi; }
-  };
-  for (const auto& kv : Mv) {
-    if (kv.first.first != cur) { flush(); cur = kv.first.first; len = 0; }
-    if (cols) { cols[total] = (int32_t)kv.first.second; vals[total] = kv.second; }
-    ++len; ++total;
+  std::stable_sort(contrib.begin(), contrib.end(),
+                   [](const auto& a, const auto& b) { return a.first < b.first; });
+  out->rows.clear(); out->rowlen.clear(); out->cols.clear(); out->vals.clear();
+  size_t k = 0;
+  while (k < contrib.size()) {
+    const auto key = contrib[k].first;
+    double acc = 0.0;
+    for (; k < contrib.size() && contrib[k].first == key; ++k) acc = acc + contrib[k].second;
+    if (out->rows.empty() || out->rows.back() != key.first) {
+      out->rows.push_back(key.first);
+      out->rowlen.push_back(0);
+    }
+    out->rowlen.back() += 1;
+    out->cols.push_back((int32_t)key.second);
+    out->vals.push_back(acc);
   }
-  flush();
-  return total;
 }
+}  // namespace
+
+extern "C" int64_t orc_kkt(void* h, int64_t t0, int64_t t1, const double* x, const double* lam, double sigma,
+                           const double* sigx, const double* dvec, double delta_w,
+                           int64_t* rows_out, int64_t* rowlen, int32_t* cols, double* vals) {
+  const Model& M = *static_cast<Model*>(h);
+  KktCache& C = g_kkt;
+  const void* key[8] = {h, (const void*)(intptr_t)t0, (const void*)(intptr_t)t1, x, lam, sigx, dvec, nullptr};
+  const bool hit = cols && std::memcmp(C.key, key, sizeof key) == 0 && C.dkey[0] == sigma && C.dkey[1] == delta_w;
+  if (!hit) {
+    kkt_compute(M, t0, t1, x, lam, sigma, sigx, dvec, delta_w, &C);
+    std::memcpy(C.key, key, sizeof key);
+    C.dkey[0] = sigma;
+    C.dkey[1] = delta_w;
+  }
+  for (size_t r = 0; r < C.rows.size(); ++r) { rows_out[r] = C.rows[r]; rowlen[r] = C.rowlen[r]; }
+  if (cols) {
+    std::memcpy(cols, C.cols.data(), C.cols.size() * sizeof(int32_t));
+    std::memcpy(vals, C.vals.data(), C.vals.size() * sizeof(double));
+    std::memset(C.key, 0, sizeof C.key);
+  }
+  return (int64_t)C.cols.size();
+}
+
+extern "C" {
 
 // Number of window rows of orc_kkt.
 int64_t orc_window_rows(void* h, int64_t t0, int64_t t1) {
@@ -703,7 +766,8 @@ int64_t orc_window_rows(void* h, int64_t t0, int64_t t1) {
 // (dc/dPd)^T y = -y at the P-balance row of the load's bus (Q likewise).
 void orc_vjp(void* h, int64_t t0, int64_t t1, const double* x, const double* y, double* gx, double* gpd, double* gqd) {
   const Model& M = *static_cast<Model*>(h);
-  for (int64_t j = 0; j < M.n; ++j) if (var_in_window(M, j, t0, t1)) gx[j] = 0.0;
+  for (const auto& rg : window_vars(M, t0, t1))
+    for (int64_t j = rg.first; j < rg.second; ++j) gx[j] = 0.0;
   std::vector<int64_t> erows, cols_i;
   std::vector<double> vals_i;
   double cv;
@@ -733,7 +797,8 @@ void orc_vjp(void* h, int64_t t0, int64_t t1, const double* x, const double* y, 
 void orc_hvp(void* h, int64_t t0, int64_t t1, const double* x, const double* lam, double sigma, const double* v,
              double* hv) {
   const Model& M = *static_cast<Model*>(h);
-  for (int64_t j = 0; j < M.n; ++j) if (var_in_window(M, j, t0, t1)) hv[j] = 0.0;
+  for (const auto& rg : window_vars(M, t0, t1))
+    for (int64_t j = rg.first; j < rg.second; ++j) hv[j] = 0.0;
   std::vector<HEnt> we;
   for_elements(M, t0, t1, [&](int kind, int64_t t, int64_t comp) {
     std::map<int64_t, double> loc;
@@ -755,15 +820,13 @@ void orc_hvp(void* h, int64_t t0, int64_t t1, const double* x, const double* lam
 void orc_jvp(void* h, int64_t t0, int64_t t1, const double* x, const double* v, double* out) {
   const Model& M = *static_cast<Model*>(h);
   std::vector<int64_t> cols; std::vector<double> vals; double cv;
-  for (int64_t i = 0; i < M.m; ++i) {
-    int kind; int64_t t, comp;
-    row_decode(M, i, &kind, &t, &comp);
-    if (t < t0 || t >= t1) continue;
-    row_eval<double>(M, x, i, &cols, &vals, &cv);
-    double acc = 0.0;
-    for (size_t p = 0; p < cols.size(); ++p) acc = std::fma(vals[p], v[cols[p]], acc);
-    out[i] = acc;
-  }
+  for (const auto& rg : window_rows(M, t0, t1))
+    for (int64_t i = rg.first; i < rg.second; ++i) {
+      row_eval<double>(M, x, i, &cols, &vals, &cv);
+      double acc = 0.0;
+      for (size_t p = 0; p < cols.size(); ++p) acc = std::fma(vals[p], v[cols[p]], acc);
+      out[i] = acc;
+    }
 }
 
 // The canonical sin/cos (for pins against the C library).

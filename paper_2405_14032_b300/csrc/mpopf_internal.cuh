@@ -62,10 +62,18 @@ struct Dev {
 
 inline constexpr int kBlock = 256;
 
+// Optional per-kernel CUDA-event timing of the evaluation launches.
+enum { KIND_BRANCH = 0, KIND_BUS = 1, KIND_GEN = 2, KIND_FSUM = 3, KIND_COUNT = 4 };
+struct Prof {
+  int cap = 0, next = 0;
+  cudaEvent_t *ev = nullptr;  // [2 cap]
+  int *kind = nullptr;        // [cap]
+};
+
 // Kernel launchers (mpopf_kernels.cu).
 cudaError_t launch_eval(const Dev &d, unsigned outputs, const double *x, const double *lam, double sigma,
                         const double *sx, const double *dv, double dw, double *f, double *grad, double *c,
-                        double *jv, double *hv, double *kv, cudaStream_t s);
+                        double *jv, double *hv, double *kv, cudaStream_t s, Prof *prof);
 int eval_launch_count(const Dev &d, unsigned outputs);
 // Pattern expansion (mpopf_setup.cu).
 cudaError_t launch_patterns(const Dev &d, int32_t *jrow, int32_t *jcol, int32_t *hrow, int32_t *hcol,
@@ -87,4 +95,5 @@ struct mpopf_handle {
   // staging for mpopf_sweep_host (allocated on first use)
   double *stage;
   size_t stage_bytes;
+  mpopf::Prof prof;
 };

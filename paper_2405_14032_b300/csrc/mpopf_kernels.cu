@@ -465,19 +465,45 @@ __global__ void __launch_bounds__(1024) k_fsum(const double *__restrict__ part, 
 
 unsigned grid_for(int64_t count) { return (unsigned)((count + kBlock - 1) / kBlock); }
 
+// Records a CUDA event pair around one launch when profiling is on.
+struct Timed {
+  Prof *p;
+  cudaStream_t s;
+  int slot;
+  Timed(Prof *prof, cudaStream_t st, int kind) : p(prof), s(st), slot(-1) {
+    if (p && p->next < p->cap) {
+      slot = p->next++;
+      p->kind[slot] = kind;
+      cudaEventRecord(p->ev[2 * slot], s);
+    }
+  }
+  ~Timed() {
+    if (slot >= 0) cudaEventRecord(p->ev[2 * slot + 1], s);
+  }
+};
+
 template <unsigned MASK>
 void launch_all(const Dev &d, unsigned rt, const double *x, const double *lam, double sigma, const double *sx,
                 const double *dv, double dw, double *f, double *grad, double *c, double *jv, double *hv, double *kv,
-                cudaStream_t s) {
+                cudaStream_t s, Prof *prof) {
   const unsigned mk = MASK ? MASK : rt;
   const unsigned rest = MPOPF_OUT_GRAD | MPOPF_OUT_CONS | MPOPF_OUT_JAC | MPOPF_OUT_HESS | MPOPF_OUT_KKT;
-  if ((mk & rest) && d.L > 0)
+  if ((mk & rest) && d.L > 0) {
+    Timed tm(prof, s, KIND_BRANCH);
     k_branch<MASK><<<grid_for((int64_t)d.T * d.L), kBlock, 0, s>>>(d, rt, x, lam, sx, dv, dw, grad, c, jv, hv, kv);
-  if (mk & rest)
+  }
+  if (mk & rest) {
+    Timed tm(prof, s, KIND_BUS);
     k_bus<MASK><<<grid_for((int64_t)d.T * d.N), kBlock, 0, s>>>(d, rt, x, lam, sx, dv, dw, grad, c, jv, hv, kv);
-  if (mk && d.G > 0)
+  }
+  if (mk && d.G > 0) {
+    Timed tm(prof, s, KIND_GEN);
     k_gen<MASK><<<grid_for((int64_t)d.T * d.G), kBlock, 0, s>>>(d, rt, x, sigma, sx, dv, dw, grad, c, jv, hv, kv);
-  if (mk & MPOPF_OUT_OBJ) k_fsum<<<1, 1024, 0, s>>>(d.fpart, d.G > 0 ? d.fpart_n : 0, f);
+  }
+  if (mk & MPOPF_OUT_OBJ) {
+    Timed tm(prof, s, KIND_FSUM);
+    k_fsum<<<1, 1024, 0, s>>>(d.fpart, d.G > 0 ? d.fpart_n : 0, f);
+  }
 }
 
 }  // namespace
@@ -494,16 +520,16 @@ int eval_launch_count(const Dev &d, unsigned mk) {
 
 cudaError_t launch_eval(const Dev &d, unsigned mk, const double *x, const double *lam, double sigma,
                         const double *sx, const double *dv, double dw, double *f, double *grad, double *c,
-                        double *jv, double *hv, double *kv, cudaStream_t s) {
+                        double *jv, double *hv, double *kv, cudaStream_t s, Prof *prof) {
   switch (mk) {
-    case MPOPF_OUT_OBJ: launch_all<MPOPF_OUT_OBJ>(d, mk, x, lam, sigma, sx, dv, dw, f, grad, c, jv, hv, kv, s); break;
-    case MPOPF_OUT_GRAD: launch_all<MPOPF_OUT_GRAD>(d, mk, x, lam, sigma, sx, dv, dw, f, grad, c, jv, hv, kv, s); break;
-    case MPOPF_OUT_CONS: launch_all<MPOPF_OUT_CONS>(d, mk, x, lam, sigma, sx, dv, dw, f, grad, c, jv, hv, kv, s); break;
-    case MPOPF_OUT_JAC: launch_all<MPOPF_OUT_JAC>(d, mk, x, lam, sigma, sx, dv, dw, f, grad, c, jv, hv, kv, s); break;
-    case MPOPF_OUT_HESS: launch_all<MPOPF_OUT_HESS>(d, mk, x, lam, sigma, sx, dv, dw, f, grad, c, jv, hv, kv, s); break;
-    case MPOPF_OUT_KKT: launch_all<MPOPF_OUT_KKT>(d, mk, x, lam, sigma, sx, dv, dw, f, grad, c, jv, hv, kv, s); break;
-    case MPOPF_OUT_ALL: launch_all<MPOPF_OUT_ALL>(d, mk, x, lam, sigma, sx, dv, dw, f, grad, c, jv, hv, kv, s); break;
-    default: launch_all<0>(d, mk, x, lam, sigma, sx, dv, dw, f, grad, c, jv, hv, kv, s); break;
+    case MPOPF_OUT_OBJ: launch_all<MPOPF_OUT_OBJ>(d, mk, x, lam, sigma, sx, dv, dw, f, grad, c, jv, hv, kv, s, prof); break;
+    case MPOPF_OUT_GRAD: launch_all<MPOPF_OUT_GRAD>(d, mk, x, lam, sigma, sx, dv, dw, f, grad, c, jv, hv, kv, s, prof); break;
+    case MPOPF_OUT_CONS: launch_all<MPOPF_OUT_CONS>(d, mk, x, lam, sigma, sx, dv, dw, f, grad, c, jv, hv, kv, s, prof); break;
+    case MPOPF_OUT_JAC: launch_all<MPOPF_OUT_JAC>(d, mk, x, lam, sigma, sx, dv, dw, f, grad, c, jv, hv, kv, s, prof); break;
+    case MPOPF_OUT_HESS: launch_all<MPOPF_OUT_HESS>(d, mk, x, lam, sigma, sx, dv, dw, f, grad, c, jv, hv, kv, s, prof); break;
+    case MPOPF_OUT_KKT: launch_all<MPOPF_OUT_KKT>(d, mk, x, lam, sigma, sx, dv, dw, f, grad, c, jv, hv, kv, s, prof); break;
+    case MPOPF_OUT_ALL: launch_all<MPOPF_OUT_ALL>(d, mk, x, lam, sigma, sx, dv, dw, f, grad, c, jv, hv, kv, s, prof); break;
+    default: launch_all<0>(d, mk, x, lam, sigma, sx, dv, dw, f, grad, c, jv, hv, kv, s, prof); break;
   }
   return cudaGetLastError();
 }
@@ -542,7 +568,7 @@ int mpopf_eval(mpopf_handle *h, unsigned outputs, const double *x, const double 
   if ((mk & (MPOPF_OUT_HESS | MPOPF_OUT_KKT)) && !lam) return fail(MPOPF_ERR_ARG, "mpopf_eval: NULL lam");
   if ((mk & MPOPF_OUT_KKT) && (!sigma_x || !dvec)) return fail(MPOPF_ERR_ARG, "mpopf_eval: NULL sigma_x or dvec");
   const cudaError_t e = launch_eval(h->d, mk, x, lam, sigma, sigma_x, dvec, delta_w, f, grad, c, jv, hv, kv,
-                                    static_cast<cudaStream_t>(stream));
+                                    static_cast<cudaStream_t>(stream), h->prof.cap ? &h->prof : nullptr);
   if (e != cudaSuccess) return fail(MPOPF_ERR_CUDA, std::string("mpopf_eval: ") + cudaGetErrorString(e));
   return MPOPF_OK;
 }
@@ -617,6 +643,47 @@ int mpopf_sweep_host(mpopf_handle *h, const double *x, const double *lam, double
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return fail(MPOPF_ERR_CUDA, std::string("mpopf_sweep_host: ") + cudaGetErrorString(e));
   return MPOPF_OK;
+}
+
+int mpopf_profile_start(mpopf_handle *h, int32_t max_launches) {
+  if (!h || max_launches < 1) return fail(MPOPF_ERR_ARG, "mpopf_profile_start: bad argument");
+  if (h->prof.cap) return fail(MPOPF_ERR_ARG, "mpopf_profile_start: already profiling");
+  Prof &p = h->prof;
+  p.ev = new cudaEvent_t[2 * (size_t)max_launches];
+  p.kind = new int[max_launches];
+  for (int i = 0; i < 2 * max_launches; ++i) {
+    const cudaError_t e = cudaEventCreate(&p.ev[i]);
+    if (e != cudaSuccess) {
+      for (int k = 0; k < i; ++k) cudaEventDestroy(p.ev[k]);
+      delete[] p.ev;
+      delete[] p.kind;
+      p = Prof();
+      return fail(MPOPF_ERR_CUDA, std::string("mpopf_profile_start: ") + cudaGetErrorString(e));
+    }
+  }
+  p.cap = max_launches;
+  p.next = 0;
+  return MPOPF_OK;
+}
+
+int mpopf_profile_stop(mpopf_handle *h, double *ms_sum, int32_t *launches) {
+  if (!h || !h->prof.cap) return fail(MPOPF_ERR_ARG, "mpopf_profile_stop: not profiling");
+  Prof &p = h->prof;
+  int rc = MPOPF_OK;
+  for (int k = 0; k < KIND_COUNT; ++k) { if (ms_sum) ms_sum[k] = 0.0; if (launches) launches[k] = 0; }
+  for (int i = 0; i < p.next; ++i) {
+    float ms = 0.f;
+    cudaError_t e = cudaEventSynchronize(p.ev[2 * i + 1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, p.ev[2 * i], p.ev[2 * i + 1]);
+    if (e != cudaSuccess) { rc = fail(MPOPF_ERR_CUDA, std::string("mpopf_profile_stop: ") + cudaGetErrorString(e)); break; }
+    if (ms_sum) ms_sum[p.kind[i]] += ms;
+    if (launches) launches[p.kind[i]] += 1;
+  }
+  for (int i = 0; i < 2 * p.cap; ++i) cudaEventDestroy(p.ev[i]);
+  delete[] p.ev;
+  delete[] p.kind;
+  p = Prof();
+  return rc;
 }
 
 }  // extern "C"

@@ -67,6 +67,8 @@ def lib():
             "mpopf_sweep": (ctypes.c_int, [_P, _P, _P, _D, _P, _P, _D, _P, _P, _P, _P, _P, _P, _P]),
             "mpopf_sweep_host": (ctypes.c_int, [_P, _P, _P, _D, _P, _P, _D, _P, _P, _P, _P, _P, _P, _P]),
             "mpopf_launch_count": (ctypes.c_int, [_P, _U]),
+            "mpopf_profile_start": (ctypes.c_int, [_P, _I32]),
+            "mpopf_profile_stop": (ctypes.c_int, [_P, _P, _P]),
             "mpopf_destroy": (None, [_P]),
             "mpopf_last_error": (ctypes.c_char_p, []),
         }
@@ -82,7 +84,8 @@ def exported_symbols():
     """Names the header declares (for the load/export check)."""
     return ["mpopf_setup", "mpopf_get_pattern", "mpopf_set_loads", "mpopf_eval", "mpopf_eval_obj",
             "mpopf_eval_grad", "mpopf_eval_cons", "mpopf_eval_jac", "mpopf_eval_hess", "mpopf_assemble_kkt",
-            "mpopf_sweep", "mpopf_sweep_host", "mpopf_launch_count", "mpopf_destroy", "mpopf_last_error"]
+            "mpopf_sweep", "mpopf_sweep_host", "mpopf_launch_count", "mpopf_profile_start", "mpopf_profile_stop",
+            "mpopf_destroy", "mpopf_last_error"]
 
 
 class MpopfError(RuntimeError):
@@ -177,6 +180,18 @@ class Handle:
 
     def launch_count(self, outputs=OUT_ALL):
         return int(lib().mpopf_launch_count(self.h, outputs))
+
+    KERNEL_KINDS = ("branch", "bus", "gen", "fsum")
+
+    def profile_start(self, max_launches):
+        _check(lib().mpopf_profile_start(self.h, int(max_launches)), "mpopf_profile_start")
+
+    def profile_stop(self):
+        """{kind: (summed ms, launches)} of the launches since profile_start."""
+        ms = np.zeros(4)
+        cnt = np.zeros(4, np.int32)
+        _check(lib().mpopf_profile_stop(self.h, ms.ctypes.data, cnt.ctypes.data), "mpopf_profile_stop")
+        return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(self.KERNEL_KINDS)}
 
     # -- evaluation -----------------------------------------------------------
     def new_outputs(self, outputs=OUT_ALL):
