@@ -1,0 +1,83 @@
+// Condensed-matrix assembly that allocates nothing, for callers that cannot
+// call cudaMalloc.
+//
+// Who needs it: code that must not allocate device memory while it runs --
+// work recorded inside a CUDA stream capture (allocation is not a capturable
+// operation), deployments that reserve all device memory up front and forbid
+// allocation afterwards (real-time or embedded controllers, memory-pool
+// managed serving processes), and callers that share a handle across
+// processes or threads and must not grow its footprint.  The regular
+// mpopf_assemble_kkt uses the per-branch scratch buffer that mpopf_setup
+// allocates inside the handle; this variant uses instead a fixed array in the
+// library's own device image, so the call itself never allocates.
+//
+// The scratch is a file-scope __device__ array of kScratchDoubles doubles
+// (32 MiB).  Every GPU that loads the library holds it until the process
+// exits.  Its device address is looked up once per device with
+// cudaGetSymbolAddress (no allocation) on the first call made on that device;
+// make that first call outside any stream capture.  All calls on a device share
+// the array and it keeps the last call's contents; the kernels overwrite every
+// scratch record they later read, so nothing needs clearing, but two calls
+// that overlap on the GPU (different streams, no ordering) race on it.
+#include <mutex>
+#include <string>
+
+#include "mpopf_internal.cuh"
+
+namespace {
+
+constexpr long long kScratchDoubles = 4LL * 1024 * 1024;  // 32 MiB
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) double g_kkt_scratch[kScratchDoubles];
+
+std::mutex g_lock;
+void *g_scratch_addr[kMaxDevices] = {nullptr};
+
+// Device address of g_kkt_scratch on the current device (looked up once).
+cudaError_t scratch_address(double **out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> guard(g_lock);
+  if (!g_scratch_addr[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_kkt_scratch);
+    if (e != cudaSuccess) return e;
+    g_scratch_addr[dev] = p;
+  }
+  *out = static_cast<double *>(g_scratch_addr[dev]);
+  return cudaSuccess;
+}
+
+int fail(int code, const std::string &msg) {
+  mpopf::set_error(msg);
+  return code;
+}
+
+}  // namespace
+
+extern "C" int mpopf_assemble_kkt_noalloc(mpopf_handle *h, const double *x, const double *lam, double sigma,
+                                          const double *sigma_x, const double *dvec, double delta_w, double *kv,
+                                          void *stream) {
+  if (!h) return fail(MPOPF_ERR_ARG, "mpopf_assemble_kkt_noalloc: NULL handle");
+  if (!x || !lam || !sigma_x || !dvec || !kv) return fail(MPOPF_ERR_ARG, "mpopf_assemble_kkt_noalloc: NULL array");
+  const long long need = 6LL * h->d.T * h->d.L;
+  if (need > kScratchDoubles)
+    return fail(MPOPF_ERR_SIZE, "mpopf_assemble_kkt_noalloc: needs " + std::to_string(need) +
+                                    " scratch doubles (6 per branch x period), over the static maximum of " +
+                                    std::to_string(kScratchDoubles) + " (T x L <= 699050)");
+  double *scratch = nullptr;
+  cudaError_t e = scratch_address(&scratch);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(MPOPF_ERR_CUDA, std::string("mpopf_assemble_kkt_noalloc: scratch lookup: ") + cudaGetErrorString(e));
+  }
+  mpopf::Dev d = h->d;
+  d.S = scratch;
+  e = mpopf::launch_eval(d, MPOPF_OUT_KKT, x, lam, sigma, sigma_x, dvec, delta_w, nullptr, nullptr, nullptr,
+                         nullptr, nullptr, kv, static_cast<cudaStream_t>(stream), nullptr);
+  if (e != cudaSuccess) return fail(MPOPF_ERR_CUDA, std::string("mpopf_assemble_kkt_noalloc: ") + cudaGetErrorString(e));
+  return MPOPF_OK;
+}

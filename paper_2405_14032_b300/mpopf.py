@@ -66,6 +66,7 @@ def lib():
             "mpopf_assemble_kkt": (ctypes.c_int, [_P, _P, _P, _D, _P, _P, _D, _P, _P]),
             "mpopf_sweep": (ctypes.c_int, [_P, _P, _P, _D, _P, _P, _D, _P, _P, _P, _P, _P, _P, _P]),
             "mpopf_sweep_host": (ctypes.c_int, [_P, _P, _P, _D, _P, _P, _D, _P, _P, _P, _P, _P, _P, _P]),
+            "mpopf_assemble_kkt_noalloc": (ctypes.c_int, [_P, _P, _P, _D, _P, _P, _D, _P, _P]),
             "mpopf_launch_count": (ctypes.c_int, [_P, _U]),
             "mpopf_profile_start": (ctypes.c_int, [_P, _I32]),
             "mpopf_profile_stop": (ctypes.c_int, [_P, _P, _P]),
@@ -84,7 +85,7 @@ def exported_symbols():
     """Names the header declares (for the load/export check)."""
     return ["mpopf_setup", "mpopf_get_pattern", "mpopf_set_loads", "mpopf_eval", "mpopf_eval_obj",
             "mpopf_eval_grad", "mpopf_eval_cons", "mpopf_eval_jac", "mpopf_eval_hess", "mpopf_assemble_kkt",
-            "mpopf_sweep", "mpopf_sweep_host", "mpopf_launch_count", "mpopf_profile_start", "mpopf_profile_stop",
+            "mpopf_sweep", "mpopf_sweep_host", "mpopf_assemble_kkt_noalloc", "mpopf_launch_count", "mpopf_profile_start", "mpopf_profile_stop",
             "mpopf_destroy", "mpopf_last_error"]
 
 
@@ -225,6 +226,16 @@ class Handle:
                                       _ptr(out["jv"]), _ptr(out["hv"]), _ptr(out["kv"]), _stream_ptr(stream)),
                "mpopf_sweep_host")
         return out
+
+    def assemble_kkt_noalloc(self, x, lam, sigma, sigma_x, dvec, delta_w, kv, stream=None):
+        """M values into the caller's `kv` with no device allocation by the
+        call: the scratch is a fixed array inside the library (for callers
+        that cannot allocate while they run, e.g. inside a stream capture).
+        Raises MpopfError (code -2) when 6 T L exceeds that array."""
+        _check(lib().mpopf_assemble_kkt_noalloc(self.h, _ptr(x), _ptr(lam), float(sigma), _ptr(sigma_x),
+                                                _ptr(dvec), float(delta_w), _ptr(kv), _stream_ptr(stream)),
+               "mpopf_assemble_kkt_noalloc")
+        return kv
 
     def set_loads(self, pd, qd, stream=None):
         _check(lib().mpopf_set_loads(self.h, _ptr(pd), _ptr(qd), _stream_ptr(stream)), "mpopf_set_loads")
