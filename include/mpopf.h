@@ -185,7 +185,7 @@ int mpopf_launch_count(const mpopf_handle *h, unsigned outputs);
  * Same inputs, output and values as mpopf_assemble_kkt; the per-branch scratch
  * it needs lives in a fixed 32 MiB array inside the library's device image
  * (held by every GPU that loads the library until exit) instead of the
- * handle.  Limit: 6 T L <= 4 Mi doubles (T x L <= 699050 branch-periods);
+ * handle.  Limit: 12 T L <= 4 Mi doubles (T x L <= 349525 branch-periods);
  * larger problems return MPOPF_ERR_SIZE.  The first call on each device looks
  * up the array's address (cudaGetSymbolAddress, no allocation): make it
  * outside any stream capture.  All calls on a device share the array, which

@@ -41,7 +41,8 @@ struct Dev {
   const int32_t *bgen_ptr, *bgen_idx;    // generators of a bus, ascending
   const int32_t *barc_ptr, *barc_idx;    // arcs of a bus, ascending arc index
   const int32_t *bload_ptr, *bload_idx;  // loads of a bus, ascending
-  const int32_t *inc_ptr, *inc_code;     // incident branches by branch index: code = 2 l + end (0 from, 1 to)
+  const int32_t *inc_ptr, *inc_code;     // slots of the bus at position p of bus_order: [inc_ptr[p], inc_ptr[p+1]),
+                                         // in branch order; code = 2 l + end (0 from, 1 to)
   const int32_t *nbr_ptr, *nbr_bus, *nbr_grp;  // distinct neighbours ascending; nbr_grp[k]..[k+1] into grp_code
   const int32_t *grp_code;               // branches joining the bus to a neighbour, ascending: 2 l + end
   const int32_t *bus_nd, *bus_ndlt;      // distinct neighbours; those with a smaller index
@@ -53,14 +54,25 @@ struct Dev {
   const int32_t *mo_va, *mo_vm, *mo_pg0, *mo_pg1, *mo_qg, *mo_p, *mo_q;
   // loads [T][D]
   const double *pd, *qd;
-  // scratch: per branch-period the 6 distinct values of the branch element's
-  // bus-variable block of M, [T][L][6]; objective partial sums
+  // Incidence slots: slot of branch l's from / to end in its bus's incident
+  // list (branch order), [2][L]; per slot: neighbour position in the bus's
+  // distinct-neighbour list (bits 0..27), group leader (bit 30: first branch to
+  // that neighbour in branch order), neighbour index below the bus's (bit 29);
+  // next slot of the same group or -1.
+  const int32_t *br_slot, *slot_info, *slot_next;
+  // Buses in the order the bus kernel processes them, and each bus's
+  // incidence slots in ascending arc index (from ends, then to ends).
+  const int32_t *bus_order, *arc_perm;
+  // scratch: one record per incidence slot and period, [T][2L][kRec]:
+  // (S_dd, S_vd, S_vv, S_vtvf, p_arc, q_arc) -- the branch element's local
+  // values seen from that end plus the arc's flow variables; objective partials
   double *S;
   double *fpart;
   int32_t fpart_n;
 };
 
 inline constexpr int kBlock = 256;
+inline constexpr int kRec = 6;  // doubles per incidence record
 
 // Optional per-kernel CUDA-event timing of the evaluation launches.
 enum { KIND_BRANCH = 0, KIND_BUS = 1, KIND_GEN = 2, KIND_FSUM = 3, KIND_COUNT = 4 };

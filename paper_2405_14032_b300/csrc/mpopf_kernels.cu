@@ -71,11 +71,35 @@ __device__ __forceinline__ void sincos_cw(double x, double *sn, double *cs) {
 template <unsigned MASK>
 __device__ __forceinline__ unsigned eff(unsigned rt) { return MASK ? MASK : rt; }
 
-// ---------------------------------------------------------------------------
-// Branch x period.
-// ---------------------------------------------------------------------------
+// -x by flipping the sign bit with an integer operation (exact; keeps the
+// scarce FP64 pipe free).
+__device__ __forceinline__ double negx(double x) {
+  return __hiloint2double(__double2hiint(x) ^ (int)0x80000000, __double2loint(x));
+}
+
+// 2x exactly with integer operations only (no branch, no FP64 instruction):
+// exponent + 1 for normal results, a one-bit left shift of the magnitude for
+// zero and subnormal inputs, infinity on overflow, Inf and NaN unchanged.
+__device__ __forceinline__ double twice(double x) {
+  const int hi = __double2hiint(x), lo = __double2loint(x);
+  const unsigned e = ((unsigned)hi >> 20) & 0x7ffu;
+  const int sign = hi & (int)0x80000000;
+  int rh = hi + 0x100000, rl = lo;
+  const int sub_h = sign | ((hi & 0x7fffffff) << 1) | (int)((unsigned)lo >> 31);
+  rh = (e == 0u) ? sub_h : rh;
+  rl = (e == 0u) ? (int)((unsigned)lo << 1) : rl;
+  rh = (e == 2046u) ? (sign | 0x7ff00000) : rh;
+  rl = (e == 2046u) ? 0 : rl;
+  rh = (e == 2047u) ? hi : rh;
+  rl = (e == 2047u) ? lo : rl;
+  return __hiloint2double(rh, rl);
+}
+
 template <unsigned MASK>
-__global__ void __launch_bounds__(kBlock) k_branch(Dev d, unsigned rt, const double *__restrict__ x,
+#ifndef MPOPF_BRANCH_MINB
+#define MPOPF_BRANCH_MINB 3
+#endif
+__global__ void __launch_bounds__(kBlock, MPOPF_BRANCH_MINB) k_branch(Dev d, unsigned rt, const double *__restrict__ x,
                                                    const double *__restrict__ lam, const double *__restrict__ sx,
                                                    const double *__restrict__ dv, double dw,
                                                    double *__restrict__ grad, double *__restrict__ c,
@@ -144,19 +168,20 @@ __global__ void __launch_bounds__(kBlock) k_branch(Dev d, unsigned rt, const dou
   const double g2ff = __ldg(bc + (int64_t)BC_G2FF * L + l), b2ff = __ldg(bc + (int64_t)BC_B2FF * L + l);
   const double g2tt = __ldg(bc + (int64_t)BC_G2TT * L + l), b2tt = __ldg(bc + (int64_t)BC_B2TT * L + l);
   // J entries of the flow rows over (va_f, va_t, vm_f, vm_t): [a, -a, b, c].
-  const double a1 = uA2, b1 = -fma(g2ff, vf, vtA1), c1 = -(vf * A1);
-  const double a2 = -uA1, b2 = -fma(-b2ff, vf, vtA2), c2 = -(vf * A2);
-  const double a3 = -uA4, b3 = -(vt * A3), c3 = -fma(g2tt, vt, vfA3);
-  const double a4 = uA3, b4 = -(vt * A4), c4 = -fma(-b2tt, vt, vfA4);
-  const double jp6 = 2.0 * pf, jq6 = 2.0 * qf, jp7 = 2.0 * pt, jq7 = 2.0 * qt;
+  // (-fma(a, b, c) == fma(-a, b, -c) and -(a b) == (-a) b exactly.)
+  const double a1 = uA2, na1 = negx(uA2), b1 = fma(-g2ff, vf, -vtA1), c1 = (-vf) * A1;
+  const double a2 = negx(uA1), na2 = uA1, b2 = fma(b2ff, vf, -vtA2), c2 = (-vf) * A2;
+  const double a3 = negx(uA4), na3 = uA4, b3 = (-vt) * A3, c3 = fma(-g2tt, vt, -vfA3);
+  const double a4 = uA3, na4 = negx(uA3), b4 = (-vt) * A4, c4 = fma(b2tt, vt, -vfA4);
+  const double jp6 = twice(pf), jq6 = twice(qf), jp7 = twice(pt), jq7 = twice(qt);
 
   if (mk & MPOPF_OUT_JAC) {
     double *j1 = jv + d.T + (int64_t)tl * 5;
     const int64_t s5 = 5 * TL;
-    j1[0] = 1.0; j1[1] = a1; j1[2] = -a1; j1[3] = b1; j1[4] = c1;
-    j1[s5 + 0] = 1.0; j1[s5 + 1] = a2; j1[s5 + 2] = -a2; j1[s5 + 3] = b2; j1[s5 + 4] = c2;
-    j1[2 * s5 + 0] = 1.0; j1[2 * s5 + 1] = a3; j1[2 * s5 + 2] = -a3; j1[2 * s5 + 3] = b3; j1[2 * s5 + 4] = c3;
-    j1[3 * s5 + 0] = 1.0; j1[3 * s5 + 1] = a4; j1[3 * s5 + 2] = -a4; j1[3 * s5 + 3] = b4; j1[3 * s5 + 4] = c4;
+    j1[0] = 1.0; j1[1] = a1; j1[2] = na1; j1[3] = b1; j1[4] = c1;
+    j1[s5 + 0] = 1.0; j1[s5 + 1] = a2; j1[s5 + 2] = na2; j1[s5 + 3] = b2; j1[s5 + 4] = c2;
+    j1[2 * s5 + 0] = 1.0; j1[2 * s5 + 1] = a3; j1[2 * s5 + 2] = na3; j1[2 * s5 + 3] = b3; j1[2 * s5 + 4] = c3;
+    j1[3 * s5 + 0] = 1.0; j1[3 * s5 + 1] = a4; j1[3 * s5 + 2] = na4; j1[3 * s5 + 3] = b4; j1[3 * s5 + 4] = c4;
     double *j5 = jv + d.j_k5 + (int64_t)tl * 2;
     j5[0] = 1.0; j5[1] = -1.0;
     double *j6 = jv + d.j_k6 + (int64_t)tl * 2;
@@ -175,11 +200,12 @@ __global__ void __launch_bounds__(kBlock) k_branch(Dev d, unsigned rt, const dou
   const double Wdvf = vt * Bsum, Wdvt = vf * Bsum;
   const double Wvfvf = fma(l2, b2ff, -(l1 * g2ff));
   const double Wvtvt = fma(l4, b2tt, -(l3 * g2tt));
-  const double h6 = 2.0 * l6, h7 = 2.0 * l7;
+  const double h6 = twice(l6), h7 = twice(l7);
+  const double nAsum = negx(Asum);
   if (mk & MPOPF_OUT_HESS) {
     double *hb = hv + d.h_br + (int64_t)tl * 10;
-    hb[0] = Wdd; hb[1] = -Wdd; hb[2] = Wdd; hb[3] = Wdvf; hb[4] = -Wdvf;
-    hb[5] = Wvfvf; hb[6] = Wdvt; hb[7] = -Wdvt; hb[8] = -Asum; hb[9] = Wvtvt;
+    hb[0] = Wdd; hb[1] = negx(Wdd); hb[2] = Wdd; hb[3] = Wdvf; hb[4] = negx(Wdvf);
+    hb[5] = Wvfvf; hb[6] = Wdvt; hb[7] = negx(Wdvt); hb[8] = nAsum; hb[9] = Wvtvt;
     double *ht = hv + d.h_th + (int64_t)tl * 4;
     ht[0] = h6; ht[1] = h6; ht[2] = h7; ht[3] = h7;
   }
@@ -198,13 +224,19 @@ __global__ void __launch_bounds__(kBlock) k_branch(Dev d, unsigned rt, const dou
   const double Svfd = fma(w34, a4, fma(w33, a3, fma(w32, a2, fma(w31, a1, Wdvf))));
   const double Svtd = fma(w44, a4, fma(w43, a3, fma(w42, a2, fma(w41, a1, Wdvt))));
   const double Svfvf = fma(w34, b4, fma(w33, b3, fma(w32, b2, fma(w31, b1, Wvfvf))));
-  const double Svtvf = fma(w44, b4, fma(w43, b3, fma(w42, b2, fma(w41, b1, -Asum))));
+  const double Svtvf = fma(w44, b4, fma(w43, b3, fma(w42, b2, fma(w41, b1, nAsum))));
   const double Svtvt = fma(w44, c4, fma(w43, c3, fma(w42, c2, fma(w41, c1, Wvtvt))));
   {
-    double2 *sp = reinterpret_cast<double2 *>(d.S + (int64_t)tl * 6);
-    sp[0] = make_double2(Sdd, Svfd);
-    sp[1] = make_double2(Svtd, Svfvf);
-    sp[2] = make_double2(Svtvf, Svtvt);
+    // incidence records of both ends (bus-major, read by k_bus)
+    double *R = d.S + (int64_t)t * 2 * L * kRec;
+    double2 *recf = reinterpret_cast<double2 *>(R + (int64_t)__ldg(d.br_slot + l) * kRec);
+    recf[0] = make_double2(Sdd, Svfd);
+    recf[1] = make_double2(Svfvf, Svtvf);
+    recf[2] = make_double2(pf, qf);
+    double2 *rect = reinterpret_cast<double2 *>(R + (int64_t)__ldg(d.br_slot + L + l) * kRec);
+    rect[0] = make_double2(Sdd, negx(Svtd));
+    rect[1] = make_double2(Svtvt, Svtvf);
+    rect[2] = make_double2(pt, qt);
   }
   // Arc-variable diagonals and the (q, p) pair of each end.
   const double t6p = D6 * jp6, t6q = D6 * jq6, t7p = D7 * jp7, t7q = D7 * jq7;
@@ -240,13 +272,13 @@ __global__ void __launch_bounds__(kBlock) k_branch(Dev d, unsigned rt, const dou
     row[k] = diag;
   };
   const int64_t mp = d.m_p + (int64_t)t * d.mb_p, mq = d.m_q + (int64_t)t * d.mb_q;
-  arc_row(kv + mp + __ldg(d.mo_p + l), w11, -w11, w31 - w8f, w41, kf, -D8f, false, 0.0, rf, D8f,
+  arc_row(kv + mp + __ldg(d.mo_p + l), w11, negx(w11), w31 - w8f, w41, kf, negx(D8f), false, 0.0, rf, D8f,
           ((sxpf + dw) + Lpp_f) + D8f);
-  arc_row(kv + mq + __ldg(d.mo_q + l), w12, -w12, w32 - w9f, w42, kf, -D9f, true, Lqp_f, rf, D9f,
+  arc_row(kv + mq + __ldg(d.mo_q + l), w12, negx(w12), w32 - w9f, w42, kf, negx(D9f), true, Lqp_f, rf, D9f,
           ((sxqf + dw) + Lqq_f) + D9f);
-  arc_row(kv + mp + __ldg(d.mo_p + L + l), w13, -w13, w33, w43 - w8t, kt, -D8t, false, 0.0, rt2, D8t,
+  arc_row(kv + mp + __ldg(d.mo_p + L + l), w13, negx(w13), w33, w43 - w8t, kt, negx(D8t), false, 0.0, rt2, D8t,
           ((sxpt + dw) + Lpp_t) + D8t);
-  arc_row(kv + mq + __ldg(d.mo_q + L + l), w14, -w14, w34, w44 - w9t, kt, -D9t, true, Lqp_t, rt2, D9t,
+  arc_row(kv + mq + __ldg(d.mo_q + L + l), w14, negx(w14), w34, w44 - w9t, kt, negx(D9t), true, Lqp_t, rt2, D9t,
           ((sxqt + dw) + Lqq_t) + D9t);
 }
 
@@ -261,9 +293,12 @@ __global__ void __launch_bounds__(kBlock) k_bus(Dev d, unsigned rt, const double
                                                 double *__restrict__ hv, double *__restrict__ kv) {
   const unsigned mk = eff<MASK>(rt);
   const int32_t N = d.N;
-  const int32_t tn = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
-  if (tn >= d.T * N) return;
-  const int32_t t = tn / N, n = tn - t * N;
+  const int32_t idx = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+  if (idx >= d.T * N) return;
+  const int32_t t = idx / N;
+  const int32_t pos = idx - t * N;  // position in the processing order
+  const int32_t n = __ldg(d.bus_order + pos);
+  const int32_t tn = t * N + n;  // (period, bus) position of every per-bus array
   const int64_t tN = (int64_t)t * N;
   const int64_t L = d.L, G = d.G;
   if (mk & MPOPF_OUT_GRAD) {
@@ -277,8 +312,11 @@ __global__ void __launch_bounds__(kBlock) k_bus(Dev d, unsigned rt, const double
   if (!(mk & (MPOPF_OUT_CONS | MPOPF_OUT_JAC | MPOPF_OUT_HESS | MPOPF_OUT_KKT))) return;
   const double vm = __ldg(x + d.x_vm + tn);
   const int32_t g0 = __ldg(d.bgen_ptr + n), g1 = __ldg(d.bgen_ptr + n + 1);
-  const int32_t a0 = __ldg(d.barc_ptr + n), a1 = __ldg(d.barc_ptr + n + 1);
+  const int32_t s0 = __ldg(d.inc_ptr + pos), s1 = __ldg(d.inc_ptr + pos + 1);  // incidence slots
   const double m2gs = __ldg(d.bus_m2gs + n), p2bs = __ldg(d.bus_p2bs + n);
+  // Incidence records of this bus (written by k_branch when M is assembled).
+  const double *R = d.S + (int64_t)t * 2 * L * kRec;
+  const bool have_rec = mk & MPOPF_OUT_KKT;
   if (mk & MPOPF_OUT_CONS) {
     const double vm2 = vm * vm;
     double aP = 0.0, aQ = 0.0;
@@ -288,11 +326,21 @@ __global__ void __launch_bounds__(kBlock) k_bus(Dev d, unsigned rt, const double
       aP = aP + __ldg(x + pgb + g);
       aQ = aQ + __ldg(x + qgb + g);
     }
-    const int64_t pab = d.x_p + 2 * (int64_t)t * L, qab = d.x_q + 2 * (int64_t)t * L;
-    for (int32_t e = a0; e < a1; ++e) {
-      const int32_t a = __ldg(d.barc_idx + e);
-      aP = aP - __ldg(x + pab + a);
-      aQ = aQ - __ldg(x + qab + a);
+    // Arc flows in ascending arc index: from ends (branch order), then to ends.
+    if (have_rec) {
+      for (int32_t e = s0; e < s1; ++e) {
+        const int32_t q = __ldg(d.arc_perm + e);
+        const double2 pq = __ldg(reinterpret_cast<const double2 *>(R + (int64_t)q * kRec) + 2);
+        aP = aP - pq.x;
+        aQ = aQ - pq.y;
+      }
+    } else {
+      const int64_t pab = d.x_p + 2 * (int64_t)t * L, qab = d.x_q + 2 * (int64_t)t * L;
+      for (int32_t e = __ldg(d.barc_ptr + n); e < __ldg(d.barc_ptr + n + 1); ++e) {
+        const int32_t a = __ldg(d.barc_idx + e);
+        aP = aP - __ldg(x + pab + a);
+        aQ = aQ - __ldg(x + qab + a);
+      }
     }
     aP = fma(__ldg(d.bus_mgs + n), vm2, aP);
     aQ = fma(__ldg(d.bus_bs + n), vm2, aQ);
@@ -313,7 +361,7 @@ __global__ void __launch_bounds__(kBlock) k_bus(Dev d, unsigned rt, const double
     r9[0] = J9;
     int k = 1;
     for (int32_t e = g0; e < g1; ++e, ++k) { r8[k] = 1.0; r9[k] = 1.0; }
-    for (int32_t e = a0; e < a1; ++e, ++k) { r8[k] = -1.0; r9[k] = -1.0; }
+    for (int32_t e = s0; e < s1; ++e, ++k) { r8[k] = -1.0; r9[k] = -1.0; }
   }
   if (!(mk & (MPOPF_OUT_HESS | MPOPF_OUT_KKT))) return;
   const double WP = __ldg(lam + d.c_k8 + tn) * m2gs, WQ = __ldg(lam + d.c_k9 + tn) * p2bs;
@@ -326,51 +374,39 @@ __global__ void __launch_bounds__(kBlock) k_bus(Dev d, unsigned rt, const double
   const int32_t nd = __ldg(d.bus_nd + n), ndlt = __ldg(d.bus_ndlt + n);
   double *va_row = kv + d.m_va + (int64_t)t * d.mb_va + __ldg(d.mo_va + n);
   double *vm_row = kv + d.m_vm + (int64_t)t * d.mb_vm + __ldg(d.mo_vm + n);
-  const double *S = d.S + (int64_t)t * L * 6;
-  // Entries shared with each distinct neighbour (sum over joining branches in
-  // branch order).
-  int32_t k = 0;
-  for (int32_t q = __ldg(d.nbr_ptr + n); q < __ldg(d.nbr_ptr + n + 1); ++q, ++k) {
-    const int32_t nb = __ldg(d.nbr_bus + q);
-    double cdd = 0.0, cvd = 0.0, cvv = 0.0;
-    bool first = true;
-    for (int32_t e = __ldg(d.nbr_grp + q); e < __ldg(d.nbr_grp + q + 1); ++e) {
-      const int32_t code = __ldg(d.grp_code + e);
-      const double *s = S + (int64_t)(code >> 1) * 6;
-      const double vd = (code & 1) ? __ldg(s + 2) : -__ldg(s + 1);  // (vm_n, va_nb)
-      if (first) {
-        cdd = -__ldg(s + 0);
-        cvd = vd;
-        cvv = __ldg(s + 4);
-        first = false;
-      } else {
-        cdd = cdd - __ldg(s + 0);
-        cvd = cvd + vd;
-        cvv = cvv + __ldg(s + 4);
-      }
-    }
-    if (nb < n) {
-      va_row[k] = cdd;
-      vm_row[nd + 1 + k] = cvv;
-    }
-    vm_row[k < ndlt ? k : k + 1] = cvd;
-  }
-  // Diagonal entries: diagonal term, reference element, incident branches in
-  // branch order, bus element.
+  // One pass over the incidence records in branch order: diagonal sums
+  // (diagonal term, reference element, branches, then the bus element) and,
+  // at the first branch to each neighbour, that neighbour's entries (summed
+  // over parallel branches in branch order).
   double Ddd = __ldg(sx + tn) + dw;
   if (n == d.ref) Ddd = Ddd + __ldg(dv + t);
   double Dvv = __ldg(sx + d.x_vm + tn) + dw;
   double Dvd = 0.0;
-  bool first = true;
-  for (int32_t e = __ldg(d.inc_ptr + n); e < __ldg(d.inc_ptr + n + 1); ++e) {
-    const int32_t code = __ldg(d.inc_code + e);
-    const double *s = S + (int64_t)(code >> 1) * 6;
-    const bool at_to = code & 1;
-    const double vd = at_to ? -__ldg(s + 2) : __ldg(s + 1);
-    Ddd = Ddd + __ldg(s + 0);
-    Dvv = Dvv + (at_to ? __ldg(s + 5) : __ldg(s + 3));
-    if (first) { Dvd = vd; first = false; }
-    else Dvd = Dvd + vd;
+  for (int32_t q = s0; q < s1; ++q) {
+    const double2 *rp = reinterpret_cast<const double2 *>(R + (int64_t)q * kRec);
+    const double2 a = __ldg(rp), b = __ldg(rp + 1);  // (S_dd, S_vd), (S_vv, S_vtvf)
+    Ddd = Ddd + a.x;
+    Dvv = Dvv + b.x;
+    Dvd = (q == s0) ? a.y : Dvd + a.y;
+    const int32_t info = __ldg(d.slot_info + q);
+    if (info & (1 << 30)) {
+      double cdd = negx(a.x), cvd = negx(a.y), cvv = b.y;
+      for (int32_t o = __ldg(d.slot_next + q); o >= 0; o = __ldg(d.slot_next + o)) {
+        const double2 *ro = reinterpret_cast<const double2 *>(R + (int64_t)o * kRec);
+        const double2 a2 = __ldg(ro), b2 = __ldg(ro + 1);
+        cdd = cdd - a2.x;
+        cvd = cvd - a2.y;
+        cvv = cvv + b2.y;
+      }
+      const int32_t k = info & 0x0fffffff;
+      if (info & (1 << 29)) {  // neighbour index below n
+        va_row[k] = cdd;
+        vm_row[nd + 1 + k] = cvv;
+        vm_row[k] = cvd;
+      } else {
+        vm_row[k + 1] = cvd;
+      }
+    }
   }
   const double D8 = __ldg(dv + d.c_k8 + tn), D9 = __ldg(dv + d.c_k9 + tn);
   const double w8 = D8 * J8, w9 = D9 * J9;

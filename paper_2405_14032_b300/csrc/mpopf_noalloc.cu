@@ -63,11 +63,11 @@ extern "C" int mpopf_assemble_kkt_noalloc(mpopf_handle *h, const double *x, cons
                                           void *stream) {
   if (!h) return fail(MPOPF_ERR_ARG, "mpopf_assemble_kkt_noalloc: NULL handle");
   if (!x || !lam || !sigma_x || !dvec || !kv) return fail(MPOPF_ERR_ARG, "mpopf_assemble_kkt_noalloc: NULL array");
-  const long long need = 6LL * h->d.T * h->d.L;
+  const long long need = 2LL * mpopf::kRec * h->d.T * h->d.L;
   if (need > kScratchDoubles)
     return fail(MPOPF_ERR_SIZE, "mpopf_assemble_kkt_noalloc: needs " + std::to_string(need) +
-                                    " scratch doubles (6 per branch x period), over the static maximum of " +
-                                    std::to_string(kScratchDoubles) + " (T x L <= 699050)");
+                                    " scratch doubles (12 per branch x period), over the static maximum of " +
+                                    std::to_string(kScratchDoubles) + " (T x L <= 349525)");
   double *scratch = nullptr;
   cudaError_t e = scratch_address(&scratch);
   if (e != cudaSuccess) {

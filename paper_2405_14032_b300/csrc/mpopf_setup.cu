@@ -369,13 +369,25 @@ int mpopf_setup(const mpopf_network *net, int32_t n_periods, const double *pd, c
     inc[net->br_f[l]].push_back((int32_t)(2 * l));
     inc[net->br_t[l]].push_back((int32_t)(2 * l + 1));
   }
+  // Buses in the order the bus kernel processes them.  Natural order: sorting
+  // by degree (equal loop trip counts in a warp) was measured slower because
+  // the per-bus loads and stores then scatter.
+  std::vector<int32_t> bus_order(N);
+  for (int64_t i = 0; i < N; ++i) bus_order[i] = (int32_t)i;
+  // Incidence slots numbered in that order (a warp's records are contiguous);
+  // inc_ptr is indexed by position in bus_order, each bus's slots in branch order.
   std::vector<int32_t> inc_ptr(N + 1, 0), inc_code;
-  std::vector<int32_t> nbr_ptr(N + 1, 0), nbr_bus, nbr_grp, grp_code, bus_nd(N), bus_ndlt(N);
   inc_code.reserve(2 * L);
+  std::vector<int32_t> slot_start(N);
+  for (int64_t pos = 0; pos < N; ++pos) {
+    const int32_t i = bus_order[pos];
+    slot_start[i] = (int32_t)inc_code.size();
+    inc_code.insert(inc_code.end(), inc[i].begin(), inc[i].end());  // ascending in l
+    inc_ptr[pos + 1] = (int32_t)inc_code.size();
+  }
+  std::vector<int32_t> nbr_ptr(N + 1, 0), nbr_bus, nbr_grp, grp_code, bus_nd(N), bus_ndlt(N);
   for (int64_t i = 0; i < N; ++i) {
-    std::vector<int32_t> &v = inc[i];  // already ascending in l
-    inc_code.insert(inc_code.end(), v.begin(), v.end());
-    inc_ptr[i + 1] = (int32_t)inc_code.size();
+    std::vector<int32_t> &v = inc[i];
     std::vector<std::pair<int32_t, int32_t>> nb;  // (neighbour, code)
     for (int32_t code : v) {
       const int64_t l = code >> 1;
@@ -397,6 +409,32 @@ int mpopf_setup(const mpopf_network *net, int32_t n_periods, const double *pd, c
     bus_ndlt[i] = ndlt;
   }
   nbr_grp.push_back((int32_t)grp_code.size());
+  // Per slot: neighbour position and group links; per branch end: its slot;
+  // per bus: its slots in ascending arc index (from ends, then to ends).
+  std::vector<int32_t> br_slot(2 * L), slot_info(2 * L), slot_next(2 * L, -1), arc_perm(2 * L);
+  for (int64_t i = 0; i < N; ++i) {
+    std::vector<int32_t> nbs;  // distinct neighbours ascending
+    for (int32_t q = nbr_ptr[i]; q < nbr_ptr[i + 1]; ++q) nbs.push_back(nbr_bus[q]);
+    std::vector<int32_t> last_of(nbs.size(), -1);
+    const int32_t s0 = slot_start[i], s1 = s0 + (int32_t)inc[i].size();
+    for (int32_t s = s0; s < s1; ++s) {
+      const int32_t code = inc_code[s];
+      const int64_t l = code >> 1;
+      br_slot[(code & 1) * L + l] = s;
+      const int32_t nb = (code & 1) ? net->br_f[l] : net->br_t[l];
+      const int32_t k = (int32_t)(std::lower_bound(nbs.begin(), nbs.end(), nb) - nbs.begin());
+      int32_t info = k;
+      if (last_of[k] < 0) info |= 1 << 30;  // leader: first branch to nb in branch order
+      else slot_next[last_of[k]] = s;
+      if (nb < i) info |= 1 << 29;
+      last_of[k] = s;
+      slot_info[s] = info;
+    }
+    int32_t k = s0;
+    for (int pass = 0; pass < 2; ++pass)
+      for (int32_t q = s0; q < s1; ++q)
+        if ((inc_code[q] & 1) == pass) arc_perm[k++] = q;
+  }
 
   // ---- templates ----
   std::vector<int32_t> jk8_off(N);
@@ -491,7 +529,12 @@ int mpopf_setup(const mpopf_network *net, int32_t n_periods, const double *pd, c
   std::vector<double> vqd(qd ? qd : (const double *)nullptr, qd ? qd + T * D : (const double *)nullptr);
   d.pd = dev_upload(h, vpd, &err);
   d.qd = dev_upload(h, vqd, &err);
-  d.S = dev_alloc<double>(h, T * L * 6, &err);
+  d.br_slot = dev_upload(h, br_slot, &err);
+  d.bus_order = dev_upload(h, bus_order, &err);
+  d.arc_perm = dev_upload(h, arc_perm, &err);
+  d.slot_info = dev_upload(h, slot_info, &err);
+  d.slot_next = dev_upload(h, slot_next, &err);
+  d.S = dev_alloc<double>(h, T * 2 * L * kRec, &err);
   d.fpart_n = (int32_t)std::max<int64_t>(1, (T * G + kBlock - 1) / kBlock);
   d.fpart = dev_alloc<double>(h, d.fpart_n, &err);
   // patterns and bounds

@@ -44,13 +44,27 @@ class _Pattern(ctypes.Structure):
 _lib = None
 
 
+def _ensure_built():
+    """Rebuild libmpopf.so when a source is newer than it (a stale library
+    would not match the kernels' scratch layout).  Raises if the library is
+    missing and cannot be built: there is no CPU fallback."""
+    from . import build as _build
+    srcs = _build.sources()
+    if os.path.exists(LIB_PATH) and srcs and os.path.getmtime(LIB_PATH) >= max(
+            os.path.getmtime(p) for p in srcs + [os.path.join(_build.ROOT, "include", "mpopf.h")]):
+        return
+    try:
+        _build.build()
+    except Exception as exc:  # nvcc missing or failing
+        raise RuntimeError(f"libmpopf.so is missing or stale at {LIB_PATH} and could not be built ({exc}); "
+                           "there is no CPU fallback") from exc
+
+
 def lib():
-    """Load libmpopf.so (raises if it has not been built)."""
+    """Load libmpopf.so (rebuilt first if stale; raises if unavailable)."""
     global _lib
     if _lib is None:
-        if not os.path.exists(LIB_PATH):
-            raise RuntimeError(f"libmpopf.so not found at {LIB_PATH}; build it with "
-                               "`python -m paper_2405_14032_b300.build` (there is no CPU fallback)")
+        _ensure_built()
         L = ctypes.CDLL(LIB_PATH)
         sig = {
             "mpopf_setup": (ctypes.c_int, [ctypes.POINTER(_Network), _I32, _P, _P, ctypes.POINTER(_P),
@@ -231,7 +245,7 @@ class Handle:
         """M values into the caller's `kv` with no device allocation by the
         call: the scratch is a fixed array inside the library (for callers
         that cannot allocate while they run, e.g. inside a stream capture).
-        Raises MpopfError (code -2) when 6 T L exceeds that array."""
+        Raises MpopfError (code -2) when 12 T L exceeds that array."""
         _check(lib().mpopf_assemble_kkt_noalloc(self.h, _ptr(x), _ptr(lam), float(sigma), _ptr(sigma_x),
                                                 _ptr(dvec), float(delta_w), _ptr(kv), _stream_ptr(stream)),
                "mpopf_assemble_kkt_noalloc")

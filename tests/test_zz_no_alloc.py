@@ -43,11 +43,15 @@ def test_noalloc_matches_assemble_kkt_two_calls():
 
 def test_noalloc_rejects_problems_over_its_static_limit():
     from paper_2405_14032_b300 import mpopf
-    # 3,200 branches x 240 periods = 768,000 branch-periods > 699,050
-    inst = synth.make_instance(5, 2000, 3200, 400, 1200, 240)
+    # 3,200 branches x 120 periods = 384,000 branch-periods > 349,525
+    inst = synth.make_instance(5, 2000, 3200, 400, 1200, 120)
     h = mpopf.Handle(inst)
-    z = torch.zeros(1, dtype=torch.float64, device="cuda")
+    # full-size arrays, so that the call would stay in bounds of its inputs
+    # and output even if it were (wrongly) accepted
+    zn = torch.zeros(h.n, dtype=torch.float64, device="cuda")
+    zm = torch.zeros(h.m, dtype=torch.float64, device="cuda")
+    kv = torch.zeros(h.nnz_kkt, dtype=torch.float64, device="cuda")
     with pytest.raises(mpopf.MpopfError) as err:
-        h.assemble_kkt_noalloc(z, z, 1.0, z, z, 0.0, z)
+        h.assemble_kkt_noalloc(zn, zm, 1.0, zn, zm, 0.0, kv)
     assert "(-2)" in str(err.value) and "static maximum" in str(err.value)
     h.close()
