@@ -101,16 +101,34 @@ class ClockSampler:
         self._stop = threading.Event()
         self._t = None
         self.ok = False
+        self.error = None
+
+    def _handle(self, nv):
+        """NVML handle of the CUDA device (by UUID; NVML and CUDA number
+        devices differently when CUDA_VISIBLE_DEVICES is set)."""
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(self.index).uuid)
+            name = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+            return nv.nvmlDeviceGetHandleByUUID(name.encode())
+        except Exception:
+            pass
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        if ids and ids[min(self.index, len(ids) - 1)].isdigit():
+            return nv.nvmlDeviceGetHandleByIndex(int(ids[min(self.index, len(ids) - 1)]))
+        return nv.nvmlDeviceGetHandleByIndex(self.index)
 
     def start(self):
         try:
             import pynvml
             pynvml.nvmlInit()
             self._nv = pynvml
-            self._h = pynvml.nvmlDeviceGetHandleByIndex(self.index)
+            self._h = self._handle(pynvml)
             self.max_mhz = pynvml.nvmlDeviceGetMaxClockInfo(self._h, pynvml.NVML_CLOCK_SM)
             self.ok = True
-        except Exception:
+        except Exception as exc:
+            self.error = repr(exc)[:200]
             return self
         self._t = threading.Thread(target=self._run, daemon=True)
         self._t.start()
@@ -131,7 +149,7 @@ class ClockSampler:
         if self._t:
             self._t.join()
         if not self.ok:
-            return None
+            return {"error": self.error}
         return {"sm_mhz": statistics.median(self.samples) if self.samples else None,
                 "sm_max_mhz": self.max_mhz, "samples": len(self.samples),
                 "reasons": [k for k, v in self.REASONS.items() if self.reasons & v],
@@ -197,6 +215,104 @@ def cpu_baseline(inst, pt, budget_s=15.0):
     return {"value": 1.0 / per_sweep, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{done} of {inst.T} periods (all callbacks + M rows of each period), "
                       f"{el:.1f} s, extrapolated to the full horizon"}
+
+
+def _events(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def adjoint_comparison(torch, vectors=256):
+    """The differentiation workload (2,000-bus network, T = 24, seed 5; 256
+    (y, v) vectors): matrix-free J^T y (+ load adjoint) and W v against the
+    plain form, which materialises J (W) with the callback and multiplies with
+    cuSPARSE (torch.sparse CSR): per vector at a fresh point, and amortised
+    over the 256 vectors at one point."""
+    from paper_2405_14032_b300 import mpopf, synth
+    inst = synth.make_instance(5, 2000, 3200, 400, 1200, 24)
+    pt = synth.make_point(5, inst)
+    h = mpopf.Handle(inst)
+    dev = lambda a: torch.as_tensor(a, dtype=torch.float64, device="cuda")
+    x, lam = dev(pt.x), dev(pt.lam)
+    Y = dev(synth.uniform(5, 5000, vectors * h.m, -1.0, 1.0).reshape(vectors, h.m))
+    V = dev(synth.normal(5, 9000, vectors * h.n).reshape(vectors, h.n))
+    pat = h.pattern()
+    # J^T as CSR: rows = J columns; permutation of the COO values (setup, untimed)
+    jr, jc = pat["jac_row"].long(), pat["jac_col"].long()
+    order = torch.argsort(jc * h.m + jr)
+    jt_crow = torch.zeros(h.n + 1, dtype=torch.int64, device="cuda")
+    jt_crow[1:] = torch.cumsum(torch.bincount(jc, minlength=h.n), 0)
+    jt_col = jr[order]
+    # W symmetric expansion as CSR (duplicates kept; SpMV sums them)
+    hr, hc = pat["hess_row"].long(), pat["hess_col"].long()
+    off = hr != hc
+    er = torch.cat([hr, hc[off]])
+    ec = torch.cat([hc, hr[off]])
+    src = torch.cat([torch.arange(h.nnz_hess, device="cuda"), torch.nonzero(off).squeeze(1)])
+    ho = torch.argsort(er * h.n + ec)
+    w_crow = torch.zeros(h.n + 1, dtype=torch.int64, device="cuda")
+    w_crow[1:] = torch.cumsum(torch.bincount(er, minlength=h.n), 0)
+    w_col, w_src = ec[ho], src[ho]
+    jv = torch.empty(h.nnz_jac, dtype=torch.float64, device="cuda")
+    hv = torch.empty(h.nnz_hess, dtype=torch.float64, device="cuda")
+    gx = torch.empty(h.n, dtype=torch.float64, device="cuda")
+
+    def plain_vjp(y, fresh):
+        if fresh:
+            h.eval(mpopf.OUT_JAC, x, out=dict(jv=jv))
+        A = torch.sparse_csr_tensor(jt_crow, jt_col, jv[order], size=(h.n, h.m))
+        return torch.mv(A, y)
+
+    def plain_hvp(v, fresh):
+        if fresh:
+            h.eval(mpopf.OUT_HESS, x, lam, pt.sigma, out=dict(hv=hv))
+        A = torch.sparse_csr_tensor(w_crow, w_col, hv[w_src], size=(h.n, h.n))
+        return torch.mv(A, v)
+
+    def timed(fn):
+        for k in range(3):
+            fn(k)
+        torch.cuda.synchronize()
+        e0, e1 = _events(torch)
+        e0.record()
+        for k in range(vectors):
+            fn(k)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / vectors
+
+    # correctness of the plain form against the matrix-free kernels
+    h.eval(mpopf.OUT_JAC, x, out=dict(jv=jv))
+    h.eval(mpopf.OUT_HESS, x, lam, pt.sigma, out=dict(hv=hv))
+    ref_v = h.vjp(x, Y[0], gx=gx, loads=False)[0].clone()
+    pv = plain_vjp(Y[0], False)
+    err_v = float((pv - ref_v).abs().max() / ref_v.abs().max())
+    ref_h = h.hvp(x, lam, pt.sigma, V[0])
+    err_h = float((plain_hvp(V[0], False) - ref_h).abs().max() / ref_h.abs().max())
+    gpd = torch.empty(inst.T * inst.net.n_load, dtype=torch.float64, device="cuda")
+    gqd = torch.empty_like(gpd)
+    res = {
+        "workload": "2000-bus / 3200-branch / 400-gen / 1200-load network, T = 24, 256 vectors",
+        "vjp_matrix_free_ms": timed(lambda k: lib_vjp(h, x, Y[k], gx, gpd, gqd)),
+        "vjp_plain_fresh_ms": timed(lambda k: plain_vjp(Y[k], True)),
+        "vjp_plain_amortised_ms": timed(lambda k: plain_vjp(Y[k], False)),
+        "hvp_matrix_free_ms": timed(lambda k: h.hvp(x, lam, pt.sigma, V[k], out=gx)),
+        "hvp_plain_fresh_ms": timed(lambda k: plain_hvp(V[k], True)),
+        "hvp_plain_amortised_ms": timed(lambda k: plain_hvp(V[k], False)),
+        "plain_vs_matrix_free_max_rel_diff": max(err_v, err_h),
+        "plain": "callback (eval_jac / eval_hess) + cuSPARSE CSR SpMV via torch.sparse",
+    }
+    res["vjp_speedup_vs_fresh"] = res["vjp_plain_fresh_ms"] / res["vjp_matrix_free_ms"]
+    res["hvp_speedup_vs_fresh"] = res["hvp_plain_fresh_ms"] / res["hvp_matrix_free_ms"]
+    h.close()
+    return res
+
+
+def lib_vjp(h, x, y, gx, gpd, gqd):
+    from paper_2405_14032_b300 import mpopf
+    import torch
+    s = mpopf._stream_ptr(None)
+    mpopf._check(mpopf.lib().mpopf_vjp(h.h, x.data_ptr(), y.data_ptr(), gx.data_ptr(), gpd.data_ptr(),
+                                       gqd.data_ptr(), s), "mpopf_vjp")
 
 
 # ---------------------------------------------------------------------------
@@ -338,6 +454,7 @@ def run_ours(args, world, rank, local):
                        "steps": ke, "api": "mpopf_sweep_host (pinned host buffers, all inputs in, all outputs out)"}
         if world == 1:
             line["cpu_baseline"] = cpu_baseline(inst, pt)
+            line["adjoint"] = adjoint_comparison(torch)
         print(json.dumps(line), flush=True)
     h.close()
     if world > 1:

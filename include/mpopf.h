@@ -174,6 +174,25 @@ int mpopf_sweep_host(mpopf_handle *h, const double *x, const double *lam, double
                      const double *dvec, double delta_w, double *f, double *grad, double *c, double *jv,
                      double *hv, double *kv, void *stream);
 
+/* Matrix-free derivative products (no J or W is materialised).  Each value
+ * follows the same element-by-element order as the condensed matrix: an
+ * element's local sum over its rows (J order), then the elements in order.
+ *
+ * mpopf_vjp: gx [n] = J^T y for y [m] (device); optionally the load adjoint
+ *   gpd, gqd [T][D] = (dc/dPd)^T y, (dc/dQd)^T y = -y at the P / Q balance row
+ *   of the load's bus (Eq. 1b, 1c); pass both or neither (NULL).
+ * mpopf_jvp: out [m] = J v for v [n]; with load tangents dpd, dqd [T][D] (both
+ *   or neither) the balance rows also get -sum_d dpd[t][d] (Q likewise), i.e.
+ *   the tangent of c(x, Pd, Qd).
+ * mpopf_hvp: hv [n] = W v, W = sigma grad^2 f + sum_i lambda_i grad^2 c_i
+ *   (Eq. 4) for lam [m], v [n].
+ * All use the handle's scratch (calls on one handle must not overlap). */
+int mpopf_vjp(mpopf_handle *h, const double *x, const double *y, double *gx, double *gpd, double *gqd, void *stream);
+int mpopf_jvp(mpopf_handle *h, const double *x, const double *v, const double *dpd, const double *dqd, double *jv_out,
+              void *stream);
+int mpopf_hvp(mpopf_handle *h, const double *x, const double *lam, double sigma, const double *v, double *hv,
+              void *stream);
+
 /* Number of kernel launches one mpopf_eval call with these output bits makes. */
 int mpopf_launch_count(const mpopf_handle *h, unsigned outputs);
 

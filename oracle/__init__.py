@@ -51,7 +51,7 @@ def load():
             "orc_window_rows": (_I64, [_P, _I64, _I64]),
             "orc_vjp": (None, [_P, _I64, _I64, _P, _P, _P, _P, _P]),
             "orc_hvp": (None, [_P, _I64, _I64, _P, _P, _D, _P, _P]),
-            "orc_jvp": (None, [_P, _I64, _I64, _P, _P, _P]),
+            "orc_jvp": (None, [_P, _I64, _I64, _P, _P, _P, _P, _P]),
             "orc_sincos": (None, [_P, _I64, _P, _P]),
             "orc_gradlag": (None, [_P, _P, _P, _D, _P]),
             "orc_gradlag_cstep": (None, [_P, _P, _P, _D, _P, _D, _P]),
@@ -187,10 +187,13 @@ class Oracle:
         _lib.orc_hvp(self.h, t0, t1, _ptr(_f64(x)), _ptr(_f64(lam)), float(sigma), _ptr(_f64(v)), _ptr(out))
         return out
 
-    def jvp(self, x, v, t0=0, t1=None):
+    def jvp(self, x, v, t0=0, t1=None, dpd=None, dqd=None):
+        """J v (plus the load terms -sum dpd, -sum dqd on the balance rows)."""
         t1 = self.T if t1 is None else t1
         out = np.full(self.m, np.nan)
-        _lib.orc_jvp(self.h, t0, t1, _ptr(_f64(x)), _ptr(_f64(v)), _ptr(out))
+        dpd = None if dpd is None else _f64(dpd)
+        dqd = None if dqd is None else _f64(dqd)
+        _lib.orc_jvp(self.h, t0, t1, _ptr(_f64(x)), _ptr(_f64(v)), _ptr(dpd), _ptr(dqd), _ptr(out))
         return out
 
     # -- pins -------------------------------------------------------------

@@ -816,8 +816,11 @@ void orc_hvp(void* h, int64_t t0, int64_t t1, const double* x, const double* lam
 }
 
 // J v for the rows of periods [t0, t1): acc = fma(J_ip, v[col_p], acc) over
-// the row's J order.
-void orc_jvp(void* h, int64_t t0, int64_t t1, const double* x, const double* v, double* out) {
+// the row's J order.  With load tangents dpd/dqd ([T][D], may be NULL) the
+// balance rows also get the load term: dc/dPd = -1, so acc = acc - dpd[t][d]
+// for the loads of the bus in ascending order (the tangent of c(x, Pd, Qd)).
+void orc_jvp(void* h, int64_t t0, int64_t t1, const double* x, const double* v, const double* dpd,
+             const double* dqd, double* out) {
   const Model& M = *static_cast<Model*>(h);
   std::vector<int64_t> cols; std::vector<double> vals; double cv;
   for (const auto& rg : window_rows(M, t0, t1))
@@ -825,6 +828,11 @@ void orc_jvp(void* h, int64_t t0, int64_t t1, const double* x, const double* v, 
       row_eval<double>(M, x, i, &cols, &vals, &cv);
       double acc = 0.0;
       for (size_t p = 0; p < cols.size(); ++p) acc = std::fma(vals[p], v[cols[p]], acc);
+      int kind; int64_t t, comp;
+      row_decode(M, i, &kind, &t, &comp);
+      const double* dl = kind == 8 ? dpd : kind == 9 ? dqd : nullptr;
+      if (dl)
+        for (int64_t d : M.bus_loads[comp]) acc = acc - dl[t * M.D + d];
       out[i] = acc;
     }
 }

@@ -1,0 +1,307 @@
+// Matrix-free derivative products of libmpopf (sm_103a, FP64): J^T y with the
+// load adjoint, J v with load tangents, and W v -- without materialising J or W.
+//
+// Same decomposition as the sweep: a branch x period kernel computes the branch
+// element's local values (the flow terms and their derivatives, recomputed from
+// x), writes the arc variables' results and one incidence record per branch end;
+// a bus x period kernel sums its records in branch order (no atomics); a
+// generator x period kernel handles pg/qg.  Every value follows the fixed
+// rounding order of the definitions (element-local sums in the row order, then
+// added in element order), so results are bitwise reproducible.
+#include "mpopf_device.cuh"
+
+namespace mpopf {
+namespace {
+
+// ---------------------------------------------------------------------------
+// J^T y.  Branch element local sums over its rows K1..K7:
+//   va_f: a1 y1, + a2 y2, + a3 y3, + a4 y4, + y5   (va_t: the exact negation)
+//   vm_f: b_k y_k (k = 1..4);  vm_t: c_k y_k
+//   p_f: fma(2pf, y6, y1);  q_f: fma(2qf, y6, y2);  p_t: fma(2pt, y7, y3);
+//   q_t: fma(2qt, y7, y4); then the bus element adds -y8 (p) or -y9 (q).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlock) k_vjp_branch(Dev d, const double *__restrict__ x,
+                                                       const double *__restrict__ y, double *__restrict__ gx) {
+  const int32_t L = d.L;
+  const int32_t tl = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+  if (tl >= d.T * L) return;
+  const int32_t t = tl / L, l = tl - t * L;
+  const int64_t TL = (int64_t)d.T * L, tN = (int64_t)t * d.N;
+  const int64_t pb = d.x_p + 2 * (int64_t)t * L, qb = d.x_q + 2 * (int64_t)t * L;
+  const int32_t f = __ldg(d.br_f + l), to = __ldg(d.br_t + l);
+  const double vf = __ldg(x + d.x_vm + tN + f), vt = __ldg(x + d.x_vm + tN + to);
+  const Flow F = flow_terms(d, l, __ldg(x + tN + f), __ldg(x + tN + to), vf, vt);
+  const FlowJ J = flow_jac(d, l, F, vf, vt);
+  const int64_t rk1 = d.T + tl;
+  const double y1 = __ldg(y + rk1), y2 = __ldg(y + rk1 + TL), y3 = __ldg(y + rk1 + 2 * TL);
+  const double y4 = __ldg(y + rk1 + 3 * TL), y5 = __ldg(y + rk1 + 4 * TL), y6 = __ldg(y + rk1 + 5 * TL);
+  const double y7 = __ldg(y + rk1 + 6 * TL);
+  const double Ld = fma(J.a4, y4, fma(J.a3, y3, fma(J.a2, y2, J.a1 * y1))) + y5;
+  const double Lvf = fma(J.b4, y4, fma(J.b3, y3, fma(J.b2, y2, J.b1 * y1)));
+  const double Lvt = fma(J.c4, y4, fma(J.c3, y3, fma(J.c2, y2, J.c1 * y1)));
+  const double pf = __ldg(x + pb + l), pt = __ldg(x + pb + L + l);
+  const double qf = __ldg(x + qb + l), qt = __ldg(x + qb + L + l);
+  const int64_t r8f = d.c_k8 + tN + f, r8t = d.c_k8 + tN + to, d89 = d.c_k9 - d.c_k8;
+  gx[pb + l] = fma(twice(pf), y6, y1) - __ldg(y + r8f);
+  gx[qb + l] = fma(twice(qf), y6, y2) - __ldg(y + r8f + d89);
+  gx[pb + L + l] = fma(twice(pt), y7, y3) - __ldg(y + r8t);
+  gx[qb + L + l] = fma(twice(qt), y7, y4) - __ldg(y + r8t + d89);
+  double *R = d.S + (int64_t)t * 2 * L * kRec;
+  *reinterpret_cast<double2 *>(R + (int64_t)__ldg(d.br_slot + l) * kRec) = make_double2(Ld, Lvf);
+  *reinterpret_cast<double2 *>(R + (int64_t)__ldg(d.br_slot + L + l) * kRec) = make_double2(negx(Ld), Lvt);
+}
+
+__global__ void __launch_bounds__(kBlock) k_vjp_bus(Dev d, const double *__restrict__ x,
+                                                    const double *__restrict__ y, double *__restrict__ gx,
+                                                    double *__restrict__ gpd, double *__restrict__ gqd) {
+  const int32_t N = d.N;
+  const int32_t idx = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+  if (idx >= d.T * N) return;
+  const int32_t t = idx / N, pos = idx - t * N;
+  const int32_t n = __ldg(d.bus_order + pos);
+  const int32_t tn = t * N + n;
+  const int32_t s0 = __ldg(d.inc_ptr + pos), s1 = __ldg(d.inc_ptr + pos + 1);
+  const double *R = d.S + (int64_t)t * 2 * d.L * kRec;
+  // va: reference element first, then the incident branches in branch order.
+  double ga = 0.0, gv = 0.0;
+  bool has_a = false, has_v = false;
+  if (n == d.ref) { ga = __ldg(y + t); has_a = true; }
+  for (int32_t q = s0; q < s1; ++q) {
+    const double2 r = __ldg(reinterpret_cast<const double2 *>(R + (int64_t)q * kRec));
+    ga = has_a ? ga + r.x : r.x;
+    gv = has_v ? gv + r.y : r.y;
+    has_a = has_v = true;
+  }
+  // vm: then the bus element (rows K8, K9).
+  const double vm = __ldg(x + d.x_vm + tn);
+  const double y8 = __ldg(y + d.c_k8 + tn), y9 = __ldg(y + d.c_k9 + tn);
+  const double Lbus = fma(__ldg(d.bus_p2bs + n) * vm, y9, (__ldg(d.bus_m2gs + n) * vm) * y8);
+  gv = has_v ? gv + Lbus : Lbus;
+  gx[tn] = ga;
+  gx[d.x_vm + tn] = gv;
+  if (gpd) {
+    const int64_t ldb = (int64_t)t * d.D;
+    for (int32_t e = __ldg(d.bload_ptr + n); e < __ldg(d.bload_ptr + n + 1); ++e) {
+      const int32_t k = __ldg(d.bload_idx + e);
+      gpd[ldb + k] = negx(y8);
+      gqd[ldb + k] = negx(y9);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_vjp_gen(Dev d, const double *__restrict__ y, double *__restrict__ gx) {
+  const int32_t G = d.G;
+  const int32_t tg = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+  if (tg >= d.T * G) return;
+  const int32_t t = tg / G, g = tg - t * G;
+  const int64_t tn = (int64_t)t * d.N + __ldg(d.gen_bus + g);
+  double a = __ldg(y + d.c_k8 + tn);  // bus element (K8, entry +1)
+  const int64_t rr = d.c_k10 + (int64_t)(t - 1) * G + g;
+  if (t >= 1) a = a + __ldg(y + rr);         // ramp row (t, g): +1
+  if (t + 1 < d.T) a = a - __ldg(y + rr + G);  // ramp row (t + 1, g): -1
+  gx[d.x_pg + tg] = a;
+  gx[d.x_qg + tg] = __ldg(y + d.c_k9 + tn);
+}
+
+// ---------------------------------------------------------------------------
+// J v (+ load tangents): one row at a time in its J order.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlock) k_jvp_branch(Dev d, const double *__restrict__ x,
+                                                       const double *__restrict__ v, double *__restrict__ out) {
+  const int32_t L = d.L;
+  const int32_t tl = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+  if (tl >= d.T * L) return;
+  const int32_t t = tl / L, l = tl - t * L;
+  const int64_t TL = (int64_t)d.T * L, tN = (int64_t)t * d.N;
+  const int64_t pb = d.x_p + 2 * (int64_t)t * L, qb = d.x_q + 2 * (int64_t)t * L;
+  const int32_t f = __ldg(d.br_f + l), to = __ldg(d.br_t + l);
+  const double vf = __ldg(x + d.x_vm + tN + f), vt = __ldg(x + d.x_vm + tN + to);
+  const Flow F = flow_terms(d, l, __ldg(x + tN + f), __ldg(x + tN + to), vf, vt);
+  const FlowJ J = flow_jac(d, l, F, vf, vt);
+  const double uf = __ldg(v + tN + f), ut = __ldg(v + tN + to);
+  const double wf = __ldg(v + d.x_vm + tN + f), wt = __ldg(v + d.x_vm + tN + to);
+  const double vpf = __ldg(v + pb + l), vpt = __ldg(v + pb + L + l);
+  const double vqf = __ldg(v + qb + l), vqt = __ldg(v + qb + L + l);
+  const int64_t rk1 = d.T + tl;
+  out[rk1] = fma(J.c1, wt, fma(J.b1, wf, fma(negx(J.a1), ut, fma(J.a1, uf, vpf))));
+  out[rk1 + TL] = fma(J.c2, wt, fma(J.b2, wf, fma(negx(J.a2), ut, fma(J.a2, uf, vqf))));
+  out[rk1 + 2 * TL] = fma(J.c3, wt, fma(J.b3, wf, fma(negx(J.a3), ut, fma(J.a3, uf, vpt))));
+  out[rk1 + 3 * TL] = fma(J.c4, wt, fma(J.b4, wf, fma(negx(J.a4), ut, fma(J.a4, uf, vqt))));
+  out[rk1 + 4 * TL] = uf - ut;
+  const double pf = __ldg(x + pb + l), pt = __ldg(x + pb + L + l);
+  const double qf = __ldg(x + qb + l), qt = __ldg(x + qb + L + l);
+  out[rk1 + 5 * TL] = fma(twice(qf), vqf, twice(pf) * vpf);
+  out[rk1 + 6 * TL] = fma(twice(qt), vqt, twice(pt) * vpt);
+}
+
+__global__ void __launch_bounds__(kBlock) k_jvp_bus(Dev d, const double *__restrict__ x,
+                                                    const double *__restrict__ v, const double *__restrict__ dpd,
+                                                    const double *__restrict__ dqd, double *__restrict__ out) {
+  const int32_t N = d.N;
+  const int32_t idx = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+  if (idx >= d.T * N) return;
+  const int32_t t = idx / N, pos = idx - t * N;
+  const int32_t n = __ldg(d.bus_order + pos);
+  const int32_t tn = t * N + n;
+  const int64_t L = d.L, G = d.G;
+  if (n == d.ref) out[t] = __ldg(v + (int64_t)t * N + n);
+  const double vm = __ldg(x + d.x_vm + tn), dvm = __ldg(v + d.x_vm + tn);
+  double aP = (__ldg(d.bus_m2gs + n) * vm) * dvm, aQ = (__ldg(d.bus_p2bs + n) * vm) * dvm;
+  const int64_t pgb = d.x_pg + (int64_t)t * G, qgb = d.x_qg + (int64_t)t * G;
+  for (int32_t e = __ldg(d.bgen_ptr + n); e < __ldg(d.bgen_ptr + n + 1); ++e) {
+    const int32_t g = __ldg(d.bgen_idx + e);
+    aP = aP + __ldg(v + pgb + g);
+    aQ = aQ + __ldg(v + qgb + g);
+  }
+  const int64_t pab = d.x_p + 2 * (int64_t)t * L, qab = d.x_q + 2 * (int64_t)t * L;
+  for (int32_t e = __ldg(d.barc_ptr + n); e < __ldg(d.barc_ptr + n + 1); ++e) {
+    const int32_t a = __ldg(d.barc_idx + e);
+    aP = aP - __ldg(v + pab + a);
+    aQ = aQ - __ldg(v + qab + a);
+  }
+  if (dpd) {
+    const int64_t ldb = (int64_t)t * d.D;
+    for (int32_t e = __ldg(d.bload_ptr + n); e < __ldg(d.bload_ptr + n + 1); ++e) {
+      const int32_t k = __ldg(d.bload_idx + e);
+      aP = aP - __ldg(dpd + ldb + k);
+      aQ = aQ - __ldg(dqd + ldb + k);
+    }
+  }
+  out[d.c_k8 + tn] = aP;
+  out[d.c_k9 + tn] = aQ;
+}
+
+__global__ void __launch_bounds__(kBlock) k_jvp_gen(Dev d, const double *__restrict__ v, double *__restrict__ out) {
+  const int32_t G = d.G;
+  const int32_t tg = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+  if (tg >= (d.T - 1) * G) return;  // ramp rows (t, g), t = 1..T-1, row index (t - 1) G + g
+  const int64_t cur = d.x_pg + G + tg;
+  out[d.c_k10 + tg] = __ldg(v + cur) - __ldg(v + cur - G);
+}
+
+// ---------------------------------------------------------------------------
+// W v.  Branch element: its W entries in order (block (0,0)..(3,3), then the
+// thermal diagonals), each entry (r, c, w) adding fma(w, v[c], .) to r and,
+// off the diagonal, fma(w, v[r], .) to c.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlock) k_hvp_branch(Dev d, const double *__restrict__ x,
+                                                       const double *__restrict__ lam, const double *__restrict__ v,
+                                                       double *__restrict__ hv) {
+  const int32_t L = d.L;
+  const int32_t tl = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+  if (tl >= d.T * L) return;
+  const int32_t t = tl / L, l = tl - t * L;
+  const int64_t TL = (int64_t)d.T * L, tN = (int64_t)t * d.N;
+  const int64_t pb = d.x_p + 2 * (int64_t)t * L, qb = d.x_q + 2 * (int64_t)t * L;
+  const int32_t f = __ldg(d.br_f + l), to = __ldg(d.br_t + l);
+  const double vf = __ldg(x + d.x_vm + tN + f), vt = __ldg(x + d.x_vm + tN + to);
+  const Flow F = flow_terms(d, l, __ldg(x + tN + f), __ldg(x + tN + to), vf, vt);
+  const int64_t rk1 = d.T + tl;
+  const FlowW W = flow_hess(d, l, F, vf, vt, __ldg(lam + rk1), __ldg(lam + rk1 + TL), __ldg(lam + rk1 + 2 * TL),
+                            __ldg(lam + rk1 + 3 * TL));
+  const double uf = __ldg(v + tN + f), ut = __ldg(v + tN + to);
+  const double wf = __ldg(v + d.x_vm + tN + f), wt = __ldg(v + d.x_vm + tN + to);
+  const double nWdd = negx(W.Wdd), nWdvf = negx(W.Wdvf), nWdvt = negx(W.Wdvt), nAsum = negx(W.Asum);
+  const double hf = fma(W.Wdvt, wt, fma(W.Wdvf, wf, fma(nWdd, ut, W.Wdd * uf)));
+  const double ht = fma(nWdvt, wt, fma(nWdvf, wf, fma(W.Wdd, ut, nWdd * uf)));
+  const double hvf = fma(nAsum, wt, fma(W.Wvfvf, wf, fma(nWdvf, ut, W.Wdvf * uf)));
+  const double hvt = fma(W.Wvtvt, wt, fma(nAsum, wf, fma(nWdvt, ut, W.Wdvt * uf)));
+  const double h6 = twice(__ldg(lam + rk1 + 5 * TL)), h7 = twice(__ldg(lam + rk1 + 6 * TL));
+  hv[pb + l] = h6 * __ldg(v + pb + l);
+  hv[qb + l] = h6 * __ldg(v + qb + l);
+  hv[pb + L + l] = h7 * __ldg(v + pb + L + l);
+  hv[qb + L + l] = h7 * __ldg(v + qb + L + l);
+  double *R = d.S + (int64_t)t * 2 * L * kRec;
+  *reinterpret_cast<double2 *>(R + (int64_t)__ldg(d.br_slot + l) * kRec) = make_double2(hf, hvf);
+  *reinterpret_cast<double2 *>(R + (int64_t)__ldg(d.br_slot + L + l) * kRec) = make_double2(ht, hvt);
+}
+
+__global__ void __launch_bounds__(kBlock) k_hvp_bus(Dev d, const double *__restrict__ lam,
+                                                    const double *__restrict__ v, double *__restrict__ hv) {
+  const int32_t N = d.N;
+  const int32_t idx = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+  if (idx >= d.T * N) return;
+  const int32_t t = idx / N, pos = idx - t * N;
+  const int32_t n = __ldg(d.bus_order + pos);
+  const int32_t tn = t * N + n;
+  const int32_t s0 = __ldg(d.inc_ptr + pos), s1 = __ldg(d.inc_ptr + pos + 1);
+  const double *R = d.S + (int64_t)t * 2 * d.L * kRec;
+  double ha = 0.0, hm = 0.0;
+  for (int32_t q = s0; q < s1; ++q) {
+    const double2 r = __ldg(reinterpret_cast<const double2 *>(R + (int64_t)q * kRec));
+    ha = (q == s0) ? r.x : ha + r.x;
+    hm = (q == s0) ? r.y : hm + r.y;
+  }
+  const double dvm = __ldg(v + d.x_vm + tn);
+  const double WP = __ldg(lam + d.c_k8 + tn) * __ldg(d.bus_m2gs + n);
+  const double WQ = __ldg(lam + d.c_k9 + tn) * __ldg(d.bus_p2bs + n);
+  const double Lbus = fma(WQ, dvm, WP * dvm);
+  hv[tn] = ha;
+  hv[d.x_vm + tn] = (s1 > s0) ? hm + Lbus : Lbus;
+}
+
+__global__ void __launch_bounds__(kBlock) k_hvp_gen(Dev d, double sigma, const double *__restrict__ v,
+                                                    double *__restrict__ hv) {
+  const int32_t G = d.G;
+  const int32_t tg = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+  if (tg >= d.T * G) return;
+  const int32_t g = tg % G;
+  hv[d.x_pg + tg] = (sigma * __ldg(d.gen_c2x2 + g)) * __ldg(v + d.x_pg + tg);
+  hv[d.x_qg + tg] = 0.0;
+}
+
+unsigned grid_for(int64_t count) { return (unsigned)((count + kBlock - 1) / kBlock); }
+
+int fail(int code, const std::string &msg) {
+  set_error(msg);
+  return code;
+}
+
+}  // namespace
+}  // namespace mpopf
+
+using namespace mpopf;
+
+extern "C" {
+
+int mpopf_vjp(mpopf_handle *h, const double *x, const double *y, double *gx, double *gpd, double *gqd, void *stream) {
+  if (!h || !x || !y || !gx) return fail(MPOPF_ERR_ARG, "mpopf_vjp: NULL argument");
+  if ((gpd == nullptr) != (gqd == nullptr)) return fail(MPOPF_ERR_ARG, "mpopf_vjp: give both gpd and gqd or neither");
+  const Dev &d = h->d;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (d.L > 0) k_vjp_branch<<<grid_for((int64_t)d.T * d.L), kBlock, 0, s>>>(d, x, y, gx);
+  k_vjp_bus<<<grid_for((int64_t)d.T * d.N), kBlock, 0, s>>>(d, x, y, gx, gpd, d.D > 0 ? gqd : nullptr);
+  if (d.G > 0) k_vjp_gen<<<grid_for((int64_t)d.T * d.G), kBlock, 0, s>>>(d, y, gx);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(MPOPF_ERR_CUDA, std::string("mpopf_vjp: ") + cudaGetErrorString(e));
+  return MPOPF_OK;
+}
+
+int mpopf_jvp(mpopf_handle *h, const double *x, const double *v, const double *dpd, const double *dqd, double *jv_out,
+              void *stream) {
+  if (!h || !x || !v || !jv_out) return fail(MPOPF_ERR_ARG, "mpopf_jvp: NULL argument");
+  if ((dpd == nullptr) != (dqd == nullptr)) return fail(MPOPF_ERR_ARG, "mpopf_jvp: give both dpd and dqd or neither");
+  const Dev &d = h->d;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (d.L > 0) k_jvp_branch<<<grid_for((int64_t)d.T * d.L), kBlock, 0, s>>>(d, x, v, jv_out);
+  k_jvp_bus<<<grid_for((int64_t)d.T * d.N), kBlock, 0, s>>>(d, x, v, d.D > 0 ? dpd : nullptr, dqd, jv_out);
+  if (d.G > 0 && d.T > 1) k_jvp_gen<<<grid_for((int64_t)(d.T - 1) * d.G), kBlock, 0, s>>>(d, v, jv_out);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(MPOPF_ERR_CUDA, std::string("mpopf_jvp: ") + cudaGetErrorString(e));
+  return MPOPF_OK;
+}
+
+int mpopf_hvp(mpopf_handle *h, const double *x, const double *lam, double sigma, const double *v, double *hv,
+              void *stream) {
+  if (!h || !x || !lam || !v || !hv) return fail(MPOPF_ERR_ARG, "mpopf_hvp: NULL argument");
+  const Dev &d = h->d;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (d.L > 0) k_hvp_branch<<<grid_for((int64_t)d.T * d.L), kBlock, 0, s>>>(d, x, lam, v, hv);
+  k_hvp_bus<<<grid_for((int64_t)d.T * d.N), kBlock, 0, s>>>(d, lam, v, hv);
+  if (d.G > 0) k_hvp_gen<<<grid_for((int64_t)d.T * d.G), kBlock, 0, s>>>(d, sigma, v, hv);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(MPOPF_ERR_CUDA, std::string("mpopf_hvp: ") + cudaGetErrorString(e));
+  return MPOPF_OK;
+}
+
+}  // extern "C"

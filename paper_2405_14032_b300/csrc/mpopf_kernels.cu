@@ -14,86 +14,13 @@
 // Every value follows one fixed sequence of binary64 operations (explicit fma
 // where the definition has one; the build disables contraction), so results
 // are bitwise reproducible from run to run.
-#include "mpopf_internal.cuh"
+#include "mpopf_device.cuh"
 
 namespace mpopf {
 namespace {
 
-// ---------------------------------------------------------------------------
-// sin and cos of the angle difference: Cody & Waite reduction by pi/2 in three
-// parts (Software Manual for the Elementary Functions, 1980), then the Taylor
-// series of sin (through r^17) and cos (through r^18), Horner in r^2, with
-// coefficients RN((-1)^k / k!).  |x| <= RN(pi/4) needs no reduction.  Outside
-// |x| < 2^30 (and for NaN/Inf) the CUDA library is used.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void sincos_cw(double x, double *sn, double *cs) {
-  const unsigned long long ax = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffULL;
-  if (ax >= 0x41D0000000000000ULL) {  // |x| >= 2^30, Inf, NaN
-    sincos(x, sn, cs);
-    return;
-  }
-  double r = x;
-  int q = 0;
-  if (ax > 0x3FE921FB54442D18ULL) {  // |x| > RN(pi/4)
-    const double k = rint(x * 0x1.45f306dc9c883p-1);
-    r = fma(-k, 0x1.921fb54442d18p+0, x);
-    r = fma(-k, 0x1.1a62633145c07p-54, r);
-    r = fma(-k, -0x1.f1976b7ed8fbcp-110, r);
-    q = (int)(__double2ll_rz(k) & 3);
-  }
-  const double r2 = r * r;
-  double p = 1.0 / 355687428096000.0;
-  p = fma(p, r2, -1.0 / 1307674368000.0);
-  p = fma(p, r2, 1.0 / 6227020800.0);
-  p = fma(p, r2, -1.0 / 39916800.0);
-  p = fma(p, r2, 1.0 / 362880.0);
-  p = fma(p, r2, -1.0 / 5040.0);
-  p = fma(p, r2, 1.0 / 120.0);
-  p = fma(p, r2, -1.0 / 6.0);
-  const double r3 = r2 * r;
-  const double s = fma(r3, p, r);
-  double c = -1.0 / 6402373705728000.0;
-  c = fma(c, r2, 1.0 / 20922789888000.0);
-  c = fma(c, r2, -1.0 / 87178291200.0);
-  c = fma(c, r2, 1.0 / 479001600.0);
-  c = fma(c, r2, -1.0 / 3628800.0);
-  c = fma(c, r2, 1.0 / 40320.0);
-  c = fma(c, r2, -1.0 / 720.0);
-  c = fma(c, r2, 1.0 / 24.0);
-  c = fma(c, r2, -1.0 / 2.0);
-  const double co = fma(r2, c, 1.0);
-  if (q == 0) { *sn = s; *cs = co; }
-  else if (q == 1) { *sn = co; *cs = -s; }
-  else if (q == 2) { *sn = -s; *cs = -co; }
-  else { *sn = -co; *cs = s; }
-}
-
 template <unsigned MASK>
 __device__ __forceinline__ unsigned eff(unsigned rt) { return MASK ? MASK : rt; }
-
-// -x by flipping the sign bit with an integer operation (exact; keeps the
-// scarce FP64 pipe free).
-__device__ __forceinline__ double negx(double x) {
-  return __hiloint2double(__double2hiint(x) ^ (int)0x80000000, __double2loint(x));
-}
-
-// 2x exactly with integer operations only (no branch, no FP64 instruction):
-// exponent + 1 for normal results, a one-bit left shift of the magnitude for
-// zero and subnormal inputs, infinity on overflow, Inf and NaN unchanged.
-__device__ __forceinline__ double twice(double x) {
-  const int hi = __double2hiint(x), lo = __double2loint(x);
-  const unsigned e = ((unsigned)hi >> 20) & 0x7ffu;
-  const int sign = hi & (int)0x80000000;
-  int rh = hi + 0x100000, rl = lo;
-  const int sub_h = sign | ((hi & 0x7fffffff) << 1) | (int)((unsigned)lo >> 31);
-  rh = (e == 0u) ? sub_h : rh;
-  rl = (e == 0u) ? (int)((unsigned)lo << 1) : rl;
-  rh = (e == 2046u) ? (sign | 0x7ff00000) : rh;
-  rl = (e == 2046u) ? 0 : rl;
-  rh = (e == 2047u) ? hi : rh;
-  rl = (e == 2047u) ? lo : rl;
-  return __hiloint2double(rh, rl);
-}
 
 template <unsigned MASK>
 #ifndef MPOPF_BRANCH_MINB

@@ -81,6 +81,9 @@ def lib():
             "mpopf_sweep": (ctypes.c_int, [_P, _P, _P, _D, _P, _P, _D, _P, _P, _P, _P, _P, _P, _P]),
             "mpopf_sweep_host": (ctypes.c_int, [_P, _P, _P, _D, _P, _P, _D, _P, _P, _P, _P, _P, _P, _P]),
             "mpopf_assemble_kkt_noalloc": (ctypes.c_int, [_P, _P, _P, _D, _P, _P, _D, _P, _P]),
+            "mpopf_vjp": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
+            "mpopf_jvp": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
+            "mpopf_hvp": (ctypes.c_int, [_P, _P, _P, _D, _P, _P, _P]),
             "mpopf_launch_count": (ctypes.c_int, [_P, _U]),
             "mpopf_profile_start": (ctypes.c_int, [_P, _I32]),
             "mpopf_profile_stop": (ctypes.c_int, [_P, _P, _P]),
@@ -99,7 +102,8 @@ def exported_symbols():
     """Names the header declares (for the load/export check)."""
     return ["mpopf_setup", "mpopf_get_pattern", "mpopf_set_loads", "mpopf_eval", "mpopf_eval_obj",
             "mpopf_eval_grad", "mpopf_eval_cons", "mpopf_eval_jac", "mpopf_eval_hess", "mpopf_assemble_kkt",
-            "mpopf_sweep", "mpopf_sweep_host", "mpopf_assemble_kkt_noalloc", "mpopf_launch_count", "mpopf_profile_start", "mpopf_profile_stop",
+            "mpopf_sweep", "mpopf_sweep_host", "mpopf_assemble_kkt_noalloc", "mpopf_vjp", "mpopf_jvp", "mpopf_hvp",
+            "mpopf_launch_count", "mpopf_profile_start", "mpopf_profile_stop",
             "mpopf_destroy", "mpopf_last_error"]
 
 
@@ -167,6 +171,7 @@ class Handle:
         self.h = h
         self.pat = pat
         self.T = int(inst.T)
+        self.n_load = int(inst.net.n_load)
         self.n, self.m = int(pat.n), int(pat.m)
         self.nnz_jac, self.nnz_hess, self.nnz_kkt = int(pat.nnz_jac), int(pat.nnz_hess), int(pat.nnz_kkt)
 
@@ -250,6 +255,34 @@ class Handle:
                                                 _ptr(dvec), float(delta_w), _ptr(kv), _stream_ptr(stream)),
                "mpopf_assemble_kkt_noalloc")
         return kv
+
+    # -- matrix-free derivative products -------------------------------------
+    def vjp(self, x, y, gx=None, loads=True, stream=None):
+        """(J^T y, (dc/dPd)^T y, (dc/dQd)^T y); the load parts are None when
+        loads is False."""
+        import torch
+        gx = torch.empty(self.n, dtype=torch.float64, device="cuda") if gx is None else gx
+        gpd = gqd = None
+        if loads:
+            gpd = torch.empty(self.T * self.n_load, dtype=torch.float64, device="cuda")
+            gqd = torch.empty_like(gpd)
+        _check(lib().mpopf_vjp(self.h, _ptr(x), _ptr(y), _ptr(gx), _ptr(gpd), _ptr(gqd), _stream_ptr(stream)),
+               "mpopf_vjp")
+        return gx, gpd, gqd
+
+    def jvp(self, x, v, dpd=None, dqd=None, out=None, stream=None):
+        import torch
+        out = torch.empty(self.m, dtype=torch.float64, device="cuda") if out is None else out
+        _check(lib().mpopf_jvp(self.h, _ptr(x), _ptr(v), _ptr(dpd), _ptr(dqd), _ptr(out), _stream_ptr(stream)),
+               "mpopf_jvp")
+        return out
+
+    def hvp(self, x, lam, sigma, v, out=None, stream=None):
+        import torch
+        out = torch.empty(self.n, dtype=torch.float64, device="cuda") if out is None else out
+        _check(lib().mpopf_hvp(self.h, _ptr(x), _ptr(lam), float(sigma), _ptr(v), _ptr(out), _stream_ptr(stream)),
+               "mpopf_hvp")
+        return out
 
     def set_loads(self, pd, qd, stream=None):
         _check(lib().mpopf_set_loads(self.h, _ptr(pd), _ptr(qd), _stream_ptr(stream)), "mpopf_set_loads")

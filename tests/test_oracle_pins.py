@@ -494,3 +494,21 @@ def test_sincos_special_values():
     assert abs(s[2] - 0.5) <= 2 * np.spacing(0.5)
     assert abs(c[3]) <= 1e-16 and s[3] == 1.0
     assert s[4] == 1e-300
+
+
+def test_jvp_load_tangent_finite_difference():
+    """J v with load tangents equals the directional derivative of the
+    textbook c(x, Pd, Qd) (linear in the loads: exact up to rounding)."""
+    inst = synth.make_instance(22, 12, 20, 3, 7, 3)
+    o = oracle.Oracle(inst)
+    pt = synth.make_point(22, inst)
+    rng = np.random.default_rng(7)
+    dpd, dqd = rng.standard_normal(inst.pd.shape), rng.standard_normal(inst.qd.shape)
+    zero = np.zeros(o.n)
+    got = o.jvp(pt.x, zero, dpd=dpd, dqd=dqd)
+    o2 = oracle.Oracle(synth.Instance(net=inst.net, T=inst.T, pd=inst.pd + dpd, qd=inst.qd + dqd))
+    want = o2.cons_textbook(pt.x) - o.cons_textbook(pt.x)
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-12)
+    v = rng.standard_normal(o.n)
+    both = o.jvp(pt.x, v, dpd=dpd, dqd=dqd)
+    np.testing.assert_allclose(both, o.jvp(pt.x, v) + got, rtol=1e-13, atol=1e-13)
