@@ -193,6 +193,40 @@ int mpopf_jvp(mpopf_handle *h, const double *x, const double *v, const double *d
 int mpopf_hvp(mpopf_handle *h, const double *x, const double *lam, double sigma, const double *v, double *hv,
               void *stream);
 
+/* Batched full sweeps of many independent instances (uneven sizes and
+ * horizons) in ONE persistent kernel launch, replayed as a CUDA graph.  The
+ * paper evaluates one model per solver; this runs many, e.g. scenario or
+ * rolling-horizon instances, with the same values as mpopf_sweep on each.
+ *
+ * mpopf_batch_create: the handles (same device, kept alive by the caller until
+ *   mpopf_batch_destroy) become one batch; allocates the work list and the
+ *   graph (setup time).
+ * mpopf_batch_set_io: per-instance DEVICE pointers (host array of k
+ *   descriptors, copied; synchronises `stream`).
+ * mpopf_batch_sweep: one graph launch on `stream`: every instance's f, grad, c,
+ *   J, W and M, bitwise equal to mpopf_sweep on that instance.
+ * mpopf_batch_set_schedule / _get_schedule: instance order in the work list
+ *   (0 as given, 1 largest first), tile size (CTA-sized chunks per work item,
+ *   1..64), persistent CTAs per SM (0 = the occupancy maximum).
+ * mpopf_batch_tune: times every schedule (reps graph launches each, CUDA
+ *   events on `stream`) and keeps the fastest; *best_ms its time per sweep.
+ * mpopf_batch_status: synchronises the device; MPOPF_ERR_CUDA if a work item's
+ *   dependency wait (bounded, ~1 s) ran out in any launch since create. */
+typedef struct mpopf_batch mpopf_batch;
+typedef struct {
+  const double *x, *lam, *sigma_x, *dvec;   /* device, [n] [m] [n] [m] of that instance */
+  double sigma, delta_w;
+  double *f, *grad, *c, *jv, *hv, *kv;      /* device outputs */
+} mpopf_batch_io;
+int mpopf_batch_create(mpopf_handle *const *hs, int32_t k, mpopf_batch **out);
+int mpopf_batch_set_io(mpopf_batch *b, const mpopf_batch_io *io, void *stream);
+int mpopf_batch_sweep(mpopf_batch *b, void *stream);
+int mpopf_batch_set_schedule(mpopf_batch *b, int32_t order, int32_t tile_chunks, int32_t ctas_per_sm);
+int mpopf_batch_get_schedule(const mpopf_batch *b, int32_t *sched /* [3] */, int32_t *grid, int32_t *n_items);
+int mpopf_batch_tune(mpopf_batch *b, void *stream, int32_t reps, double *best_ms);
+int mpopf_batch_status(mpopf_batch *b);
+void mpopf_batch_destroy(mpopf_batch *b);
+
 /* Number of kernel launches one mpopf_eval call with these output bits makes. */
 int mpopf_launch_count(const mpopf_handle *h, unsigned outputs);
 

@@ -96,6 +96,23 @@ cudaError_t launch_patterns(const Dev &d, int32_t *jrow, int32_t *jcol, int32_t 
 
 void set_error(const std::string &msg);
 
+// Batched evaluation: many instances in one persistent launch.
+struct BatchIO {
+  const double *x, *lam, *sx, *dv;
+  double *f, *grad, *c, *jv, *hv, *kv;
+  double sigma, dw;
+};
+enum { ITEM_BRANCH = 0, ITEM_GEN = 1, ITEM_BUS = 2, ITEM_FSUM = 3 };
+struct BatchItem {
+  int32_t inst, kind, first, count;  // units [first, first + count) of that kind of that instance
+};
+// ctl layout: [0] next item, [1] wait-limit flag, [2, 2 + K) branch items done,
+// [2 + K, 2 + 2K) generator items done.
+cudaError_t batch_kernel_node(cudaKernelNodeParams *p, void **args, const Dev *devs, const BatchIO *io,
+                              const BatchItem *items, int32_t n_items, const int32_t *need, int32_t *ctl,
+                              int32_t K, int32_t grid);
+int batch_max_ctas_per_sm();
+
 }  // namespace mpopf
 
 // The handle (opaque to callers).

@@ -22,19 +22,28 @@ namespace {
 template <unsigned MASK>
 __device__ __forceinline__ unsigned eff(unsigned rt) { return MASK ? MASK : rt; }
 
-template <unsigned MASK>
 #ifndef MPOPF_BRANCH_MINB
 #define MPOPF_BRANCH_MINB 3
 #endif
-__global__ void __launch_bounds__(kBlock, MPOPF_BRANCH_MINB) k_branch(Dev d, unsigned rt, const double *__restrict__ x,
-                                                   const double *__restrict__ lam, const double *__restrict__ sx,
-                                                   const double *__restrict__ dv, double dw,
-                                                   double *__restrict__ grad, double *__restrict__ c,
-                                                   double *__restrict__ jv, double *__restrict__ hv,
-                                                   double *__restrict__ kv) {
+// Loads of values another CTA wrote in the same launch go through L2 (the
+// persistent batch kernel); separate launches may use the read-only path.
+template <bool COH>
+__device__ __forceinline__ double2 ld_rec(const double *p) {
+  return COH ? __ldcg(reinterpret_cast<const double2 *>(p)) : __ldg(reinterpret_cast<const double2 *>(p));
+}
+template <bool COH>
+__device__ __forceinline__ double ld_part(const double *p) {
+  return COH ? __ldcg(p) : *p;
+}
+
+template <unsigned MASK>
+__device__ __forceinline__ void branch_body(const Dev &d, int32_t tl, unsigned rt, const double *__restrict__ x,
+                                            const double *__restrict__ lam, const double *__restrict__ sx,
+                                            const double *__restrict__ dv, double dw, double *__restrict__ grad,
+                                            double *__restrict__ c, double *__restrict__ jv,
+                                            double *__restrict__ hv, double *__restrict__ kv) {
   const unsigned mk = eff<MASK>(rt);
   const int32_t L = d.L;
-  const int32_t tl = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
   if (tl >= d.T * L) return;
   const int32_t t = tl / L, l = tl - t * L;
   const int64_t TL = (int64_t)d.T * L;
@@ -209,18 +218,28 @@ __global__ void __launch_bounds__(kBlock, MPOPF_BRANCH_MINB) k_branch(Dev d, uns
           ((sxqt + dw) + Lqq_t) + D9t);
 }
 
+template <unsigned MASK>
+__global__ void __launch_bounds__(kBlock, MPOPF_BRANCH_MINB) k_branch(Dev d, unsigned rt, const double *__restrict__ x,
+                                                                      const double *__restrict__ lam,
+                                                                      const double *__restrict__ sx,
+                                                                      const double *__restrict__ dv, double dw,
+                                                                      double *__restrict__ grad, double *__restrict__ c,
+                                                                      double *__restrict__ jv, double *__restrict__ hv,
+                                                                      double *__restrict__ kv) {
+  branch_body<MASK>(d, (int32_t)(blockIdx.x * blockDim.x + threadIdx.x), rt, x, lam, sx, dv, dw, grad, c, jv, hv, kv);
+}
+
 // ---------------------------------------------------------------------------
 // Bus x period.
 // ---------------------------------------------------------------------------
-template <unsigned MASK>
-__global__ void __launch_bounds__(kBlock) k_bus(Dev d, unsigned rt, const double *__restrict__ x,
-                                                const double *__restrict__ lam, const double *__restrict__ sx,
-                                                const double *__restrict__ dv, double dw, double *__restrict__ grad,
-                                                double *__restrict__ c, double *__restrict__ jv,
-                                                double *__restrict__ hv, double *__restrict__ kv) {
+template <unsigned MASK, bool COH>
+__device__ __forceinline__ void bus_body(const Dev &d, int32_t idx, unsigned rt, const double *__restrict__ x,
+                                         const double *__restrict__ lam, const double *__restrict__ sx,
+                                         const double *__restrict__ dv, double dw, double *__restrict__ grad,
+                                         double *__restrict__ c, double *__restrict__ jv, double *__restrict__ hv,
+                                         double *__restrict__ kv) {
   const unsigned mk = eff<MASK>(rt);
   const int32_t N = d.N;
-  const int32_t idx = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
   if (idx >= d.T * N) return;
   const int32_t t = idx / N;
   const int32_t pos = idx - t * N;  // position in the processing order
@@ -257,7 +276,7 @@ __global__ void __launch_bounds__(kBlock) k_bus(Dev d, unsigned rt, const double
     if (have_rec) {
       for (int32_t e = s0; e < s1; ++e) {
         const int32_t q = __ldg(d.arc_perm + e);
-        const double2 pq = __ldg(reinterpret_cast<const double2 *>(R + (int64_t)q * kRec) + 2);
+        const double2 pq = ld_rec<COH>(R + (int64_t)q * kRec + 4);
         aP = aP - pq.x;
         aQ = aQ - pq.y;
       }
@@ -310,8 +329,8 @@ __global__ void __launch_bounds__(kBlock) k_bus(Dev d, unsigned rt, const double
   double Dvv = __ldg(sx + d.x_vm + tn) + dw;
   double Dvd = 0.0;
   for (int32_t q = s0; q < s1; ++q) {
-    const double2 *rp = reinterpret_cast<const double2 *>(R + (int64_t)q * kRec);
-    const double2 a = __ldg(rp), b = __ldg(rp + 1);  // (S_dd, S_vd), (S_vv, S_vtvf)
+    const double2 a = ld_rec<COH>(R + (int64_t)q * kRec);      // (S_dd, S_vd)
+    const double2 b = ld_rec<COH>(R + (int64_t)q * kRec + 2);  // (S_vv, S_vtvf)
     Ddd = Ddd + a.x;
     Dvv = Dvv + b.x;
     Dvd = (q == s0) ? a.y : Dvd + a.y;
@@ -319,8 +338,7 @@ __global__ void __launch_bounds__(kBlock) k_bus(Dev d, unsigned rt, const double
     if (info & (1 << 30)) {
       double cdd = negx(a.x), cvd = negx(a.y), cvv = b.y;
       for (int32_t o = __ldg(d.slot_next + q); o >= 0; o = __ldg(d.slot_next + o)) {
-        const double2 *ro = reinterpret_cast<const double2 *>(R + (int64_t)o * kRec);
-        const double2 a2 = __ldg(ro), b2 = __ldg(ro + 1);
+        const double2 a2 = ld_rec<COH>(R + (int64_t)o * kRec), b2 = ld_rec<COH>(R + (int64_t)o * kRec + 2);
         cdd = cdd - a2.x;
         cvd = cvd - a2.y;
         cvv = cvv + b2.y;
@@ -348,14 +366,27 @@ __global__ void __launch_bounds__(kBlock) k_bus(Dev d, unsigned rt, const double
 // Generator x period.
 // ---------------------------------------------------------------------------
 template <unsigned MASK>
-__global__ void __launch_bounds__(kBlock) k_gen(Dev d, unsigned rt, const double *__restrict__ x,
-                                                double sigma, const double *__restrict__ sx,
+__global__ void __launch_bounds__(kBlock) k_bus(Dev d, unsigned rt, const double *__restrict__ x,
+                                                const double *__restrict__ lam, const double *__restrict__ sx,
                                                 const double *__restrict__ dv, double dw, double *__restrict__ grad,
                                                 double *__restrict__ c, double *__restrict__ jv,
                                                 double *__restrict__ hv, double *__restrict__ kv) {
+  bus_body<MASK, false>(d, (int32_t)(blockIdx.x * blockDim.x + threadIdx.x), rt, x, lam, sx, dv, dw, grad, c, jv, hv,
+                        kv);
+}
+
+// ---------------------------------------------------------------------------
+// Generator x period.  Called by whole CTAs (the objective's block tree);
+// blk = index of the CTA-sized tile, where the tile's partial sum is stored.
+// ---------------------------------------------------------------------------
+template <unsigned MASK>
+__device__ __forceinline__ void gen_body(const Dev &d, int32_t tg, int32_t blk, unsigned rt,
+                                         const double *__restrict__ x, double sigma, const double *__restrict__ sx,
+                                         const double *__restrict__ dv, double dw, double *__restrict__ grad,
+                                         double *__restrict__ c, double *__restrict__ jv, double *__restrict__ hv,
+                                         double *__restrict__ kv) {
   const unsigned mk = eff<MASK>(rt);
   const int32_t G = d.G;
-  const int32_t tg = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
   const bool live = tg < d.T * G;
   const int32_t t = live ? tg / G : 0, g = live ? tg - t * G : 0;
   double pg = 0.0;
@@ -368,7 +399,7 @@ __global__ void __launch_bounds__(kBlock) k_gen(Dev d, unsigned rt, const double
       if ((int)threadIdx.x < s) red[threadIdx.x] = red[threadIdx.x] + red[threadIdx.x + s];
       __syncthreads();
     }
-    if (threadIdx.x == 0) d.fpart[blockIdx.x] = red[0];
+    if (threadIdx.x == 0) d.fpart[blk] = red[0];
   }
   if (!live) return;
   const double c2x2 = __ldg(d.gen_c2x2 + g);
@@ -399,7 +430,7 @@ __global__ void __launch_bounds__(kBlock) k_gen(Dev d, unsigned rt, const double
   double diag = ((__ldg(sx + d.x_pg + tg) + dw) + Wobj) + D8;
   if (t >= 1) {
     const double D10 = __ldg(dv + rr);
-    pr[k++] = -D10;
+    pr[k++] = negx(D10);
     diag = diag + D10;
   }
   if (t + 1 < d.T) diag = diag + __ldg(dv + rr + G);
@@ -411,19 +442,35 @@ __global__ void __launch_bounds__(kBlock) k_gen(Dev d, unsigned rt, const double
   qr[1 + rank] = (__ldg(sx + d.x_qg + tg) + dw) + D9;
 }
 
-// Objective: fixed-order reduction of the per-block partial sums.
-__global__ void __launch_bounds__(1024) k_fsum(const double *__restrict__ part, int32_t count,
-                                               double *__restrict__ f) {
-  __shared__ double red[1024];
+template <unsigned MASK>
+__global__ void __launch_bounds__(kBlock) k_gen(Dev d, unsigned rt, const double *__restrict__ x, double sigma,
+                                                const double *__restrict__ sx, const double *__restrict__ dv, double dw,
+                                                double *__restrict__ grad, double *__restrict__ c,
+                                                double *__restrict__ jv, double *__restrict__ hv,
+                                                double *__restrict__ kv) {
+  gen_body<MASK>(d, (int32_t)(blockIdx.x * blockDim.x + threadIdx.x), (int32_t)blockIdx.x, rt, x, sigma, sx, dv, dw,
+                 grad, c, jv, hv, kv);
+}
+
+// Objective: fixed-order reduction of the per-tile partial sums by one CTA of
+// kBlock threads (strided sequential sums, then a tree).
+template <bool COH>
+__device__ __forceinline__ void fsum_body(const double *part, int32_t count, double *f) {
+  __shared__ double red[kBlock];
   double a = 0.0;
-  for (int32_t i = threadIdx.x; i < count; i += 1024) a = a + part[i];
+  for (int32_t i = threadIdx.x; i < count; i += kBlock) a = a + ld_part<COH>(part + i);
   red[threadIdx.x] = a;
   __syncthreads();
-  for (int s = 512; s > 0; s >>= 1) {
+  for (int s = kBlock / 2; s > 0; s >>= 1) {
     if ((int)threadIdx.x < s) red[threadIdx.x] = red[threadIdx.x] + red[threadIdx.x + s];
     __syncthreads();
   }
   if (threadIdx.x == 0) *f = red[0];
+}
+
+__global__ void __launch_bounds__(kBlock) k_fsum(const double *__restrict__ part, int32_t count,
+                                                 double *__restrict__ f) {
+  fsum_body<false>(part, count, f);
 }
 
 unsigned grid_for(int64_t count) { return (unsigned)((count + kBlock - 1) / kBlock); }
@@ -465,11 +512,110 @@ void launch_all(const Dev &d, unsigned rt, const double *x, const double *lam, d
   }
   if (mk & MPOPF_OUT_OBJ) {
     Timed tm(prof, s, KIND_FSUM);
-    k_fsum<<<1, 1024, 0, s>>>(d.fpart, d.G > 0 ? d.fpart_n : 0, f);
+    k_fsum<<<1, kBlock, 0, s>>>(d.fpart, d.G > 0 ? d.fpart_n : 0, f);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Persistent batch kernel: CTAs take items (CTA-sized tiles of one instance's
+// branch, generator, bus or objective work) from a global counter in list
+// order.  The list holds every branch and generator item before any bus or
+// objective item, so an item's prerequisites were all taken earlier by running
+// CTAs; a bus item waits until its instance's branch items are done (their
+// incidence records written), an objective item until its generator items are.
+// The wait is bounded: past the limit the flag ctl[1] is set and the item is
+// computed anyway (the host reports an error).
+// ---------------------------------------------------------------------------
+constexpr long long kWaitLimit = 1LL << 22;  // x ~0.25 us sleep: about a second
+
+__device__ __forceinline__ int32_t ld_acquire(const int32_t *p) {
+  int32_t v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__global__ void __launch_bounds__(kBlock, MPOPF_BRANCH_MINB) k_batch(const Dev *__restrict__ devs,
+                                                                     const BatchIO *__restrict__ io,
+                                                                     const BatchItem *__restrict__ items,
+                                                                     int32_t n_items, const int32_t *__restrict__ need,
+                                                                     int32_t *__restrict__ ctl, int32_t K) {
+  __shared__ int32_t s_item;
+  for (;;) {
+    __syncthreads();  // the previous item is finished by every thread
+    if (threadIdx.x == 0) s_item = atomicAdd(ctl, 1);
+    __syncthreads();
+    const int32_t it = s_item;
+    if (it >= n_items) return;
+    const BatchItem I = items[it];
+    const Dev &d = devs[I.inst];
+    const BatchIO &b = io[I.inst];
+    if (I.kind >= ITEM_BUS) {
+      if (threadIdx.x == 0) {
+        const int32_t off = I.kind == ITEM_BUS ? 0 : K;
+        const int32_t *cnt = ctl + 2 + off + I.inst;
+        const int32_t target = need[off + I.inst];
+        long long spins = 0;
+        while (ld_acquire(cnt) < target) {
+          if (++spins > kWaitLimit) {
+            atomicExch(ctl + 1, 1);
+            break;
+          }
+          __nanosleep(256);
+        }
+      }
+      __syncthreads();
+    }
+    const int32_t end = I.first + I.count;
+    switch (I.kind) {
+      case ITEM_BRANCH:
+        for (int32_t c0 = I.first; c0 < end; c0 += kBlock)
+          if (c0 + (int32_t)threadIdx.x < end)
+            branch_body<MPOPF_OUT_ALL>(d, c0 + threadIdx.x, MPOPF_OUT_ALL, b.x, b.lam, b.sx, b.dv, b.dw, b.grad, b.c,
+                                       b.jv, b.hv, b.kv);
+        break;
+      case ITEM_GEN:
+        for (int32_t c0 = I.first; c0 < end; c0 += kBlock)  // whole CTA: the objective tile tree
+          gen_body<MPOPF_OUT_ALL>(d, c0 + threadIdx.x < end ? c0 + threadIdx.x : d.T * d.G, c0 / kBlock,
+                                  MPOPF_OUT_ALL, b.x, b.sigma, b.sx, b.dv, b.dw, b.grad, b.c, b.jv, b.hv, b.kv);
+        break;
+      case ITEM_BUS:
+        for (int32_t c0 = I.first; c0 < end; c0 += kBlock)
+          if (c0 + (int32_t)threadIdx.x < end)
+            bus_body<MPOPF_OUT_ALL, true>(d, c0 + threadIdx.x, MPOPF_OUT_ALL, b.x, b.lam, b.sx, b.dv, b.dw, b.grad,
+                                          b.c, b.jv, b.hv, b.kv);
+        break;
+      default:
+        fsum_body<true>(d.fpart, d.G > 0 ? d.fpart_n : 0, b.f);
+        break;
+    }
+    if (I.kind <= ITEM_GEN) {  // publish this item's writes, then count it done
+      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0) atomicAdd(ctl + 2 + (I.kind == ITEM_BRANCH ? 0 : K) + I.inst, 1);
+    }
   }
 }
 
 }  // namespace
+
+int batch_max_ctas_per_sm() {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch, kBlock, 0) != cudaSuccess) return 1;
+  return n > 0 ? n : 1;
+}
+
+cudaError_t batch_kernel_node(cudaKernelNodeParams *p, void **args, const Dev *devs, const BatchIO *io,
+                              const BatchItem *items, int32_t n_items, const int32_t *need, int32_t *ctl,
+                              int32_t K, int32_t grid) {
+  (void)devs; (void)io; (void)items; (void)n_items; (void)need; (void)ctl; (void)K;
+  p->func = reinterpret_cast<void *>(k_batch);
+  p->gridDim = dim3((unsigned)grid);
+  p->blockDim = dim3(kBlock);
+  p->sharedMemBytes = 0;
+  p->kernelParams = args;
+  p->extra = nullptr;
+  return cudaSuccess;
+}
 
 int eval_launch_count(const Dev &d, unsigned mk) {
   const unsigned rest = MPOPF_OUT_GRAD | MPOPF_OUT_CONS | MPOPF_OUT_JAC | MPOPF_OUT_HESS | MPOPF_OUT_KKT;

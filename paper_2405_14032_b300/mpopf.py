@@ -41,6 +41,11 @@ class _Pattern(ctypes.Structure):
                                 "xl", "xu", "gl", "gu")]
 
 
+class _BatchIO(ctypes.Structure):
+    _fields_ = [("x", _P), ("lam", _P), ("sigma_x", _P), ("dvec", _P), ("sigma", _D), ("delta_w", _D),
+                ("f", _P), ("grad", _P), ("c", _P), ("jv", _P), ("hv", _P), ("kv", _P)]
+
+
 _lib = None
 
 
@@ -84,6 +89,14 @@ def lib():
             "mpopf_vjp": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
             "mpopf_jvp": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
             "mpopf_hvp": (ctypes.c_int, [_P, _P, _P, _D, _P, _P, _P]),
+            "mpopf_batch_create": (ctypes.c_int, [_P, _I32, ctypes.POINTER(_P)]),
+            "mpopf_batch_set_io": (ctypes.c_int, [_P, _P, _P]),
+            "mpopf_batch_sweep": (ctypes.c_int, [_P, _P]),
+            "mpopf_batch_set_schedule": (ctypes.c_int, [_P, _I32, _I32, _I32]),
+            "mpopf_batch_get_schedule": (ctypes.c_int, [_P, _P, _P, _P]),
+            "mpopf_batch_tune": (ctypes.c_int, [_P, _P, _I32, _P]),
+            "mpopf_batch_status": (ctypes.c_int, [_P]),
+            "mpopf_batch_destroy": (None, [_P]),
             "mpopf_launch_count": (ctypes.c_int, [_P, _U]),
             "mpopf_profile_start": (ctypes.c_int, [_P, _I32]),
             "mpopf_profile_stop": (ctypes.c_int, [_P, _P, _P]),
@@ -103,6 +116,8 @@ def exported_symbols():
     return ["mpopf_setup", "mpopf_get_pattern", "mpopf_set_loads", "mpopf_eval", "mpopf_eval_obj",
             "mpopf_eval_grad", "mpopf_eval_cons", "mpopf_eval_jac", "mpopf_eval_hess", "mpopf_assemble_kkt",
             "mpopf_sweep", "mpopf_sweep_host", "mpopf_assemble_kkt_noalloc", "mpopf_vjp", "mpopf_jvp", "mpopf_hvp",
+            "mpopf_batch_create", "mpopf_batch_set_io", "mpopf_batch_sweep", "mpopf_batch_set_schedule",
+            "mpopf_batch_get_schedule", "mpopf_batch_tune", "mpopf_batch_status", "mpopf_batch_destroy",
             "mpopf_launch_count", "mpopf_profile_start", "mpopf_profile_stop",
             "mpopf_destroy", "mpopf_last_error"]
 
@@ -286,3 +301,59 @@ class Handle:
 
     def set_loads(self, pd, qd, stream=None):
         _check(lib().mpopf_set_loads(self.h, _ptr(pd), _ptr(qd), _stream_ptr(stream)), "mpopf_set_loads")
+
+
+class Batch:
+    """Many handles swept together by one persistent launch (CUDA graph)."""
+
+    def __init__(self, handles):
+        self.handles = list(handles)
+        arr = (_P * len(self.handles))(*[h.h.value for h in self.handles])
+        b = ctypes.c_void_p()
+        _check(lib().mpopf_batch_create(arr, len(self.handles), ctypes.byref(b)), "mpopf_batch_create")
+        self.b = b
+        self._io = None
+
+    def set_io(self, ios, stream=None):
+        """ios: per instance a dict with x, lam, sigma, sigma_x, dvec, delta_w and
+        output tensors f, grad, c, jv, hv, kv (all CUDA float64)."""
+        arr = (_BatchIO * len(ios))()
+        for i, io in enumerate(ios):
+            arr[i] = _BatchIO(_ptr(io["x"]), _ptr(io["lam"]), _ptr(io["sigma_x"]), _ptr(io["dvec"]),
+                              float(io["sigma"]), float(io["delta_w"]), _ptr(io["f"]), _ptr(io["grad"]),
+                              _ptr(io["c"]), _ptr(io["jv"]), _ptr(io["hv"]), _ptr(io["kv"]))
+        self._io = ios  # keep the tensors alive
+        _check(lib().mpopf_batch_set_io(self.b, arr, _stream_ptr(stream)), "mpopf_batch_set_io")
+
+    def sweep(self, stream=None):
+        _check(lib().mpopf_batch_sweep(self.b, _stream_ptr(stream)), "mpopf_batch_sweep")
+
+    def set_schedule(self, order, tile_chunks, ctas_per_sm):
+        _check(lib().mpopf_batch_set_schedule(self.b, order, tile_chunks, ctas_per_sm), "mpopf_batch_set_schedule")
+
+    def schedule(self):
+        s = np.zeros(3, np.int32)
+        g = np.zeros(1, np.int32)
+        k = np.zeros(1, np.int32)
+        _check(lib().mpopf_batch_get_schedule(self.b, s.ctypes.data, g.ctypes.data, k.ctypes.data),
+               "mpopf_batch_get_schedule")
+        return dict(order=int(s[0]), tile_chunks=int(s[1]), ctas_per_sm=int(s[2]), grid=int(g[0]), items=int(k[0]))
+
+    def tune(self, reps=5, stream=None):
+        best = np.zeros(1)
+        _check(lib().mpopf_batch_tune(self.b, _stream_ptr(stream), int(reps), best.ctypes.data), "mpopf_batch_tune")
+        return float(best[0])
+
+    def status(self):
+        _check(lib().mpopf_batch_status(self.b), "mpopf_batch_status")
+
+    def close(self):
+        if getattr(self, "b", None) is not None and self.b.value:
+            lib().mpopf_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
