@@ -207,9 +207,13 @@ int mpopf_hvp(mpopf_handle *h, const double *x, const double *lam, double sigma,
  *   J, W and M, bitwise equal to mpopf_sweep on that instance.
  * mpopf_batch_set_schedule / _get_schedule: instance order in the work list
  *   (0 as given, 1 largest first), tile size (CTA-sized chunks per work item,
- *   1..64), persistent CTAs per SM (0 = the occupancy maximum).
- * mpopf_batch_tune: times every schedule (reps graph launches each, CUDA
- *   events on `stream`) and keeps the fastest; *best_ms its time per sweep.
+ *   1..64), persistent CTAs per SM (0 = the occupancy maximum), periods per
+ *   dependency chunk (0 = the whole horizon; with P > 0 the bus work of a chunk
+ *   of P periods waits only for that chunk's branch work and overlaps the
+ *   next chunk's); sched[4] = (order, tile, CTAs per SM, P).
+ * mpopf_batch_tune: times candidate schedules (coordinate search; reps graph
+ *   launches each, CUDA events on `stream`) and keeps the fastest; *best_ms its
+ *   time per sweep.
  * mpopf_batch_status: synchronises the device; MPOPF_ERR_CUDA if a work item's
  *   dependency wait (bounded, ~1 s) ran out in any launch since create. */
 typedef struct mpopf_batch mpopf_batch;
@@ -221,8 +225,9 @@ typedef struct {
 int mpopf_batch_create(mpopf_handle *const *hs, int32_t k, mpopf_batch **out);
 int mpopf_batch_set_io(mpopf_batch *b, const mpopf_batch_io *io, void *stream);
 int mpopf_batch_sweep(mpopf_batch *b, void *stream);
-int mpopf_batch_set_schedule(mpopf_batch *b, int32_t order, int32_t tile_chunks, int32_t ctas_per_sm);
-int mpopf_batch_get_schedule(const mpopf_batch *b, int32_t *sched /* [3] */, int32_t *grid, int32_t *n_items);
+int mpopf_batch_set_schedule(mpopf_batch *b, int32_t order, int32_t tile_chunks, int32_t ctas_per_sm,
+                             int32_t chunk_periods);
+int mpopf_batch_get_schedule(const mpopf_batch *b, int32_t *sched /* [4] */, int32_t *grid, int32_t *n_items);
 int mpopf_batch_tune(mpopf_batch *b, void *stream, int32_t reps, double *best_ms);
 int mpopf_batch_status(mpopf_batch *b);
 void mpopf_batch_destroy(mpopf_batch *b);

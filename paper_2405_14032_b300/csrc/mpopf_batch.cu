@@ -2,11 +2,14 @@
 // uneven size in one persistent launch, replayed as a CUDA graph, with a
 // schedule chosen by measurement (autotuner).
 //
-// The work list holds CTA-sized tiles ("items") of every instance: all branch
-// tiles, then generator tiles, then bus tiles, then one objective item per
-// instance.  The schedule decides the instance order in the list (as given, or
-// largest first), the tile size (1, 2 or 4 CTA-sized chunks per item) and the
-// persistent grid (CTAs per SM).  Results do not depend on the schedule: each
+// The work list holds tiles ("items") of every instance: generator tiles,
+// branch tiles and bus tiles, then one objective item per instance.  The
+// horizon of each instance is cut into chunks of P periods; the bus tiles of a
+// chunk wait only for that chunk's branch tiles (whose incidence records they
+// sum) and come in the list one chunk behind them, so bus work overlaps branch
+// work.  The schedule decides the instance order (as given, or largest first),
+// the tile size (CTA-sized chunks per item), the persistent grid (CTAs per SM)
+// and P (0: the whole horizon).  Results do not depend on the schedule: each
 // value is computed by the same sequence of operations whichever CTA runs it.
 #include <algorithm>
 #include <cstring>
@@ -25,15 +28,15 @@ struct mpopf_batch {
   Dev *d_devs = nullptr;
   BatchIO *d_io = nullptr;
   BatchItem *d_items = nullptr;
-  int32_t *d_need = nullptr;  // [2K]: branch items, generator items per instance
-  int32_t *d_ctl = nullptr;   // [2 + 2K]
-  int32_t n_items = 0;
-  int32_t sched[3] = {0, 1, 0};  // order (0 given, 1 largest first), tile chunks, CTAs per SM (0 = max)
+  int32_t *d_need = nullptr;  // [n_counters]
+  int32_t *d_ctl = nullptr;   // [2 + n_counters]
+  int32_t n_items = 0, n_counters = 0, cap_counters = 0;
+  // order (0 given, 1 largest first), tile chunks, CTAs per SM (0 = max), periods per chunk (0 = all)
+  int32_t sched[4] = {0, 1, 0, 0};
   int32_t grid = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  void *args[7];
-  int32_t K_arg = 0;
+  void *args[6];
   bool io_set = false;
 };
 
@@ -54,26 +57,65 @@ cudaError_t build_items(mpopf_batch *b) {
   if (b->sched[0] == 1)
     std::stable_sort(order.begin(), order.end(),
                      [&](int32_t a, int32_t c) { return work_of(b->hs[a]->d) > work_of(b->hs[c]->d); });
-  const int32_t chunk = kBlock * std::max(1, b->sched[1]);
+  const int32_t tile = kBlock * std::max(1, b->sched[1]);
   std::vector<BatchItem> items;
-  std::vector<int32_t> need(2 * K, 0);
-  auto add = [&](int32_t kind, int32_t k, int64_t units) {
-    for (int64_t f = 0; f < units; f += chunk) {
-      items.push_back(BatchItem{k, kind, (int32_t)f, (int32_t)std::min<int64_t>(chunk, units - f)});
-      if (kind == ITEM_BRANCH) ++need[k];
-      if (kind == ITEM_GEN) ++need[K + k];
+  std::vector<int32_t> need;
+  auto add = [&](int32_t kind, int32_t k, int64_t u0, int64_t u1, int32_t wait, int32_t signal) {
+    for (int64_t f = u0; f < u1; f += tile) {
+      items.push_back(BatchItem{k, kind, (int32_t)f, (int32_t)std::min<int64_t>(tile, u1 - f), wait, signal});
+      if (signal >= 0) ++need[signal];
     }
   };
-  for (int32_t k : order) add(ITEM_BRANCH, k, (int64_t)b->hs[k]->d.T * b->hs[k]->d.L);
-  for (int32_t k : order) add(ITEM_GEN, k, (int64_t)b->hs[k]->d.T * b->hs[k]->d.G);
-  for (int32_t k : order) add(ITEM_BUS, k, (int64_t)b->hs[k]->d.T * b->hs[k]->d.N);
-  for (int32_t k : order) items.push_back(BatchItem{k, ITEM_FSUM, 0, 1});
+  std::vector<int32_t> gen_counter(K, -1);
+  for (int32_t k : order) {  // generator tiles first (no prerequisites)
+    const Dev &d = b->hs[k]->d;
+    gen_counter[k] = (int32_t)need.size();
+    need.push_back(0);
+    add(ITEM_GEN, k, 0, (int64_t)d.T * d.G, -1, gen_counter[k]);
+  }
+  // Branch and bus tiles by period chunks, the bus tiles one chunk behind.
+  struct Chunk { int32_t k, t0, t1, counter; };
+  std::vector<std::vector<Chunk>> per(K);
+  int32_t rounds = 0;
+  for (int32_t k : order) {
+    const Dev &d = b->hs[k]->d;
+    const int32_t P = b->sched[3] > 0 ? b->sched[3] : d.T;
+    for (int32_t t0 = 0; t0 < d.T; t0 += P) {
+      per[k].push_back(Chunk{k, t0, std::min(d.T, t0 + P), (int32_t)need.size()});
+      need.push_back(0);
+    }
+    rounds = std::max(rounds, (int32_t)per[k].size());
+  }
+  for (int32_t r = 0; r <= rounds; ++r)
+    for (int32_t k : order) {
+      const Dev &d = b->hs[k]->d;
+      if (r < (int32_t)per[k].size()) {
+        const Chunk &c = per[k][r];
+        add(ITEM_BRANCH, k, (int64_t)c.t0 * d.L, (int64_t)c.t1 * d.L, -1, c.counter);
+      }
+      if (r >= 1 && r - 1 < (int32_t)per[k].size()) {
+        const Chunk &c = per[k][r - 1];
+        add(ITEM_BUS, k, (int64_t)c.t0 * d.N, (int64_t)c.t1 * d.N, d.L > 0 ? c.counter : -1, -1);
+      }
+    }
+  for (int32_t k : order) items.push_back(BatchItem{k, ITEM_FSUM, 0, 1, gen_counter[k], -1});
+  cudaError_t e = cudaSuccess;
+  if ((int32_t)need.size() > b->cap_counters) {
+    cudaFree(b->d_need);
+    cudaFree(b->d_ctl);
+    b->d_need = nullptr;
+    b->d_ctl = nullptr;
+    e = cudaMalloc(&b->d_need, need.size() * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_ctl, (2 + need.size()) * sizeof(int32_t));
+    b->cap_counters = (int32_t)need.size();
+  }
   if (b->d_items) cudaFree(b->d_items);
   b->d_items = nullptr;
-  cudaError_t e = cudaMalloc(&b->d_items, items.size() * sizeof(BatchItem));
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_items, items.size() * sizeof(BatchItem));
   if (e == cudaSuccess) e = cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(b->d_need, need.data(), need.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
   b->n_items = (int32_t)items.size();
+  b->n_counters = (int32_t)need.size();
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
   const int per_sm = b->sched[2] > 0 ? std::min(b->sched[2], batch_max_ctas_per_sm()) : batch_max_ctas_per_sm();
@@ -93,22 +135,20 @@ cudaError_t build_graph(mpopf_batch *b) {
   mp.dst = b->d_ctl;
   mp.value = 0;
   mp.elementSize = 4;
-  mp.width = (size_t)(2 + 2 * b->K);
+  mp.width = (size_t)(2 + b->n_counters);
   mp.height = 1;
   mp.pitch = 0;
   cudaGraphNode_t nmem = nullptr, nker = nullptr;
   e = cudaGraphAddMemsetNode(&nmem, b->graph, nullptr, 0, &mp);
   if (e != cudaSuccess) return e;
-  b->K_arg = b->K;
   b->args[0] = &b->d_devs;
   b->args[1] = &b->d_io;
   b->args[2] = &b->d_items;
   b->args[3] = &b->n_items;
   b->args[4] = &b->d_need;
   b->args[5] = &b->d_ctl;
-  b->args[6] = &b->K_arg;
   cudaKernelNodeParams kp = {};
-  e = batch_kernel_node(&kp, b->args, b->d_devs, b->d_io, b->d_items, b->n_items, b->d_need, b->d_ctl, b->K, b->grid);
+  e = batch_kernel_node(&kp, b->args, b->grid);
   if (e == cudaSuccess) e = cudaGraphAddKernelNode(&nker, b->graph, &nmem, 1, &kp);
   if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
   return e;
@@ -143,8 +183,6 @@ int mpopf_batch_create(mpopf_handle *const *hs, int32_t k, mpopf_batch **out) {
   if (e == cudaSuccess) e = cudaMemcpy(b->d_devs, devs.data(), k * sizeof(Dev), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_io, k * sizeof(BatchIO));
   if (e == cudaSuccess) e = cudaMemset(b->d_io, 0, k * sizeof(BatchIO));
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_need, 2 * k * sizeof(int32_t));
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_ctl, (2 + 2 * k) * sizeof(int32_t));
   if (e == cudaSuccess) e = build_items(b);
   if (e == cudaSuccess) e = build_graph(b);
   if (e != cudaSuccess) {
@@ -193,12 +231,14 @@ int mpopf_batch_status(mpopf_batch *b) {
   return MPOPF_OK;
 }
 
-int mpopf_batch_set_schedule(mpopf_batch *b, int32_t order, int32_t tile_chunks, int32_t ctas_per_sm) {
-  if (!b || order < 0 || order > 1 || tile_chunks < 1 || tile_chunks > 64 || ctas_per_sm < 0)
+int mpopf_batch_set_schedule(mpopf_batch *b, int32_t order, int32_t tile_chunks, int32_t ctas_per_sm,
+                             int32_t chunk_periods) {
+  if (!b || order < 0 || order > 1 || tile_chunks < 1 || tile_chunks > 64 || ctas_per_sm < 0 || chunk_periods < 0)
     return fail(MPOPF_ERR_ARG, "mpopf_batch_set_schedule: bad argument");
   b->sched[0] = order;
   b->sched[1] = tile_chunks;
   b->sched[2] = ctas_per_sm;
+  b->sched[3] = chunk_periods;
   cudaError_t e = cudaDeviceSynchronize();
   if (e == cudaSuccess) e = build_items(b);
   if (e == cudaSuccess) e = build_graph(b);
@@ -208,7 +248,7 @@ int mpopf_batch_set_schedule(mpopf_batch *b, int32_t order, int32_t tile_chunks,
 
 int mpopf_batch_get_schedule(const mpopf_batch *b, int32_t *sched, int32_t *grid, int32_t *n_items) {
   if (!b || !sched) return fail(MPOPF_ERR_ARG, "mpopf_batch_get_schedule: NULL argument");
-  std::memcpy(sched, b->sched, sizeof b->sched);
+  std::memcpy(sched, b->sched, sizeof b->sched);  // [4]
   if (grid) *grid = b->grid;
   if (n_items) *n_items = b->n_items;
   return MPOPF_OK;
@@ -223,30 +263,42 @@ int mpopf_batch_tune(mpopf_batch *b, void *stream, int32_t reps, double *best_ms
     return fail(MPOPF_ERR_CUDA, "mpopf_batch_tune: event creation failed");
   const int maxc = batch_max_ctas_per_sm();
   double best = 1e300;
-  int32_t best_s[3] = {b->sched[0], b->sched[1], b->sched[2]};
+  int32_t best_s[4] = {b->sched[0], b->sched[1], b->sched[2], b->sched[3]};
+  int32_t maxT = 1;
+  for (auto *h : b->hs) maxT = std::max(maxT, h->d.T);
+  std::vector<int32_t> chunks = {0};
+  for (int32_t P : {1, 2, 4, 8, 16}) if (P < maxT) chunks.push_back(P);
   int rc = MPOPF_OK;
-  for (int32_t order = 0; order <= 1 && rc == MPOPF_OK; ++order)
-    for (int32_t tile : {1, 2, 4})
-      for (int32_t cps = 1; cps <= maxc; ++cps) {
-        rc = mpopf_batch_set_schedule(b, order, tile, cps);
-        if (rc != MPOPF_OK) break;
-        for (int w = 0; w < 2; ++w) cudaGraphLaunch(b->exec, st);
-        cudaEventRecord(e0, st);
-        for (int r = 0; r < reps; ++r) cudaGraphLaunch(b->exec, st);
-        cudaEventRecord(e1, st);
-        if (cudaEventSynchronize(e1) != cudaSuccess) { rc = fail(MPOPF_ERR_CUDA, "mpopf_batch_tune: launch failed"); break; }
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms / reps < best) {
-          best = ms / reps;
-          best_s[0] = order; best_s[1] = tile; best_s[2] = cps;
-        }
-      }
+  auto trial = [&](int32_t order, int32_t tile, int32_t cps, int32_t P) {
+    if (rc != MPOPF_OK) return;
+    rc = mpopf_batch_set_schedule(b, order, tile, cps, P);
+    if (rc != MPOPF_OK) return;
+    for (int w = 0; w < 2; ++w) cudaGraphLaunch(b->exec, st);
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < reps; ++r) cudaGraphLaunch(b->exec, st);
+    cudaEventRecord(e1, st);
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      rc = fail(MPOPF_ERR_CUDA, "mpopf_batch_tune: launch failed");
+      return;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms / reps < best) {
+      best = ms / reps;
+      best_s[0] = order; best_s[1] = tile; best_s[2] = cps; best_s[3] = P;
+    }
+  };
+  // coordinate search: grid and tile with whole-horizon chunks, then the chunk
+  // length, then the instance order
+  for (int32_t cps = 1; cps <= maxc; ++cps)
+    for (int32_t tile : {1, 2, 4}) trial(0, tile, cps, 0);
+  for (int32_t P : chunks) trial(0, best_s[1], best_s[2], P);
+  trial(1, best_s[1], best_s[2], best_s[3]);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc != MPOPF_OK) return rc;
   if (best_ms) *best_ms = best;
-  return mpopf_batch_set_schedule(b, best_s[0], best_s[1], best_s[2]);
+  return mpopf_batch_set_schedule(b, best_s[0], best_s[1], best_s[2], best_s[3]);
 }
 
 void mpopf_batch_destroy(mpopf_batch *b) {

@@ -105,12 +105,11 @@ struct BatchIO {
 enum { ITEM_BRANCH = 0, ITEM_GEN = 1, ITEM_BUS = 2, ITEM_FSUM = 3 };
 struct BatchItem {
   int32_t inst, kind, first, count;  // units [first, first + count) of that kind of that instance
+  int32_t wait, signal;              // dependency counter waited on / incremented when done (-1: none)
 };
-// ctl layout: [0] next item, [1] wait-limit flag, [2, 2 + K) branch items done,
-// [2 + K, 2 + 2K) generator items done.
-cudaError_t batch_kernel_node(cudaKernelNodeParams *p, void **args, const Dev *devs, const BatchIO *io,
-                              const BatchItem *items, int32_t n_items, const int32_t *need, int32_t *ctl,
-                              int32_t K, int32_t grid);
+// ctl layout: [0] next item, [1] wait-limit flag, [2 + c] dependency counter c;
+// need[c] = number of items that signal counter c.
+cudaError_t batch_kernel_node(cudaKernelNodeParams *p, void **args, int32_t grid);
 int batch_max_ctas_per_sm();
 
 }  // namespace mpopf

@@ -538,8 +538,16 @@ __global__ void __launch_bounds__(kBlock, MPOPF_BRANCH_MINB) k_batch(const Dev *
                                                                      const BatchIO *__restrict__ io,
                                                                      const BatchItem *__restrict__ items,
                                                                      int32_t n_items, const int32_t *__restrict__ need,
-                                                                     int32_t *__restrict__ ctl, int32_t K) {
+                                                                     int32_t *__restrict__ ctl) {
   __shared__ int32_t s_item;
+  __shared__ int32_t s_inst;
+  // The instance's descriptors, copied to shared memory when the instance
+  // changes (the bodies read their fields many times).
+  __shared__ __align__(16) unsigned char s_dev[sizeof(Dev)];
+  __shared__ __align__(16) unsigned char s_io[sizeof(BatchIO)];
+  if (threadIdx.x == 0) s_inst = -1;
+  const Dev &d = *reinterpret_cast<const Dev *>(s_dev);
+  const BatchIO &b = *reinterpret_cast<const BatchIO *>(s_io);
   for (;;) {
     __syncthreads();  // the previous item is finished by every thread
     if (threadIdx.x == 0) s_item = atomicAdd(ctl, 1);
@@ -547,13 +555,21 @@ __global__ void __launch_bounds__(kBlock, MPOPF_BRANCH_MINB) k_batch(const Dev *
     const int32_t it = s_item;
     if (it >= n_items) return;
     const BatchItem I = items[it];
-    const Dev &d = devs[I.inst];
-    const BatchIO &b = io[I.inst];
-    if (I.kind >= ITEM_BUS) {
+    if (I.inst != s_inst) {
+      const uint32_t *src = reinterpret_cast<const uint32_t *>(devs + I.inst);
+      for (int w = threadIdx.x; w < (int)(sizeof(Dev) / 4); w += kBlock)
+        reinterpret_cast<uint32_t *>(s_dev)[w] = src[w];
+      const uint32_t *srci = reinterpret_cast<const uint32_t *>(io + I.inst);
+      for (int w = threadIdx.x; w < (int)(sizeof(BatchIO) / 4); w += kBlock)
+        reinterpret_cast<uint32_t *>(s_io)[w] = srci[w];
+      __syncthreads();
+      if (threadIdx.x == 0) s_inst = I.inst;
+      // s_inst is read again only after the barrier at the top of the loop
+    }
+    if (I.wait >= 0) {
       if (threadIdx.x == 0) {
-        const int32_t off = I.kind == ITEM_BUS ? 0 : K;
-        const int32_t *cnt = ctl + 2 + off + I.inst;
-        const int32_t target = need[off + I.inst];
+        const int32_t *cnt = ctl + 2 + I.wait;
+        const int32_t target = need[I.wait];
         long long spins = 0;
         while (ld_acquire(cnt) < target) {
           if (++spins > kWaitLimit) {
@@ -588,10 +604,10 @@ __global__ void __launch_bounds__(kBlock, MPOPF_BRANCH_MINB) k_batch(const Dev *
         fsum_body<true>(d.fpart, d.G > 0 ? d.fpart_n : 0, b.f);
         break;
     }
-    if (I.kind <= ITEM_GEN) {  // publish this item's writes, then count it done
+    if (I.signal >= 0) {  // publish this item's writes, then count it done
       __threadfence();
       __syncthreads();
-      if (threadIdx.x == 0) atomicAdd(ctl + 2 + (I.kind == ITEM_BRANCH ? 0 : K) + I.inst, 1);
+      if (threadIdx.x == 0) atomicAdd(ctl + 2 + I.signal, 1);
     }
   }
 }
@@ -604,10 +620,7 @@ int batch_max_ctas_per_sm() {
   return n > 0 ? n : 1;
 }
 
-cudaError_t batch_kernel_node(cudaKernelNodeParams *p, void **args, const Dev *devs, const BatchIO *io,
-                              const BatchItem *items, int32_t n_items, const int32_t *need, int32_t *ctl,
-                              int32_t K, int32_t grid) {
-  (void)devs; (void)io; (void)items; (void)n_items; (void)need; (void)ctl; (void)K;
+cudaError_t batch_kernel_node(cudaKernelNodeParams *p, void **args, int32_t grid) {
   p->func = reinterpret_cast<void *>(k_batch);
   p->gridDim = dim3((unsigned)grid);
   p->blockDim = dim3(kBlock);
