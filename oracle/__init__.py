@@ -59,6 +59,9 @@ def load():
             "orc_cons_cstep": (None, [_P, _P, _P, _D, _P]),
             "orc_obj_textbook": (_D, [_P, _P]),
             "orc_branch_terms": (None, [_P, _P]),
+            "orc_ipm_prepare": (None, [_P] * 7 + [_D, _D, _D] + [_P] * 4),
+            "orc_ipm_rhs": (None, [_P] * 10 + [_D, _D, _D, _D, _P, _P]),
+            "orc_ipm_recover": (None, [_P] * 10 + [_D, _D, _D, _D] + [_P] * 6),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(lib, name)
@@ -220,6 +223,27 @@ class Oracle:
 
     def obj_textbook(self, x):
         return float(_lib.orc_obj_textbook(self.h, _ptr(_f64(x))))
+
+    # -- interior-point algebra around M (Sec. III-B) ------------------------
+    def ipm_prepare(self, x, s, zlx, zux, zls, zus, delta_w, delta_c, eps):
+        sigx, dvec, cvec, sigs = np.empty(self.n), np.empty(self.m), np.empty(self.m), np.empty(self.m)
+        _lib.orc_ipm_prepare(self.h, *[_ptr(_f64(a)) for a in (x, s, zlx, zux, zls, zus)], float(delta_w),
+                             float(delta_c), float(eps), _ptr(sigx), _ptr(dvec), _ptr(cvec), _ptr(sigs))
+        return sigx, dvec, cvec, sigs
+
+    def ipm_rhs(self, x, s, y, zlx, zux, zls, zus, grad, c, mu, delta_w, delta_c, eps):
+        rhs, w = np.empty(self.n), np.empty(self.m)
+        _lib.orc_ipm_rhs(self.h, *[_ptr(_f64(a)) for a in (x, s, y, zlx, zux, zls, zus, grad, c)], float(mu),
+                         float(delta_w), float(delta_c), float(eps), _ptr(rhs), _ptr(w))
+        return rhs, w
+
+    def ipm_recover(self, x, s, y, zlx, zux, zls, zus, c, dx, mu, delta_w, delta_c, eps):
+        outs = [np.empty(self.m), np.empty(self.m), np.empty(self.n), np.empty(self.n), np.empty(self.m),
+                np.empty(self.m)]
+        _lib.orc_ipm_recover(self.h, *[_ptr(_f64(a)) for a in (x, s, y, zlx, zux, zls, zus, c, dx)], float(mu),
+                             float(delta_w), float(delta_c), float(eps), *[_ptr(a) for a in outs])
+        ds, dy, dzlx, dzux, dzls, dzus = outs
+        return dict(ds=ds, dy=dy, dzlx=dzlx, dzux=dzux, dzls=dzls, dzus=dzus)
 
     def branch_terms(self):
         L = self.inst.net.n_branch

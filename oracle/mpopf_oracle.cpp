@@ -837,6 +837,131 @@ void orc_jvp(void* h, int64_t t0, int64_t t1, const double* x, const double* v, 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Interior-point algebra around the condensed matrix (Sec. III-B).
+// Bounds: x in [xl, xu] (Eq. 1g-1i), slacks s in [sl, su] with sl = gl, su = gu
+// for inequality rows and the relaxation gl - eps, gu + eps for equality rows
+// (gl == gu; the paper relaxes g(x) = 0 to s in [-eps, eps]).  An infinite
+// bound contributes nothing (its dual is taken as 0).
+//   Sigma = zl / (v - vl) + zu / (vu - v)                      (lower, then upper)
+//   C = 1 / fma(delta_c, Sigma_s, 1 + delta_c delta_w),  D = (Sigma_s + delta_w) C
+//   pzl = fma(zl, v - vl, -mu),  pzu = fma(zu, vu - v, -mu)
+//   base_x = (((grad - zl_x) + zu_x) + pzl_x/(x - xl)) - pzu_x/(xu - x)
+//   q_s = (((zu_s - zl_s) + y) + pzl_s/(s - sl)) - pzu_s/(su - s),  q_y = c - s
+//   rhs = base_x + J^T w with w = fma(C, q_s, D q_y) - y  (the two transposed
+//     products J^T y of p_x and J^T (C q_s + D q_y) merged into one)
+//   ds = C ((fma(delta_c, q_s, (J dx)) - q_y)     (eliminating rows 2-3 of Eq. 5)
+//   dy = fma(Sigma_s + delta_w, ds, -q_s)
+//   dzl = fma(-zl, dv, pzl) / (v - vl),  dzu = fma(zu, dv, pzu) / (vu - v)
+// ---------------------------------------------------------------------------
+namespace {
+struct BarrierTerms {
+  double sig, pzl, pzu, dl, du;
+  bool has_l, has_u;
+};
+BarrierTerms barrier(double v, double lo, double hi, double zl, double zu, double mu) {
+  BarrierTerms b{};
+  b.has_l = std::isfinite(lo);
+  b.has_u = std::isfinite(hi);
+  double a = 0.0, c = 0.0;
+  if (b.has_l) { b.dl = v - lo; a = zl / b.dl; b.pzl = std::fma(zl, b.dl, -mu); }
+  if (b.has_u) { b.du = hi - v; c = zu / b.du; b.pzu = std::fma(zu, b.du, -mu); }
+  b.sig = a + c;
+  return b;
+}
+void slack_bounds(double gl, double gu, double eps, double* sl, double* su) {
+  if (gl == gu) { *sl = gl - eps; *su = gu + eps; } else { *sl = gl; *su = gu; }
+}
+}  // namespace
+
+extern "C" {
+
+// Sigma_x [n]; D, C [m] (and Sigma_s [m] if not NULL).
+void orc_ipm_prepare(void* h, const double* x, const double* s, const double* zlx, const double* zux, const double* zls,
+                     const double* zus, double delta_w, double delta_c, double eps, double* sigx, double* dvec,
+                     double* cvec, double* sigs) {
+  const Model& M = *static_cast<Model*>(h);
+  std::vector<double> xl(M.n), xu(M.n), gl(M.m), gu(M.m);
+  orc_bounds(h, xl.data(), xu.data(), gl.data(), gu.data());
+  for (int64_t j = 0; j < M.n; ++j) sigx[j] = barrier(x[j], xl[j], xu[j], zlx[j], zux[j], 0.0).sig;
+  const double e = 1.0 + delta_c * delta_w;
+  for (int64_t i = 0; i < M.m; ++i) {
+    double sl, su;
+    slack_bounds(gl[i], gu[i], eps, &sl, &su);
+    const double sg = barrier(s[i], sl, su, zls[i], zus[i], 0.0).sig;
+    const double c = 1.0 / std::fma(delta_c, sg, e);
+    cvec[i] = c;
+    dvec[i] = (sg + delta_w) * c;
+    if (sigs) sigs[i] = sg;
+  }
+}
+
+// Condensed right-hand side rhs [n]; w [m] (if not NULL) is the row vector of
+// the merged transposed product.
+void orc_ipm_rhs(void* h, const double* x, const double* s, const double* y, const double* zlx, const double* zux,
+                 const double* zls, const double* zus, const double* grad, const double* c, double mu,
+                 double delta_w, double delta_c, double eps, double* rhs, double* w_out) {
+  const Model& M = *static_cast<Model*>(h);
+  std::vector<double> xl(M.n), xu(M.n), gl(M.m), gu(M.m), w(M.m), jt(M.n);
+  orc_bounds(h, xl.data(), xu.data(), gl.data(), gu.data());
+  const double e = 1.0 + delta_c * delta_w;
+  for (int64_t i = 0; i < M.m; ++i) {
+    double sl, su;
+    slack_bounds(gl[i], gu[i], eps, &sl, &su);
+    const BarrierTerms b = barrier(s[i], sl, su, zls[i], zus[i], mu);
+    double qs = (zus[i] - zls[i]) + y[i];
+    qs = qs + (b.has_l ? b.pzl / b.dl : 0.0);
+    qs = qs - (b.has_u ? b.pzu / b.du : 0.0);
+    const double qy = c[i] - s[i];
+    const double cc = 1.0 / std::fma(delta_c, b.sig, e);
+    const double dd = (b.sig + delta_w) * cc;
+    w[i] = std::fma(cc, qs, dd * qy) - y[i];
+  }
+  orc_vjp(h, 0, M.T, x, w.data(), jt.data(), nullptr, nullptr);
+  for (int64_t j = 0; j < M.n; ++j) {
+    const BarrierTerms b = barrier(x[j], xl[j], xu[j], zlx[j], zux[j], mu);
+    double base = (grad[j] - zlx[j]) + zux[j];
+    base = base + (b.has_l ? b.pzl / b.dl : 0.0);
+    base = base - (b.has_u ? b.pzu / b.du : 0.0);
+    rhs[j] = base + jt[j];
+  }
+  if (w_out) for (int64_t i = 0; i < M.m; ++i) w_out[i] = w[i];
+}
+
+// Step recovery from dx [n]: ds, dy, dzl_s, dzu_s [m]; dzl_x, dzu_x [n].
+void orc_ipm_recover(void* h, const double* x, const double* s, const double* y, const double* zlx, const double* zux,
+                     const double* zls, const double* zus, const double* c, const double* dx, double mu,
+                     double delta_w, double delta_c, double eps, double* ds, double* dy, double* dzlx,
+                     double* dzux, double* dzls, double* dzus) {
+  const Model& M = *static_cast<Model*>(h);
+  std::vector<double> xl(M.n), xu(M.n), gl(M.m), gu(M.m), jdx(M.m);
+  orc_bounds(h, xl.data(), xu.data(), gl.data(), gu.data());
+  orc_jvp(h, 0, M.T, x, dx, nullptr, nullptr, jdx.data());
+  const double e = 1.0 + delta_c * delta_w;
+  for (int64_t i = 0; i < M.m; ++i) {
+    double sl, su;
+    slack_bounds(gl[i], gu[i], eps, &sl, &su);
+    const BarrierTerms b = barrier(s[i], sl, su, zls[i], zus[i], mu);
+    double qs = (zus[i] - zls[i]) + y[i];
+    qs = qs + (b.has_l ? b.pzl / b.dl : 0.0);
+    qs = qs - (b.has_u ? b.pzu / b.du : 0.0);
+    const double qy = c[i] - s[i];
+    const double cc = 1.0 / std::fma(delta_c, b.sig, e);
+    const double d = cc * (std::fma(delta_c, qs, jdx[i]) - qy);
+    ds[i] = d;
+    dy[i] = std::fma(b.sig + delta_w, d, -qs);
+    dzls[i] = b.has_l ? std::fma(-zls[i], d, b.pzl) / b.dl : 0.0;
+    dzus[i] = b.has_u ? std::fma(zus[i], d, b.pzu) / b.du : 0.0;
+  }
+  for (int64_t j = 0; j < M.n; ++j) {
+    const BarrierTerms b = barrier(x[j], xl[j], xu[j], zlx[j], zux[j], mu);
+    dzlx[j] = b.has_l ? std::fma(-zlx[j], dx[j], b.pzl) / b.dl : 0.0;
+    dzux[j] = b.has_u ? std::fma(zux[j], dx[j], b.pzu) / b.du : 0.0;
+  }
+}
+
+}  // extern "C"
+
 // The canonical sin/cos (for pins against the C library).
 void orc_sincos(const double* x, int64_t n, double* s, double* c) {
   for (int64_t i = 0; i < n; ++i) sincos_cw(x[i], &s[i], &c[i]);

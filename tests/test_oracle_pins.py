@@ -512,3 +512,101 @@ def test_jvp_load_tangent_finite_difference():
     v = rng.standard_normal(o.n)
     both = o.jvp(pt.x, v, dpd=dpd, dqd=dqd)
     np.testing.assert_allclose(both, o.jvp(pt.x, v) + got, rtol=1e-13, atol=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# Interior-point algebra around M (Sec. III-B): pinned by a dense solve of the
+# full lifted KKT system of Eq. (5)
+# ---------------------------------------------------------------------------
+def _ipm_point(inst, o, seed, eps):
+    rng = np.random.default_rng(seed)
+    xl, xu, gl, gu = o.bounds()
+    pt = synth.make_point(seed, inst)
+    x = pt.x.copy()
+    fin = np.isfinite(xl) & np.isfinite(xu)
+    x[fin] = xl[fin] + (0.1 + 0.8 * rng.uniform(size=fin.sum())) * (xu[fin] - xl[fin])
+    sl = np.where(gl == gu, gl - eps, gl)
+    su = np.where(gl == gu, gu + eps, gu)
+    both = np.isfinite(sl) & np.isfinite(su)
+    s = np.where(np.isfinite(su), su - rng.uniform(0.1, 1.0, o.m), sl + rng.uniform(0.1, 1.0, o.m))
+    s[both] = sl[both] + (0.1 + 0.8 * rng.uniform(size=both.sum())) * (su[both] - sl[both])
+    zlx = np.where(np.isfinite(xl), rng.uniform(0.1, 2.0, o.n), 0.0)
+    zux = np.where(np.isfinite(xu), rng.uniform(0.1, 2.0, o.n), 0.0)
+    zls = np.where(np.isfinite(sl), rng.uniform(0.1, 2.0, o.m), 0.0)
+    zus = np.where(np.isfinite(su), rng.uniform(0.1, 2.0, o.m), 0.0)
+    y = rng.uniform(-1, 1, o.m)
+    return x, s, y, zlx, zux, zls, zus, xl, xu, sl, su
+
+
+def test_ipm_condensation_solves_full_lifted_system():
+    """Delta x from M_cond dx = q_x + A^T (C q_s + D q_y), with Delta s, Delta y
+    and the Delta z recovered from it, solves the full 7-block system of
+    Eq. (5) (assembled densely), so the condensation, the right-hand side and
+    the recovery formulas are those of the printed block system."""
+    inst = synth.make_instance(61, 5, 7, 2, 3, 2)
+    o = oracle.Oracle(inst)
+    n, m = o.n, o.m
+    eps, mu, dw, dc = 1e-2, 0.05, 1e-3, 1e-4
+    x, s, y, zlx, zux, zls, zus, xl, xu, sl, su = _ipm_point(inst, o, 62, eps)
+    lam = -y  # W = sigma grad^2 f + sum lam_i grad^2 c_i with the paper's p_x = grad f - J^T y
+    r = o.eval(x, lam, 1.0)
+    jr, jc = o.jac_pattern()
+    A = H.dense_jac(jr, jc, r["jv"], m, n)
+    hr, hc = o.hess_pattern()
+    W = H.dense_sym(hr, hc, r["hv"], n)
+    sigx, dvec, cvec, sigs = o.ipm_prepare(x, s, zlx, zux, zls, zus, dw, dc, eps)
+    rowptr, cols, kv = o.kkt_csr(x, lam, 1.0, sigx, dvec, dw)
+    Mc = H.csr_to_dense_sym(rowptr, cols, kv, n)
+    rhs, _ = o.ipm_rhs(x, s, y, zlx, zux, zls, zus, r["g"], r["c"], mu, dw, dc, eps)
+    dx = np.linalg.solve(Mc, rhs)
+    rec = o.ipm_recover(x, s, y, zlx, zux, zls, zus, r["c"], dx, mu, dw, dc, eps)
+    # full system
+    fl, fu = np.isfinite(xl), np.isfinite(xu)
+    gl_, gu_ = np.isfinite(sl), np.isfinite(su)
+    il, iu, jl, ju = np.nonzero(fl)[0], np.nonzero(fu)[0], np.nonzero(gl_)[0], np.nonzero(gu_)[0]
+    sizes = [n, m, m, il.size, iu.size, jl.size, ju.size]
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    K = np.zeros((off[-1], off[-1]))
+    X, S_, Y, ZLX, ZUX, ZLS, ZUS = (slice(off[k], off[k + 1]) for k in range(7))
+    K[X, X] = W + dw * np.eye(n)
+    K[X, Y] = A.T
+    K[X, ZLX][il, np.arange(il.size)] = -1.0
+    K[X, ZUX][iu, np.arange(iu.size)] = 1.0
+    K[S_, S_] = dw * np.eye(m)
+    K[S_, Y] = -np.eye(m)
+    K[S_, ZLS][jl, np.arange(jl.size)] = -1.0
+    K[S_, ZUS][ju, np.arange(ju.size)] = 1.0
+    K[Y, X] = A
+    K[Y, S_] = -np.eye(m)
+    K[Y, Y] = -dc * np.eye(m)
+    K[ZLX, X][np.arange(il.size), il] = zlx[il]
+    K[ZLX, ZLX] = np.diag(x[il] - xl[il])
+    K[ZUX, X][np.arange(iu.size), iu] = -zux[iu]
+    K[ZUX, ZUX] = np.diag(xu[iu] - x[iu])
+    K[ZLS, S_][np.arange(jl.size), jl] = zls[jl]
+    K[ZLS, ZLS] = np.diag(s[jl] - sl[jl])
+    K[ZUS, S_][np.arange(ju.size), ju] = -zus[ju]
+    K[ZUS, ZUS] = np.diag(su[ju] - s[ju])
+    p = np.concatenate([r["g"] - A.T @ y - zlx + zux, -zls + zus + y, r["c"] - s,
+                        zlx[il] * (x[il] - xl[il]) - mu, zux[iu] * (xu[iu] - x[iu]) - mu,
+                        zls[jl] * (s[jl] - sl[jl]) - mu, zus[ju] * (su[ju] - s[ju]) - mu])
+    full = np.linalg.solve(K, p)
+    scale = np.abs(full).max()
+    np.testing.assert_allclose(dx, full[X], rtol=0, atol=1e-9 * scale)
+    np.testing.assert_allclose(rec["ds"], full[S_], rtol=0, atol=1e-9 * scale)
+    np.testing.assert_allclose(rec["dy"], full[Y], rtol=0, atol=1e-9 * scale)
+    np.testing.assert_allclose(rec["dzlx"][il], full[ZLX], rtol=0, atol=1e-9 * scale)
+    np.testing.assert_allclose(rec["dzux"][iu], full[ZUX], rtol=0, atol=1e-9 * scale)
+    np.testing.assert_allclose(rec["dzls"][jl], full[ZLS], rtol=0, atol=1e-9 * scale)
+    np.testing.assert_allclose(rec["dzus"][ju], full[ZUS], rtol=0, atol=1e-9 * scale)
+    assert np.all(rec["dzlx"][~fl] == 0) and np.all(rec["dzus"][~gu_] == 0)
+    # The recovery as printed, C (dc q_s - (q_y + A dx)), does not solve Eq. (5);
+    # C (A dx + dc q_s - q_y) (eliminating its rows 2 and 3) does (above).
+    with np.errstate(invalid="ignore", divide="ignore"):
+        qs = (zus - zls) + y + np.where(gl_, (zls * (s - sl) - mu) / (s - sl), 0.0) \
+            - np.where(gu_, (zus * (su - s) - mu) / (su - s), 0.0)
+    printed = cvec * (dc * qs - ((r["c"] - s) + A @ dx))
+    assert np.abs(printed - full[S_]).max() > 1e-3 * scale
+    # C and D are the paper's: C = (dc Sigma_s + (1 + dc dw) I)^-1, D = (Sigma_s + dw I) C
+    np.testing.assert_allclose(cvec, 1.0 / (dc * sigs + 1.0 + dc * dw), rtol=1e-15)
+    np.testing.assert_allclose(dvec, (sigs + dw) * cvec, rtol=1e-15)
