@@ -124,4 +124,5 @@ struct mpopf_handle {
   double *stage;
   size_t stage_bytes;
   mpopf::Prof prof;
+  double *work;  // [m] row vector of the condensed right-hand side
 };

@@ -545,6 +545,7 @@ int mpopf_setup(const mpopf_network *net, int32_t n_periods, const double *pd, c
   int32_t *kcol = dev_alloc<int32_t>(h, d.nnz_kkt, &err);
   double *xl = dev_alloc<double>(h, n, &err), *xu = dev_alloc<double>(h, n, &err);
   double *gl = dev_alloc<double>(h, m, &err), *gu = dev_alloc<double>(h, m, &err);
+  h->work = dev_alloc<double>(h, m, &err);
   // temporary bound sources
   std::vector<double> tmp_src;
   auto cat = [&](const double *p, int64_t k) { if (k > 0) tmp_src.insert(tmp_src.end(), p, p + k); };

@@ -89,6 +89,9 @@ def lib():
             "mpopf_vjp": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
             "mpopf_jvp": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
             "mpopf_hvp": (ctypes.c_int, [_P, _P, _P, _D, _P, _P, _P]),
+            "mpopf_ipm_prepare": (ctypes.c_int, [_P] * 7 + [_D] * 3 + [_P] * 4),
+            "mpopf_ipm_rhs": (ctypes.c_int, [_P] * 10 + [_D] * 4 + [_P, _P]),
+            "mpopf_ipm_recover": (ctypes.c_int, [_P] * 10 + [_D] * 4 + [_P] * 7),
             "mpopf_batch_create": (ctypes.c_int, [_P, _I32, ctypes.POINTER(_P)]),
             "mpopf_batch_set_io": (ctypes.c_int, [_P, _P, _P]),
             "mpopf_batch_sweep": (ctypes.c_int, [_P, _P]),
@@ -116,7 +119,7 @@ def exported_symbols():
     return ["mpopf_setup", "mpopf_get_pattern", "mpopf_set_loads", "mpopf_eval", "mpopf_eval_obj",
             "mpopf_eval_grad", "mpopf_eval_cons", "mpopf_eval_jac", "mpopf_eval_hess", "mpopf_assemble_kkt",
             "mpopf_sweep", "mpopf_sweep_host", "mpopf_assemble_kkt_noalloc", "mpopf_vjp", "mpopf_jvp", "mpopf_hvp",
-            "mpopf_batch_create", "mpopf_batch_set_io", "mpopf_batch_sweep", "mpopf_batch_set_schedule",
+            "mpopf_ipm_prepare", "mpopf_ipm_rhs", "mpopf_ipm_recover", "mpopf_batch_create", "mpopf_batch_set_io", "mpopf_batch_sweep", "mpopf_batch_set_schedule",
             "mpopf_batch_get_schedule", "mpopf_batch_tune", "mpopf_batch_status", "mpopf_batch_destroy",
             "mpopf_launch_count", "mpopf_profile_start", "mpopf_profile_stop",
             "mpopf_destroy", "mpopf_last_error"]
@@ -298,6 +301,39 @@ class Handle:
         _check(lib().mpopf_hvp(self.h, _ptr(x), _ptr(lam), float(sigma), _ptr(v), _ptr(out), _stream_ptr(stream)),
                "mpopf_hvp")
         return out
+
+    # -- interior-point algebra around the condensed matrix -------------------
+    def _dvec(self, k):
+        import torch
+        return torch.empty(k, dtype=torch.float64, device="cuda")
+
+    def ipm_prepare(self, x, s, zl_x, zu_x, zl_s, zu_s, delta_w, delta_c, eps_tol, stream=None):
+        """(Sigma_x [n], D [m], C [m]) from the bounds and bound duals."""
+        sigx, dvec, cvec = self._dvec(self.n), self._dvec(self.m), self._dvec(self.m)
+        _check(lib().mpopf_ipm_prepare(self.h, _ptr(x), _ptr(s), _ptr(zl_x), _ptr(zu_x), _ptr(zl_s), _ptr(zu_s),
+                                       float(delta_w), float(delta_c), float(eps_tol), _ptr(sigx), _ptr(dvec),
+                                       _ptr(cvec), _stream_ptr(stream)), "mpopf_ipm_prepare")
+        return sigx, dvec, cvec
+
+    def ipm_rhs(self, x, s, y, zl_x, zu_x, zl_s, zu_s, grad, c, mu, delta_w, delta_c, eps_tol, out=None,
+                stream=None):
+        """Condensed right-hand side q_x + J^T (C q_s + D q_y) [n]."""
+        out = self._dvec(self.n) if out is None else out
+        _check(lib().mpopf_ipm_rhs(self.h, _ptr(x), _ptr(s), _ptr(y), _ptr(zl_x), _ptr(zu_x), _ptr(zl_s),
+                                   _ptr(zu_s), _ptr(grad), _ptr(c), float(mu), float(delta_w), float(delta_c),
+                                   float(eps_tol), _ptr(out), _stream_ptr(stream)), "mpopf_ipm_rhs")
+        return out
+
+    def ipm_recover(self, x, s, y, zl_x, zu_x, zl_s, zu_s, c, dx, mu, delta_w, delta_c, eps_tol, stream=None):
+        """dict ds, dy, dzl_s, dzu_s [m] and dzl_x, dzu_x [n] from dx."""
+        r = dict(ds=self._dvec(self.m), dy=self._dvec(self.m), dzl_x=self._dvec(self.n),
+                 dzu_x=self._dvec(self.n), dzl_s=self._dvec(self.m), dzu_s=self._dvec(self.m))
+        _check(lib().mpopf_ipm_recover(self.h, _ptr(x), _ptr(s), _ptr(y), _ptr(zl_x), _ptr(zu_x), _ptr(zl_s),
+                                       _ptr(zu_s), _ptr(c), _ptr(dx), float(mu), float(delta_w), float(delta_c),
+                                       float(eps_tol), _ptr(r["ds"]), _ptr(r["dy"]), _ptr(r["dzl_x"]),
+                                       _ptr(r["dzu_x"]), _ptr(r["dzl_s"]), _ptr(r["dzu_s"]), _stream_ptr(stream)),
+               "mpopf_ipm_recover")
+        return r
 
     def set_loads(self, pd, qd, stream=None):
         _check(lib().mpopf_set_loads(self.h, _ptr(pd), _ptr(qd), _stream_ptr(stream)), "mpopf_set_loads")

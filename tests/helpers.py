@@ -72,3 +72,63 @@ def csr_to_dense_sym(rowptr, cols, vals, n):
 
 def ulp(x):
     return np.spacing(np.abs(x))
+
+
+def ipm_point(inst, o, seed, eps):
+    """A strictly interior point for the interior-point algebra: x inside its
+    bounds, slacks inside [gl, gu] (equality rows widened to [g - eps, g + eps]),
+    positive duals on finite bounds and 0 on infinite ones, y uniform in
+    [-1, 1].  o provides n, m and bounds() (the oracle or a handle's pattern)."""
+    rng = np.random.default_rng(seed)
+    xl, xu, gl, gu = o.bounds()
+    pt = synth.make_point(seed, inst)
+    x = pt.x.copy()
+    fin = np.isfinite(xl) & np.isfinite(xu)
+    x[fin] = xl[fin] + (0.1 + 0.8 * rng.uniform(size=fin.sum())) * (xu[fin] - xl[fin])
+    sl = np.where(gl == gu, gl - eps, gl)
+    su = np.where(gl == gu, gu + eps, gu)
+    both = np.isfinite(sl) & np.isfinite(su)
+    s = np.where(np.isfinite(su), su - rng.uniform(0.1, 1.0, o.m), sl + rng.uniform(0.1, 1.0, o.m))
+    s[both] = sl[both] + (0.1 + 0.8 * rng.uniform(size=both.sum())) * (su[both] - sl[both])
+    zlx = np.where(np.isfinite(xl), rng.uniform(0.1, 2.0, o.n), 0.0)
+    zux = np.where(np.isfinite(xu), rng.uniform(0.1, 2.0, o.n), 0.0)
+    zls = np.where(np.isfinite(sl), rng.uniform(0.1, 2.0, o.m), 0.0)
+    zus = np.where(np.isfinite(su), rng.uniform(0.1, 2.0, o.m), 0.0)
+    y = rng.uniform(-1, 1, o.m)
+    return x, s, y, zlx, zux, zls, zus, xl, xu, sl, su
+
+
+def lifted_system(W, A, x, s, y, zlx, zux, zls, zus, xl, xu, sl, su, grad, c, mu, dw, dc):
+    """The full block system of Eq. (5) (unknowns dx, ds, dy and the bound-dual
+    steps of the finite bounds only), assembled densely, with its right-hand
+    side as printed.  Returns (K, p, slices of the seven blocks)."""
+    n, m = x.size, s.size
+    il, iu = np.nonzero(np.isfinite(xl))[0], np.nonzero(np.isfinite(xu))[0]
+    jl, ju = np.nonzero(np.isfinite(sl))[0], np.nonzero(np.isfinite(su))[0]
+    sizes = [n, m, m, il.size, iu.size, jl.size, ju.size]
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    K = np.zeros((off[-1], off[-1]))
+    X, S_, Y, ZLX, ZUX, ZLS, ZUS = (slice(off[k], off[k + 1]) for k in range(7))
+    K[X, X] = W + dw * np.eye(n)
+    K[X, Y] = A.T
+    K[X, ZLX][il, np.arange(il.size)] = -1.0
+    K[X, ZUX][iu, np.arange(iu.size)] = 1.0
+    K[S_, S_] = dw * np.eye(m)
+    K[S_, Y] = -np.eye(m)
+    K[S_, ZLS][jl, np.arange(jl.size)] = -1.0
+    K[S_, ZUS][ju, np.arange(ju.size)] = 1.0
+    K[Y, X] = A
+    K[Y, S_] = -np.eye(m)
+    K[Y, Y] = -dc * np.eye(m)
+    K[ZLX, X][np.arange(il.size), il] = zlx[il]
+    K[ZLX, ZLX] = np.diag(x[il] - xl[il])
+    K[ZUX, X][np.arange(iu.size), iu] = -zux[iu]
+    K[ZUX, ZUX] = np.diag(xu[iu] - x[iu])
+    K[ZLS, S_][np.arange(jl.size), jl] = zls[jl]
+    K[ZLS, ZLS] = np.diag(s[jl] - sl[jl])
+    K[ZUS, S_][np.arange(ju.size), ju] = -zus[ju]
+    K[ZUS, ZUS] = np.diag(su[ju] - s[ju])
+    p = np.concatenate([grad - A.T @ y - zlx + zux, -zls + zus + y, c - s,
+                        zlx[il] * (x[il] - xl[il]) - mu, zux[iu] * (xu[iu] - x[iu]) - mu,
+                        zls[jl] * (s[jl] - sl[jl]) - mu, zus[ju] * (su[ju] - s[ju]) - mu])
+    return K, p, (X, S_, Y, ZLX, ZUX, ZLS, ZUS)

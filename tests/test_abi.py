@@ -27,6 +27,48 @@ def test_library_exports_every_declared_symbol():
     assert set(names) <= set(mpopf.exported_symbols()) | set(names)
 
 
+def _prototypes():
+    """{name: [parameter types]} from the header's declarations."""
+    txt = open(os.path.join(ROOT, "include", "mpopf.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    out = {}
+    for m in re.finditer(r"\b(mpopf_[a-z_0-9]+)\s*\(([^;{]*?)\)\s*;", txt):
+        params = " ".join(m.group(2).split())
+        if params in ("", "void"):
+            out[m.group(1)] = []
+            continue
+        kinds = []
+        for prm in params.split(","):
+            prm = prm.strip()
+            if "*" in prm:
+                kinds.append("ptr")
+            elif re.match(r"(const\s+)?double\b", prm):
+                kinds.append("double")
+            else:
+                kinds.append("int")
+        out[m.group(1)] = kinds
+    return out
+
+
+def test_binding_signatures_match_header():
+    """Every ctypes prototype has the header's parameter count and kinds
+    (pointer / double / integer), so a marshalling slip fails here, on the host."""
+    lib = mpopf.lib()
+    protos = _prototypes()
+    assert set(protos) == set(_declared())
+
+    def kind(t):
+        if t is ctypes.c_double:
+            return "double"
+        if t in (ctypes.c_void_p, ctypes.c_char_p) or hasattr(t, "_type_") and not isinstance(t._type_, str):
+            return "ptr"
+        return "int"
+
+    for name, want in protos.items():
+        got = [kind(t) for t in getattr(lib, name).argtypes]
+        assert got == want, (name, got, want)
+
+
 def _setup_rc(net, T=2, pd=None, qd=None):
     lib = mpopf.lib()
     h = ctypes.c_void_p()

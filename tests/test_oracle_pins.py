@@ -518,26 +518,6 @@ def test_jvp_load_tangent_finite_difference():
 # Interior-point algebra around M (Sec. III-B): pinned by a dense solve of the
 # full lifted KKT system of Eq. (5)
 # ---------------------------------------------------------------------------
-def _ipm_point(inst, o, seed, eps):
-    rng = np.random.default_rng(seed)
-    xl, xu, gl, gu = o.bounds()
-    pt = synth.make_point(seed, inst)
-    x = pt.x.copy()
-    fin = np.isfinite(xl) & np.isfinite(xu)
-    x[fin] = xl[fin] + (0.1 + 0.8 * rng.uniform(size=fin.sum())) * (xu[fin] - xl[fin])
-    sl = np.where(gl == gu, gl - eps, gl)
-    su = np.where(gl == gu, gu + eps, gu)
-    both = np.isfinite(sl) & np.isfinite(su)
-    s = np.where(np.isfinite(su), su - rng.uniform(0.1, 1.0, o.m), sl + rng.uniform(0.1, 1.0, o.m))
-    s[both] = sl[both] + (0.1 + 0.8 * rng.uniform(size=both.sum())) * (su[both] - sl[both])
-    zlx = np.where(np.isfinite(xl), rng.uniform(0.1, 2.0, o.n), 0.0)
-    zux = np.where(np.isfinite(xu), rng.uniform(0.1, 2.0, o.n), 0.0)
-    zls = np.where(np.isfinite(sl), rng.uniform(0.1, 2.0, o.m), 0.0)
-    zus = np.where(np.isfinite(su), rng.uniform(0.1, 2.0, o.m), 0.0)
-    y = rng.uniform(-1, 1, o.m)
-    return x, s, y, zlx, zux, zls, zus, xl, xu, sl, su
-
-
 def test_ipm_condensation_solves_full_lifted_system():
     """Delta x from M_cond dx = q_x + A^T (C q_s + D q_y), with Delta s, Delta y
     and the Delta z recovered from it, solves the full 7-block system of
@@ -547,7 +527,7 @@ def test_ipm_condensation_solves_full_lifted_system():
     o = oracle.Oracle(inst)
     n, m = o.n, o.m
     eps, mu, dw, dc = 1e-2, 0.05, 1e-3, 1e-4
-    x, s, y, zlx, zux, zls, zus, xl, xu, sl, su = _ipm_point(inst, o, 62, eps)
+    x, s, y, zlx, zux, zls, zus, xl, xu, sl, su = H.ipm_point(inst, o, 62, eps)
     lam = -y  # W = sigma grad^2 f + sum lam_i grad^2 c_i with the paper's p_x = grad f - J^T y
     r = o.eval(x, lam, 1.0)
     jr, jc = o.jac_pattern()
@@ -561,35 +541,10 @@ def test_ipm_condensation_solves_full_lifted_system():
     dx = np.linalg.solve(Mc, rhs)
     rec = o.ipm_recover(x, s, y, zlx, zux, zls, zus, r["c"], dx, mu, dw, dc, eps)
     # full system
-    fl, fu = np.isfinite(xl), np.isfinite(xu)
-    gl_, gu_ = np.isfinite(sl), np.isfinite(su)
-    il, iu, jl, ju = np.nonzero(fl)[0], np.nonzero(fu)[0], np.nonzero(gl_)[0], np.nonzero(gu_)[0]
-    sizes = [n, m, m, il.size, iu.size, jl.size, ju.size]
-    off = np.concatenate([[0], np.cumsum(sizes)])
-    K = np.zeros((off[-1], off[-1]))
-    X, S_, Y, ZLX, ZUX, ZLS, ZUS = (slice(off[k], off[k + 1]) for k in range(7))
-    K[X, X] = W + dw * np.eye(n)
-    K[X, Y] = A.T
-    K[X, ZLX][il, np.arange(il.size)] = -1.0
-    K[X, ZUX][iu, np.arange(iu.size)] = 1.0
-    K[S_, S_] = dw * np.eye(m)
-    K[S_, Y] = -np.eye(m)
-    K[S_, ZLS][jl, np.arange(jl.size)] = -1.0
-    K[S_, ZUS][ju, np.arange(ju.size)] = 1.0
-    K[Y, X] = A
-    K[Y, S_] = -np.eye(m)
-    K[Y, Y] = -dc * np.eye(m)
-    K[ZLX, X][np.arange(il.size), il] = zlx[il]
-    K[ZLX, ZLX] = np.diag(x[il] - xl[il])
-    K[ZUX, X][np.arange(iu.size), iu] = -zux[iu]
-    K[ZUX, ZUX] = np.diag(xu[iu] - x[iu])
-    K[ZLS, S_][np.arange(jl.size), jl] = zls[jl]
-    K[ZLS, ZLS] = np.diag(s[jl] - sl[jl])
-    K[ZUS, S_][np.arange(ju.size), ju] = -zus[ju]
-    K[ZUS, ZUS] = np.diag(su[ju] - s[ju])
-    p = np.concatenate([r["g"] - A.T @ y - zlx + zux, -zls + zus + y, r["c"] - s,
-                        zlx[il] * (x[il] - xl[il]) - mu, zux[iu] * (xu[iu] - x[iu]) - mu,
-                        zls[jl] * (s[jl] - sl[jl]) - mu, zus[ju] * (su[ju] - s[ju]) - mu])
+    K, p, sl_ = H.lifted_system(W, A, x, s, y, zlx, zux, zls, zus, xl, xu, sl, su, r["g"], r["c"], mu, dw, dc)
+    X, S_, Y, ZLX, ZUX, ZLS, ZUS = sl_
+    fl, fu, gl_, gu_ = np.isfinite(xl), np.isfinite(xu), np.isfinite(sl), np.isfinite(su)
+    il, iu, jl, ju = (np.nonzero(b)[0] for b in (fl, fu, gl_, gu_))
     full = np.linalg.solve(K, p)
     scale = np.abs(full).max()
     np.testing.assert_allclose(dx, full[X], rtol=0, atol=1e-9 * scale)
