@@ -410,6 +410,68 @@ def batched_comparison(torch, reps=20):
     return res
 
 
+def ipm_timing(torch, h, reps=50, eps=1e-2, mu=0.05, dw=1e-3, dc=1e-4):
+    """The interior-point algebra around M (Sec. III-B) on the benchmark
+    instance: mpopf_ipm_prepare, mpopf_ipm_rhs and mpopf_ipm_recover at an
+    interior point built from the pattern's bounds (midpoints of finite
+    intervals, 0.5 inside one-sided bounds, duals 1 on finite bounds), each
+    timed alone with CUDA events over reps calls."""
+    pat = h.pattern()
+    xl, xu, gl, gu = (pat[k] for k in ("xl", "xu", "gl", "gu"))
+    inf = float("inf")
+
+    def interior(lo, hi, other):
+        fl, fu = torch.isfinite(lo), torch.isfinite(hi)
+        v = torch.where(fl & fu, 0.5 * (lo + hi), other)
+        v = torch.where(fl & ~fu, lo + 0.5, v)
+        return torch.where(~fl & fu, hi - 0.5, v)
+
+    eq = gl == gu
+    sl, su = torch.where(eq, gl - eps, gl), torch.where(eq, gu + eps, gu)
+    x = interior(xl, xu, torch.zeros_like(xl))
+    s = interior(sl, su, torch.zeros_like(sl))
+    one = lambda b: torch.where(torch.isfinite(b), 1.0, 0.0).double()
+    zlx, zux, zls, zus = one(xl), one(xu), one(sl), one(su)
+    y = torch.full_like(s, 0.25)
+    from paper_2405_14032_b300 import mpopf
+    out = h.eval(mpopf.OUT_OBJ | mpopf.OUT_GRAD | mpopf.OUT_CONS, x)
+    sigx, dvec, cvec, recip = h.ipm_prepare(x, s, zlx, zux, zls, zus, dw, dc, eps)
+    rhs = h.ipm_rhs(x, s, y, out["grad"], out["c"], recip, dvec, cvec, mu)
+    dx = rhs.clone()
+    rec = h.ipm_recover(x, s, y, zlx, zux, zls, zus, out["c"], recip, cvec, dx, mu, dw, dc)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = _events(torch)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    n, m = h.n, h.m
+    t_prep = timed(lambda: h.ipm_prepare(x, s, zlx, zux, zls, zus, dw, dc, eps, recip=recip))
+    t_rhs = timed(lambda: h.ipm_rhs(x, s, y, out["grad"], out["c"], recip, dvec, cvec, mu, out=rhs))
+    t_rec = timed(lambda: h.ipm_recover(x, s, y, zlx, zux, zls, zus, out["c"], recip, cvec, dx, mu, dw, dc, out=rec))
+    gx = torch.empty_like(x)
+    t_vjp = timed(lambda: h.vjp(x, y, gx=gx, loads=False))
+    jv = torch.empty_like(y)
+    t_jvp = timed(lambda: h.jvp(x, dx, out=jv))
+    # each array read or written once (the J products: x, the vector and the result)
+    b_prep = 8 * (8 * n + 9 * m)
+    b_rhs = 8 * (8 * m + (n + m + n) + 5 * n)
+    b_rec = 8 * ((n + n + m) + 13 * m + 7 * n)
+    g = lambda b, t: b / (t * 1e-3) / 1e9
+    return {"prepare_ms": t_prep, "rhs_ms": t_rhs, "recover_ms": t_rec, "vjp_ms": t_vjp, "jvp_ms": t_jvp,
+            "prepare_gbs": g(b_prep, t_prep), "rhs_gbs": g(b_rhs, t_rhs), "recover_gbs": g(b_rec, t_rec),
+            "algorithmic_bytes": {"prepare": b_prep, "rhs": b_rhs, "recover": b_rec},
+            "note": "rhs and recover include one matrix-free J product each (J^T w, J dx; timed alone as "
+                    "vjp_ms / jvp_ms); all divisions in prepare"}
+
+
 def lib_vjp(h, x, y, gx, gpd, gqd):
     from paper_2405_14032_b300 import mpopf
     import torch
@@ -559,6 +621,7 @@ def run_ours(args, world, rank, local):
             line["cpu_baseline"] = cpu_baseline(inst, pt)
             line["adjoint"] = adjoint_comparison(torch)
             line["batched"] = batched_comparison(torch)
+            line["ipm"] = ipm_timing(torch, h)
         print(json.dumps(line), flush=True)
     h.close()
     if world > 1:

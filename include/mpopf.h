@@ -200,41 +200,47 @@ int mpopf_hvp(mpopf_handle *h, const double *x, const double *lam, double sigma,
  * s in [gl, gu] for inequality rows and in [gl - eps_tol, gu + eps_tol] for
  * equality rows (gl == gu), the paper's relaxation of g(x) = 0 to a band of
  * half-width eps.  A +-INFINITY bound contributes nothing and its dual is
- * ignored; a finite bound must be strictly inactive (v strictly inside).
- * With d = v - lo, e = hi - v for v in {x, s}:
- *   Sigma = zl/d + zu/e,  C = 1/(1 + delta_c (Sigma_s + delta_w)),
+ * ignored.  Precondition: every finite bound is strictly inactive (v strictly
+ * inside, at a finite distance).
+ * With rl = 1/(v - lo), ru = 1/(hi - v) (0 for an infinite bound), v in {x, s}:
+ *   Sigma = zl rl + zu ru,  C = 1/(1 + delta_c (Sigma_s + delta_w)),
  *   D = (Sigma_s + delta_w) C.
- * mpopf_ipm_prepare: sigma_x [n], dvec = D [m], cvec = C [m]; sigma_x and dvec
- *   are the Sigma_x and D that mpopf_assemble_kkt / mpopf_sweep take.
- * mpopf_ipm_rhs: rhs [n] = q_x + A^T (C q_s + D q_y) with A = J(x) and
- *   q_x = grad f - A^T y - zl_x + zu_x + (zl_x d - mu)/d - (zu_x e - mu)/e,
- *   q_s = zu_s - zl_s + y + (zl_s d - mu)/d - (zu_s e - mu)/e, q_y = c - s;
- *   grad [n] = grad f(x) and c [m] = c(x) as the eval callbacks return them.
- *   The two transposed products are merged into one J^T w, w = C q_s + D q_y - y,
- *   kept in the handle's scratch.  With the Lagrangian f - y^T c the Hessian
- *   block of M is W at lambda = -y, sigma = 1, and dx solves M dx = rhs, the
- *   condensed form of Eq. 5 with its right-hand side as printed.
+ * mpopf_ipm_prepare: sigma_x [n], dvec = D [m], cvec = C [m] (sigma_x and dvec
+ *   are the Sigma_x and D that mpopf_assemble_kkt / mpopf_sweep take) and the
+ *   workspace recip [2n + 2m] = rl_x [n], ru_x [n], rl_s [m], ru_s [m], which
+ *   the two calls below read.  All divisions of the algebra happen here.
+ * mpopf_ipm_rhs: rhs [n] = q_x + A^T (C q_s + D q_y) with A = J(x); after
+ *   eliminating the bound-dual rows of Eq. 5 the dual terms cancel and
+ *   q_x = grad f - A^T y + mu (ru_x - rl_x),  q_s = y + mu (ru_s - rl_s),
+ *   q_y = c - s; grad [n] = grad f(x) and c [m] = c(x) as the eval callbacks
+ *   return them; recip, dvec, cvec from mpopf_ipm_prepare at the same point.
+ *   The two transposed products are merged into one J^T w,
+ *   w = C q_s + D q_y - y, kept in the handle's scratch.  With the Lagrangian
+ *   f - y^T c the Hessian block of M is W at lambda = -y, sigma = 1, and dx
+ *   solves M dx = rhs, the condensed form of Eq. 5 with its right-hand side as
+ *   printed.
  * mpopf_ipm_recover: from dx [n] the remaining blocks of Eq. 5:
  *   ds = C (A dx + delta_c q_s - q_y),  dy = (Sigma_s + delta_w) ds - q_s,
- *   dzl = ((zl d - mu) - zl dv)/d,  dzu = ((zu e - mu) + zu dv)/e  (v = x, s),
+ *   dzl = zl - rl (mu + zl dv),  dzu = zu - ru (mu - zu dv)   (v = x, s; dv = dx, ds)
  *   into ds, dy, dzl_s, dzu_s [m] and dzl_x, dzu_x [n] (0 where the bound is
- *   infinite).  The recovered ds is the one that solves Eq. 5; the sign of
- *   A dx printed with the recovery formula does not.
- * Values follow a fixed rounding order (fma where written above as one
- * product-sum) and equal the CPU reference bit for bit.  The rhs and recover
- * calls use the handle's scratch (calls on one handle must not overlap).
- * Errors: MPOPF_ERR_ARG for a NULL pointer, MPOPF_ERR_CUDA for a failed
- * launch; nothing is written on an argument error. */
+ *   infinite); recip and cvec from mpopf_ipm_prepare at the same point.  The
+ *   recovered ds is the one that solves Eq. 5; the sign of A dx printed with
+ *   the recovery formula does not.
+ * Values follow a fixed rounding order and equal the CPU reference bit for
+ * bit.  rhs and recover use the handle's scratch (calls on one handle must
+ * not overlap).  Errors: MPOPF_ERR_ARG for a NULL pointer (nothing is
+ * launched), MPOPF_ERR_CUDA for a failed launch. */
 int mpopf_ipm_prepare(mpopf_handle *h, const double *x, const double *s, const double *zl_x, const double *zu_x,
                       const double *zl_s, const double *zu_s, double delta_w, double delta_c, double eps_tol,
-                      double *sigma_x, double *dvec, double *cvec, void *stream);
-int mpopf_ipm_rhs(mpopf_handle *h, const double *x, const double *s, const double *y, const double *zl_x,
-                  const double *zu_x, const double *zl_s, const double *zu_s, const double *grad, const double *c,
-                  double mu, double delta_w, double delta_c, double eps_tol, double *rhs, void *stream);
+                      double *sigma_x, double *dvec, double *cvec, double *recip, void *stream);
+int mpopf_ipm_rhs(mpopf_handle *h, const double *x, const double *s, const double *y, const double *grad,
+                  const double *c, const double *recip, const double *dvec, const double *cvec, double mu,
+                  double *rhs, void *stream);
 int mpopf_ipm_recover(mpopf_handle *h, const double *x, const double *s, const double *y, const double *zl_x,
-                      const double *zu_x, const double *zl_s, const double *zu_s, const double *c, const double *dx,
-                      double mu, double delta_w, double delta_c, double eps_tol, double *ds, double *dy,
-                      double *dzl_x, double *dzu_x, double *dzl_s, double *dzu_s, void *stream);
+                      const double *zu_x, const double *zl_s, const double *zu_s, const double *c,
+                      const double *recip, const double *cvec, const double *dx, double mu, double delta_w,
+                      double delta_c, double *ds, double *dy, double *dzl_x, double *dzu_x, double *dzl_s,
+                      double *dzu_s, void *stream);
 
 /* Batched full sweeps of many independent instances (uneven sizes and
  * horizons) in ONE persistent kernel launch, replayed as a CUDA graph.  The

@@ -59,7 +59,7 @@ def load():
             "orc_cons_cstep": (None, [_P, _P, _P, _D, _P]),
             "orc_obj_textbook": (_D, [_P, _P]),
             "orc_branch_terms": (None, [_P, _P]),
-            "orc_ipm_prepare": (None, [_P] * 7 + [_D, _D, _D] + [_P] * 4),
+            "orc_ipm_prepare": (None, [_P] * 7 + [_D, _D, _D] + [_P] * 5),
             "orc_ipm_rhs": (None, [_P] * 10 + [_D, _D, _D, _D, _P, _P]),
             "orc_ipm_recover": (None, [_P] * 10 + [_D, _D, _D, _D] + [_P] * 6),
         }
@@ -226,10 +226,13 @@ class Oracle:
 
     # -- interior-point algebra around M (Sec. III-B) ------------------------
     def ipm_prepare(self, x, s, zlx, zux, zls, zus, delta_w, delta_c, eps):
+        """(Sigma_x, D, C, Sigma_s, recip) with recip = [rl_x, ru_x, rl_s, ru_s]."""
         sigx, dvec, cvec, sigs = np.empty(self.n), np.empty(self.m), np.empty(self.m), np.empty(self.m)
+        recip = np.empty(2 * self.n + 2 * self.m)
         _lib.orc_ipm_prepare(self.h, *[_ptr(_f64(a)) for a in (x, s, zlx, zux, zls, zus)], float(delta_w),
-                             float(delta_c), float(eps), _ptr(sigx), _ptr(dvec), _ptr(cvec), _ptr(sigs))
-        return sigx, dvec, cvec, sigs
+                             float(delta_c), float(eps), _ptr(sigx), _ptr(dvec), _ptr(cvec), _ptr(sigs),
+                             _ptr(recip))
+        return sigx, dvec, cvec, sigs, recip
 
     def ipm_rhs(self, x, s, y, zlx, zux, zls, zus, grad, c, mu, delta_w, delta_c, eps):
         rhs, w = np.empty(self.n), np.empty(self.m)

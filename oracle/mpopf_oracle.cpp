@@ -843,32 +843,33 @@ void orc_jvp(void* h, int64_t t0, int64_t t1, const double* x, const double* v, 
 // for inequality rows and the relaxation gl - eps, gu + eps for equality rows
 // (gl == gu; the paper relaxes g(x) = 0 to s in [-eps, eps]).  An infinite
 // bound contributes nothing (its dual is taken as 0).
-//   Sigma = zl / (v - vl) + zu / (vu - v)                      (lower, then upper)
+// For v in {x, s} with distances dl = v - vl, du = vu - v to its finite bounds:
+//   rl = 1/dl, ru = 1/du                      (0 for an infinite bound)
+//   Sigma = fma(zl, rl, zu ru)
 //   C = 1 / fma(delta_c, Sigma_s, 1 + delta_c delta_w),  D = (Sigma_s + delta_w) C
-//   pzl = fma(zl, v - vl, -mu),  pzu = fma(zu, vu - v, -mu)
-//   base_x = (((grad - zl_x) + zu_x) + pzl_x/(x - xl)) - pzu_x/(xu - x)
-//   q_s = (((zu_s - zl_s) + y) + pzl_s/(s - sl)) - pzu_s/(su - s),  q_y = c - s
-//   rhs = base_x + J^T w with w = fma(C, q_s, D q_y) - y  (the two transposed
-//     products J^T y of p_x and J^T (C q_s + D q_y) merged into one)
-//   ds = C ((fma(delta_c, q_s, (J dx)) - q_y)     (eliminating rows 2-3 of Eq. 5)
+// Eliminating the bound-dual rows of Eq. 5 (complementarity zl dl - mu) from
+// the dual rows, the dual terms cancel: -zl + (zl dl - mu)/dl = -mu rl, so
+//   q_x = fma(mu, ru - rl, grad) - J^T y,   q_s = fma(mu, ru - rl, y),
+//   q_y = c - s,
+//   rhs = fma(mu, ru_x - rl_x, grad) + J^T w,  w = fma(C, q_s, D q_y) - y
+//     (J^T y of q_x and J^T (C q_s + D q_y) merged into one product),
+//   ds = C (fma(delta_c, q_s, J dx) - q_y)   (eliminating rows 2-3 of Eq. 5)
 //   dy = fma(Sigma_s + delta_w, ds, -q_s)
-//   dzl = fma(-zl, dv, pzl) / (v - vl),  dzu = fma(zu, dv, pzu) / (vu - v)
+//   dzl = fma(-rl, fma(zl, dv, mu), zl)  = ((zl dl - mu) - zl dv) / dl
+//   dzu = fma(-ru, fma(-zu, dv, mu), zu) = ((zu du - mu) + zu dv) / du
 // ---------------------------------------------------------------------------
 namespace {
-struct BarrierTerms {
-  double sig, pzl, pzu, dl, du;
+struct Recip {
+  double rl, ru;
   bool has_l, has_u;
 };
-BarrierTerms barrier(double v, double lo, double hi, double zl, double zu, double mu) {
-  BarrierTerms b{};
-  b.has_l = std::isfinite(lo);
-  b.has_u = std::isfinite(hi);
-  double a = 0.0, c = 0.0;
-  if (b.has_l) { b.dl = v - lo; a = zl / b.dl; b.pzl = std::fma(zl, b.dl, -mu); }
-  if (b.has_u) { b.du = hi - v; c = zu / b.du; b.pzu = std::fma(zu, b.du, -mu); }
-  b.sig = a + c;
-  return b;
+Recip recips(double v, double lo, double hi) {
+  Recip r{0.0, 0.0, std::isfinite(lo), std::isfinite(hi)};
+  if (r.has_l) r.rl = 1.0 / (v - lo);
+  if (r.has_u) r.ru = 1.0 / (hi - v);
+  return r;
 }
+double sigma_of(const Recip& r, double zl, double zu) { return std::fma(zl, r.rl, zu * r.ru); }
 void slack_bounds(double gl, double gu, double eps, double* sl, double* su) {
   if (gl == gu) { *sl = gl - eps; *su = gu + eps; } else { *sl = gl; *su = gu; }
 }
@@ -876,23 +877,30 @@ void slack_bounds(double gl, double gu, double eps, double* sl, double* su) {
 
 extern "C" {
 
-// Sigma_x [n]; D, C [m] (and Sigma_s [m] if not NULL).
+// Sigma_x [n]; D, C [m]; if not NULL: Sigma_s [m] and the reciprocals
+// recip [2n + 2m] = rl_x [n], ru_x [n], rl_s [m], ru_s [m].
 void orc_ipm_prepare(void* h, const double* x, const double* s, const double* zlx, const double* zux, const double* zls,
                      const double* zus, double delta_w, double delta_c, double eps, double* sigx, double* dvec,
-                     double* cvec, double* sigs) {
+                     double* cvec, double* sigs, double* recip) {
   const Model& M = *static_cast<Model*>(h);
   std::vector<double> xl(M.n), xu(M.n), gl(M.m), gu(M.m);
   orc_bounds(h, xl.data(), xu.data(), gl.data(), gu.data());
-  for (int64_t j = 0; j < M.n; ++j) sigx[j] = barrier(x[j], xl[j], xu[j], zlx[j], zux[j], 0.0).sig;
+  for (int64_t j = 0; j < M.n; ++j) {
+    const Recip r = recips(x[j], xl[j], xu[j]);
+    sigx[j] = sigma_of(r, zlx[j], zux[j]);
+    if (recip) { recip[j] = r.rl; recip[M.n + j] = r.ru; }
+  }
   const double e = 1.0 + delta_c * delta_w;
   for (int64_t i = 0; i < M.m; ++i) {
     double sl, su;
     slack_bounds(gl[i], gu[i], eps, &sl, &su);
-    const double sg = barrier(s[i], sl, su, zls[i], zus[i], 0.0).sig;
+    const Recip r = recips(s[i], sl, su);
+    const double sg = sigma_of(r, zls[i], zus[i]);
     const double c = 1.0 / std::fma(delta_c, sg, e);
     cvec[i] = c;
     dvec[i] = (sg + delta_w) * c;
     if (sigs) sigs[i] = sg;
+    if (recip) { recip[2 * M.n + i] = r.rl; recip[2 * M.n + M.m + i] = r.ru; }
   }
 }
 
@@ -908,22 +916,18 @@ void orc_ipm_rhs(void* h, const double* x, const double* s, const double* y, con
   for (int64_t i = 0; i < M.m; ++i) {
     double sl, su;
     slack_bounds(gl[i], gu[i], eps, &sl, &su);
-    const BarrierTerms b = barrier(s[i], sl, su, zls[i], zus[i], mu);
-    double qs = (zus[i] - zls[i]) + y[i];
-    qs = qs + (b.has_l ? b.pzl / b.dl : 0.0);
-    qs = qs - (b.has_u ? b.pzu / b.du : 0.0);
+    const Recip r = recips(s[i], sl, su);
+    const double sg = sigma_of(r, zls[i], zus[i]);
+    const double cc = 1.0 / std::fma(delta_c, sg, e);
+    const double dd = (sg + delta_w) * cc;
+    const double qs = std::fma(mu, r.ru - r.rl, y[i]);
     const double qy = c[i] - s[i];
-    const double cc = 1.0 / std::fma(delta_c, b.sig, e);
-    const double dd = (b.sig + delta_w) * cc;
     w[i] = std::fma(cc, qs, dd * qy) - y[i];
   }
   orc_vjp(h, 0, M.T, x, w.data(), jt.data(), nullptr, nullptr);
   for (int64_t j = 0; j < M.n; ++j) {
-    const BarrierTerms b = barrier(x[j], xl[j], xu[j], zlx[j], zux[j], mu);
-    double base = (grad[j] - zlx[j]) + zux[j];
-    base = base + (b.has_l ? b.pzl / b.dl : 0.0);
-    base = base - (b.has_u ? b.pzu / b.du : 0.0);
-    rhs[j] = base + jt[j];
+    const Recip r = recips(x[j], xl[j], xu[j]);
+    rhs[j] = std::fma(mu, r.ru - r.rl, grad[j]) + jt[j];
   }
   if (w_out) for (int64_t i = 0; i < M.m; ++i) w_out[i] = w[i];
 }
@@ -941,22 +945,21 @@ void orc_ipm_recover(void* h, const double* x, const double* s, const double* y,
   for (int64_t i = 0; i < M.m; ++i) {
     double sl, su;
     slack_bounds(gl[i], gu[i], eps, &sl, &su);
-    const BarrierTerms b = barrier(s[i], sl, su, zls[i], zus[i], mu);
-    double qs = (zus[i] - zls[i]) + y[i];
-    qs = qs + (b.has_l ? b.pzl / b.dl : 0.0);
-    qs = qs - (b.has_u ? b.pzu / b.du : 0.0);
+    const Recip r = recips(s[i], sl, su);
+    const double sg = sigma_of(r, zls[i], zus[i]);
+    const double cc = 1.0 / std::fma(delta_c, sg, e);
+    const double qs = std::fma(mu, r.ru - r.rl, y[i]);
     const double qy = c[i] - s[i];
-    const double cc = 1.0 / std::fma(delta_c, b.sig, e);
     const double d = cc * (std::fma(delta_c, qs, jdx[i]) - qy);
     ds[i] = d;
-    dy[i] = std::fma(b.sig + delta_w, d, -qs);
-    dzls[i] = b.has_l ? std::fma(-zls[i], d, b.pzl) / b.dl : 0.0;
-    dzus[i] = b.has_u ? std::fma(zus[i], d, b.pzu) / b.du : 0.0;
+    dy[i] = std::fma(sg + delta_w, d, -qs);
+    dzls[i] = r.has_l ? std::fma(-r.rl, std::fma(zls[i], d, mu), zls[i]) : 0.0;
+    dzus[i] = r.has_u ? std::fma(-r.ru, std::fma(-zus[i], d, mu), zus[i]) : 0.0;
   }
   for (int64_t j = 0; j < M.n; ++j) {
-    const BarrierTerms b = barrier(x[j], xl[j], xu[j], zlx[j], zux[j], mu);
-    dzlx[j] = b.has_l ? std::fma(-zlx[j], dx[j], b.pzl) / b.dl : 0.0;
-    dzux[j] = b.has_u ? std::fma(zux[j], dx[j], b.pzu) / b.du : 0.0;
+    const Recip r = recips(x[j], xl[j], xu[j]);
+    dzlx[j] = r.has_l ? std::fma(-r.rl, std::fma(zlx[j], dx[j], mu), zlx[j]) : 0.0;
+    dzux[j] = r.has_u ? std::fma(-r.ru, std::fma(-zux[j], dx[j], mu), zux[j]) : 0.0;
   }
 }
 

@@ -2,11 +2,16 @@
 // the diagonal scalings Sigma_x, Sigma_s, C, D from the bounds and duals (with
 // the relaxation of equality rows to [g - eps, g + eps]), the condensed
 // right-hand side q_x + A^T (C q_s + D q_y), and the recovery of the slack,
-// multiplier and bound-dual steps from dx.  Elementwise kernels plus the
-// matrix-free J^T w / J v kernels; every value follows the same written order
-// as the CPU oracle.  The recovered slack step is the one Eq. (5) implies,
-// ds = C (A dx + delta_c q_s - q_y); the printed form with -A dx does not solve
-// the printed block system.
+// multiplier and bound-dual steps from dx.
+//
+// FP64 division is the expensive operation on this GPU (a reciprocal sequence
+// on the FP64 pipe), so every division happens once, in mpopf_ipm_prepare: the
+// reciprocals rl = 1/(v - lo), ru = 1/(hi - v) go to a caller workspace and
+// the right-hand side and the recovery are division-free.  With the bound-dual
+// rows of Eq. (5) eliminated, the dual terms cancel (-zl + (zl dl - mu)/dl =
+// -mu rl), which is the form used here and by the CPU oracle.  The recovered
+// slack step is the one Eq. (5) implies, ds = C (A dx + delta_c q_s - q_y).
+// Every value follows the oracle's written rounding order.
 #include <string>
 
 #include "mpopf_internal.cuh"
@@ -19,132 +24,108 @@ extern "C" int mpopf_jvp(mpopf_handle *h, const double *x, const double *v, cons
 namespace mpopf {
 namespace {
 
-__device__ __forceinline__ bool finite(double v) {
-  return ((__double2hiint(v) >> 20) & 0x7ff) != 0x7ff;
+__device__ __forceinline__ bool finite(double v) { return ((__double2hiint(v) >> 20) & 0x7ff) != 0x7ff; }
+
+// rl = 1/(v - lo), ru = 1/(hi - v); 0 for an infinite bound.
+__device__ __forceinline__ void recips(double v, double lo, double hi, double *rl, double *ru) {
+  *rl = finite(lo) ? 1.0 / (v - lo) : 0.0;
+  *ru = finite(hi) ? 1.0 / (hi - v) : 0.0;
 }
 
-struct Barrier {
-  double sig, pzl, pzu, dl, du;
-  bool has_l, has_u;
-};
-
-// Sigma = zl/(v - lo) + zu/(hi - v); pzl = fma(zl, v - lo, -mu), pzu = fma(zu, hi - v, -mu).
-__device__ __forceinline__ Barrier barrier(double v, double lo, double hi, double zl, double zu, double mu) {
-  Barrier b;
-  b.has_l = finite(lo);
-  b.has_u = finite(hi);
-  b.pzl = b.pzu = b.dl = b.du = 0.0;
-  double a = 0.0, c = 0.0;
-  if (b.has_l) { b.dl = v - lo; a = zl / b.dl; b.pzl = fma(zl, b.dl, -mu); }
-  if (b.has_u) { b.du = hi - v; c = zu / b.du; b.pzu = fma(zu, b.du, -mu); }
-  b.sig = a + c;
-  return b;
-}
-
-__device__ __forceinline__ void slack_bounds(double gl, double gu, double eps, double *sl, double *su) {
-  if (gl == gu) { *sl = gl - eps; *su = gu + eps; } else { *sl = gl; *su = gu; }
-}
+__device__ __forceinline__ double sigma_of(double rl, double ru, double zl, double zu) { return fma(zl, rl, zu * ru); }
 
 __global__ void __launch_bounds__(kBlock) k_prep_vars(int64_t n, const double *__restrict__ x,
                                                       const double *__restrict__ xl, const double *__restrict__ xu,
                                                       const double *__restrict__ zl, const double *__restrict__ zu,
-                                                      double *__restrict__ sigx) {
+                                                      double *__restrict__ sigx, double *__restrict__ rl_out,
+                                                      double *__restrict__ ru_out) {
   const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= n) return;
-  sigx[j] = barrier(x[j], xl[j], xu[j], zl[j], zu[j], 0.0).sig;
+  double rl, ru;
+  recips(x[j], xl[j], xu[j], &rl, &ru);
+  sigx[j] = sigma_of(rl, ru, zl[j], zu[j]);
+  rl_out[j] = rl;
+  ru_out[j] = ru;
 }
 
+// C = 1 / fma(delta_c, Sigma_s, e) with e = 1 + delta_c delta_w; for
+// delta_c == 0 that is exactly 1 and the division is skipped (ZERO_DC).
+template <bool ZERO_DC>
 __global__ void __launch_bounds__(kBlock) k_prep_rows(int64_t m, const double *__restrict__ s,
                                                       const double *__restrict__ gl, const double *__restrict__ gu,
                                                       const double *__restrict__ zl, const double *__restrict__ zu,
                                                       double dw, double dc, double e, double eps,
-                                                      double *__restrict__ dvec, double *__restrict__ cvec) {
+                                                      double *__restrict__ dvec, double *__restrict__ cvec,
+                                                      double *__restrict__ rl_out, double *__restrict__ ru_out) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= m) return;
-  double sl, su;
-  slack_bounds(gl[i], gu[i], eps, &sl, &su);
-  const double sg = barrier(s[i], sl, su, zl[i], zu[i], 0.0).sig;
-  const double c = 1.0 / fma(dc, sg, e);
+  double lo = gl[i], hi = gu[i];
+  if (lo == hi) { lo = lo - eps; hi = hi + eps; }
+  double rl, ru;
+  recips(s[i], lo, hi, &rl, &ru);
+  const double sg = sigma_of(rl, ru, zl[i], zu[i]);
+  const double c = ZERO_DC ? 1.0 : 1.0 / fma(dc, sg, e);
   cvec[i] = c;
   dvec[i] = (sg + dw) * c;
+  rl_out[i] = rl;
+  ru_out[i] = ru;
 }
 
-// q_s, q_y and the barrier terms of row i.
-struct RowQ {
-  double qs, qy, sig, cc;
-  Barrier b;
-};
-__device__ __forceinline__ RowQ row_q(int64_t i, const double *s, const double *y, const double *gl, const double *gu,
-                                      const double *zl, const double *zu, const double *c, double mu, double dc,
-                                      double e, double eps) {
-  RowQ r;
-  double sl, su;
-  slack_bounds(gl[i], gu[i], eps, &sl, &su);
-  r.b = barrier(s[i], sl, su, zl[i], zu[i], mu);
-  double qs = (zu[i] - zl[i]) + y[i];
-  qs = qs + (r.b.has_l ? r.b.pzl / r.b.dl : 0.0);
-  qs = qs - (r.b.has_u ? r.b.pzu / r.b.du : 0.0);
-  r.qs = qs;
-  r.qy = c[i] - s[i];
-  r.sig = r.b.sig;
-  r.cc = 1.0 / fma(dc, r.b.sig, e);
-  return r;
-}
-
+// w = fma(C, q_s, D q_y) - y with q_s = fma(mu, ru - rl, y), q_y = c - s.
 __global__ void __launch_bounds__(kBlock) k_rhs_rows(int64_t m, const double *__restrict__ s,
-                                                     const double *__restrict__ y, const double *__restrict__ gl,
-                                                     const double *__restrict__ gu, const double *__restrict__ zl,
-                                                     const double *__restrict__ zu, const double *__restrict__ c,
-                                                     double mu, double dw, double dc, double e, double eps,
+                                                     const double *__restrict__ y, const double *__restrict__ c,
+                                                     const double *__restrict__ rl, const double *__restrict__ ru,
+                                                     const double *__restrict__ dvec,
+                                                     const double *__restrict__ cvec, double mu,
                                                      double *__restrict__ w) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= m) return;
-  const RowQ r = row_q(i, s, y, gl, gu, zl, zu, c, mu, dc, e, eps);
-  const double dd = (r.sig + dw) * r.cc;
-  w[i] = fma(r.cc, r.qs, dd * r.qy) - y[i];
+  const double yi = y[i];
+  const double qs = fma(mu, ru[i] - rl[i], yi);
+  const double qy = c[i] - s[i];
+  w[i] = fma(cvec[i], qs, dvec[i] * qy) - yi;
 }
 
-__global__ void __launch_bounds__(kBlock) k_rhs_vars(int64_t n, const double *__restrict__ x,
-                                                     const double *__restrict__ xl, const double *__restrict__ xu,
-                                                     const double *__restrict__ zl, const double *__restrict__ zu,
-                                                     const double *__restrict__ grad, double mu,
-                                                     double *__restrict__ rhs) {
+// rhs = fma(mu, ru - rl, grad) + (J^T w), the product already in rhs.
+__global__ void __launch_bounds__(kBlock) k_rhs_vars(int64_t n, const double *__restrict__ grad,
+                                                     const double *__restrict__ rl, const double *__restrict__ ru,
+                                                     double mu, double *__restrict__ rhs) {
   const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= n) return;
-  const Barrier b = barrier(x[j], xl[j], xu[j], zl[j], zu[j], mu);
-  double base = (grad[j] - zl[j]) + zu[j];
-  base = base + (b.has_l ? b.pzl / b.dl : 0.0);
-  base = base - (b.has_u ? b.pzu / b.du : 0.0);
-  rhs[j] = base + rhs[j];  // rhs holds J^T w
+  rhs[j] = fma(mu, ru[j] - rl[j], grad[j]) + rhs[j];
 }
 
+// A zero reciprocal marks an infinite bound (finite bounds are strictly
+// inactive, so their reciprocals are positive).
 __global__ void __launch_bounds__(kBlock) k_rec_rows(int64_t m, const double *__restrict__ s,
-                                                     const double *__restrict__ y, const double *__restrict__ gl,
-                                                     const double *__restrict__ gu, const double *__restrict__ zl,
-                                                     const double *__restrict__ zu, const double *__restrict__ c,
-                                                     double mu, double dw, double dc, double e, double eps,
+                                                     const double *__restrict__ y, const double *__restrict__ c,
+                                                     const double *__restrict__ zl, const double *__restrict__ zu,
+                                                     const double *__restrict__ rlv, const double *__restrict__ ruv,
+                                                     const double *__restrict__ cvec, double mu, double dw, double dc,
                                                      double *__restrict__ ds, double *__restrict__ dy,
                                                      double *__restrict__ dzl, double *__restrict__ dzu) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= m) return;
-  const RowQ r = row_q(i, s, y, gl, gu, zl, zu, c, mu, dc, e, eps);
-  const double d = r.cc * (fma(dc, r.qs, ds[i]) - r.qy);  // ds holds J dx
+  const double rl = rlv[i], ru = ruv[i], zli = zl[i], zui = zu[i];
+  const double sg = sigma_of(rl, ru, zli, zui);
+  const double qs = fma(mu, ru - rl, y[i]);
+  const double qy = c[i] - s[i];
+  const double d = cvec[i] * (fma(dc, qs, ds[i]) - qy);  // ds holds J dx
   ds[i] = d;
-  dy[i] = fma(r.sig + dw, d, -r.qs);
-  dzl[i] = r.b.has_l ? fma(-zl[i], d, r.b.pzl) / r.b.dl : 0.0;
-  dzu[i] = r.b.has_u ? fma(zu[i], d, r.b.pzu) / r.b.du : 0.0;
+  dy[i] = fma(sg + dw, d, -qs);
+  dzl[i] = rl != 0.0 ? fma(-rl, fma(zli, d, mu), zli) : 0.0;
+  dzu[i] = ru != 0.0 ? fma(-ru, fma(-zui, d, mu), zui) : 0.0;
 }
 
-__global__ void __launch_bounds__(kBlock) k_rec_vars(int64_t n, const double *__restrict__ x,
-                                                     const double *__restrict__ xl, const double *__restrict__ xu,
-                                                     const double *__restrict__ zl, const double *__restrict__ zu,
-                                                     const double *__restrict__ dx, double mu,
-                                                     double *__restrict__ dzl, double *__restrict__ dzu) {
+__global__ void __launch_bounds__(kBlock) k_rec_vars(int64_t n, const double *__restrict__ zl,
+                                                     const double *__restrict__ zu, const double *__restrict__ rlv,
+                                                     const double *__restrict__ ruv, const double *__restrict__ dx,
+                                                     double mu, double *__restrict__ dzl, double *__restrict__ dzu) {
   const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= n) return;
-  const Barrier b = barrier(x[j], xl[j], xu[j], zl[j], zu[j], mu);
-  dzl[j] = b.has_l ? fma(-zl[j], dx[j], b.pzl) / b.dl : 0.0;
-  dzu[j] = b.has_u ? fma(zu[j], dx[j], b.pzu) / b.du : 0.0;
+  const double rl = rlv[j], ru = ruv[j], v = dx[j];
+  dzl[j] = rl != 0.0 ? fma(-rl, fma(zl[j], v, mu), zl[j]) : 0.0;
+  dzu[j] = ru != 0.0 ? fma(-ru, fma(-zu[j], v, mu), zu[j]) : 0.0;
 }
 
 unsigned grid_for(int64_t count) { return (unsigned)((count + kBlock - 1) / kBlock); }
@@ -169,58 +150,63 @@ extern "C" {
 
 int mpopf_ipm_prepare(mpopf_handle *h, const double *x, const double *s, const double *zl_x, const double *zu_x,
                       const double *zl_s, const double *zu_s, double delta_w, double delta_c, double eps_tol,
-                      double *sigma_x, double *dvec, double *cvec, void *stream) {
-  if (!h || !x || !s || !zl_x || !zu_x || !zl_s || !zu_s || !sigma_x || !dvec || !cvec)
+                      double *sigma_x, double *dvec, double *cvec, double *recip, void *stream) {
+  if (!h || !x || !s || !zl_x || !zu_x || !zl_s || !zu_s || !sigma_x || !dvec || !cvec || !recip)
     return fail(MPOPF_ERR_ARG, "mpopf_ipm_prepare: NULL argument");
   const Dev &d = h->d;
   const mpopf_pattern &P = h->pat;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t n = d.n, m = d.m;
   const double e = 1.0 + delta_c * delta_w;
-  if (d.n > 0) k_prep_vars<<<grid_for(d.n), kBlock, 0, st>>>(d.n, x, P.xl, P.xu, zl_x, zu_x, sigma_x);
-  if (d.m > 0)
-    k_prep_rows<<<grid_for(d.m), kBlock, 0, st>>>(d.m, s, P.gl, P.gu, zl_s, zu_s, delta_w, delta_c, e, eps_tol, dvec,
-                                                  cvec);
+  if (n > 0) k_prep_vars<<<grid_for(n), kBlock, 0, st>>>(n, x, P.xl, P.xu, zl_x, zu_x, sigma_x, recip, recip + n);
+  if (m > 0) {
+    double *rl = recip + 2 * n, *ru = recip + 2 * n + m;
+    if (delta_c == 0.0)
+      k_prep_rows<true><<<grid_for(m), kBlock, 0, st>>>(m, s, P.gl, P.gu, zl_s, zu_s, delta_w, delta_c, e, eps_tol,
+                                                        dvec, cvec, rl, ru);
+    else
+      k_prep_rows<false><<<grid_for(m), kBlock, 0, st>>>(m, s, P.gl, P.gu, zl_s, zu_s, delta_w, delta_c, e,
+                                                         eps_tol, dvec, cvec, rl, ru);
+  }
   return check_launch("mpopf_ipm_prepare");
 }
 
-int mpopf_ipm_rhs(mpopf_handle *h, const double *x, const double *s, const double *y, const double *zl_x,
-                  const double *zu_x, const double *zl_s, const double *zu_s, const double *grad, const double *c,
-                  double mu, double delta_w, double delta_c, double eps_tol, double *rhs, void *stream) {
-  if (!h || !x || !s || !y || !zl_x || !zu_x || !zl_s || !zu_s || !grad || !c || !rhs)
+int mpopf_ipm_rhs(mpopf_handle *h, const double *x, const double *s, const double *y, const double *grad,
+                  const double *c, const double *recip, const double *dvec, const double *cvec, double mu,
+                  double *rhs, void *stream) {
+  if (!h || !x || !s || !y || !grad || !c || !recip || !dvec || !cvec || !rhs)
     return fail(MPOPF_ERR_ARG, "mpopf_ipm_rhs: NULL argument");
   const Dev &d = h->d;
-  const mpopf_pattern &P = h->pat;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const double e = 1.0 + delta_c * delta_w;
+  const int64_t n = d.n, m = d.m;
   double *w = h->work;
-  if (d.m > 0)
-    k_rhs_rows<<<grid_for(d.m), kBlock, 0, st>>>(d.m, s, y, P.gl, P.gu, zl_s, zu_s, c, mu, delta_w, delta_c, e,
-                                                 eps_tol, w);
+  if (m > 0)
+    k_rhs_rows<<<grid_for(m), kBlock, 0, st>>>(m, s, y, c, recip + 2 * n, recip + 2 * n + m, dvec, cvec, mu, w);
   int rc = check_launch("mpopf_ipm_rhs");
   if (rc != MPOPF_OK) return rc;
   rc = mpopf_vjp(h, x, w, rhs, nullptr, nullptr, stream);
   if (rc != MPOPF_OK) return rc;
-  if (d.n > 0) k_rhs_vars<<<grid_for(d.n), kBlock, 0, st>>>(d.n, x, P.xl, P.xu, zl_x, zu_x, grad, mu, rhs);
+  if (n > 0) k_rhs_vars<<<grid_for(n), kBlock, 0, st>>>(n, grad, recip, recip + n, mu, rhs);
   return check_launch("mpopf_ipm_rhs");
 }
 
 int mpopf_ipm_recover(mpopf_handle *h, const double *x, const double *s, const double *y, const double *zl_x,
-                      const double *zu_x, const double *zl_s, const double *zu_s, const double *c, const double *dx,
-                      double mu, double delta_w, double delta_c, double eps_tol, double *ds, double *dy,
-                      double *dzl_x, double *dzu_x, double *dzl_s, double *dzu_s, void *stream) {
-  if (!h || !x || !s || !y || !zl_x || !zu_x || !zl_s || !zu_s || !c || !dx || !ds || !dy || !dzl_x || !dzu_x ||
-      !dzl_s || !dzu_s)
+                      const double *zu_x, const double *zl_s, const double *zu_s, const double *c,
+                      const double *recip, const double *cvec, const double *dx, double mu, double delta_w,
+                      double delta_c, double *ds, double *dy, double *dzl_x, double *dzu_x, double *dzl_s,
+                      double *dzu_s, void *stream) {
+  if (!h || !x || !s || !y || !zl_x || !zu_x || !zl_s || !zu_s || !c || !recip || !cvec || !dx || !ds || !dy ||
+      !dzl_x || !dzu_x || !dzl_s || !dzu_s)
     return fail(MPOPF_ERR_ARG, "mpopf_ipm_recover: NULL argument");
   const Dev &d = h->d;
-  const mpopf_pattern &P = h->pat;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const double e = 1.0 + delta_c * delta_w;
+  const int64_t n = d.n, m = d.m;
   int rc = mpopf_jvp(h, x, dx, nullptr, nullptr, ds, stream);  // ds = J dx
   if (rc != MPOPF_OK) return rc;
-  if (d.m > 0)
-    k_rec_rows<<<grid_for(d.m), kBlock, 0, st>>>(d.m, s, y, P.gl, P.gu, zl_s, zu_s, c, mu, delta_w, delta_c, e,
-                                                 eps_tol, ds, dy, dzl_s, dzu_s);
-  if (d.n > 0) k_rec_vars<<<grid_for(d.n), kBlock, 0, st>>>(d.n, x, P.xl, P.xu, zl_x, zu_x, dx, mu, dzl_x, dzu_x);
+  if (m > 0)
+    k_rec_rows<<<grid_for(m), kBlock, 0, st>>>(m, s, y, c, zl_s, zu_s, recip + 2 * n, recip + 2 * n + m, cvec, mu,
+                                               delta_w, delta_c, ds, dy, dzl_s, dzu_s);
+  if (n > 0) k_rec_vars<<<grid_for(n), kBlock, 0, st>>>(n, zl_x, zu_x, recip, recip + n, dx, mu, dzl_x, dzu_x);
   return check_launch("mpopf_ipm_recover");
 }
 

@@ -89,9 +89,9 @@ def lib():
             "mpopf_vjp": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
             "mpopf_jvp": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
             "mpopf_hvp": (ctypes.c_int, [_P, _P, _P, _D, _P, _P, _P]),
-            "mpopf_ipm_prepare": (ctypes.c_int, [_P] * 7 + [_D] * 3 + [_P] * 4),
-            "mpopf_ipm_rhs": (ctypes.c_int, [_P] * 10 + [_D] * 4 + [_P, _P]),
-            "mpopf_ipm_recover": (ctypes.c_int, [_P] * 10 + [_D] * 4 + [_P] * 7),
+            "mpopf_ipm_prepare": (ctypes.c_int, [_P] * 7 + [_D] * 3 + [_P] * 5),
+            "mpopf_ipm_rhs": (ctypes.c_int, [_P] * 9 + [_D] + [_P, _P]),
+            "mpopf_ipm_recover": (ctypes.c_int, [_P] * 12 + [_D] * 3 + [_P] * 7),
             "mpopf_batch_create": (ctypes.c_int, [_P, _I32, ctypes.POINTER(_P)]),
             "mpopf_batch_set_io": (ctypes.c_int, [_P, _P, _P]),
             "mpopf_batch_sweep": (ctypes.c_int, [_P, _P]),
@@ -307,32 +307,36 @@ class Handle:
         import torch
         return torch.empty(k, dtype=torch.float64, device="cuda")
 
-    def ipm_prepare(self, x, s, zl_x, zu_x, zl_s, zu_s, delta_w, delta_c, eps_tol, stream=None):
-        """(Sigma_x [n], D [m], C [m]) from the bounds and bound duals."""
+    def ipm_prepare(self, x, s, zl_x, zu_x, zl_s, zu_s, delta_w, delta_c, eps_tol, recip=None, stream=None):
+        """(Sigma_x [n], D [m], C [m], recip [2n + 2m]) from the bounds and bound
+        duals; recip (the reciprocals 1/(v - lo), 1/(hi - v)) feeds ipm_rhs and
+        ipm_recover at the same point."""
         sigx, dvec, cvec = self._dvec(self.n), self._dvec(self.m), self._dvec(self.m)
+        recip = self._dvec(2 * (self.n + self.m)) if recip is None else recip
         _check(lib().mpopf_ipm_prepare(self.h, _ptr(x), _ptr(s), _ptr(zl_x), _ptr(zu_x), _ptr(zl_s), _ptr(zu_s),
                                        float(delta_w), float(delta_c), float(eps_tol), _ptr(sigx), _ptr(dvec),
-                                       _ptr(cvec), _stream_ptr(stream)), "mpopf_ipm_prepare")
-        return sigx, dvec, cvec
+                                       _ptr(cvec), _ptr(recip), _stream_ptr(stream)), "mpopf_ipm_prepare")
+        return sigx, dvec, cvec, recip
 
-    def ipm_rhs(self, x, s, y, zl_x, zu_x, zl_s, zu_s, grad, c, mu, delta_w, delta_c, eps_tol, out=None,
-                stream=None):
+    def ipm_rhs(self, x, s, y, grad, c, recip, dvec, cvec, mu, out=None, stream=None):
         """Condensed right-hand side q_x + J^T (C q_s + D q_y) [n]."""
         out = self._dvec(self.n) if out is None else out
-        _check(lib().mpopf_ipm_rhs(self.h, _ptr(x), _ptr(s), _ptr(y), _ptr(zl_x), _ptr(zu_x), _ptr(zl_s),
-                                   _ptr(zu_s), _ptr(grad), _ptr(c), float(mu), float(delta_w), float(delta_c),
-                                   float(eps_tol), _ptr(out), _stream_ptr(stream)), "mpopf_ipm_rhs")
+        _check(lib().mpopf_ipm_rhs(self.h, _ptr(x), _ptr(s), _ptr(y), _ptr(grad), _ptr(c), _ptr(recip),
+                                   _ptr(dvec), _ptr(cvec), float(mu), _ptr(out), _stream_ptr(stream)),
+               "mpopf_ipm_rhs")
         return out
 
-    def ipm_recover(self, x, s, y, zl_x, zu_x, zl_s, zu_s, c, dx, mu, delta_w, delta_c, eps_tol, stream=None):
+    def ipm_recover(self, x, s, y, zl_x, zu_x, zl_s, zu_s, c, recip, cvec, dx, mu, delta_w, delta_c, out=None,
+                    stream=None):
         """dict ds, dy, dzl_s, dzu_s [m] and dzl_x, dzu_x [n] from dx."""
-        r = dict(ds=self._dvec(self.m), dy=self._dvec(self.m), dzl_x=self._dvec(self.n),
-                 dzu_x=self._dvec(self.n), dzl_s=self._dvec(self.m), dzu_s=self._dvec(self.m))
+        r = out if out is not None else dict(
+            ds=self._dvec(self.m), dy=self._dvec(self.m), dzl_x=self._dvec(self.n), dzu_x=self._dvec(self.n),
+            dzl_s=self._dvec(self.m), dzu_s=self._dvec(self.m))
         _check(lib().mpopf_ipm_recover(self.h, _ptr(x), _ptr(s), _ptr(y), _ptr(zl_x), _ptr(zu_x), _ptr(zl_s),
-                                       _ptr(zu_s), _ptr(c), _ptr(dx), float(mu), float(delta_w), float(delta_c),
-                                       float(eps_tol), _ptr(r["ds"]), _ptr(r["dy"]), _ptr(r["dzl_x"]),
-                                       _ptr(r["dzu_x"]), _ptr(r["dzl_s"]), _ptr(r["dzu_s"]), _stream_ptr(stream)),
-               "mpopf_ipm_recover")
+                                       _ptr(zu_s), _ptr(c), _ptr(recip), _ptr(cvec), _ptr(dx), float(mu),
+                                       float(delta_w), float(delta_c), _ptr(r["ds"]), _ptr(r["dy"]),
+                                       _ptr(r["dzl_x"]), _ptr(r["dzu_x"]), _ptr(r["dzl_s"]), _ptr(r["dzu_s"]),
+                                       _stream_ptr(stream)), "mpopf_ipm_recover")
         return r
 
     def set_loads(self, pd, qd, stream=None):

@@ -50,20 +50,23 @@ def test_prepare_rhs_recover_match_oracle(case, dw, dc):
     rng = np.random.default_rng(72)
     dx = rng.standard_normal(o.n)
 
-    sigx, dvec, cvec = h.ipm_prepare(D["x"], D["s"], D["zlx"], D["zux"], D["zls"], D["zus"], dw, dc, EPS)
-    rsigx, rdvec, rcvec, _ = o.ipm_prepare(P["x"], P["s"], P["zlx"], P["zux"], P["zls"], P["zus"], dw, dc, EPS)
-    for k, got, want in (("sigx", sigx, rsigx), ("dvec", dvec, rdvec), ("cvec", cvec, rcvec)):
+    sigx, dvec, cvec, recip = h.ipm_prepare(D["x"], D["s"], D["zlx"], D["zux"], D["zls"], D["zus"], dw, dc, EPS)
+    rsigx, rdvec, rcvec, _, rrecip = o.ipm_prepare(P["x"], P["s"], P["zlx"], P["zux"], P["zls"], P["zus"], dw, dc,
+                                                   EPS)
+    for k, got, want in (("sigx", sigx, rsigx), ("dvec", dvec, rdvec), ("cvec", cvec, rcvec),
+                         ("recip", recip, rrecip)):
         assert np.array_equal(_np(got), want), f"{name}:{k}"
 
     # grad f and c(x) from the oracle on both sides, so that only the algebra is compared
     args = (P["x"], P["s"], P["y"], P["zlx"], P["zux"], P["zls"], P["zus"])
-    dargs = tuple(D[k] for k in ("x", "s", "y", "zlx", "zux", "zls", "zus"))
-    rhs = h.ipm_rhs(*dargs, _dev(ref["g"]), _dev(ref["c"]), MU, dw, dc, EPS)
+    dx_, ds_, dy_ = D["x"], D["s"], D["y"]
+    g, c = _dev(ref["g"]), _dev(ref["c"])
+    rhs = h.ipm_rhs(dx_, ds_, dy_, g, c, recip, dvec, cvec, MU)
     rrhs, _ = o.ipm_rhs(*args, ref["g"], ref["c"], MU, dw, dc, EPS)
     e, n = assert_close(f"{name}:rhs", _np(rhs), rrhs)
     assert e == n, f"{name}:rhs {e}/{n} bitwise"  # same element order as the oracle's J^T w
 
-    rec = h.ipm_recover(*dargs, _dev(ref["c"]), _dev(dx), MU, dw, dc, EPS)
+    rec = h.ipm_recover(dx_, ds_, dy_, D["zlx"], D["zux"], D["zls"], D["zus"], c, recip, cvec, _dev(dx), MU, dw, dc)
     rrec = o.ipm_recover(*args, ref["c"], dx, MU, dw, dc, EPS)
     for k, rk in (("ds", "ds"), ("dy", "dy"), ("dzl_x", "dzlx"), ("dzu_x", "dzux"), ("dzl_s", "dzls"),
                   ("dzu_s", "dzus")):
@@ -81,14 +84,14 @@ def test_recovered_step_solves_lifted_system():
     x, s, y, zlx, zux, zls, zus, xl, xu, sl, su = H.ipm_point(inst, o, 74, EPS)
     dx_, ds_, dy_ = _dev(x), _dev(s), _dev(y)
     dz = [_dev(a) for a in (zlx, zux, zls, zus)]
-    sigx, dvec, cvec = h.ipm_prepare(dx_, ds_, *dz, DW, DC, EPS)
+    sigx, dvec, cvec, recip = h.ipm_prepare(dx_, ds_, *dz, DW, DC, EPS)
     out = h.eval(mpopf.OUT_ALL, dx_, _dev(-y), 1.0, sigx, dvec, DW)
-    rhs = h.ipm_rhs(dx_, ds_, dy_, *dz, out["grad"], out["c"], MU, DW, DC, EPS)
+    rhs = h.ipm_rhs(dx_, ds_, dy_, out["grad"], out["c"], recip, dvec, cvec, MU)
     pat = {k: _np(v) for k, v in h.pattern().items()}
     n, m = o.n, o.m
     M = H.csr_to_dense_sym(pat["kkt_rowptr"], pat["kkt_col"], _np(out["kv"]), n)
     step = np.linalg.solve(M, _np(rhs))
-    rec = h.ipm_recover(dx_, ds_, dy_, *dz, out["c"], _dev(step), MU, DW, DC, EPS)
+    rec = h.ipm_recover(dx_, ds_, dy_, *dz, out["c"], recip, cvec, _dev(step), MU, DW, DC)
     A = H.dense_jac(pat["jac_row"], pat["jac_col"], _np(out["jv"]), m, n)
     W = H.dense_sym(pat["hess_row"], pat["hess_col"], _np(out["hv"]), n)
     K, p, sl_ = H.lifted_system(W, A, x, s, y, zlx, zux, zls, zus, xl, xu, sl, su, _np(out["grad"]),
@@ -109,5 +112,5 @@ def test_null_argument_is_rejected():
     lib = mpopf.lib()
     z = torch.zeros(cs.o.n, dtype=torch.float64, device="cuda")
     rc = lib.mpopf_ipm_prepare(cs.h.h, z.data_ptr(), None, None, None, None, None, 0.0, 0.0, 0.0, None, None,
-                               None, None)
+                               None, None, None)
     assert rc == -1 and b"NULL" in lib.mpopf_last_error()

@@ -518,7 +518,8 @@ def test_jvp_load_tangent_finite_difference():
 # Interior-point algebra around M (Sec. III-B): pinned by a dense solve of the
 # full lifted KKT system of Eq. (5)
 # ---------------------------------------------------------------------------
-def test_ipm_condensation_solves_full_lifted_system():
+@pytest.mark.parametrize("dw,dc", [(1e-3, 1e-4), (0.0, 0.0), (0.3, 0.7)])
+def test_ipm_condensation_solves_full_lifted_system(dw, dc):
     """Delta x from M_cond dx = q_x + A^T (C q_s + D q_y), with Delta s, Delta y
     and the Delta z recovered from it, solves the full 7-block system of
     Eq. (5) (assembled densely), so the condensation, the right-hand side and
@@ -526,7 +527,7 @@ def test_ipm_condensation_solves_full_lifted_system():
     inst = synth.make_instance(61, 5, 7, 2, 3, 2)
     o = oracle.Oracle(inst)
     n, m = o.n, o.m
-    eps, mu, dw, dc = 1e-2, 0.05, 1e-3, 1e-4
+    eps, mu = 1e-2, 0.05
     x, s, y, zlx, zux, zls, zus, xl, xu, sl, su = H.ipm_point(inst, o, 62, eps)
     lam = -y  # W = sigma grad^2 f + sum lam_i grad^2 c_i with the paper's p_x = grad f - J^T y
     r = o.eval(x, lam, 1.0)
@@ -534,7 +535,7 @@ def test_ipm_condensation_solves_full_lifted_system():
     A = H.dense_jac(jr, jc, r["jv"], m, n)
     hr, hc = o.hess_pattern()
     W = H.dense_sym(hr, hc, r["hv"], n)
-    sigx, dvec, cvec, sigs = o.ipm_prepare(x, s, zlx, zux, zls, zus, dw, dc, eps)
+    sigx, dvec, cvec, sigs, recip = o.ipm_prepare(x, s, zlx, zux, zls, zus, dw, dc, eps)
     rowptr, cols, kv = o.kkt_csr(x, lam, 1.0, sigx, dvec, dw)
     Mc = H.csr_to_dense_sym(rowptr, cols, kv, n)
     rhs, _ = o.ipm_rhs(x, s, y, zlx, zux, zls, zus, r["g"], r["c"], mu, dw, dc, eps)
@@ -565,3 +566,15 @@ def test_ipm_condensation_solves_full_lifted_system():
     # C and D are the paper's: C = (dc Sigma_s + (1 + dc dw) I)^-1, D = (Sigma_s + dw I) C
     np.testing.assert_allclose(cvec, 1.0 / (dc * sigs + 1.0 + dc * dw), rtol=1e-15)
     np.testing.assert_allclose(dvec, (sigs + dw) * cvec, rtol=1e-15)
+    # Sigma = Z (V - VL)^-1 + Z (VU - V)^-1 over finite bounds; the reciprocals
+    # are those distances' inverses and 0 for an infinite bound
+    with np.errstate(invalid="ignore", divide="ignore"):
+        for v, lo, hi, zl, zu, sig, rl, ru in ((x, xl, xu, zlx, zux, sigx, recip[:n], recip[n:2 * n]),
+                                              (s, sl, su, zls, zus, sigs, recip[2 * n:2 * n + m],
+                                               recip[2 * n + m:])):
+            il_, iu_ = np.isfinite(lo), np.isfinite(hi)
+            np.testing.assert_allclose(rl[il_], 1.0 / (v - lo)[il_], rtol=2e-16)
+            np.testing.assert_allclose(ru[iu_], 1.0 / (hi - v)[iu_], rtol=2e-16)
+            assert np.all(rl[~il_] == 0) and np.all(ru[~iu_] == 0)
+            ref = np.where(il_, zl / (v - lo), 0.0) + np.where(iu_, zu / (hi - v), 0.0)
+            np.testing.assert_allclose(sig, ref, rtol=1e-14)
