@@ -410,6 +410,89 @@ def batched_comparison(torch, reps=20):
     return res
 
 
+def graph_sweeps(torch, count=1000):
+    """Small sweeps are launch-bound, so they are replayed as one CUDA graph of
+    `count` sweeps at perturbed iterates (x_k = x + 1e-3 N(0, 1), drawn on the
+    device from a seeded generator), against the same sweeps launched one by
+    one: the 2,000-bus, T = 24 network and the single-period (T = 1) 10k-bus
+    network."""
+    from paper_2405_14032_b300 import mpopf, synth
+    dev = lambda a: torch.as_tensor(a, dtype=torch.float64, device="cuda")
+    res = {}
+    for name, (N, L, G, D, T, seed) in (("2000_bus_T24", (2000, 3200, 400, 1200, 24, 2)),
+                                         ("10k_bus_T1", (10000, 16000, 2000, 6000, 1, 3))):
+        inst = synth.make_instance(seed, N, L, G, D, T)
+        pt = synth.make_point(seed, inst)
+        h = mpopf.Handle(inst)
+        gen = torch.Generator(device="cuda").manual_seed(seed)
+        X = dev(pt.x) + 1e-3 * torch.randn((count, h.n), generator=gen, device="cuda", dtype=torch.float64)
+        lam, sx, dv = dev(pt.lam), dev(pt.sigma_x), dev(pt.dvec)
+        out = h.new_outputs()
+        sweep = lambda k: h.sweep(X[k], lam, pt.sigma, sx, dv, pt.delta_w, out=out)
+        for k in range(3):
+            sweep(k)
+        torch.cuda.synchronize()
+        e0, e1 = _events(torch)
+        e0.record()
+        for k in range(count):
+            sweep(k)
+        e1.record()
+        torch.cuda.synchronize()
+        plain_ms = e0.elapsed_time(e1)
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            sweep(0)
+        torch.cuda.current_stream().wait_stream(side)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            for k in range(count):
+                sweep(k)
+        g.replay()
+        torch.cuda.synchronize()
+        e0.record()
+        g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        graph_ms = e0.elapsed_time(e1)
+        alg = algorithmic_bytes(h.n, h.m, h.nnz_jac, h.nnz_hess, h.nnz_kkt, D, T)
+        res[name] = {"sweeps": count, "n": h.n, "m": h.m, "graph_ms_per_sweep": graph_ms / count,
+                     "plain_ms_per_sweep": plain_ms / count, "sweeps_per_s_graph": count / (graph_ms * 1e-3),
+                     "sweeps_per_s_plain": count / (plain_ms * 1e-3),
+                     "algorithmic_bytes_per_sweep": alg, "gbs_graph": alg * count / (graph_ms * 1e-3) / 1e9}
+        del g
+        h.close()
+    return res
+
+
+def csc_timing(torch, h, out, reps=20):
+    """COO -> CSC compression of the benchmark instance's J and W values (the
+    pattern built once on the host, untimed; each compression one kernel)."""
+    from paper_2405_14032_b300 import mpopf
+    res = {}
+    for which, key, nnz_coo in ((mpopf.CSC_JAC, "jv", h.nnz_jac), (mpopf.CSC_HESS, "hv", h.nnz_hess)):
+        t0 = time.perf_counter()
+        nnz = h.csc_pattern(which)["nnz"]
+        build_s = time.perf_counter() - t0
+        dst = torch.empty(nnz, dtype=torch.float64, device="cuda")
+        for _ in range(3):
+            h.coo_to_csc(which, out[key], out=dst)
+        torch.cuda.synchronize()
+        e0, e1 = _events(torch)
+        e0.record()
+        for _ in range(reps):
+            h.coo_to_csc(which, out[key], out=dst)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        # COO values read once, source index read once, CSC values written once (+ run starts for W)
+        alg = 8 * nnz_coo + 4 * nnz_coo + 8 * nnz + (8 * (nnz + 1) if nnz != nnz_coo else 0)
+        res["jac" if which == mpopf.CSC_JAC else "hess"] = {
+            "nnz_coo": nnz_coo, "nnz_csc": nnz, "ms": ms, "gbs": alg / (ms * 1e-3) / 1e9,
+            "pattern_build_s": build_s}
+    return res
+
+
 def ipm_timing(torch, h, reps=50, eps=1e-2, mu=0.05, dw=1e-3, dc=1e-4):
     """The interior-point algebra around M (Sec. III-B) on the benchmark
     instance: mpopf_ipm_prepare, mpopf_ipm_rhs and mpopf_ipm_recover at an
@@ -622,6 +705,8 @@ def run_ours(args, world, rank, local):
             line["adjoint"] = adjoint_comparison(torch)
             line["batched"] = batched_comparison(torch)
             line["ipm"] = ipm_timing(torch, h)
+            line["small_sweeps"] = graph_sweeps(torch)
+            line["csc"] = csc_timing(torch, h, out)
         print(json.dumps(line), flush=True)
     h.close()
     if world > 1:

@@ -242,6 +242,29 @@ int mpopf_ipm_recover(mpopf_handle *h, const double *x, const double *s, const d
                       double delta_c, double *ds, double *dy, double *dzl_x, double *dzu_x, double *dzl_s,
                       double *dzu_s, void *stream);
 
+/* COO -> CSC compression of J (m x n) and of the lower-triangle W (n x n)
+ * (Sec. III-A: the COO matrices may be compressed to CSC).  CSC entries are
+ * ordered by column, then row; entries of the COO pattern with the same
+ * (row, column) (W has them: the groups of its pattern overlap on diagonals)
+ * become one CSC entry holding their sum, added in COO order starting from the
+ * first.  J has no duplicates, so its CSC values are a permutation.
+ * mpopf_csc_pattern: fills *out with device pointers owned by the handle
+ *   (valid until mpopf_destroy): colptr [n + 1] (int64), rowidx [nnz] (int32).
+ *   The first call for a matrix builds the pattern (host counting sorts,
+ *   device allocation, synchronous); later calls return it.
+ * mpopf_coo_to_csc: csc_vals [nnz] from coo_vals [nnz_jac or nnz_hess] (the
+ *   values mpopf_eval_jac / mpopf_eval_hess write), device arrays, asynchronous
+ *   on the stream; MPOPF_ERR_ARG if the pattern was not built first.
+ * which: MPOPF_CSC_JAC or MPOPF_CSC_HESS (MPOPF_ERR_ARG otherwise). */
+enum { MPOPF_CSC_JAC = 0, MPOPF_CSC_HESS = 1 };
+typedef struct {
+  int64_t nnz;
+  const int64_t *colptr; /* [n + 1] */
+  const int32_t *rowidx; /* [nnz], ascending within a column */
+} mpopf_csc;
+int mpopf_csc_pattern(mpopf_handle *h, int32_t which, mpopf_csc *out);
+int mpopf_coo_to_csc(mpopf_handle *h, int32_t which, const double *coo_vals, double *csc_vals, void *stream);
+
 /* Batched full sweeps of many independent instances (uneven sizes and
  * horizons) in ONE persistent kernel launch, replayed as a CUDA graph.  The
  * paper evaluates one model per solver; this runs many, e.g. scenario or

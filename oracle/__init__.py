@@ -59,6 +59,8 @@ def load():
             "orc_cons_cstep": (None, [_P, _P, _P, _D, _P]),
             "orc_obj_textbook": (_D, [_P, _P]),
             "orc_branch_terms": (None, [_P, _P]),
+            "orc_csc_nnz": (ctypes.c_int64, [_P, ctypes.c_int32]),
+            "orc_csc": (None, [_P, ctypes.c_int32, _P, _P, _P, _P]),
             "orc_ipm_prepare": (None, [_P] * 7 + [_D, _D, _D] + [_P] * 5),
             "orc_ipm_rhs": (None, [_P] * 10 + [_D, _D, _D, _D, _P, _P]),
             "orc_ipm_recover": (None, [_P] * 10 + [_D, _D, _D, _D] + [_P] * 6),
@@ -223,6 +225,18 @@ class Oracle:
 
     def obj_textbook(self, x):
         return float(_lib.orc_obj_textbook(self.h, _ptr(_f64(x))))
+
+    # -- COO -> CSC compression (Sec. III-A) ----------------------------------
+    def csc(self, which, coo=None):
+        """(colptr [n + 1], rowidx, vals or None) of J (which = 0) or the lower W
+        (which = 1); duplicates summed in COO order."""
+        nnz = int(_lib.orc_csc_nnz(self.h, int(which)))
+        colptr = np.empty(self.n + 1, np.int64)
+        rowidx = np.empty(nnz, np.int32)
+        vals = None if coo is None else np.empty(nnz)
+        _lib.orc_csc(self.h, int(which), None if coo is None else _ptr(_f64(coo)), _ptr(colptr), _ptr(rowidx),
+                     None if vals is None else _ptr(vals))
+        return colptr, rowidx, vals
 
     # -- interior-point algebra around M (Sec. III-B) ------------------------
     def ipm_prepare(self, x, s, zlx, zux, zls, zus, delta_w, delta_c, eps):

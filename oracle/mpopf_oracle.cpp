@@ -965,6 +965,66 @@ void orc_ipm_recover(void* h, const double* x, const double* s, const double* y,
 
 }  // extern "C"
 
+// ---------------------------------------------------------------------------
+// COO -> CSC compression of J and of the lower-triangle W (Sec. III-A: the
+// COO matrices may be compressed to CSC).  Plain definition: entries ordered
+// by (column, row); entries with the same (row, column) (only W has them) are
+// one CSC entry whose value is their sum, added in COO order starting from the
+// first.  which = 0: J (m x n), which = 1: W (n x n, lower triangle).
+// ---------------------------------------------------------------------------
+namespace {
+struct CooEntry {
+  int32_t col, row;
+  int64_t e;
+};
+std::vector<CooEntry> coo_sorted(void* h, int32_t which) {
+  int64_t sz[4];
+  orc_sizes(h, sz);
+  const int64_t nnz = which == 0 ? sz[2] : sz[3];
+  std::vector<int32_t> r(nnz), c(nnz);
+  if (which == 0) orc_jac_pattern(h, r.data(), c.data());
+  else orc_hess_pattern(h, r.data(), c.data());
+  std::vector<CooEntry> v(nnz);
+  for (int64_t e = 0; e < nnz; ++e) v[e] = CooEntry{c[e], r[e], e};
+  std::sort(v.begin(), v.end(), [](const CooEntry& a, const CooEntry& b) {
+    if (a.col != b.col) return a.col < b.col;
+    if (a.row != b.row) return a.row < b.row;
+    return a.e < b.e;
+  });
+  return v;
+}
+}  // namespace
+
+extern "C" {
+int64_t orc_csc_nnz(void* h, int32_t which) {
+  const std::vector<CooEntry> v = coo_sorted(h, which);
+  int64_t k = 0;
+  for (size_t p = 0; p < v.size(); ++p)
+    if (p == 0 || v[p].col != v[p - 1].col || v[p].row != v[p - 1].row) ++k;
+  return k;
+}
+
+// colptr [ncols + 1], rowidx [orc_csc_nnz]; vals (if coo != NULL) [orc_csc_nnz].
+void orc_csc(void* h, int32_t which, const double* coo, int64_t* colptr, int32_t* rowidx, double* vals) {
+  const Model& M = *static_cast<Model*>(h);
+  const std::vector<CooEntry> v = coo_sorted(h, which);
+  for (int64_t j = 0; j <= M.n; ++j) colptr[j] = 0;
+  int64_t k = -1;
+  for (size_t p = 0; p < v.size(); ++p) {
+    const bool fresh = p == 0 || v[p].col != v[p - 1].col || v[p].row != v[p - 1].row;
+    if (fresh) {
+      ++k;
+      rowidx[k] = v[p].row;
+      colptr[v[p].col + 1] += 1;
+      if (coo) vals[k] = coo[v[p].e];
+    } else if (coo) {
+      vals[k] = vals[k] + coo[v[p].e];
+    }
+  }
+  for (int64_t j = 0; j < M.n; ++j) colptr[j + 1] += colptr[j];
+}
+}  // extern "C"
+
 // The canonical sin/cos (for pins against the C library).
 void orc_sincos(const double* x, int64_t n, double* s, double* c) {
   for (int64_t i = 0; i < n; ++i) sincos_cw(x[i], &s[i], &c[i]);

@@ -115,14 +115,28 @@ int batch_max_ctas_per_sm();
 }  // namespace mpopf
 
 // The handle (opaque to callers).
+namespace mpopf {
+constexpr int kMaxBlocks = 96;
+// CSC compression of J (0) or W (1), built on first request.
+struct CscState {
+  bool built;
+  int64_t nnz;
+  int64_t *colptr;  // [n + 1]
+  int32_t *rowidx;  // [nnz]
+  int32_t *src;     // COO entry of each sorted position
+  int64_t *seg;     // [nnz + 1] run starts into src (W with duplicates); NULL: one entry per slot
+};
+}  // namespace mpopf
+
 struct mpopf_handle {
   mpopf::Dev d;
   mpopf_pattern pat;
-  void *blocks[96];  // device allocations owned by the handle
+  void *blocks[mpopf::kMaxBlocks];  // device allocations owned by the handle
   int nblocks;
   // staging for mpopf_sweep_host (allocated on first use)
   double *stage;
   size_t stage_bytes;
   mpopf::Prof prof;
   double *work;  // [m] row vector of the condensed right-hand side
+  mpopf::CscState csc[2];
 };

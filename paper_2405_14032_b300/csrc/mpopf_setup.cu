@@ -240,6 +240,7 @@ T *dev_upload(mpopf_handle *h, const std::vector<T> &v, cudaError_t *err) {
   if (*err != cudaSuccess) return nullptr;
   void *p = nullptr;
   const size_t bytes = std::max<size_t>(v.size(), 1) * sizeof(T);
+  if (h->nblocks >= kMaxBlocks) { *err = cudaErrorMemoryAllocation; return nullptr; }
   *err = cudaMalloc(&p, bytes);
   if (*err != cudaSuccess) return nullptr;
   h->blocks[h->nblocks++] = p;
@@ -251,6 +252,7 @@ template <class T>
 T *dev_alloc(mpopf_handle *h, int64_t count, cudaError_t *err) {
   if (*err != cudaSuccess) return nullptr;
   void *p = nullptr;
+  if (h->nblocks >= kMaxBlocks) { *err = cudaErrorMemoryAllocation; return nullptr; }
   *err = cudaMalloc(&p, std::max<int64_t>(count, 1) * sizeof(T));
   if (*err != cudaSuccess) return nullptr;
   h->blocks[h->nblocks++] = p;

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libmpopf.so")
 
 OUT_OBJ, OUT_GRAD, OUT_CONS, OUT_JAC, OUT_HESS, OUT_KKT = 1, 2, 4, 8, 16, 32
 OUT_ALL = 63
+CSC_JAC, CSC_HESS = 0, 1
 
 _P = ctypes.c_void_p
 _D = ctypes.c_double
@@ -31,6 +32,10 @@ class _Network(ctypes.Structure):
             "bus_gs", "bus_bs", "bus_vmin", "bus_vmax", "br_f", "br_t", "br_r", "br_x", "br_b", "br_tap",
             "br_shift", "br_smax", "br_angmin", "br_angmax", "gen_bus", "gen_c2", "gen_c1", "gen_c0",
             "gen_pmin", "gen_pmax", "gen_qmin", "gen_qmax", "gen_ramp", "load_bus")]
+
+
+class _Csc(ctypes.Structure):
+    _fields_ = [("nnz", ctypes.c_int64), ("colptr", _P), ("rowidx", _P)]
 
 
 class _Pattern(ctypes.Structure):
@@ -89,6 +94,8 @@ def lib():
             "mpopf_vjp": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
             "mpopf_jvp": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
             "mpopf_hvp": (ctypes.c_int, [_P, _P, _P, _D, _P, _P, _P]),
+            "mpopf_csc_pattern": (ctypes.c_int, [_P, _I32, ctypes.POINTER(_Csc)]),
+            "mpopf_coo_to_csc": (ctypes.c_int, [_P, _I32, _P, _P, _P]),
             "mpopf_ipm_prepare": (ctypes.c_int, [_P] * 7 + [_D] * 3 + [_P] * 5),
             "mpopf_ipm_rhs": (ctypes.c_int, [_P] * 9 + [_D] + [_P, _P]),
             "mpopf_ipm_recover": (ctypes.c_int, [_P] * 12 + [_D] * 3 + [_P] * 7),
@@ -119,7 +126,7 @@ def exported_symbols():
     return ["mpopf_setup", "mpopf_get_pattern", "mpopf_set_loads", "mpopf_eval", "mpopf_eval_obj",
             "mpopf_eval_grad", "mpopf_eval_cons", "mpopf_eval_jac", "mpopf_eval_hess", "mpopf_assemble_kkt",
             "mpopf_sweep", "mpopf_sweep_host", "mpopf_assemble_kkt_noalloc", "mpopf_vjp", "mpopf_jvp", "mpopf_hvp",
-            "mpopf_ipm_prepare", "mpopf_ipm_rhs", "mpopf_ipm_recover", "mpopf_batch_create", "mpopf_batch_set_io", "mpopf_batch_sweep", "mpopf_batch_set_schedule",
+            "mpopf_csc_pattern", "mpopf_coo_to_csc", "mpopf_ipm_prepare", "mpopf_ipm_rhs", "mpopf_ipm_recover", "mpopf_batch_create", "mpopf_batch_set_io", "mpopf_batch_sweep", "mpopf_batch_set_schedule",
             "mpopf_batch_get_schedule", "mpopf_batch_tune", "mpopf_batch_status", "mpopf_batch_destroy",
             "mpopf_launch_count", "mpopf_profile_start", "mpopf_profile_stop",
             "mpopf_destroy", "mpopf_last_error"]
@@ -300,6 +307,29 @@ class Handle:
         out = torch.empty(self.n, dtype=torch.float64, device="cuda") if out is None else out
         _check(lib().mpopf_hvp(self.h, _ptr(x), _ptr(lam), float(sigma), _ptr(v), _ptr(out), _stream_ptr(stream)),
                "mpopf_hvp")
+        return out
+
+    # -- COO -> CSC compression -------------------------------------------------
+    def csc_pattern(self, which):
+        """dict(colptr [n + 1] int64, rowidx [nnz] int32) of J (CSC_JAC) or the
+        lower W (CSC_HESS), zero-copy views of handle-owned device memory
+        (built on the first call)."""
+        import torch
+        c = _Csc()
+        _check(lib().mpopf_csc_pattern(self.h, int(which), ctypes.byref(c)), "mpopf_csc_pattern")
+        self._csc_nnz = getattr(self, "_csc_nnz", {})
+        self._csc_nnz[int(which)] = int(c.nnz)
+        return dict(colptr=torch.as_tensor(_DeviceArray(c.colptr, self.n + 1, "<i8"), device="cuda"),
+                    rowidx=torch.as_tensor(_DeviceArray(c.rowidx, c.nnz, "<i4"), device="cuda"), nnz=int(c.nnz))
+
+    def coo_to_csc(self, which, coo_vals, out=None, stream=None):
+        """CSC values of J or W from their COO values (csc_pattern first)."""
+        nnz = getattr(self, "_csc_nnz", {}).get(int(which))
+        if nnz is None:
+            nnz = self.csc_pattern(which)["nnz"]
+        out = self._dvec(nnz) if out is None else out
+        _check(lib().mpopf_coo_to_csc(self.h, int(which), _ptr(coo_vals), _ptr(out), _stream_ptr(stream)),
+               "mpopf_coo_to_csc")
         return out
 
     # -- interior-point algebra around the condensed matrix -------------------

@@ -578,3 +578,37 @@ def test_ipm_condensation_solves_full_lifted_system(dw, dc):
             assert np.all(rl[~il_] == 0) and np.all(ru[~iu_] == 0)
             ref = np.where(il_, zl / (v - lo), 0.0) + np.where(iu_, zu / (hi - v), 0.0)
             np.testing.assert_allclose(sig, ref, rtol=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# COO -> CSC compression (Sec. III-A): against scipy's conversion and a dense
+# reconstruction with duplicates accumulated in COO order
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("which", [0, 1])
+def test_csc_compression_matches_scipy_and_dense(which):
+    import scipy.sparse as sp
+    for inst in (synth.config_instance("cfg1"), synth.make_instance(63, 40, 70, 9, 20, 3)):
+        o = oracle.Oracle(inst)
+        r, c = o.jac_pattern() if which == 0 else o.hess_pattern()
+        nrows = o.m if which == 0 else o.n
+        vals = np.random.default_rng(64).standard_normal(r.size)
+        colptr, rowidx, cv = o.csc(which, vals)
+        ref = sp.coo_matrix((vals, (r.astype(np.int64), c.astype(np.int64))), shape=(nrows, o.n)).tocsc()
+        ref.sum_duplicates()
+        ref.sort_indices()
+        assert np.array_equal(colptr, ref.indptr) and np.array_equal(rowidx, ref.indices)
+        np.testing.assert_allclose(cv, ref.data, rtol=1e-15, atol=1e-15)
+        # duplicates summed in COO order, exactly
+        dense = np.zeros((nrows, o.n))
+        np.add.at(dense, (r, c), vals)
+        back = np.zeros((nrows, o.n))
+        for j in range(o.n):
+            back[rowidx[colptr[j]:colptr[j + 1]], j] = cv[colptr[j]:colptr[j + 1]]
+        assert np.array_equal(back, dense)
+        if which == 0:
+            assert colptr[-1] == r.size  # J has no duplicate (row, col)
+        else:
+            assert colptr[-1] < r.size and np.all(rowidx >= np.repeat(np.arange(o.n), np.diff(colptr)))
+        assert np.all(np.diff(colptr) >= 0)
+        for j in range(o.n):
+            assert np.all(np.diff(rowidx[colptr[j]:colptr[j + 1]]) > 0)
