@@ -39,7 +39,7 @@ def load():
     if _lib is None:
         lib = ctypes.CDLL(build())
         sigs = {
-            "orc_new": (_P, [_P] * 9),
+            "orc_new": (_P, [_P] * 10),
             "orc_free": (None, [_P]),
             "orc_sizes": (None, [_P, _P]),
             "orc_bounds": (None, [_P, _P, _P, _P, _P]),
@@ -100,6 +100,7 @@ class Oracle:
                                  net.gen_qmin, net.gen_qmax, net.gen_ramp])),
             np.ascontiguousarray(net.load_bus, dtype=np.int32),
             _f64(inst.pd), _f64(inst.qd),
+            None if net.gen_qramp is None else _f64(net.gen_qramp),
         ]
         self.h = lib.orc_new(*[_ptr(a) for a in self._keep])
         out = np.zeros(4, np.int64)

@@ -139,6 +139,8 @@ struct Model {
   std::vector<double> br_r, br_x, br_b, tap, shift, smax, angmin, angmax;
   std::vector<int32_t> gbus;
   std::vector<double> c2, c1, c0, pmin, pmax, qmin, qmax, ramp;
+  bool has_qramp;             // reactive ramp rows K11 present
+  std::vector<double> qramp;  // [G] reactive ramp limits (if has_qramp)
   std::vector<int32_t> lbus;
   std::vector<double> pd, qd;  // [T][D]
   // pi-model admittance terms per branch (Y_ff = gff + j bff, ...)
@@ -170,12 +172,13 @@ void var_decode(const Model& M, int64_t j, int* kind, int64_t* t, int64_t* comp)
 }
 
 // Constraint rows: K0 ref (t); K1..K7 per branch (t*L + l); K8, K9 per bus;
-// K10 ramp ((t-1)*G + g, t >= 1).
+// K10 ramp ((t-1)*G + g, t >= 1); K11 reactive ramp (same indexing, optional).
 inline int64_t r_k0(const Model&, int64_t t) { return t; }
 inline int64_t r_br(const Model& M, int k, int64_t t, int64_t l) { return M.T + (k - 1) * M.T * M.L + t * M.L + l; }
 inline int64_t r_k8(const Model& M, int64_t t, int64_t n) { return M.T + 7 * M.T * M.L + t * M.N + n; }
 inline int64_t r_k9(const Model& M, int64_t t, int64_t n) { return M.T + 7 * M.T * M.L + M.T * M.N + t * M.N + n; }
 inline int64_t r_k10(const Model& M, int64_t t, int64_t g) { return M.T + 7 * M.T * M.L + 2 * M.T * M.N + (t - 1) * M.G + g; }
+inline int64_t r_k11(const Model& M, int64_t t, int64_t g) { return r_k10(M, M.T, 0) + (t - 1) * M.G + g; }
 
 // Row kind (0..10), period, component.
 void row_decode(const Model& M, int64_t i, int* kind, int64_t* t, int64_t* comp) {
@@ -185,7 +188,9 @@ void row_decode(const Model& M, int64_t i, int* kind, int64_t* t, int64_t* comp)
   i -= 7 * M.T * M.L;
   if (i < 2 * M.T * M.N) { *kind = 8 + (int)(i / (M.T * M.N)); i %= (M.T * M.N); *t = i / M.N; *comp = i % M.N; return; }
   i -= 2 * M.T * M.N;
-  *kind = 10; *t = 1 + i / M.G; *comp = i % M.G;
+  *kind = 10;
+  if (i >= (M.T - 1) * M.G) { *kind = 11; i -= (M.T - 1) * M.G; }
+  *t = 1 + i / M.G; *comp = i % M.G;
 }
 
 // Number of J entries of row i (its J order, see row_eval).
@@ -208,6 +213,7 @@ std::vector<std::pair<int64_t, int64_t>> window_rows(const Model& M, int64_t t0,
   r.push_back({r_k9(M, t0, 0), r_k9(M, t1, 0)});
   const int64_t a = std::max<int64_t>(t0, 1), b = std::max<int64_t>(t1, 1);
   r.push_back({r_k10(M, a, 0), r_k10(M, b, 0)});
+  if (M.has_qramp) r.push_back({r_k11(M, a, 0), r_k11(M, b, 0)});
   return r;
 }
 
@@ -362,16 +368,17 @@ void row_eval(const Model& M, const S* x, int64_t i, std::vector<int64_t>* cols,
     for (int64_t a : M.bus_arcs[n]) push(P ? v_p(M, t, a) : v_q(M, t, a), S(-1.0));
     return;
   }
-  // kind 10: ramp
+  // kind 10: ramp of pg; kind 11: ramp of qg
   const int64_t g = comp;
-  *cval = x[v_pg(M, t, g)] - x[v_pg(M, t - 1, g)];
-  push(v_pg(M, t, g), S(1.0)); push(v_pg(M, t - 1, g), S(-1.0));
+  const int64_t jt = kind == 10 ? v_pg(M, t, g) : v_qg(M, t, g), jp = kind == 10 ? v_pg(M, t - 1, g) : v_qg(M, t - 1, g);
+  *cval = x[jt] - x[jp];
+  push(jt, S(1.0)); push(jp, S(-1.0));
 }
 
 // ---------------------------------------------------------------------------
 // Elements (pattern instances) and their W entries.
 // ---------------------------------------------------------------------------
-enum ElemKind { E_OBJ = 0, E_REF = 1, E_BR = 2, E_BUS = 3, E_RAMP = 4 };
+enum ElemKind { E_OBJ = 0, E_REF = 1, E_BR = 2, E_BUS = 3, E_RAMP = 4, E_QRAMP = 5 };
 struct HEnt { int64_t r, c; double v; };
 
 inline void lower_push(std::vector<HEnt>* out, int64_t a, int64_t b, double v) {
@@ -450,6 +457,7 @@ void elem_rows(const Model& M, int kind, int64_t t, int64_t comp, std::vector<in
   if (kind == E_BR) for (int k = 1; k <= 7; ++k) rows->push_back(r_br(M, k, t, comp));
   if (kind == E_BUS) { rows->push_back(r_k8(M, t, comp)); rows->push_back(r_k9(M, t, comp)); }
   if (kind == E_RAMP) rows->push_back(r_k10(M, t, comp));
+  if (kind == E_QRAMP) rows->push_back(r_k11(M, t, comp));
 }
 
 int64_t elem_count(const Model& M, int kind) {
@@ -466,9 +474,10 @@ int64_t elem_count(const Model& M, int kind) {
 // Ramp elements of period t touch pg at t and t-1, so t = t1 is included.
 template <class F>
 void for_elements(const Model& M, int64_t t0, int64_t t1, F fn) {
-  for (int kind = E_OBJ; kind <= E_RAMP; ++kind) {
+  for (int kind = E_OBJ; kind <= E_QRAMP; ++kind) {
+    if (kind == E_QRAMP && !M.has_qramp) break;
     int64_t ta = t0, tb = t1;
-    if (kind == E_RAMP) { ta = std::max<int64_t>(t0, 1); tb = std::min<int64_t>(t1 + 1, M.T); }
+    if (kind == E_RAMP || kind == E_QRAMP) { ta = std::max<int64_t>(t0, 1); tb = std::min<int64_t>(t1 + 1, M.T); }
     for (int64_t t = ta; t < tb; ++t)
       for (int64_t c = 0; c < elem_count(M, kind); ++c) fn(kind, t, c);
   }
@@ -491,7 +500,8 @@ void* orc_new(const int64_t* dims /* N, L, G, D, ref, T */,
               const double* bus /* [4][N]: gs, bs, vmin, vmax */,
               const int32_t* br_ft /* [2][L] */, const double* br /* [8][L]: r, x, b, tap, shift, smax, angmin, angmax */,
               const int32_t* gen_bus, const double* gen /* [8][G]: c2, c1, c0, pmin, pmax, qmin, qmax, ramp */,
-              const int32_t* load_bus, const double* pd, const double* qd) {
+              const int32_t* load_bus, const double* pd, const double* qd,
+              const double* qramp /* [G] reactive ramp limits, or NULL for none */) {
   Model* M = new Model();
   M->N = dims[0]; M->L = dims[1]; M->G = dims[2]; M->D = dims[3]; M->ref = dims[4]; M->T = dims[5];
   const int64_t N = M->N, L = M->L, G = M->G, D = M->D, T = M->T;
@@ -503,6 +513,8 @@ void* orc_new(const int64_t* dims /* N, L, G, D, ref, T */,
   M->gbus.assign(gen_bus, gen_bus + G);
   M->c2 = cp(gen, G); M->c1 = cp(gen + G, G); M->c0 = cp(gen + 2 * G, G); M->pmin = cp(gen + 3 * G, G);
   M->pmax = cp(gen + 4 * G, G); M->qmin = cp(gen + 5 * G, G); M->qmax = cp(gen + 6 * G, G); M->ramp = cp(gen + 7 * G, G);
+  M->has_qramp = qramp != nullptr;
+  if (M->has_qramp) M->qramp = cp(qramp, G);
   M->lbus.assign(load_bus, load_bus + D);
   M->pd = cp(pd, T * D); M->qd = cp(qd, T * D);
   branch_terms(*M);
@@ -511,7 +523,7 @@ void* orc_new(const int64_t* dims /* N, L, G, D, ref, T */,
   for (int64_t a = 0; a < 2 * L; ++a) M->bus_arcs[a < L ? M->f[a] : M->t[a - L]].push_back(a);
   for (int64_t d = 0; d < D; ++d) M->bus_loads[M->lbus[d]].push_back(d);
   M->n = T * (2 * N + 2 * G + 4 * L);
-  M->m = T * (1 + 7 * L + 2 * N) + G * (T - 1);
+  M->m = T * (1 + 7 * L + 2 * N) + G * (T - 1) * (M->has_qramp ? 2 : 1);
   M->jrp.assign(M->m + 1, 0);
   for (int64_t i = 0; i < M->m; ++i) M->jrp[i + 1] = M->jrp[i] + row_len(*M, i);
   return M;
@@ -551,6 +563,7 @@ void orc_bounds(void* h, double* xl, double* xu, double* gl, double* gu) {
     if (kind == 5) { lo = M.angmin[comp]; hi = M.angmax[comp]; }
     if (kind == 6 || kind == 7) { lo = -inf; hi = 0.0; }
     if (kind == 10) { lo = -M.ramp[comp]; hi = M.ramp[comp]; }
+    if (kind == 11) { lo = -M.qramp[comp]; hi = M.qramp[comp]; }
     gl[i] = lo; gu[i] = hi;
   }
 }
@@ -1110,6 +1123,8 @@ void cons_textbook(const Model& M, const S* x, S* c) {
     }
     if (t >= 1)
       for (int64_t g = 0; g < M.G; ++g) c[r_k10(M, t, g)] = x[v_pg(M, t, g)] - x[v_pg(M, t - 1, g)];
+    if (t >= 1 && M.has_qramp)
+      for (int64_t g = 0; g < M.G; ++g) c[r_k11(M, t, g)] = x[v_qg(M, t, g)] - x[v_qg(M, t - 1, g)];
   }
 }
 }  // namespace

@@ -113,6 +113,7 @@ class Network:
     gen_qmax: np.ndarray
     gen_ramp: np.ndarray
     load_bus: np.ndarray
+    gen_qramp: np.ndarray | None = None  # reactive ramp limits [G]; None: no reactive ramp rows
 
 
 @dataclasses.dataclass
@@ -202,14 +203,23 @@ def make_instance(seed: int, n_bus: int, n_branch: int, n_gen: int, n_load: int,
     return Instance(net=net, T=int(T), pd=pd, qd=qd)
 
 
+def with_reactive_ramp(inst: Instance, frac: float = 0.2) -> Instance:
+    """The same instance with reactive ramp limits Q_ramp = frac * Qmax (the
+    counterpart of the real ramp limits 0.2 * Pmax)."""
+    net = dataclasses.replace(inst.net, gen_qramp=frac * np.asarray(inst.net.gen_qmax, np.float64))
+    return Instance(net=net, T=inst.T, pd=inst.pd, qd=inst.qd)
+
+
 def sizes(net: Network, T: int) -> tuple[int, int]:
-    """(n, m): variables T(2N + 2G + 4L) and constraints T(1 + 7L + 2N) + G(T - 1).
+    """(n, m): variables T(2N + 2G + 4L) and constraints T(1 + 7L + 2N) + G(T - 1),
+    plus G(T - 1) reactive ramp rows when the network has them.
 
     Interface sizes only (the variable and row counts of the model, Table II),
     so that evaluation vectors of the right length can be drawn.
     """
     N, L, G = net.n_bus, net.n_branch, net.n_gen
-    return T * (2 * N + 2 * G + 4 * L), T * (1 + 7 * L + 2 * N) + G * (T - 1)
+    ramps = 2 if net.gen_qramp is not None else 1
+    return T * (2 * N + 2 * G + 4 * L), T * (1 + 7 * L + 2 * N) + ramps * G * (T - 1)
 
 
 @dataclasses.dataclass

@@ -19,9 +19,11 @@ from tests import helpers as H
 HERE = os.path.dirname(os.path.abspath(__file__))
 
 
-@pytest.fixture(scope="module")
-def cfg1():
+@pytest.fixture(scope="module", params=["cfg1", "cfg1_reactive_ramp"])
+def cfg1(request):
     inst = synth.config_instance("cfg1")
+    if request.param == "cfg1_reactive_ramp":
+        inst = synth.with_reactive_ramp(inst)
     pt = synth.make_point(1, inst)
     o = oracle.Oracle(inst)
     return inst, pt, o
