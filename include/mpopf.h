@@ -31,7 +31,7 @@
  *     va[t][i] at t N + i;  vm at T N + t N + i;  pg at 2TN + t G + g;
  *     qg at 2TN + TG + t G + g;  p[t][a] at 2TN + 2TG + 2tL + a;
  *     q[t][a] at 2TN + 2TG + 2TL + 2tL + a.
- *   constraint rows [m], m = T (1 + 7L + 2N) + G (T - 1):
+ *   constraint rows [m], m = T (1 + 7L + 2N) + G (T - 1) (+ G (T - 1) with K11):
  *     K0  reference angle       t                      va[t][ref]              = 0
  *     K1  from-end P flow      T + 0TL + tL + l        p[t][l]   - P_fr        = 0
  *     K2  from-end Q flow      T + 1TL + tL + l        q[t][l]   - Q_fr        = 0
@@ -43,6 +43,9 @@
  *     K8  P balance            T + 7TL + tN + n        sum pg - sum p_a - gs vm^2 - sum Pd = 0
  *     K9  Q balance            T + 7TL + TN + tN + n   sum qg - sum q_a + bs vm^2 - sum Qd = 0
  *     K10 P ramp (t >= 1)      T + 7TL + 2TN + (t-1)G + g   pg[t] - pg[t-1] in [-ramp, ramp]
+ *     K11 Q ramp (t >= 1)      T + 7TL + 2TN + (T-1)G + (t-1)G + g   qg[t] - qg[t-1] in
+ *                              [-qramp, qramp]; only when gen_qramp is given (the
+ *                              reactive ramp that Eq. 1 of the paper leaves commented out)
  *   Flows are the pi-model of a branch with series admittance 1/(r + jx),
  *   charging b, tap tau and shift phi (Eq. 1d, 1e print the mutual term only).
  *   Objective (Eq. 1a): f = sum_{t,g} c2 pg^2 + c1 pg + c0.
@@ -51,7 +54,8 @@
  *   J (COO): rows ascending; within a row the J order
  *     K0 [va_ref]; K1..K4 [arc, va_f, va_t, vm_f, vm_t]; K5 [va_f, va_t];
  *     K6/K7 [p_a, q_a]; K8 [vm_n, pg of the bus ascending, p_a of the bus
- *     ascending]; K9 the same with qg, q_a; K10 [pg_t, pg_{t-1}].
+ *     ascending]; K9 the same with qg, q_a; K10 [pg_t, pg_{t-1}];
+ *     K11 [qg_t, qg_{t-1}].
  *   W = sigma grad^2 f + sum_i lambda_i grad^2 c_i (Eq. 4), lower COO
  *     (row >= col), duplicates allowed (a consumer sums them), groups in order:
  *     objective (t, g) [pg,pg]; branch (t, l) 10 entries over (va_f, va_t,
@@ -105,6 +109,7 @@ typedef struct {
   const double *gen_c2, *gen_c1, *gen_c0;                       /* [G] */
   const double *gen_pmin, *gen_pmax, *gen_qmin, *gen_qmax, *gen_ramp; /* [G] */
   const int32_t *load_bus;                                      /* [D] */
+  const double *gen_qramp; /* [G] reactive ramp limits (>= 0), or NULL: no K11 rows */
 } mpopf_network;
 
 /* Sizes and patterns.  Every pointer is DEVICE memory owned by the handle and

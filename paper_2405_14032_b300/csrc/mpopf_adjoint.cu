@@ -100,7 +100,13 @@ __global__ void __launch_bounds__(kBlock) k_vjp_gen(Dev d, const double *__restr
   if (t >= 1) a = a + __ldg(y + rr);         // ramp row (t, g): +1
   if (t + 1 < d.T) a = a - __ldg(y + rr + G);  // ramp row (t + 1, g): -1
   gx[d.x_pg + tg] = a;
-  gx[d.x_qg + tg] = __ldg(y + d.c_k9 + tn);
+  double b = __ldg(y + d.c_k9 + tn);  // bus element (K9, entry +1)
+  if (d.qramp) {
+    const int64_t rq = d.c_k11 + (int64_t)(t - 1) * G + g;
+    if (t >= 1) b = b + __ldg(y + rq);         // reactive ramp row (t, g): +1
+    if (t + 1 < d.T) b = b - __ldg(y + rq + G);  // reactive ramp row (t + 1, g): -1
+  }
+  gx[d.x_qg + tg] = b;
 }
 
 // ---------------------------------------------------------------------------
@@ -177,6 +183,10 @@ __global__ void __launch_bounds__(kBlock) k_jvp_gen(Dev d, const double *__restr
   if (tg >= (d.T - 1) * G) return;  // ramp rows (t, g), t = 1..T-1, row index (t - 1) G + g
   const int64_t cur = d.x_pg + G + tg;
   out[d.c_k10 + tg] = __ldg(v + cur) - __ldg(v + cur - G);
+  if (d.qramp) {
+    const int64_t qc = d.x_qg + G + tg;
+    out[d.c_k11 + tg] = __ldg(v + qc) - __ldg(v + qc - G);
+  }
 }
 
 // ---------------------------------------------------------------------------

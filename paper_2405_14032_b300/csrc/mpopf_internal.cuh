@@ -24,14 +24,15 @@ struct Dev {
   // variable block starts (va at 0)
   int64_t x_vm, x_pg, x_qg, x_p, x_q;
   // constraint block starts (K0 at 0, K_k (1..7) at T + (k-1) T L)
-  int64_t c_k8, c_k9, c_k10;
+  int64_t c_k8, c_k9, c_k10, c_k11;  // c_k11: reactive ramp rows (if qramp)
+  int32_t qramp;                     // 1: reactive ramp rows K11 present
   // J value starts (K0 at 0, K_k (1..4) at T + 5 (k-1) T L)
-  int64_t j_k5, j_k6, j_k7, j_k8, j_k9, j_k10, jk8_per;
+  int64_t j_k5, j_k6, j_k7, j_k8, j_k9, j_k10, j_k11, jk8_per;
   // W value starts (objective at 0)
   int64_t h_br, h_th, h_sh;
   // M: region start of each variable kind and per-period block sizes
   int64_t m_va, m_vm, m_pg, m_qg, m_p, m_q;
-  int64_t mb_va, mb_vm, mb_pg0, mb_pg1, mb_qg, mb_p, mb_q;
+  int64_t mb_va, mb_vm, mb_pg0, mb_pg1, mb_qg, mb_qg1, mb_p, mb_q;  // qg: t = 0 block, t >= 1 blocks
   int64_t nnz_jac, nnz_hess, nnz_kkt;
   // network
   const int32_t *br_f, *br_t;
@@ -51,7 +52,7 @@ struct Dev {
   const int32_t *arc_rank;               // position among the arcs of its bus
   const int32_t *jk8_off;                // offset of the K8 (and K9) J row of bus n inside a period block
   // M row offsets inside a period block
-  const int32_t *mo_va, *mo_vm, *mo_pg0, *mo_pg1, *mo_qg, *mo_p, *mo_q;
+  const int32_t *mo_va, *mo_vm, *mo_pg0, *mo_pg1, *mo_qg, *mo_qg1, *mo_p, *mo_q;
   // loads [T][D]
   const double *pd, *qd;
   // Incidence slots: slot of branch l's from / to end in its bus's incident
@@ -92,7 +93,7 @@ cudaError_t launch_patterns(const Dev &d, int32_t *jrow, int32_t *jcol, int32_t 
                             int64_t *krowptr, int32_t *kcol, double *xl, double *xu, double *gl, double *gu,
                             const double *vmin, const double *vmax, const double *pmin, const double *pmax,
                             const double *qmin, const double *qmax, const double *angmin, const double *angmax,
-                            const double *ramp, cudaStream_t s);
+                            const double *ramp, const double *qramp, cudaStream_t s);
 
 void set_error(const std::string &msg);
 

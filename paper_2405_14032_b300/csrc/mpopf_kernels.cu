@@ -410,11 +410,19 @@ __device__ __forceinline__ void gen_body(const Dev &d, int32_t tg, int32_t blk, 
   const double Wobj = sigma * c2x2;
   if (mk & MPOPF_OUT_HESS) hv[tg] = Wobj;
   const int64_t rr = d.c_k10 + (int64_t)(t - 1) * G + g;  // ramp row (t, g)
+  const int64_t rq = d.c_k11 + (int64_t)(t - 1) * G + g;  // reactive ramp row (t, g), if present
   if (t >= 1) {
-    if (mk & MPOPF_OUT_CONS) c[rr] = pg - __ldg(x + d.x_pg + tg - G);
+    if (mk & MPOPF_OUT_CONS) {
+      c[rr] = pg - __ldg(x + d.x_pg + tg - G);
+      if (d.qramp) c[rq] = __ldg(x + d.x_qg + tg) - __ldg(x + d.x_qg + tg - G);
+    }
     if (mk & MPOPF_OUT_JAC) {
       jv[d.j_k10 + 2 * ((int64_t)(t - 1) * G + g)] = 1.0;
       jv[d.j_k10 + 2 * ((int64_t)(t - 1) * G + g) + 1] = -1.0;
+      if (d.qramp) {
+        jv[d.j_k11 + 2 * ((int64_t)(t - 1) * G + g)] = 1.0;
+        jv[d.j_k11 + 2 * ((int64_t)(t - 1) * G + g) + 1] = -1.0;
+      }
     }
   }
   if (!(mk & MPOPF_OUT_KKT)) return;
@@ -436,10 +444,21 @@ __device__ __forceinline__ void gen_body(const Dev &d, int32_t tg, int32_t blk, 
   if (t + 1 < d.T) diag = diag + __ldg(dv + rr + G);
   for (int32_t e = 0; e < rank; ++e) pr[k++] = D8;
   pr[k] = diag;
-  double *qr = kv + d.m_qg + (int64_t)t * d.mb_qg + __ldg(d.mo_qg + g);
+  double *qr = kv + d.m_qg + (t == 0 ? (int64_t)__ldg(d.mo_qg + g)
+                                     : d.mb_qg + (int64_t)(t - 1) * d.mb_qg1 + __ldg(d.mo_qg1 + g));
   qr[0] = w9;
-  for (int32_t e = 0; e < rank; ++e) qr[1 + e] = D9;
-  qr[1 + rank] = (__ldg(sx + d.x_qg + tg) + dw) + D9;
+  k = 1;
+  double qdiag = (__ldg(sx + d.x_qg + tg) + dw) + D9;
+  if (d.qramp) {
+    if (t >= 1) {
+      const double D11 = __ldg(dv + rq);
+      qr[k++] = negx(D11);
+      qdiag = qdiag + D11;
+    }
+    if (t + 1 < d.T) qdiag = qdiag + __ldg(dv + rq + G);
+  }
+  for (int32_t e = 0; e < rank; ++e) qr[k++] = D9;
+  qr[k] = qdiag;
 }
 
 template <unsigned MASK>

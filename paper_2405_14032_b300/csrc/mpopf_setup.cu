@@ -78,10 +78,13 @@ __global__ void k_pat_jac(Dev d, int32_t *__restrict__ jrow, int32_t *__restrict
     return;
   }
   r -= 2 * T * N;
+  // K10 ramp of pg, then (if present) K11 ramp of qg: [var(t) (+1), var(t - 1) (-1)]
+  const bool q = r >= (T - 1) * G;
+  if (q) r -= (T - 1) * G;
   const int64_t t = 1 + r / G, g = r - (t - 1) * G;
-  const int64_t o = d.j_k10 + r * 2;
-  jrow[o] = (int32_t)i; jcol[o] = (int32_t)(d.x_pg + t * G + g);
-  jrow[o + 1] = (int32_t)i; jcol[o + 1] = (int32_t)(d.x_pg + (t - 1) * G + g);
+  const int64_t o = (q ? d.j_k11 : d.j_k10) + r * 2, base = q ? d.x_qg : d.x_pg;
+  jrow[o] = (int32_t)i; jcol[o] = (int32_t)(base + t * G + g);
+  jrow[o + 1] = (int32_t)i; jcol[o + 1] = (int32_t)(base + (t - 1) * G + g);
 }
 
 __global__ void k_pat_hess(Dev d, int32_t *__restrict__ hrow, int32_t *__restrict__ hcol) {
@@ -154,8 +157,9 @@ __global__ void k_pat_kkt(Dev d, int64_t *__restrict__ rowptr, int32_t *__restri
     put(j);
   } else if (j < d.x_p) {
     const int64_t tg = j - d.x_qg, t = tg / G, g = tg - t * G, nb = d.gen_bus[g];
-    start = d.m_qg + t * d.mb_qg + d.mo_qg[g];
+    start = d.m_qg + (t == 0 ? (int64_t)d.mo_qg[g] : d.mb_qg + (t - 1) * d.mb_qg1 + d.mo_qg1[g]);
     put(d.x_vm + t * N + nb);
+    if (d.qramp && t >= 1) put(d.x_qg + (t - 1) * G + g);
     for (int32_t q = d.bgen_ptr[nb]; q < d.bgen_ptr[nb] + d.gen_rank[g]; ++q) put(d.x_qg + t * G + d.bgen_idx[q]);
     put(j);
   } else {
@@ -182,7 +186,7 @@ __global__ void k_pat_kkt(Dev d, int64_t *__restrict__ rowptr, int32_t *__restri
 __global__ void k_bounds(Dev d, double *__restrict__ xl, double *__restrict__ xu, double *__restrict__ gl,
                          double *__restrict__ gu, const double *vmin, const double *vmax, const double *pmin,
                          const double *pmax, const double *qmin, const double *qmax, const double *angmin,
-                         const double *angmax, const double *ramp) {
+                         const double *angmax, const double *ramp, const double *qramp) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t N = d.N, G = d.G, L = d.L, T = d.T;
   if (i < d.n) {
@@ -201,6 +205,10 @@ __global__ void k_bounds(Dev d, double *__restrict__ xl, double *__restrict__ xu
       const int64_t l = ((i - T) - (k - 1) * TL) % L;
       if (k == 5) { lo = angmin[l]; hi = angmax[l]; }
       if (k == 6 || k == 7) { lo = -INFINITY; hi = 0.0; }
+    } else if (d.qramp && i >= d.c_k11) {
+      const int64_t g = (i - d.c_k11) % G;
+      lo = -qramp[g];
+      hi = qramp[g];
     } else if (i >= d.c_k10) {
       const int64_t g = (i - d.c_k10) % G;
       lo = -ramp[g];
@@ -219,13 +227,13 @@ cudaError_t launch_patterns(const Dev &d, int32_t *jrow, int32_t *jcol, int32_t 
                             int64_t *krowptr, int32_t *kcol, double *xl, double *xu, double *gl, double *gu,
                             const double *vmin, const double *vmax, const double *pmin, const double *pmax,
                             const double *qmin, const double *qmax, const double *angmin, const double *angmax,
-                            const double *ramp, cudaStream_t s) {
+                            const double *ramp, const double *qramp, cudaStream_t s) {
   if (d.m > 0) k_pat_jac<<<grid_for(d.m), kBlock, 0, s>>>(d, jrow, jcol);
   if (d.nnz_hess > 0) k_pat_hess<<<grid_for(d.nnz_hess), kBlock, 0, s>>>(d, hrow, hcol);
   if (d.n > 0) k_pat_kkt<<<grid_for(d.n), kBlock, 0, s>>>(d, krowptr, kcol);
   const int64_t nm = d.n > d.m ? d.n : d.m;
   k_bounds<<<grid_for(nm), kBlock, 0, s>>>(d, xl, xu, gl, gu, vmin, vmax, pmin, pmax, qmin, qmax, angmin, angmax,
-                                          ramp);
+                                          ramp, qramp);
   return cudaGetLastError();
 }
 
@@ -287,7 +295,8 @@ int mpopf_setup(const mpopf_network *net, int32_t n_periods, const double *pd, c
   if (net->ref_bus < 0 || net->ref_bus >= N) return fail(MPOPF_ERR_ARG, "mpopf_setup: ref_bus out of range");
   // Sizes first (before touching any array), so oversized problems fail cleanly.
   const int64_t n = T * (2 * N + 2 * G + 4 * L);
-  const int64_t m = T * (1 + 7 * L + 2 * N) + G * (T - 1);
+  const bool qramp = G > 0 && net->gen_qramp != nullptr;
+  const int64_t m = T * (1 + 7 * L + 2 * N) + G * (T - 1) * (qramp ? 2 : 1);
   if (n >= ((int64_t)1 << 31) || m >= ((int64_t)1 << 31) || T * L >= ((int64_t)1 << 31))
     return fail(MPOPF_ERR_SIZE, "mpopf_setup: n or m >= 2^31 (32-bit pattern indices)");
   if (N > 0 && (!net->bus_gs || !net->bus_bs || !net->bus_vmin || !net->bus_vmax))
@@ -310,6 +319,9 @@ int mpopf_setup(const mpopf_network *net, int32_t n_periods, const double *pd, c
   }
   for (int64_t g = 0; g < G; ++g)
     if (net->gen_bus[g] < 0 || net->gen_bus[g] >= N) return fail(MPOPF_ERR_ARG, "mpopf_setup: generator bus out of range");
+  if (qramp)
+    for (int64_t g = 0; g < G; ++g)
+      if (!(net->gen_qramp[g] >= 0.0)) return fail(MPOPF_ERR_ARG, "mpopf_setup: reactive ramp limit must be >= 0");
   for (int64_t k = 0; k < D; ++k)
     if (net->load_bus[k] < 0 || net->load_bus[k] >= N) return fail(MPOPF_ERR_ARG, "mpopf_setup: load bus out of range");
 
@@ -452,7 +464,8 @@ int mpopf_setup(const mpopf_network *net, int32_t n_periods, const double *pd, c
     for (size_t k = 0; k < len.size(); ++k) { (*off)[k] = (int32_t)s; s += len[k]; }
     return s;
   };
-  std::vector<int64_t> len_va(N), len_vm(N), len_pg0(G), len_pg1(G), len_qg(G), len_p(2 * L), len_q(2 * L);
+  std::vector<int64_t> len_va(N), len_vm(N), len_pg0(G), len_pg1(G), len_qg(G), len_qg1(G), len_p(2 * L),
+      len_q(2 * L);
   for (int64_t i = 0; i < N; ++i) {
     len_va[i] = bus_ndlt[i] + 1;
     len_vm[i] = (bus_nd[i] > 0 ? bus_nd[i] + 1 : 0) + bus_ndlt[i] + 1;
@@ -461,6 +474,7 @@ int mpopf_setup(const mpopf_network *net, int32_t n_periods, const double *pd, c
     len_pg0[g] = 1 + gen_rank[g] + 1;
     len_pg1[g] = 2 + gen_rank[g] + 1;
     len_qg[g] = 1 + gen_rank[g] + 1;
+    len_qg1[g] = (qramp ? 2 : 1) + gen_rank[g] + 1;
   }
   for (int64_t a = 0; a < 2 * L; ++a) {
     const int64_t bus = a < L ? net->br_f[a] : net->br_t[a - L];
@@ -468,10 +482,11 @@ int mpopf_setup(const mpopf_network *net, int32_t n_periods, const double *pd, c
     len_p[a] = 4 + kb + arc_rank[a] + 1;
     len_q[a] = 4 + kb + 1 + arc_rank[a] + 1;
   }
-  std::vector<int32_t> mo_va, mo_vm, mo_pg0, mo_pg1, mo_qg, mo_p, mo_q;
+  std::vector<int32_t> mo_va, mo_vm, mo_pg0, mo_pg1, mo_qg, mo_qg1, mo_p, mo_q;
   const int64_t mb_va = prefix(len_va, &mo_va), mb_vm = prefix(len_vm, &mo_vm);
   const int64_t mb_pg0 = prefix(len_pg0, &mo_pg0), mb_pg1 = prefix(len_pg1, &mo_pg1);
-  const int64_t mb_qg = prefix(len_qg, &mo_qg), mb_p = prefix(len_p, &mo_p), mb_q = prefix(len_q, &mo_q);
+  const int64_t mb_qg = prefix(len_qg, &mo_qg), mb_qg1 = prefix(len_qg1, &mo_qg1);
+  const int64_t mb_p = prefix(len_p, &mo_p), mb_q = prefix(len_q, &mo_q);
   const int64_t big = (int64_t)1 << 31;
   if (mb_vm >= big || mb_p >= big || mb_q >= big || jk8_per * 1 >= big)
     return fail(MPOPF_ERR_SIZE, "mpopf_setup: one period of M exceeds 32-bit offsets");
@@ -483,17 +498,19 @@ int mpopf_setup(const mpopf_network *net, int32_t n_periods, const double *pd, c
   d.n = n; d.m = m;
   d.x_vm = T * N; d.x_pg = 2 * T * N; d.x_qg = 2 * T * N + T * G; d.x_p = 2 * T * N + 2 * T * G;
   d.x_q = d.x_p + 2 * T * L;
-  d.c_k8 = T + 7 * T * L; d.c_k9 = d.c_k8 + T * N; d.c_k10 = d.c_k9 + T * N;
+  d.c_k8 = T + 7 * T * L; d.c_k9 = d.c_k8 + T * N; d.c_k10 = d.c_k9 + T * N; d.c_k11 = d.c_k10 + (T - 1) * G;
+  d.qramp = qramp ? 1 : 0;
   d.j_k5 = T + 20 * T * L; d.j_k6 = d.j_k5 + 2 * T * L; d.j_k7 = d.j_k6 + 2 * T * L; d.j_k8 = d.j_k7 + 2 * T * L;
   d.jk8_per = jk8_per; d.j_k9 = d.j_k8 + T * jk8_per; d.j_k10 = d.j_k9 + T * jk8_per;
-  d.nnz_jac = d.j_k10 + 2 * (T - 1) * G;
+  d.j_k11 = d.j_k10 + 2 * (T - 1) * G;
+  d.nnz_jac = d.j_k11 + (qramp ? 2 * (T - 1) * G : 0);
   d.h_br = T * G; d.h_th = d.h_br + 10 * T * L; d.h_sh = d.h_th + 4 * T * L; d.nnz_hess = d.h_sh + 2 * T * N;
-  d.mb_va = mb_va; d.mb_vm = mb_vm; d.mb_pg0 = mb_pg0; d.mb_pg1 = mb_pg1; d.mb_qg = mb_qg; d.mb_p = mb_p; d.mb_q = mb_q;
+  d.mb_va = mb_va; d.mb_vm = mb_vm; d.mb_pg0 = mb_pg0; d.mb_pg1 = mb_pg1; d.mb_qg = mb_qg; d.mb_qg1 = mb_qg1; d.mb_p = mb_p; d.mb_q = mb_q;
   d.m_va = 0;
   d.m_vm = d.m_va + T * mb_va;
   d.m_pg = d.m_vm + T * mb_vm;
   d.m_qg = d.m_pg + mb_pg0 + (T - 1) * mb_pg1;
-  d.m_p = d.m_qg + T * mb_qg;
+  d.m_p = d.m_qg + mb_qg + (T - 1) * mb_qg1;
   d.m_q = d.m_p + T * mb_p;
   d.nnz_kkt = d.m_q + T * mb_q;
 
@@ -526,7 +543,7 @@ int mpopf_setup(const mpopf_network *net, int32_t n_periods, const double *pd, c
   d.jk8_off = dev_upload(h, jk8_off, &err);
   d.mo_va = dev_upload(h, mo_va, &err); d.mo_vm = dev_upload(h, mo_vm, &err);
   d.mo_pg0 = dev_upload(h, mo_pg0, &err); d.mo_pg1 = dev_upload(h, mo_pg1, &err);
-  d.mo_qg = dev_upload(h, mo_qg, &err); d.mo_p = dev_upload(h, mo_p, &err); d.mo_q = dev_upload(h, mo_q, &err);
+  d.mo_qg = dev_upload(h, mo_qg, &err); d.mo_qg1 = dev_upload(h, mo_qg1, &err); d.mo_p = dev_upload(h, mo_p, &err); d.mo_q = dev_upload(h, mo_q, &err);
   std::vector<double> vpd(pd ? pd : (const double *)nullptr, pd ? pd + T * D : (const double *)nullptr);
   std::vector<double> vqd(qd ? qd : (const double *)nullptr, qd ? qd + T * D : (const double *)nullptr);
   d.pd = dev_upload(h, vpd, &err);
@@ -553,6 +570,7 @@ int mpopf_setup(const mpopf_network *net, int32_t n_periods, const double *pd, c
   auto cat = [&](const double *p, int64_t k) { if (k > 0) tmp_src.insert(tmp_src.end(), p, p + k); };
   cat(net->bus_vmin, N); cat(net->bus_vmax, N);
   if (G > 0) { cat(net->gen_pmin, G); cat(net->gen_pmax, G); cat(net->gen_qmin, G); cat(net->gen_qmax, G); cat(net->gen_ramp, G); }
+  if (qramp) cat(net->gen_qramp, G);
   if (L > 0) { cat(net->br_angmin, L); cat(net->br_angmax, L); }
   double *src = dev_upload(h, tmp_src, &err);
   if (err != cudaSuccess) {
@@ -565,9 +583,10 @@ int mpopf_setup(const mpopf_network *net, int32_t n_periods, const double *pd, c
   }
   const double *vmin = src, *vmax = src + N;
   const double *pmin = src + 2 * N, *pmax = pmin + G, *qmin = pmax + G, *qmax = qmin + G, *ramp = qmax + G;
-  const double *angmin = src + 2 * N + 5 * G, *angmax = angmin + L;
+  const double *qramp_src = qramp ? ramp + G : nullptr;
+  const double *angmin = src + 2 * N + 5 * G + (qramp ? G : 0), *angmax = angmin + L;
   err = launch_patterns(d, jrow, jcol, hrow, hcol, krp, kcol, xl, xu, gl, gu, vmin, vmax, pmin, pmax, qmin, qmax,
-                        angmin, angmax, ramp, 0);
+                        angmin, angmax, ramp, qramp_src, 0);
   if (err == cudaSuccess) err = cudaDeviceSynchronize();
   if (err != cudaSuccess) {
     std::string msg = std::string("mpopf_setup: pattern expansion: ") + cudaGetErrorString(err);

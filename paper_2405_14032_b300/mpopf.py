@@ -31,7 +31,7 @@ class _Network(ctypes.Structure):
         (name, _P) for name in (
             "bus_gs", "bus_bs", "bus_vmin", "bus_vmax", "br_f", "br_t", "br_r", "br_x", "br_b", "br_tap",
             "br_shift", "br_smax", "br_angmin", "br_angmax", "gen_bus", "gen_c2", "gen_c1", "gen_c0",
-            "gen_pmin", "gen_pmax", "gen_qmin", "gen_qmax", "gen_ramp", "load_bus")]
+            "gen_pmin", "gen_pmax", "gen_qmin", "gen_qmax", "gen_ramp", "load_bus", "gen_qramp")]
 
 
 class _Csc(ctypes.Structure):
@@ -185,7 +185,8 @@ class Handle:
             br_angmax=arr(net.br_angmax, f64), gen_bus=arr(net.gen_bus, i32), gen_c2=arr(net.gen_c2, f64),
             gen_c1=arr(net.gen_c1, f64), gen_c0=arr(net.gen_c0, f64), gen_pmin=arr(net.gen_pmin, f64),
             gen_pmax=arr(net.gen_pmax, f64), gen_qmin=arr(net.gen_qmin, f64), gen_qmax=arr(net.gen_qmax, f64),
-            gen_ramp=arr(net.gen_ramp, f64), load_bus=arr(net.load_bus, i32))
+            gen_ramp=arr(net.gen_ramp, f64), load_bus=arr(net.load_bus, i32),
+            gen_qramp=None if net.gen_qramp is None else arr(net.gen_qramp, f64))
         pd = arr(inst.pd, f64)
         qd = arr(inst.qd, f64)
         h = ctypes.c_void_p()

@@ -83,7 +83,7 @@ def _setup_rc(net, T=2, pd=None, qd=None):
     c = mpopf._Network(
         n_bus=net.n_bus, n_branch=net.n_branch, n_gen=net.n_gen, n_load=net.n_load, ref_bus=net.ref_bus,
         **{k: arr(getattr(net, k), np.int32 if k in ("br_f", "br_t", "gen_bus", "load_bus") else np.float64)
-           for k, _ in mpopf._Network._fields_[5:]})
+           for k, _ in mpopf._Network._fields_[5:] if getattr(net, k) is not None})
     pd = np.zeros((T, net.n_load)) if pd is None else pd
     qd = np.zeros((T, net.n_load)) if qd is None else qd
     rc = lib.mpopf_setup(ctypes.byref(c), T, arr(pd, np.float64), arr(qd, np.float64), ctypes.byref(h),
@@ -113,6 +113,10 @@ def test_rejects_bad_arguments_on_host():
     bad.br_tap = np.zeros(14)
     rc, msg = _setup_rc(bad)
     assert rc == -1 and "tap" in msg
+    bad = synth.make_network(3, 10, 14, 2, 3)
+    bad.gen_qramp = np.array([0.1, -0.2])
+    rc, msg = _setup_rc(bad)
+    assert rc == -1 and "reactive ramp" in msg
 
 
 def test_rejects_oversized_problem_before_allocation():

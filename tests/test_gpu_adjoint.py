@@ -33,6 +33,7 @@ CASES = {
     "edge_T5": lambda: (H.instance(_edge_network(), 5), 43),
     "ragged_T3": lambda: (synth.make_instance(41, 333, 530, 67, 200, 3), 41),
     "single_bus": lambda: (H.instance(H.network(1, [], [], [], [], [], gen_bus=[0, 0], load_bus=[0]), 3), 44),
+    "qramp_T4": lambda: (synth.with_reactive_ramp(synth.make_instance(50, 120, 190, 25, 70, 4)), 50),
 }
 
 

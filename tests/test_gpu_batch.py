@@ -20,8 +20,11 @@ def _dev(a):
 def _setup(shapes):
     from paper_2405_14032_b300 import mpopf
     hs, ios, refs = [], [], []
-    for k, (N, L, G, D, T) in enumerate(shapes):
+    for k, shape in enumerate(shapes):
+        N, L, G, D, T = shape[:5]
         inst = synth.make_instance(100 + k, N, L, G, D, T)
+        if len(shape) > 5 and shape[5] == "qramp":
+            inst = synth.with_reactive_ramp(inst)
         pt = synth.make_point(100 + k, inst)
         h = mpopf.Handle(inst)
         io = dict(x=_dev(pt.x), lam=_dev(pt.lam), sigma=pt.sigma, sigma_x=_dev(pt.sigma_x), dvec=_dev(pt.dvec),
@@ -49,7 +52,7 @@ def _check_all(b, ios, refs):
 
 
 SMALL = [(40, 64, 8, 20, 3), (73, 117, 15, 44, 2), (130, 208, 26, 78, 5), (31, 50, 6, 19, 1), (250, 400, 50, 150, 4),
-         (12, 20, 0, 5, 3), (600, 960, 120, 360, 7)]
+         (12, 20, 0, 5, 3), (600, 960, 120, 360, 7), (90, 140, 20, 50, 4, "qramp")]
 
 
 def test_batch_equals_individual_sweeps_every_schedule():

@@ -99,6 +99,10 @@ def _wide_angle_case():
 
 CASES = dict(_cases())
 CASES["wide_angles"] = _wide_angle_case
+# the reactive ramp rows K11 (optional variant)
+CASES["qramp_T3"] = lambda: Case(synth.with_reactive_ramp(synth.make_instance(47, 200, 320, 40, 120, 3)), 47)
+CASES["qramp_edge_T5"] = lambda: Case(synth.with_reactive_ramp(H.instance(_edge_network(), 5)), 48)
+CASES["qramp_T1"] = lambda: Case(synth.with_reactive_ramp(H.instance(_edge_network(), 1)), 49)
 
 
 @pytest.fixture(scope="module", params=sorted(CASES))
