@@ -22,8 +22,13 @@ namespace {
 template <unsigned MASK>
 __device__ __forceinline__ unsigned eff(unsigned rt) { return MASK ? MASK : rt; }
 
+// Branch kernel launch shape: threads per CTA and resident CTAs per SM (the
+// register cap follows from them); measured choice below.
 #ifndef MPOPF_BRANCH_MINB
 #define MPOPF_BRANCH_MINB 3
+#endif
+#ifndef MPOPF_BRANCH_BLOCK
+#define MPOPF_BRANCH_BLOCK kBlock
 #endif
 // Loads of values another CTA wrote in the same launch go through L2 (the
 // persistent batch kernel); separate launches may use the read-only path.
@@ -219,7 +224,7 @@ __device__ __forceinline__ void branch_body(const Dev &d, int32_t tl, unsigned r
 }
 
 template <unsigned MASK>
-__global__ void __launch_bounds__(kBlock, MPOPF_BRANCH_MINB) k_branch(Dev d, unsigned rt, const double *__restrict__ x,
+__global__ void __launch_bounds__(MPOPF_BRANCH_BLOCK, MPOPF_BRANCH_MINB) k_branch(Dev d, unsigned rt, const double *__restrict__ x,
                                                                       const double *__restrict__ lam,
                                                                       const double *__restrict__ sx,
                                                                       const double *__restrict__ dv, double dw,
@@ -519,7 +524,8 @@ void launch_all(const Dev &d, unsigned rt, const double *x, const double *lam, d
   const unsigned rest = MPOPF_OUT_GRAD | MPOPF_OUT_CONS | MPOPF_OUT_JAC | MPOPF_OUT_HESS | MPOPF_OUT_KKT;
   if ((mk & rest) && d.L > 0) {
     Timed tm(prof, s, KIND_BRANCH);
-    k_branch<MASK><<<grid_for((int64_t)d.T * d.L), kBlock, 0, s>>>(d, rt, x, lam, sx, dv, dw, grad, c, jv, hv, kv);
+    k_branch<MASK><<<(unsigned)(((int64_t)d.T * d.L + MPOPF_BRANCH_BLOCK - 1) / MPOPF_BRANCH_BLOCK),
+                     MPOPF_BRANCH_BLOCK, 0, s>>>(d, rt, x, lam, sx, dv, dw, grad, c, jv, hv, kv);
   }
   if (mk & rest) {
     Timed tm(prof, s, KIND_BUS);
