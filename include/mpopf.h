@@ -20,7 +20,8 @@
  *     the handle's scratch buffer).
  *   - Return value: MPOPF_OK (0) or a negative code; mpopf_last_error() gives a
  *     message (thread-local).  No call allocates device memory except
- *     mpopf_setup (and, once, mpopf_sweep_host for its staging buffers).
+ *     mpopf_setup (and, once, mpopf_sweep_host for its staging buffers,
+ *     mpopf_csc_pattern for a CSC pattern, each on first use).
  *   - Outputs are deterministic: identical inputs give bitwise-identical
  *     outputs (no atomics on values).  There is no CPU fallback: without a
  *     CUDA device every call returns MPOPF_ERR_CUDA.
@@ -172,9 +173,15 @@ int mpopf_sweep(mpopf_handle *h, const double *x, const double *lam, double sigm
                 double *kv, void *stream);
 
 /* Full sweep from HOST buffers: copies x, lam, sigma_x, dvec to the device,
- * runs mpopf_sweep and copies all six outputs back to the host buffers, then
- * synchronises `stream`.  Staging buffers are allocated on the first call and
- * kept by the handle. */
+ * runs the sweep and copies all six outputs back to the host buffers; returns
+ * when the outputs are in the host buffers.  The horizon is processed in up to
+ * eight windows of periods: the inputs of a window are copied in on one
+ * internal stream, its branch and bus work runs on `stream`, and its outputs
+ * are copied out on a second internal stream, so copies in both directions
+ * overlap each other and the kernels (with pinned host buffers); the generator
+ * work and the objective run last, over the whole horizon.  The outputs equal
+ * those of mpopf_sweep bit for bit.  Staging buffers, the two streams and
+ * their events are created on the first call and kept by the handle. */
 int mpopf_sweep_host(mpopf_handle *h, const double *x, const double *lam, double sigma, const double *sigma_x,
                      const double *dvec, double delta_w, double *f, double *grad, double *c, double *jv,
                      double *hv, double *kv, void *stream);

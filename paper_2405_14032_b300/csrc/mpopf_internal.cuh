@@ -129,6 +129,15 @@ struct CscState {
 };
 }  // namespace mpopf
 
+namespace mpopf {
+// Streams and events of the pipelined host-buffer sweep (created on first use).
+constexpr int kHostWindows = 8;
+struct HostPipe {
+  cudaStream_t in, out;
+  cudaEvent_t start, gen, ev_in[kHostWindows], ev_c[kHostWindows];
+};
+}  // namespace mpopf
+
 struct mpopf_handle {
   mpopf::Dev d;
   mpopf_pattern pat;
@@ -140,4 +149,9 @@ struct mpopf_handle {
   mpopf::Prof prof;
   double *work;  // [m] row vector of the condensed right-hand side
   mpopf::CscState csc[2];
+  mpopf::HostPipe *pipe;
 };
+
+namespace mpopf {
+void hostpipe_destroy(mpopf_handle *h);
+}  // namespace mpopf

@@ -175,12 +175,28 @@ def test_cfg2_full():
     assert abs(out["f"][0] - ref["f"]) <= 1e-12 * abs(ref["f"])
 
 
-def test_sweep_host_matches_device():
-    cs = Case(synth.config_instance("cfg1"), 1)
+HOST_CASES = {
+    "cfg1": lambda: Case(synth.config_instance("cfg1"), 1),               # T = 4: four one-period windows
+    "ragged_T13": lambda: Case(synth.make_instance(52, 150, 240, 30, 90, 13), 52),  # windows of 2, last of 1
+    "edge_T1": lambda: Case(H.instance(_edge_network(), 1), 42),          # one window, no ramp rows
+    "no_gens_no_loads": CASES["no_gens_no_loads"],
+    "qramp_T3": CASES["qramp_T3"],
+    "cfg2": lambda: Case(synth.config_instance("cfg2"), 2),               # T = 24: eight windows of 3
+}
+
+
+@pytest.mark.parametrize("name", sorted(HOST_CASES))
+def test_sweep_host_matches_device(name):
+    """The host-buffer entry point (inputs and outputs copied in period
+    windows, overlapped with the kernels) equals the device sweep bit for bit,
+    twice in a row (the pipeline's streams and events are reused)."""
+    cs = HOST_CASES[name]()
     pt = cs.pt
     dev = cs.run()
-    out = dict(f=np.empty(1), grad=np.empty(cs.h.n), c=np.empty(cs.h.m), jv=np.empty(cs.h.nnz_jac),
-               hv=np.empty(cs.h.nnz_hess), kv=np.empty(cs.h.nnz_kkt))
-    cs.h.sweep_host(pt.x, pt.lam, pt.sigma, pt.sigma_x, pt.dvec, pt.delta_w, out)
-    for k in out:
-        assert np.array_equal(out[k], dev[k]), k
+    for _ in range(2):
+        out = dict(f=np.full(1, np.nan), grad=np.full(cs.h.n, np.nan), c=np.full(cs.h.m, np.nan),
+                   jv=np.full(cs.h.nnz_jac, np.nan), hv=np.full(cs.h.nnz_hess, np.nan),
+                   kv=np.full(cs.h.nnz_kkt, np.nan))
+        cs.h.sweep_host(pt.x, pt.lam, pt.sigma, pt.sigma_x, pt.dvec, pt.delta_w, out)
+        for k in out:
+            assert np.array_equal(out[k], dev[k]), (name, k)
