@@ -24,15 +24,14 @@ struct Dev {
   // variable block starts (va at 0)
   int64_t x_vm, x_pg, x_qg, x_p, x_q;
   // constraint block starts (K0 at 0, K_k (1..7) at T + (k-1) T L)
-  int64_t c_k8, c_k9, c_k10, c_k11;  // c_k11: reactive ramp rows (if qramp)
-  int32_t qramp;                     // 1: reactive ramp rows K11 present
+  int64_t c_k8, c_k9, c_k10;
   // J value starts (K0 at 0, K_k (1..4) at T + 5 (k-1) T L)
-  int64_t j_k5, j_k6, j_k7, j_k8, j_k9, j_k10, j_k11, jk8_per;
+  int64_t j_k5, j_k6, j_k7, j_k8, j_k9, j_k10, jk8_per;
   // W value starts (objective at 0)
   int64_t h_br, h_th, h_sh;
   // M: region start of each variable kind and per-period block sizes
   int64_t m_va, m_vm, m_pg, m_qg, m_p, m_q;
-  int64_t mb_va, mb_vm, mb_pg0, mb_pg1, mb_qg, mb_qg1, mb_p, mb_q;  // qg: t = 0 block, t >= 1 blocks
+  int64_t mb_va, mb_vm, mb_pg0, mb_pg1, mb_qg, mb_p, mb_q;
   int64_t nnz_jac, nnz_hess, nnz_kkt;
   // network
   const int32_t *br_f, *br_t;
@@ -52,7 +51,7 @@ struct Dev {
   const int32_t *arc_rank;               // position among the arcs of its bus
   const int32_t *jk8_off;                // offset of the K8 (and K9) J row of bus n inside a period block
   // M row offsets inside a period block
-  const int32_t *mo_va, *mo_vm, *mo_pg0, *mo_pg1, *mo_qg, *mo_qg1, *mo_p, *mo_q;
+  const int32_t *mo_va, *mo_vm, *mo_pg0, *mo_pg1, *mo_qg, *mo_p, *mo_q;
   // loads [T][D]
   const double *pd, *qd;
   // Incidence slots: slot of branch l's from / to end in its bus's incident
@@ -70,6 +69,11 @@ struct Dev {
   double *S;
   double *fpart;
   int32_t fpart_n;
+  // Reactive ramp rows K11 (present iff qramp): row and J starts; the qg rows
+  // of M at t >= 1 then use their own template (block size, row offsets).
+  int32_t qramp;
+  int64_t c_k11, j_k11, mb_qg1;
+  const int32_t *mo_qg1;
 };
 
 inline constexpr int kBlock = 256;

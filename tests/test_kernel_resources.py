@@ -1,0 +1,33 @@
+"""Register and spill budget of the dominant sweep kernel, from the compiler's
+resource report (no GPU needed).  The branch kernel is FP64-bound at three
+256-thread CTAs per SM (80 registers); its spills are sensitive to unrelated
+changes (a field inserted in the middle of the device descriptor once raised
+them from 32 to 72 bytes and the kernel time by 4%), so the budget is pinned."""
+import os
+import re
+import shutil
+import subprocess
+
+import pytest
+
+from paper_2405_14032_b300 import build
+
+NVCC = build.NVCC
+
+
+@pytest.mark.skipif(not (os.path.exists(NVCC) or shutil.which("nvcc")), reason="nvcc not available")
+def test_branch_kernel_register_and_spill_budget(tmp_path):
+    src = os.path.join(build.HERE, "csrc", "mpopf_kernels.cu")
+    flags = [f for f in build.FLAGS if f not in ("-shared", "-lineinfo")]
+    cmd = [NVCC, *flags, "-Xptxas", "-v", "-I", os.path.join(build.ROOT, "include"), "-c", src,
+           "-o", str(tmp_path / "k.o")]
+    out = subprocess.run(cmd, capture_output=True, text=True, check=True).stderr
+    # the report block of the full-sweep instantiation k_branch<63>
+    m = re.search(r"Compiling entry function '[^']*k_branchILj63E[^']*'.*?Used (\d+) registers", out, re.S)
+    assert m, "no resource report for k_branch<63>"
+    block = out[m.start():m.end()]
+    regs = int(m.group(1))
+    spill = re.search(r"(\d+) bytes spill stores, (\d+) bytes spill loads", block)
+    stores, loads = (int(spill.group(1)), int(spill.group(2))) if spill else (0, 0)
+    assert regs <= 80, regs
+    assert stores <= 40 and loads <= 40, (stores, loads)
