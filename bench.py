@@ -465,6 +465,29 @@ def graph_sweeps(torch, count=1000):
     return res
 
 
+def unfused_timing(torch, h, x, lam, sigma, sx, dv, dw, out, reps=20):
+    """The six callbacks called one by one (f, grad f, c, J, W, then M, which
+    recomputes the branch derivatives), as an NLP solver without the fused
+    sweep would call them, against the one fused sweep."""
+    from paper_2405_14032_b300 import mpopf
+
+    def seq():
+        for bit in (mpopf.OUT_OBJ, mpopf.OUT_GRAD, mpopf.OUT_CONS, mpopf.OUT_JAC, mpopf.OUT_HESS, mpopf.OUT_KKT):
+            h.eval(bit, x, lam, sigma, sx, dv, dw, out=out)
+
+    for _ in range(3):
+        seq()
+    torch.cuda.synchronize()
+    e0, e1 = _events(torch)
+    e0.record()
+    for _ in range(reps):
+        seq()
+    e1.record()
+    torch.cuda.synchronize()
+    return {"unfused_ms": e0.elapsed_time(e1) / reps,
+            "calls": "mpopf_eval with one output bit each: OBJ, GRAD, CONS, JAC, HESS, KKT"}
+
+
 def csc_timing(torch, h, out, reps=20):
     """COO -> CSC compression of the benchmark instance's J and W values (the
     pattern built once on the host, untimed; each compression one kernel)."""
@@ -692,7 +715,8 @@ def run_ours(args, world, rank, local):
                        "l2": "inputs + outputs 2.7 GB per step > 126 MB L2; no flush",
                        "iterates": "two perturbed iterates alternated"},
             "hbm": {"algorithmic_bytes_per_sweep": alg, "gbs": gbs, "peak_gbs": hbm_peak,
-                    "frac": gbs / hbm_peak if hbm_peak else None, "peak_source": "MEASURED_PEAKS.json"},
+                    "frac": gbs / hbm_peak if hbm_peak else None, "peak_source": "MEASURED_PEAKS.json",
+                    "nominal_gbs": 7700.0, "frac_nominal": gbs / 7700.0},
             "roofline": roof,
             "kernels_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
             "clocks": clk,
@@ -722,6 +746,9 @@ def run_ours(args, world, rank, local):
             line["ipm"] = ipm_timing(torch, h)
             line["small_sweeps"] = graph_sweeps(torch)
             line["csc"] = csc_timing(torch, h, out)
+            line["unfused"] = unfused_timing(torch, h, xs[0], lam, pt.sigma, sx, dv, pt.delta_w, out)
+            line["unfused"]["fused_ms"] = ms_step
+            line["unfused"]["speedup_fused"] = line["unfused"]["unfused_ms"] / ms_step
         print(json.dumps(line), flush=True)
     h.close()
     if world > 1:
