@@ -283,6 +283,10 @@ __device__ __forceinline__ void bus_body(const Dev &d, int32_t idx, unsigned rt,
     }
     // Arc flows in ascending arc index: from ends (branch order), then to ends.
     if (have_rec) {
+      // unrolled so that the record loads of several arcs are in flight
+      // together (measured: 0.264 -> 0.253 ms at 10k buses x 168; the adds
+      // keep their order)
+#pragma unroll 4
       for (int32_t e = s0; e < s1; ++e) {
         const int32_t q = __ldg(d.arc_perm + e);
         const double2 pq = ld_rec<COH>(R + (int64_t)q * kRec + 4);
