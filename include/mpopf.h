@@ -82,7 +82,8 @@ enum {
   MPOPF_ERR_ARG = -1,   /* bad argument (NULL pointer, index out of range, ...) */
   MPOPF_ERR_SIZE = -2,  /* sizes overflow the index types (n, m must be < 2^31) */
   MPOPF_ERR_CUDA = -3,  /* CUDA error (no device, launch failure, ...) */
-  MPOPF_ERR_ALLOC = -4  /* device allocation failed */
+  MPOPF_ERR_ALLOC = -4,  /* device allocation failed */
+  MPOPF_ERR_NUMERIC = -5 /* numerical failure (mpopf_kkt_factor: M not positive definite) */
 };
 
 /* Output selection bits for mpopf_eval. */
@@ -276,6 +277,26 @@ typedef struct {
 } mpopf_csc;
 int mpopf_csc_pattern(mpopf_handle *h, int32_t which, mpopf_csc *out);
 int mpopf_coo_to_csc(mpopf_handle *h, int32_t which, const double *coo_vals, double *csc_vals, void *stream);
+
+/* Factorisation and solve of the condensed matrix M (Sec. III-B: the paper
+ * factorises M with the sparse direct solver cuDSS; cuDSS is not available
+ * here, so cuSOLVER's sparse Cholesky stands in: a library step, not one of
+ * this library's kernels).
+ * mpopf_kkt_factor: kv [nnz_kkt] are the lower CSR values of M on the device
+ *   (mpopf_assemble_kkt / mpopf_sweep).  The first call orders the symmetrised
+ *   pattern (METIS nested dissection, host), builds the permuted full pattern
+ *   and runs the symbolic analysis (synchronous, allocates); every call
+ *   gathers the values (one kernel) and runs the numeric Cholesky
+ *   factorisation on the device, then checks for a zero pivot (synchronous).
+ *   Returns MPOPF_ERR_NUMERIC when M is not positive definite (the caller
+ *   raises delta_w, as an interior-point inertia correction does); then
+ *   *zero_pivot (if not NULL) is the row of M where it was found, else -1.
+ * mpopf_kkt_solve: dx [n] = M^{-1} rhs [n] with the last successful
+ *   factorisation (MPOPF_ERR_ARG if there is none); asynchronous.
+ * Values are the library's (within its rounding; not bitwise against the CPU
+ * reference). */
+int mpopf_kkt_factor(mpopf_handle *h, const double *kv, int64_t *zero_pivot, void *stream);
+int mpopf_kkt_solve(mpopf_handle *h, const double *rhs, double *dx, void *stream);
 
 /* Batched full sweeps of many independent instances (uneven sizes and
  * horizons) in ONE persistent kernel launch, replayed as a CUDA graph.  The

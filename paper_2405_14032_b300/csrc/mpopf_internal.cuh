@@ -134,6 +134,7 @@ struct CscState {
 }  // namespace mpopf
 
 namespace mpopf {
+struct KktSolver;
 // Streams and events of the pipelined host-buffer sweep (created on first use).
 constexpr int kHostWindows = 8;
 struct HostPipe {
@@ -154,8 +155,10 @@ struct mpopf_handle {
   double *work;  // [m] row vector of the condensed right-hand side
   mpopf::CscState csc[2];
   mpopf::HostPipe *pipe;
+  mpopf::KktSolver *solver;  // library factorisation of M (built on first use)
 };
 
 namespace mpopf {
 void hostpipe_destroy(mpopf_handle *h);
+void kkt_solver_destroy(mpopf_handle *h);
 }  // namespace mpopf

@@ -625,6 +625,7 @@ int mpopf_set_loads(mpopf_handle *h, const double *d_pd, const double *d_qd, voi
 void mpopf_destroy(mpopf_handle *h) {
   if (!h) return;
   hostpipe_destroy(h);
+  kkt_solver_destroy(h);
   free_blocks(h);
   delete h;
 }

@@ -94,6 +94,8 @@ def lib():
             "mpopf_vjp": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
             "mpopf_jvp": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
             "mpopf_hvp": (ctypes.c_int, [_P, _P, _P, _D, _P, _P, _P]),
+            "mpopf_kkt_factor": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int64), _P]),
+            "mpopf_kkt_solve": (ctypes.c_int, [_P, _P, _P, _P]),
             "mpopf_csc_pattern": (ctypes.c_int, [_P, _I32, ctypes.POINTER(_Csc)]),
             "mpopf_coo_to_csc": (ctypes.c_int, [_P, _I32, _P, _P, _P]),
             "mpopf_ipm_prepare": (ctypes.c_int, [_P] * 7 + [_D] * 3 + [_P] * 5),
@@ -126,7 +128,7 @@ def exported_symbols():
     return ["mpopf_setup", "mpopf_get_pattern", "mpopf_set_loads", "mpopf_eval", "mpopf_eval_obj",
             "mpopf_eval_grad", "mpopf_eval_cons", "mpopf_eval_jac", "mpopf_eval_hess", "mpopf_assemble_kkt",
             "mpopf_sweep", "mpopf_sweep_host", "mpopf_assemble_kkt_noalloc", "mpopf_vjp", "mpopf_jvp", "mpopf_hvp",
-            "mpopf_csc_pattern", "mpopf_coo_to_csc", "mpopf_ipm_prepare", "mpopf_ipm_rhs", "mpopf_ipm_recover", "mpopf_batch_create", "mpopf_batch_set_io", "mpopf_batch_sweep", "mpopf_batch_set_schedule",
+            "mpopf_kkt_factor", "mpopf_kkt_solve", "mpopf_csc_pattern", "mpopf_coo_to_csc", "mpopf_ipm_prepare", "mpopf_ipm_rhs", "mpopf_ipm_recover", "mpopf_batch_create", "mpopf_batch_set_io", "mpopf_batch_sweep", "mpopf_batch_set_schedule",
             "mpopf_batch_get_schedule", "mpopf_batch_tune", "mpopf_batch_status", "mpopf_batch_destroy",
             "mpopf_launch_count", "mpopf_profile_start", "mpopf_profile_stop",
             "mpopf_destroy", "mpopf_last_error"]
@@ -308,6 +310,23 @@ class Handle:
         out = torch.empty(self.n, dtype=torch.float64, device="cuda") if out is None else out
         _check(lib().mpopf_hvp(self.h, _ptr(x), _ptr(lam), float(sigma), _ptr(v), _ptr(out), _stream_ptr(stream)),
                "mpopf_hvp")
+        return out
+
+    # -- library factorisation of M ---------------------------------------------
+    def kkt_factor(self, kv, stream=None):
+        """Cholesky factorisation of M from its lower CSR values; returns -1, or
+        the row of a zero / negative pivot when M is not positive definite."""
+        zp = ctypes.c_int64(-1)
+        rc = lib().mpopf_kkt_factor(self.h, _ptr(kv), ctypes.byref(zp), _stream_ptr(stream))
+        if rc == -5:
+            return int(zp.value)
+        _check(rc, "mpopf_kkt_factor")
+        return -1
+
+    def kkt_solve(self, rhs, out=None, stream=None):
+        """M^{-1} rhs with the last factorisation."""
+        out = self._dvec(self.n) if out is None else out
+        _check(lib().mpopf_kkt_solve(self.h, _ptr(rhs), _ptr(out), _stream_ptr(stream)), "mpopf_kkt_solve")
         return out
 
     # -- COO -> CSC compression -------------------------------------------------
