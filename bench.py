@@ -634,24 +634,34 @@ def ipm_timing(torch, h, reps=50, eps=1e-2, mu=0.05, dw=1e-3, dc=1e-4):
     neg_y = -y
     sw = h.new_outputs()
 
-    def iteration():
+    def iteration(stored):
         sx_, dv_, cv_, rc_ = h.ipm_prepare(x, s, zlx, zux, zls, zus, dw, dc, eps, recip=recip)
         h.sweep(x, neg_y, 1.0, sx_, dv_, dw, out=sw)
-        h.ipm_rhs(x, s, y, sw["grad"], sw["c"], rc_, dv_, cv_, mu, out=rhs)
-        h.ipm_recover(x, s, y, zlx, zux, zls, zus, sw["c"], rc_, cv_, dx, mu, dw, dc, out=rec)
+        jv = sw["jv"] if stored else None
+        h.ipm_rhs(x, s, y, sw["grad"], sw["c"], rc_, dv_, cv_, mu, out=rhs, jv=jv)
+        h.ipm_recover(x, s, y, zlx, zux, zls, zus, sw["c"], rc_, cv_, dx, mu, dw, dc, out=rec, jv=jv)
 
-    t_iter = timed(iteration)
+    t_iter = timed(lambda: iteration(False))
+    t_iter_jv = timed(lambda: iteration(True))
+    jvs = sw["jv"]  # J at x from the last sweep
+    t_rhs_jv = timed(lambda: h.ipm_rhs(x, s, y, out["grad"], out["c"], recip, dvec, cvec, mu, out=rhs, jv=jvs))
+    t_rec_jv = timed(lambda: h.ipm_recover(x, s, y, zlx, zux, zls, zus, out["c"], recip, cvec, dx, mu, dw, dc,
+                                           out=rec, jv=jvs))
     gx = torch.empty_like(x)
     t_vjp = timed(lambda: h.vjp(x, y, gx=gx, loads=False))
-    jv = torch.empty_like(y)
-    t_jvp = timed(lambda: h.jvp(x, dx, out=jv))
+    jvo = torch.empty_like(y)
+    t_jvp = timed(lambda: h.jvp(x, dx, out=jvo))
+    t_vjp_jv = timed(lambda: h.vjp(x, y, gx=gx, loads=False, jv=jvs))
+    t_jvp_jv = timed(lambda: h.jvp(x, dx, out=jvo, jv=jvs))
     # each array read or written once (the J products: x, the vector and the result)
     b_prep = 8 * (8 * n + 9 * m)
     b_rhs = 8 * (8 * m + (n + m + n) + 5 * n)
     b_rec = 8 * ((n + n + m) + 13 * m + 7 * n)
     g = lambda b, t: b / (t * 1e-3) / 1e9
     return {"prepare_ms": t_prep, "rhs_ms": t_rhs, "recover_ms": t_rec, "vjp_ms": t_vjp, "jvp_ms": t_jvp,
-            "iteration_ms_without_factorisation": t_iter,
+            "iteration_ms_without_factorisation": t_iter, "iteration_ms_stored_j": t_iter_jv,
+            "rhs_stored_j_ms": t_rhs_jv, "recover_stored_j_ms": t_rec_jv, "vjp_stored_j_ms": t_vjp_jv,
+            "jvp_stored_j_ms": t_jvp_jv,
             "prepare_gbs": g(b_prep, t_prep), "rhs_gbs": g(b_rhs, t_rhs), "recover_gbs": g(b_rec, t_rec),
             "algorithmic_bytes": {"prepare": b_prep, "rhs": b_rhs, "recover": b_rec},
             "note": "rhs and recover include one matrix-free J product each (J^T w, J dx; timed alone as "

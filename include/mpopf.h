@@ -201,6 +201,14 @@ int mpopf_sweep_host(mpopf_handle *h, const double *x, const double *lam, double
  *   (Eq. 4) for lam [m], v [n].
  * All use the handle's scratch (calls on one handle must not overlap). */
 int mpopf_vjp(mpopf_handle *h, const double *x, const double *y, double *gx, double *gpd, double *gqd, void *stream);
+/* The same products with J's values as mpopf_eval_jac / mpopf_sweep wrote them
+ * at the same x (jv [nnz_jac], device; NULL: recompute, as above): the branch
+ * rows are read instead of recomputed (no sin/cos, about a quarter of the FP64
+ * work), with bit-for-bit the same results. */
+int mpopf_vjp_jv(mpopf_handle *h, const double *x, const double *jv, const double *y, double *gx, double *gpd,
+                 double *gqd, void *stream);
+int mpopf_jvp_jv(mpopf_handle *h, const double *x, const double *jv, const double *v, const double *dpd,
+                 const double *dqd, double *jv_out, void *stream);
 int mpopf_jvp(mpopf_handle *h, const double *x, const double *v, const double *dpd, const double *dqd, double *jv_out,
               void *stream);
 int mpopf_hvp(mpopf_handle *h, const double *x, const double *lam, double sigma, const double *v, double *hv,
@@ -239,6 +247,9 @@ int mpopf_hvp(mpopf_handle *h, const double *x, const double *lam, double sigma,
  *   infinite); recip and cvec from mpopf_ipm_prepare at the same point.  The
  *   recovered ds is the one that solves Eq. 5; the sign of A dx printed with
  *   the recovery formula does not.
+ * jv (rhs, recover; may be NULL): the J values [nnz_jac] the sweep wrote at the
+ *   same x; with them the J products read J (mpopf_vjp_jv / mpopf_jvp_jv)
+ *   instead of recomputing its branch rows, with identical results.
  * Values follow a fixed rounding order and equal the CPU reference bit for
  * bit.  rhs and recover use the handle's scratch (calls on one handle must
  * not overlap).  Errors: MPOPF_ERR_ARG for a NULL pointer (nothing is
@@ -246,14 +257,14 @@ int mpopf_hvp(mpopf_handle *h, const double *x, const double *lam, double sigma,
 int mpopf_ipm_prepare(mpopf_handle *h, const double *x, const double *s, const double *zl_x, const double *zu_x,
                       const double *zl_s, const double *zu_s, double delta_w, double delta_c, double eps_tol,
                       double *sigma_x, double *dvec, double *cvec, double *recip, void *stream);
-int mpopf_ipm_rhs(mpopf_handle *h, const double *x, const double *s, const double *y, const double *grad,
-                  const double *c, const double *recip, const double *dvec, const double *cvec, double mu,
-                  double *rhs, void *stream);
-int mpopf_ipm_recover(mpopf_handle *h, const double *x, const double *s, const double *y, const double *zl_x,
-                      const double *zu_x, const double *zl_s, const double *zu_s, const double *c,
-                      const double *recip, const double *cvec, const double *dx, double mu, double delta_w,
-                      double delta_c, double *ds, double *dy, double *dzl_x, double *dzu_x, double *dzl_s,
-                      double *dzu_s, void *stream);
+int mpopf_ipm_rhs(mpopf_handle *h, const double *x, const double *jv, const double *s, const double *y,
+                  const double *grad, const double *c, const double *recip, const double *dvec, const double *cvec,
+                  double mu, double *rhs, void *stream);
+int mpopf_ipm_recover(mpopf_handle *h, const double *x, const double *jv, const double *s, const double *y,
+                      const double *zl_x, const double *zu_x, const double *zl_s, const double *zu_s,
+                      const double *c, const double *recip, const double *cvec, const double *dx, double mu,
+                      double delta_w, double delta_c, double *ds, double *dy, double *dzl_x, double *dzu_x,
+                      double *dzl_s, double *dzu_s, void *stream);
 
 /* COO -> CSC compression of J (m x n) and of the lower-triangle W (n x n)
  * (Sec. III-A: the COO matrices may be compressed to CSC).  CSC entries are

@@ -260,6 +260,84 @@ __global__ void __launch_bounds__(kBlock) k_hvp_gen(Dev d, double sigma, const d
   hv[d.x_qg + tg] = 0.0;
 }
 
+// ---------------------------------------------------------------------------
+// The same two branch kernels reading J's values as the sweep wrote them
+// (K1..K4 rows [1, a, -a, b, c], K5 [1, -1], K6/K7 [2p, 2q]) instead of
+// recomputing the flow derivatives: identical sums in identical order, so the
+// results equal those of k_vjp_branch / k_jvp_branch bit for bit when jv was
+// evaluated at the same x.  Bus and generator kernels are shared.
+// ---------------------------------------------------------------------------
+struct StoredJ {
+  double a1, b1, c1, na1, a2, b2, c2, na2, a3, b3, c3, na3, a4, b4, c4, na4, jp6, jq6, jp7, jq7;
+};
+
+__device__ __forceinline__ StoredJ stored_j(const Dev &d, const double *__restrict__ jv, int32_t tl) {
+  const int64_t s5 = 5 * (int64_t)d.T * d.L;
+  const double *j1 = jv + d.T + (int64_t)tl * 5;
+  StoredJ J;
+  J.a1 = __ldg(j1 + 1); J.na1 = __ldg(j1 + 2); J.b1 = __ldg(j1 + 3); J.c1 = __ldg(j1 + 4);
+  J.a2 = __ldg(j1 + s5 + 1); J.na2 = __ldg(j1 + s5 + 2); J.b2 = __ldg(j1 + s5 + 3); J.c2 = __ldg(j1 + s5 + 4);
+  J.a3 = __ldg(j1 + 2 * s5 + 1); J.na3 = __ldg(j1 + 2 * s5 + 2); J.b3 = __ldg(j1 + 2 * s5 + 3);
+  J.c3 = __ldg(j1 + 2 * s5 + 4);
+  J.a4 = __ldg(j1 + 3 * s5 + 1); J.na4 = __ldg(j1 + 3 * s5 + 2); J.b4 = __ldg(j1 + 3 * s5 + 3);
+  J.c4 = __ldg(j1 + 3 * s5 + 4);
+  // scalar loads: the K6/K7 blocks start at odd offsets when T is odd
+  const double *j6 = jv + d.j_k6 + (int64_t)tl * 2, *j7 = jv + d.j_k7 + (int64_t)tl * 2;
+  J.jp6 = __ldg(j6); J.jq6 = __ldg(j6 + 1); J.jp7 = __ldg(j7); J.jq7 = __ldg(j7 + 1);
+  return J;
+}
+
+__global__ void __launch_bounds__(kBlock) k_vjp_branch_jv(Dev d, const double *__restrict__ jv,
+                                                          const double *__restrict__ y, double *__restrict__ gx) {
+  const int32_t L = d.L;
+  const int32_t tl = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+  if (tl >= d.T * L) return;
+  const int32_t t = tl / L, l = tl - t * L;
+  const int64_t TL = (int64_t)d.T * L, tN = (int64_t)t * d.N;
+  const int64_t pb = d.x_p + 2 * (int64_t)t * L, qb = d.x_q + 2 * (int64_t)t * L;
+  const int32_t f = __ldg(d.br_f + l), to = __ldg(d.br_t + l);
+  const StoredJ J = stored_j(d, jv, tl);
+  const int64_t rk1 = d.T + tl;
+  const double y1 = __ldg(y + rk1), y2 = __ldg(y + rk1 + TL), y3 = __ldg(y + rk1 + 2 * TL);
+  const double y4 = __ldg(y + rk1 + 3 * TL), y5 = __ldg(y + rk1 + 4 * TL), y6 = __ldg(y + rk1 + 5 * TL);
+  const double y7 = __ldg(y + rk1 + 6 * TL);
+  const double Ld = fma(J.a4, y4, fma(J.a3, y3, fma(J.a2, y2, J.a1 * y1))) + y5;
+  const double Lvf = fma(J.b4, y4, fma(J.b3, y3, fma(J.b2, y2, J.b1 * y1)));
+  const double Lvt = fma(J.c4, y4, fma(J.c3, y3, fma(J.c2, y2, J.c1 * y1)));
+  const int64_t r8f = d.c_k8 + tN + f, r8t = d.c_k8 + tN + to, d89 = d.c_k9 - d.c_k8;
+  gx[pb + l] = fma(J.jp6, y6, y1) - __ldg(y + r8f);
+  gx[qb + l] = fma(J.jq6, y6, y2) - __ldg(y + r8f + d89);
+  gx[pb + L + l] = fma(J.jp7, y7, y3) - __ldg(y + r8t);
+  gx[qb + L + l] = fma(J.jq7, y7, y4) - __ldg(y + r8t + d89);
+  double *R = d.S + (int64_t)t * 2 * L * kRec;
+  *reinterpret_cast<double2 *>(R + (int64_t)__ldg(d.br_slot + l) * kRec) = make_double2(Ld, Lvf);
+  *reinterpret_cast<double2 *>(R + (int64_t)__ldg(d.br_slot + L + l) * kRec) = make_double2(negx(Ld), Lvt);
+}
+
+__global__ void __launch_bounds__(kBlock) k_jvp_branch_jv(Dev d, const double *__restrict__ jv,
+                                                          const double *__restrict__ v, double *__restrict__ out) {
+  const int32_t L = d.L;
+  const int32_t tl = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+  if (tl >= d.T * L) return;
+  const int32_t t = tl / L, l = tl - t * L;
+  const int64_t TL = (int64_t)d.T * L, tN = (int64_t)t * d.N;
+  const int64_t pb = d.x_p + 2 * (int64_t)t * L, qb = d.x_q + 2 * (int64_t)t * L;
+  const int32_t f = __ldg(d.br_f + l), to = __ldg(d.br_t + l);
+  const StoredJ J = stored_j(d, jv, tl);
+  const double uf = __ldg(v + tN + f), ut = __ldg(v + tN + to);
+  const double wf = __ldg(v + d.x_vm + tN + f), wt = __ldg(v + d.x_vm + tN + to);
+  const double vpf = __ldg(v + pb + l), vpt = __ldg(v + pb + L + l);
+  const double vqf = __ldg(v + qb + l), vqt = __ldg(v + qb + L + l);
+  const int64_t rk1 = d.T + tl;
+  out[rk1] = fma(J.c1, wt, fma(J.b1, wf, fma(J.na1, ut, fma(J.a1, uf, vpf))));
+  out[rk1 + TL] = fma(J.c2, wt, fma(J.b2, wf, fma(J.na2, ut, fma(J.a2, uf, vqf))));
+  out[rk1 + 2 * TL] = fma(J.c3, wt, fma(J.b3, wf, fma(J.na3, ut, fma(J.a3, uf, vpt))));
+  out[rk1 + 3 * TL] = fma(J.c4, wt, fma(J.b4, wf, fma(J.na4, ut, fma(J.a4, uf, vqt))));
+  out[rk1 + 4 * TL] = uf - ut;
+  out[rk1 + 5 * TL] = fma(J.jq6, vqf, J.jp6 * vpf);
+  out[rk1 + 6 * TL] = fma(J.jq7, vqt, J.jp7 * vpt);
+}
+
 unsigned grid_for(int64_t count) { return (unsigned)((count + kBlock - 1) / kBlock); }
 
 int fail(int code, const std::string &msg) {
@@ -274,12 +352,16 @@ using namespace mpopf;
 
 extern "C" {
 
-int mpopf_vjp(mpopf_handle *h, const double *x, const double *y, double *gx, double *gpd, double *gqd, void *stream) {
+int mpopf_vjp_jv(mpopf_handle *h, const double *x, const double *jv, const double *y, double *gx, double *gpd,
+                 double *gqd, void *stream) {
   if (!h || !x || !y || !gx) return fail(MPOPF_ERR_ARG, "mpopf_vjp: NULL argument");
   if ((gpd == nullptr) != (gqd == nullptr)) return fail(MPOPF_ERR_ARG, "mpopf_vjp: give both gpd and gqd or neither");
   const Dev &d = h->d;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (d.L > 0) k_vjp_branch<<<grid_for((int64_t)d.T * d.L), kBlock, 0, s>>>(d, x, y, gx);
+  if (d.L > 0) {
+    if (jv) k_vjp_branch_jv<<<grid_for((int64_t)d.T * d.L), kBlock, 0, s>>>(d, jv, y, gx);
+    else k_vjp_branch<<<grid_for((int64_t)d.T * d.L), kBlock, 0, s>>>(d, x, y, gx);
+  }
   k_vjp_bus<<<grid_for((int64_t)d.T * d.N), kBlock, 0, s>>>(d, x, y, gx, gpd, d.D > 0 ? gqd : nullptr);
   if (d.G > 0) k_vjp_gen<<<grid_for((int64_t)d.T * d.G), kBlock, 0, s>>>(d, y, gx);
   const cudaError_t e = cudaGetLastError();
@@ -287,18 +369,30 @@ int mpopf_vjp(mpopf_handle *h, const double *x, const double *y, double *gx, dou
   return MPOPF_OK;
 }
 
-int mpopf_jvp(mpopf_handle *h, const double *x, const double *v, const double *dpd, const double *dqd, double *jv_out,
-              void *stream) {
+int mpopf_vjp(mpopf_handle *h, const double *x, const double *y, double *gx, double *gpd, double *gqd, void *stream) {
+  return mpopf_vjp_jv(h, x, nullptr, y, gx, gpd, gqd, stream);
+}
+
+int mpopf_jvp_jv(mpopf_handle *h, const double *x, const double *jv, const double *v, const double *dpd,
+                 const double *dqd, double *jv_out, void *stream) {
   if (!h || !x || !v || !jv_out) return fail(MPOPF_ERR_ARG, "mpopf_jvp: NULL argument");
   if ((dpd == nullptr) != (dqd == nullptr)) return fail(MPOPF_ERR_ARG, "mpopf_jvp: give both dpd and dqd or neither");
   const Dev &d = h->d;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (d.L > 0) k_jvp_branch<<<grid_for((int64_t)d.T * d.L), kBlock, 0, s>>>(d, x, v, jv_out);
+  if (d.L > 0) {
+    if (jv) k_jvp_branch_jv<<<grid_for((int64_t)d.T * d.L), kBlock, 0, s>>>(d, jv, v, jv_out);
+    else k_jvp_branch<<<grid_for((int64_t)d.T * d.L), kBlock, 0, s>>>(d, x, v, jv_out);
+  }
   k_jvp_bus<<<grid_for((int64_t)d.T * d.N), kBlock, 0, s>>>(d, x, v, d.D > 0 ? dpd : nullptr, dqd, jv_out);
   if (d.G > 0 && d.T > 1) k_jvp_gen<<<grid_for((int64_t)(d.T - 1) * d.G), kBlock, 0, s>>>(d, v, jv_out);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(MPOPF_ERR_CUDA, std::string("mpopf_jvp: ") + cudaGetErrorString(e));
   return MPOPF_OK;
+}
+
+int mpopf_jvp(mpopf_handle *h, const double *x, const double *v, const double *dpd, const double *dqd, double *jv_out,
+              void *stream) {
+  return mpopf_jvp_jv(h, x, nullptr, v, dpd, dqd, jv_out, stream);
 }
 
 int mpopf_hvp(mpopf_handle *h, const double *x, const double *lam, double sigma, const double *v, double *hv,

@@ -16,10 +16,10 @@
 
 #include "mpopf_internal.cuh"
 
-extern "C" int mpopf_vjp(mpopf_handle *h, const double *x, const double *y, double *gx, double *gpd, double *gqd,
-                         void *stream);
-extern "C" int mpopf_jvp(mpopf_handle *h, const double *x, const double *v, const double *dpd, const double *dqd,
-                         double *jv_out, void *stream);
+extern "C" int mpopf_vjp_jv(mpopf_handle *h, const double *x, const double *jv, const double *y, double *gx,
+                            double *gpd, double *gqd, void *stream);
+extern "C" int mpopf_jvp_jv(mpopf_handle *h, const double *x, const double *jv, const double *v, const double *dpd,
+                            const double *dqd, double *jv_out, void *stream);
 
 namespace mpopf {
 namespace {
@@ -171,9 +171,9 @@ int mpopf_ipm_prepare(mpopf_handle *h, const double *x, const double *s, const d
   return check_launch("mpopf_ipm_prepare");
 }
 
-int mpopf_ipm_rhs(mpopf_handle *h, const double *x, const double *s, const double *y, const double *grad,
-                  const double *c, const double *recip, const double *dvec, const double *cvec, double mu,
-                  double *rhs, void *stream) {
+int mpopf_ipm_rhs(mpopf_handle *h, const double *x, const double *jv, const double *s, const double *y,
+                  const double *grad, const double *c, const double *recip, const double *dvec, const double *cvec,
+                  double mu, double *rhs, void *stream) {
   if (!h || !x || !s || !y || !grad || !c || !recip || !dvec || !cvec || !rhs)
     return fail(MPOPF_ERR_ARG, "mpopf_ipm_rhs: NULL argument");
   const Dev &d = h->d;
@@ -184,24 +184,24 @@ int mpopf_ipm_rhs(mpopf_handle *h, const double *x, const double *s, const doubl
     k_rhs_rows<<<grid_for(m), kBlock, 0, st>>>(m, s, y, c, recip + 2 * n, recip + 2 * n + m, dvec, cvec, mu, w);
   int rc = check_launch("mpopf_ipm_rhs");
   if (rc != MPOPF_OK) return rc;
-  rc = mpopf_vjp(h, x, w, rhs, nullptr, nullptr, stream);
+  rc = mpopf_vjp_jv(h, x, jv, w, rhs, nullptr, nullptr, stream);
   if (rc != MPOPF_OK) return rc;
   if (n > 0) k_rhs_vars<<<grid_for(n), kBlock, 0, st>>>(n, grad, recip, recip + n, mu, rhs);
   return check_launch("mpopf_ipm_rhs");
 }
 
-int mpopf_ipm_recover(mpopf_handle *h, const double *x, const double *s, const double *y, const double *zl_x,
-                      const double *zu_x, const double *zl_s, const double *zu_s, const double *c,
-                      const double *recip, const double *cvec, const double *dx, double mu, double delta_w,
-                      double delta_c, double *ds, double *dy, double *dzl_x, double *dzu_x, double *dzl_s,
-                      double *dzu_s, void *stream) {
+int mpopf_ipm_recover(mpopf_handle *h, const double *x, const double *jv, const double *s, const double *y,
+                      const double *zl_x, const double *zu_x, const double *zl_s, const double *zu_s,
+                      const double *c, const double *recip, const double *cvec, const double *dx, double mu,
+                      double delta_w, double delta_c, double *ds, double *dy, double *dzl_x, double *dzu_x,
+                      double *dzl_s, double *dzu_s, void *stream) {
   if (!h || !x || !s || !y || !zl_x || !zu_x || !zl_s || !zu_s || !c || !recip || !cvec || !dx || !ds || !dy ||
       !dzl_x || !dzu_x || !dzl_s || !dzu_s)
     return fail(MPOPF_ERR_ARG, "mpopf_ipm_recover: NULL argument");
   const Dev &d = h->d;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int64_t n = d.n, m = d.m;
-  int rc = mpopf_jvp(h, x, dx, nullptr, nullptr, ds, stream);  // ds = J dx
+  int rc = mpopf_jvp_jv(h, x, jv, dx, nullptr, nullptr, ds, stream);  // ds = J dx
   if (rc != MPOPF_OK) return rc;
   if (m > 0)
     k_rec_rows<<<grid_for(m), kBlock, 0, st>>>(m, s, y, c, zl_s, zu_s, recip + 2 * n, recip + 2 * n + m, cvec, mu,

@@ -99,8 +99,10 @@ def lib():
             "mpopf_csc_pattern": (ctypes.c_int, [_P, _I32, ctypes.POINTER(_Csc)]),
             "mpopf_coo_to_csc": (ctypes.c_int, [_P, _I32, _P, _P, _P]),
             "mpopf_ipm_prepare": (ctypes.c_int, [_P] * 7 + [_D] * 3 + [_P] * 5),
-            "mpopf_ipm_rhs": (ctypes.c_int, [_P] * 9 + [_D] + [_P, _P]),
-            "mpopf_ipm_recover": (ctypes.c_int, [_P] * 12 + [_D] * 3 + [_P] * 7),
+            "mpopf_ipm_rhs": (ctypes.c_int, [_P] * 10 + [_D] + [_P, _P]),
+            "mpopf_ipm_recover": (ctypes.c_int, [_P] * 13 + [_D] * 3 + [_P] * 7),
+            "mpopf_vjp_jv": (ctypes.c_int, [_P] * 8),
+            "mpopf_jvp_jv": (ctypes.c_int, [_P] * 8),
             "mpopf_batch_create": (ctypes.c_int, [_P, _I32, ctypes.POINTER(_P)]),
             "mpopf_batch_set_io": (ctypes.c_int, [_P, _P, _P]),
             "mpopf_batch_sweep": (ctypes.c_int, [_P, _P]),
@@ -128,10 +130,11 @@ def exported_symbols():
     return ["mpopf_setup", "mpopf_get_pattern", "mpopf_set_loads", "mpopf_eval", "mpopf_eval_obj",
             "mpopf_eval_grad", "mpopf_eval_cons", "mpopf_eval_jac", "mpopf_eval_hess", "mpopf_assemble_kkt",
             "mpopf_sweep", "mpopf_sweep_host", "mpopf_assemble_kkt_noalloc", "mpopf_vjp", "mpopf_jvp", "mpopf_hvp",
-            "mpopf_kkt_factor", "mpopf_kkt_solve", "mpopf_csc_pattern", "mpopf_coo_to_csc", "mpopf_ipm_prepare", "mpopf_ipm_rhs", "mpopf_ipm_recover", "mpopf_batch_create", "mpopf_batch_set_io", "mpopf_batch_sweep", "mpopf_batch_set_schedule",
-            "mpopf_batch_get_schedule", "mpopf_batch_tune", "mpopf_batch_status", "mpopf_batch_destroy",
-            "mpopf_launch_count", "mpopf_profile_start", "mpopf_profile_stop",
-            "mpopf_destroy", "mpopf_last_error"]
+            "mpopf_vjp_jv", "mpopf_jvp_jv", "mpopf_kkt_factor", "mpopf_kkt_solve", "mpopf_csc_pattern",
+            "mpopf_coo_to_csc", "mpopf_ipm_prepare", "mpopf_ipm_rhs", "mpopf_ipm_recover", "mpopf_batch_create",
+            "mpopf_batch_set_io", "mpopf_batch_sweep", "mpopf_batch_set_schedule", "mpopf_batch_get_schedule",
+            "mpopf_batch_tune", "mpopf_batch_status", "mpopf_batch_destroy", "mpopf_launch_count",
+            "mpopf_profile_start", "mpopf_profile_stop", "mpopf_destroy", "mpopf_last_error"]
 
 
 class MpopfError(RuntimeError):
@@ -285,24 +288,25 @@ class Handle:
         return kv
 
     # -- matrix-free derivative products -------------------------------------
-    def vjp(self, x, y, gx=None, loads=True, stream=None):
+    def vjp(self, x, y, gx=None, loads=True, jv=None, stream=None):
         """(J^T y, (dc/dPd)^T y, (dc/dQd)^T y); the load parts are None when
-        loads is False."""
+        loads is False; jv: J values at x (optional: read instead of recomputed)."""
         import torch
         gx = torch.empty(self.n, dtype=torch.float64, device="cuda") if gx is None else gx
         gpd = gqd = None
         if loads:
             gpd = torch.empty(self.T * self.n_load, dtype=torch.float64, device="cuda")
             gqd = torch.empty_like(gpd)
-        _check(lib().mpopf_vjp(self.h, _ptr(x), _ptr(y), _ptr(gx), _ptr(gpd), _ptr(gqd), _stream_ptr(stream)),
-               "mpopf_vjp")
+        _check(lib().mpopf_vjp_jv(self.h, _ptr(x), _ptr(jv), _ptr(y), _ptr(gx), _ptr(gpd), _ptr(gqd),
+                                  _stream_ptr(stream)), "mpopf_vjp")
         return gx, gpd, gqd
 
-    def jvp(self, x, v, dpd=None, dqd=None, out=None, stream=None):
+    def jvp(self, x, v, dpd=None, dqd=None, out=None, jv=None, stream=None):
+        """J v [m]; jv: J values at x (optional: read instead of recomputed)."""
         import torch
         out = torch.empty(self.m, dtype=torch.float64, device="cuda") if out is None else out
-        _check(lib().mpopf_jvp(self.h, _ptr(x), _ptr(v), _ptr(dpd), _ptr(dqd), _ptr(out), _stream_ptr(stream)),
-               "mpopf_jvp")
+        _check(lib().mpopf_jvp_jv(self.h, _ptr(x), _ptr(jv), _ptr(v), _ptr(dpd), _ptr(dqd), _ptr(out),
+                                  _stream_ptr(stream)), "mpopf_jvp")
         return out
 
     def hvp(self, x, lam, sigma, v, out=None, stream=None):
@@ -368,22 +372,24 @@ class Handle:
                                        _ptr(cvec), _ptr(recip), _stream_ptr(stream)), "mpopf_ipm_prepare")
         return sigx, dvec, cvec, recip
 
-    def ipm_rhs(self, x, s, y, grad, c, recip, dvec, cvec, mu, out=None, stream=None):
-        """Condensed right-hand side q_x + J^T (C q_s + D q_y) [n]."""
+    def ipm_rhs(self, x, s, y, grad, c, recip, dvec, cvec, mu, out=None, jv=None, stream=None):
+        """Condensed right-hand side q_x + J^T (C q_s + D q_y) [n]; jv: J values
+        at x from the sweep (optional: read instead of recomputed)."""
         out = self._dvec(self.n) if out is None else out
-        _check(lib().mpopf_ipm_rhs(self.h, _ptr(x), _ptr(s), _ptr(y), _ptr(grad), _ptr(c), _ptr(recip),
-                                   _ptr(dvec), _ptr(cvec), float(mu), _ptr(out), _stream_ptr(stream)),
+        _check(lib().mpopf_ipm_rhs(self.h, _ptr(x), _ptr(jv), _ptr(s), _ptr(y), _ptr(grad), _ptr(c),
+                                   _ptr(recip), _ptr(dvec), _ptr(cvec), float(mu), _ptr(out), _stream_ptr(stream)),
                "mpopf_ipm_rhs")
         return out
 
     def ipm_recover(self, x, s, y, zl_x, zu_x, zl_s, zu_s, c, recip, cvec, dx, mu, delta_w, delta_c, out=None,
-                    stream=None):
-        """dict ds, dy, dzl_s, dzu_s [m] and dzl_x, dzu_x [n] from dx."""
+                    jv=None, stream=None):
+        """dict ds, dy, dzl_s, dzu_s [m] and dzl_x, dzu_x [n] from dx; jv as in
+        ipm_rhs."""
         r = out if out is not None else dict(
             ds=self._dvec(self.m), dy=self._dvec(self.m), dzl_x=self._dvec(self.n), dzu_x=self._dvec(self.n),
             dzl_s=self._dvec(self.m), dzu_s=self._dvec(self.m))
-        _check(lib().mpopf_ipm_recover(self.h, _ptr(x), _ptr(s), _ptr(y), _ptr(zl_x), _ptr(zu_x), _ptr(zl_s),
-                                       _ptr(zu_s), _ptr(c), _ptr(recip), _ptr(cvec), _ptr(dx), float(mu),
+        _check(lib().mpopf_ipm_recover(self.h, _ptr(x), _ptr(jv), _ptr(s), _ptr(y), _ptr(zl_x), _ptr(zu_x),
+                                       _ptr(zl_s), _ptr(zu_s), _ptr(c), _ptr(recip), _ptr(cvec), _ptr(dx), float(mu),
                                        float(delta_w), float(delta_c), _ptr(r["ds"]), _ptr(r["dy"]),
                                        _ptr(r["dzl_x"]), _ptr(r["dzu_x"]), _ptr(r["dzl_s"]), _ptr(r["dzu_s"]),
                                        _stream_ptr(stream)), "mpopf_ipm_recover")

@@ -64,6 +64,26 @@ def test_products_match_oracle(case):
     assert_close(f"{name}:hvp", _np(hv), o.hvp(pt.x, pt.lam, pt.sigma, v))
 
 
+def test_products_from_stored_jacobian(case):
+    """With J's values from the sweep at the same x, J^T y and J v read them
+    instead of recomputing the branch rows: bit for bit the same results."""
+    from paper_2405_14032_b300 import mpopf
+    name, inst, pt, h, o = case
+    rng = np.random.default_rng(15)
+    y, v = rng.standard_normal(o.m), rng.standard_normal(o.n)
+    xd = _dev(pt.x)
+    jv = h.eval(mpopf.OUT_JAC, xd)["jv"]
+    gx, gpd, gqd = h.vjp(xd, _dev(y), jv=jv)
+    rgx, rgpd, rgqd = o.vjp(pt.x, y)
+    assert np.array_equal(_np(gx), rgx) and np.array_equal(_np(gpd), rgpd) and np.array_equal(_np(gqd), rgqd)
+    assert np.array_equal(_np(h.jvp(xd, _dev(v), jv=jv)), o.jvp(pt.x, v))
+    if inst.net.n_load:
+        T, D = inst.T, inst.net.n_load
+        dpd, dqd = rng.standard_normal(T * D), rng.standard_normal(T * D)
+        assert np.array_equal(_np(h.jvp(xd, _dev(v), dpd=_dev(dpd), dqd=_dev(dqd), jv=jv)),
+                              o.jvp(pt.x, v, dpd=dpd, dqd=dqd))
+
+
 def test_dot_product_identity(case):
     name, inst, pt, h, o = case
     rng = np.random.default_rng(12)

@@ -40,8 +40,9 @@ def _point(cs, seed):
     return dict(x=x, s=s, y=y, zlx=zlx, zux=zux, zls=zls, zus=zus)
 
 
+@pytest.mark.parametrize("stored_j", [False, True])
 @pytest.mark.parametrize("dw,dc", [(DW, DC), (0.0, 0.0), (0.5, 2.0)])
-def test_prepare_rhs_recover_match_oracle(case, dw, dc):
+def test_prepare_rhs_recover_match_oracle(case, dw, dc, stored_j):
     name, cs = case
     o, h = cs.o, cs.h
     P = _point(cs, 71)
@@ -61,12 +62,15 @@ def test_prepare_rhs_recover_match_oracle(case, dw, dc):
     args = (P["x"], P["s"], P["y"], P["zlx"], P["zux"], P["zls"], P["zus"])
     dx_, ds_, dy_ = D["x"], D["s"], D["y"]
     g, c = _dev(ref["g"]), _dev(ref["c"])
-    rhs = h.ipm_rhs(dx_, ds_, dy_, g, c, recip, dvec, cvec, MU)
+    from paper_2405_14032_b300 import mpopf
+    jv = h.eval(mpopf.OUT_JAC, dx_)["jv"] if stored_j else None
+    rhs = h.ipm_rhs(dx_, ds_, dy_, g, c, recip, dvec, cvec, MU, jv=jv)
     rrhs, _ = o.ipm_rhs(*args, ref["g"], ref["c"], MU, dw, dc, EPS)
     e, n = assert_close(f"{name}:rhs", _np(rhs), rrhs)
     assert e == n, f"{name}:rhs {e}/{n} bitwise"  # same element order as the oracle's J^T w
 
-    rec = h.ipm_recover(dx_, ds_, dy_, D["zlx"], D["zux"], D["zls"], D["zus"], c, recip, cvec, _dev(dx), MU, dw, dc)
+    rec = h.ipm_recover(dx_, ds_, dy_, D["zlx"], D["zux"], D["zls"], D["zus"], c, recip, cvec, _dev(dx), MU, dw, dc,
+                        jv=jv)
     rrec = o.ipm_recover(*args, ref["c"], dx, MU, dw, dc, EPS)
     for k, rk in (("ds", "ds"), ("dy", "dy"), ("dzl_x", "dzlx"), ("dzu_x", "dzux"), ("dzl_s", "dzls"),
                   ("dzu_s", "dzus")):

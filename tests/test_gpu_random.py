@@ -75,6 +75,10 @@ def test_random_instance_bitwise(k):
     rgx, rgpd, rgqd = o.vjp(pt.x, y)
     assert np.array_equal(_np(gx), rgx) and np.array_equal(_np(gpd), rgpd) and np.array_equal(_np(gqd), rgqd), tag
     assert np.array_equal(_np(h.jvp(_dev(pt.x), _dev(v))), o.jvp(pt.x, v)), tag
+    # the same products reading the sweep's J values
+    gxs = h.vjp(_dev(pt.x), _dev(y), loads=False, jv=out["jv"])[0]
+    assert np.array_equal(_np(gxs), rgx), tag
+    assert np.array_equal(_np(h.jvp(_dev(pt.x), _dev(v), jv=out["jv"])), o.jvp(pt.x, v)), tag
     assert np.array_equal(_np(h.hvp(_dev(pt.x), _dev(pt.lam), pt.sigma, _dev(v))),
                           o.hvp(pt.x, pt.lam, pt.sigma, v)), tag
 
