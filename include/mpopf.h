@@ -331,7 +331,8 @@ int mpopf_kkt_solve(mpopf_handle *h, const double *rhs, double *dx, void *stream
  *   launches each, CUDA events on `stream`) and keeps the fastest; *best_ms its
  *   time per sweep.
  * mpopf_batch_status: synchronises the device; MPOPF_ERR_CUDA if a work item's
- *   dependency wait (bounded, ~1 s) ran out in any launch since create. */
+ *   dependency wait (bounded, ~1 s) ran out in the last launch (each launch
+ *   clears the flag with the counters). */
 typedef struct mpopf_batch mpopf_batch;
 typedef struct {
   const double *x, *lam, *sigma_x, *dvec;   /* device, [n] [m] [n] [m] of that instance */
@@ -346,6 +347,13 @@ int mpopf_batch_set_schedule(mpopf_batch *b, int32_t order, int32_t tile_chunks,
 int mpopf_batch_get_schedule(const mpopf_batch *b, int32_t *sched /* [4] */, int32_t *grid, int32_t *n_items);
 int mpopf_batch_tune(mpopf_batch *b, void *stream, int32_t reps, double *best_ms);
 int mpopf_batch_status(mpopf_batch *b);
+/* Failure-path test hook.  on != 0 raises the dependency target of the first
+ * bus tile that waits, so that its wait can never be met: the next sweep waits
+ * out the bounded limit (about a second), sets the error flag, computes the
+ * tile anyway and finishes; mpopf_batch_status then returns MPOPF_ERR_CUDA.
+ * on == 0 restores the target (so do mpopf_batch_set_schedule and _tune).
+ * Nothing faults or hangs; this exists to test that error path. */
+int mpopf_batch_test_stall(mpopf_batch *b, int32_t on);
 void mpopf_batch_destroy(mpopf_batch *b);
 
 /* Number of kernel launches one mpopf_eval call with these output bits makes. */

@@ -38,6 +38,8 @@ struct mpopf_batch {
   cudaGraphExec_t exec = nullptr;
   void *args[6];
   bool io_set = false;
+  std::vector<int32_t> need_host;  // dependency targets as built (the stall hook restores them)
+  int32_t stall_counter = -1;      // counter whose target the stall hook raised, or -1
 };
 
 namespace {
@@ -116,6 +118,8 @@ cudaError_t build_items(mpopf_batch *b) {
   if (e == cudaSuccess) e = cudaMemcpy(b->d_need, need.data(), need.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
   b->n_items = (int32_t)items.size();
   b->n_counters = (int32_t)need.size();
+  b->need_host = need;
+  b->stall_counter = -1;
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
   const int per_sm = b->sched[2] > 0 ? std::min(b->sched[2], batch_max_ctas_per_sm()) : batch_max_ctas_per_sm();
@@ -228,6 +232,32 @@ int mpopf_batch_status(mpopf_batch *b) {
   if (e == cudaSuccess) e = cudaMemcpy(&flag, b->d_ctl + 1, sizeof(int32_t), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return fail(MPOPF_ERR_CUDA, std::string("mpopf_batch_status: ") + cudaGetErrorString(e));
   if (flag) return fail(MPOPF_ERR_CUDA, "mpopf_batch_status: a dependency wait exceeded its limit");
+  return MPOPF_OK;
+}
+
+int mpopf_batch_test_stall(mpopf_batch *b, int32_t on) {
+  if (!b) return fail(MPOPF_ERR_ARG, "mpopf_batch_test_stall: NULL batch");
+  cudaError_t e = cudaSuccess;
+  if (b->stall_counter >= 0) {  // restore
+    const int32_t c = b->stall_counter;
+    e = cudaMemcpy(b->d_need + c, &b->need_host[c], sizeof(int32_t), cudaMemcpyHostToDevice);
+    b->stall_counter = -1;
+  }
+  if (e == cudaSuccess && on) {
+    // the first counter a bus tile waits on (a chunk of some instance's branch tiles)
+    int32_t c = -1;
+    std::vector<BatchItem> items(b->n_items);
+    e = cudaMemcpy(items.data(), b->d_items, items.size() * sizeof(BatchItem), cudaMemcpyDeviceToHost);
+    for (const BatchItem &it : items)
+      if (it.kind == ITEM_BUS && it.wait >= 0) { c = it.wait; break; }
+    if (e == cudaSuccess && c < 0) return fail(MPOPF_ERR_ARG, "mpopf_batch_test_stall: no bus tile waits");
+    if (e == cudaSuccess) {
+      const int32_t raised = b->need_host[c] + 1;
+      e = cudaMemcpy(b->d_need + c, &raised, sizeof(int32_t), cudaMemcpyHostToDevice);
+      b->stall_counter = c;
+    }
+  }
+  if (e != cudaSuccess) return fail(MPOPF_ERR_CUDA, std::string("mpopf_batch_test_stall: ") + cudaGetErrorString(e));
   return MPOPF_OK;
 }
 

@@ -110,6 +110,7 @@ def lib():
             "mpopf_batch_get_schedule": (ctypes.c_int, [_P, _P, _P, _P]),
             "mpopf_batch_tune": (ctypes.c_int, [_P, _P, _I32, _P]),
             "mpopf_batch_status": (ctypes.c_int, [_P]),
+            "mpopf_batch_test_stall": (ctypes.c_int, [_P, _I32]),
             "mpopf_batch_destroy": (None, [_P]),
             "mpopf_launch_count": (ctypes.c_int, [_P, _U]),
             "mpopf_profile_start": (ctypes.c_int, [_P, _I32]),
@@ -133,7 +134,7 @@ def exported_symbols():
             "mpopf_vjp_jv", "mpopf_jvp_jv", "mpopf_kkt_factor", "mpopf_kkt_solve", "mpopf_csc_pattern",
             "mpopf_coo_to_csc", "mpopf_ipm_prepare", "mpopf_ipm_rhs", "mpopf_ipm_recover", "mpopf_batch_create",
             "mpopf_batch_set_io", "mpopf_batch_sweep", "mpopf_batch_set_schedule", "mpopf_batch_get_schedule",
-            "mpopf_batch_tune", "mpopf_batch_status", "mpopf_batch_destroy", "mpopf_launch_count",
+            "mpopf_batch_tune", "mpopf_batch_status", "mpopf_batch_test_stall", "mpopf_batch_destroy", "mpopf_launch_count",
             "mpopf_profile_start", "mpopf_profile_stop", "mpopf_destroy", "mpopf_last_error"]
 
 
@@ -441,6 +442,10 @@ class Batch:
         best = np.zeros(1)
         _check(lib().mpopf_batch_tune(self.b, _stream_ptr(stream), int(reps), best.ctypes.data), "mpopf_batch_tune")
         return float(best[0])
+
+    def test_stall(self, on):
+        """Failure-path test hook (see mpopf_batch_test_stall)."""
+        _check(lib().mpopf_batch_test_stall(self.b, int(bool(on))), "mpopf_batch_test_stall")
 
     def status(self):
         _check(lib().mpopf_batch_status(self.b), "mpopf_batch_status")

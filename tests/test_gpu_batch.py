@@ -83,3 +83,33 @@ def test_batch_64_uneven_instances():
     b.tune(reps=2)
     _check_all(b, ios, refs)
     b.close()
+
+
+def test_dependency_wait_timeout_is_reported_not_hung():
+    """A bus tile whose dependency target can never be met (test hook) waits out
+    its bounded limit, the launch finishes, mpopf_batch_status reports the
+    error, the outputs are still complete (the tile is computed after the
+    wait), and once the target is restored the next launch is clean."""
+    import time
+
+    from paper_2405_14032_b300 import mpopf
+    hs, ios, refs = _setup(SMALL[:3])
+    b = mpopf.Batch(hs)
+    b.set_io(ios)
+    _check_all(b, ios, refs)
+    b.test_stall(True)
+    for io in ios:
+        for k in KEYS:
+            io[k].fill_(float("nan"))
+    t0 = time.perf_counter()
+    b.sweep()
+    with pytest.raises(mpopf.MpopfError, match="dependency wait"):
+        b.status()
+    waited = time.perf_counter() - t0
+    assert 0.05 < waited < 60.0
+    for io, ref in zip(ios, refs):
+        for k in KEYS:
+            assert torch.equal(io[k], ref[k]), k
+    b.test_stall(False)
+    _check_all(b, ios, refs)
+    b.close()
