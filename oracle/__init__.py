@@ -7,6 +7,7 @@ input generator :mod:`paper_2405_14032_b300.synth`.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import subprocess
@@ -34,43 +35,70 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+def _bind(lib):
+    """Set the ctypes signatures of an oracle library."""
+    sigs = {
+        "orc_new": (_P, [_P] * 10),
+        "orc_free": (None, [_P]),
+        "orc_sizes": (None, [_P, _P]),
+        "orc_bounds": (None, [_P, _P, _P, _P, _P]),
+        "orc_jac_pattern": (None, [_P, _P, _P]),
+        "orc_hess_pattern": (None, [_P, _P, _P]),
+        "orc_jac_rowptr": (None, [_P, _P]),
+        "orc_eval": (None, [_P, _I64, _I64, _P, _P, _D, _P, _P, _P, _P, _P]),
+        "orc_kkt": (_I64, [_P, _I64, _I64, _P, _P, _D, _P, _P, _D, _P, _P, _P, _P]),
+        "orc_window_rows": (_I64, [_P, _I64, _I64]),
+        "orc_vjp": (None, [_P, _I64, _I64, _P, _P, _P, _P, _P]),
+        "orc_hvp": (None, [_P, _I64, _I64, _P, _P, _D, _P, _P]),
+        "orc_jvp": (None, [_P, _I64, _I64, _P, _P, _P, _P, _P]),
+        "orc_sincos": (None, [_P, _I64, _P, _P]),
+        "orc_gradlag": (None, [_P, _P, _P, _D, _P]),
+        "orc_gradlag_cstep": (None, [_P, _P, _P, _D, _P, _D, _P]),
+        "orc_cons_textbook": (None, [_P, _P, _P]),
+        "orc_cons_cstep": (None, [_P, _P, _P, _D, _P]),
+        "orc_obj_textbook": (_D, [_P, _P]),
+        "orc_branch_terms": (None, [_P, _P]),
+        "orc_csc_nnz": (ctypes.c_int64, [_P, ctypes.c_int32]),
+        "orc_csc": (None, [_P, ctypes.c_int32, _P, _P, _P, _P]),
+        "orc_ipm_prepare": (None, [_P] * 7 + [_D, _D, _D] + [_P] * 5),
+        "orc_ipm_rhs": (None, [_P] * 10 + [_D, _D, _D, _D, _P, _P]),
+        "orc_ipm_recover": (None, [_P] * 10 + [_D, _D, _D, _D] + [_P] * 6),
+    }
+    for name, (res, args) in sigs.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
 def load():
     global _lib
     if _lib is None:
-        lib = ctypes.CDLL(build())
-        sigs = {
-            "orc_new": (_P, [_P] * 10),
-            "orc_free": (None, [_P]),
-            "orc_sizes": (None, [_P, _P]),
-            "orc_bounds": (None, [_P, _P, _P, _P, _P]),
-            "orc_jac_pattern": (None, [_P, _P, _P]),
-            "orc_hess_pattern": (None, [_P, _P, _P]),
-            "orc_jac_rowptr": (None, [_P, _P]),
-            "orc_eval": (None, [_P, _I64, _I64, _P, _P, _D, _P, _P, _P, _P, _P]),
-            "orc_kkt": (_I64, [_P, _I64, _I64, _P, _P, _D, _P, _P, _D, _P, _P, _P, _P]),
-            "orc_window_rows": (_I64, [_P, _I64, _I64]),
-            "orc_vjp": (None, [_P, _I64, _I64, _P, _P, _P, _P, _P]),
-            "orc_hvp": (None, [_P, _I64, _I64, _P, _P, _D, _P, _P]),
-            "orc_jvp": (None, [_P, _I64, _I64, _P, _P, _P, _P, _P]),
-            "orc_sincos": (None, [_P, _I64, _P, _P]),
-            "orc_gradlag": (None, [_P, _P, _P, _D, _P]),
-            "orc_gradlag_cstep": (None, [_P, _P, _P, _D, _P, _D, _P]),
-            "orc_cons_textbook": (None, [_P, _P, _P]),
-            "orc_cons_cstep": (None, [_P, _P, _P, _D, _P]),
-            "orc_obj_textbook": (_D, [_P, _P]),
-            "orc_branch_terms": (None, [_P, _P]),
-            "orc_csc_nnz": (ctypes.c_int64, [_P, ctypes.c_int32]),
-            "orc_csc": (None, [_P, ctypes.c_int32, _P, _P, _P, _P]),
-            "orc_ipm_prepare": (None, [_P] * 7 + [_D, _D, _D] + [_P] * 5),
-            "orc_ipm_rhs": (None, [_P] * 10 + [_D, _D, _D, _D, _P, _P]),
-            "orc_ipm_recover": (None, [_P] * 10 + [_D, _D, _D, _D] + [_P] * 6),
-        }
-        for name, (res, args) in sigs.items():
-            fn = getattr(lib, name)
-            fn.restype = res
-            fn.argtypes = args
-        _lib = lib
+        _lib = _bind(ctypes.CDLL(build()))
     return _lib
+
+
+def build_variant(source: str, directory: str) -> str:
+    """Compile a modified copy of the oracle source (the tests plant mistakes in
+    it to show that the pins catch them); returns the library path."""
+    src = os.path.join(directory, "oracle_variant.cpp")
+    out = os.path.join(directory, "liboracle_variant.so")
+    with open(src, "w") as fh:
+        fh.write(source)
+    subprocess.check_call(["g++", *_FLAGS, "-o", out, src])
+    return out
+
+
+@contextlib.contextmanager
+def using(path: str):
+    """Oracle objects created inside use the library at `path`."""
+    global _lib
+    saved = load()
+    _lib = _bind(ctypes.CDLL(path))
+    try:
+        yield _lib
+    finally:
+        _lib = saved
 
 
 def _ptr(a):
@@ -86,6 +114,7 @@ class Oracle:
 
     def __init__(self, inst):
         lib = load()
+        self._lib = lib  # the library this object's handle belongs to
         net = inst.net
         self.inst = inst
         self.T = inst.T
@@ -108,32 +137,32 @@ class Oracle:
         self.n, self.m, self.nnz_jac, self.nnz_hess = (int(v) for v in out)
 
     def __del__(self):
-        if getattr(self, "h", None) and _lib is not None:
-            _lib.orc_free(self.h)
+        if getattr(self, "h", None) and getattr(self, "_lib", None) is not None:
+            self._lib.orc_free(self.h)
             self.h = None
 
     # -- patterns ---------------------------------------------------------
     def bounds(self):
         xl, xu = np.empty(self.n), np.empty(self.n)
         gl, gu = np.empty(self.m), np.empty(self.m)
-        _lib.orc_bounds(self.h, _ptr(xl), _ptr(xu), _ptr(gl), _ptr(gu))
+        self._lib.orc_bounds(self.h, _ptr(xl), _ptr(xu), _ptr(gl), _ptr(gu))
         return xl, xu, gl, gu
 
     def jac_pattern(self):
         r = np.empty(self.nnz_jac, np.int32)
         c = np.empty(self.nnz_jac, np.int32)
-        _lib.orc_jac_pattern(self.h, _ptr(r), _ptr(c))
+        self._lib.orc_jac_pattern(self.h, _ptr(r), _ptr(c))
         return r, c
 
     def hess_pattern(self):
         r = np.empty(self.nnz_hess, np.int32)
         c = np.empty(self.nnz_hess, np.int32)
-        _lib.orc_hess_pattern(self.h, _ptr(r), _ptr(c))
+        self._lib.orc_hess_pattern(self.h, _ptr(r), _ptr(c))
         return r, c
 
     def jac_rowptr(self):
         rp = np.empty(self.m + 1, np.int64)
-        _lib.orc_jac_rowptr(self.h, _ptr(rp))
+        self._lib.orc_jac_rowptr(self.h, _ptr(rp))
         return rp
 
     # -- callbacks --------------------------------------------------------
@@ -150,7 +179,7 @@ class Oracle:
             c = np.full(self.m, np.nan) if "c" in want else None
             jv = np.full(self.nnz_jac, np.nan) if "jv" in want else None
             hv = np.full(self.nnz_hess, np.nan) if "hv" in want else None
-        _lib.orc_eval(self.h, t0, t1, _ptr(x), _ptr(lam), float(sigma),
+        self._lib.orc_eval(self.h, t0, t1, _ptr(x), _ptr(lam), float(sigma),
                       _ptr(f), _ptr(g), _ptr(c), _ptr(jv), _ptr(hv))
         return dict(f=None if f is None else float(f[0]), g=g, c=c, jv=jv, hv=hv)
 
@@ -159,14 +188,14 @@ class Oracle:
         (global row ids, row lengths, columns, values)."""
         t1 = self.T if t1 is None else t1
         x, lam, sx, dv = _f64(x), _f64(lam), _f64(sigma_x), _f64(dvec)
-        nr = _lib.orc_window_rows(self.h, t0, t1)
+        nr = self._lib.orc_window_rows(self.h, t0, t1)
         rows = np.empty(nr, np.int64)
         rowlen = np.empty(nr, np.int64)
-        nnz = _lib.orc_kkt(self.h, t0, t1, _ptr(x), _ptr(lam), float(sigma), _ptr(sx), _ptr(dv),
+        nnz = self._lib.orc_kkt(self.h, t0, t1, _ptr(x), _ptr(lam), float(sigma), _ptr(sx), _ptr(dv),
                            float(delta_w), _ptr(rows), _ptr(rowlen), None, None)
         cols = np.empty(nnz, np.int32)
         vals = np.empty(nnz, np.float64)
-        _lib.orc_kkt(self.h, t0, t1, _ptr(x), _ptr(lam), float(sigma), _ptr(sx), _ptr(dv),
+        self._lib.orc_kkt(self.h, t0, t1, _ptr(x), _ptr(lam), float(sigma), _ptr(sx), _ptr(dv),
                      float(delta_w), _ptr(rows), _ptr(rowlen), _ptr(cols), _ptr(vals))
         return rows, rowlen, cols, vals
 
@@ -184,13 +213,13 @@ class Oracle:
         D = self.inst.net.n_load
         gpd = np.full(self.T * D, np.nan)
         gqd = np.full(self.T * D, np.nan)
-        _lib.orc_vjp(self.h, t0, t1, _ptr(x), _ptr(y), _ptr(gx), _ptr(gpd), _ptr(gqd))
+        self._lib.orc_vjp(self.h, t0, t1, _ptr(x), _ptr(y), _ptr(gx), _ptr(gpd), _ptr(gqd))
         return gx, gpd, gqd
 
     def hvp(self, x, lam, sigma, v, t0=0, t1=None):
         t1 = self.T if t1 is None else t1
         out = np.full(self.n, np.nan)
-        _lib.orc_hvp(self.h, t0, t1, _ptr(_f64(x)), _ptr(_f64(lam)), float(sigma), _ptr(_f64(v)), _ptr(out))
+        self._lib.orc_hvp(self.h, t0, t1, _ptr(_f64(x)), _ptr(_f64(lam)), float(sigma), _ptr(_f64(v)), _ptr(out))
         return out
 
     def jvp(self, x, v, t0=0, t1=None, dpd=None, dqd=None):
@@ -199,43 +228,43 @@ class Oracle:
         out = np.full(self.m, np.nan)
         dpd = None if dpd is None else _f64(dpd)
         dqd = None if dqd is None else _f64(dqd)
-        _lib.orc_jvp(self.h, t0, t1, _ptr(_f64(x)), _ptr(_f64(v)), _ptr(dpd), _ptr(dqd), _ptr(out))
+        self._lib.orc_jvp(self.h, t0, t1, _ptr(_f64(x)), _ptr(_f64(v)), _ptr(dpd), _ptr(dqd), _ptr(out))
         return out
 
     # -- pins -------------------------------------------------------------
     def cons_textbook(self, x):
         c = np.empty(self.m)
-        _lib.orc_cons_textbook(self.h, _ptr(_f64(x)), _ptr(c))
+        self._lib.orc_cons_textbook(self.h, _ptr(_f64(x)), _ptr(c))
         return c
 
     def cons_cstep(self, x, dx, h=1e-30):
         dc = np.empty(self.m)
-        _lib.orc_cons_cstep(self.h, _ptr(_f64(x)), _ptr(_f64(dx)), float(h), _ptr(dc))
+        self._lib.orc_cons_cstep(self.h, _ptr(_f64(x)), _ptr(_f64(dx)), float(h), _ptr(dc))
         return dc
 
     def gradlag(self, x, lam, sigma):
         out = np.empty(self.n)
-        _lib.orc_gradlag(self.h, _ptr(_f64(x)), _ptr(_f64(lam)), float(sigma), _ptr(out))
+        self._lib.orc_gradlag(self.h, _ptr(_f64(x)), _ptr(_f64(lam)), float(sigma), _ptr(out))
         return out
 
     def gradlag_cstep(self, x, lam, sigma, dx, h=1e-30):
         out = np.empty(self.n)
-        _lib.orc_gradlag_cstep(self.h, _ptr(_f64(x)), _ptr(_f64(lam)), float(sigma), _ptr(_f64(dx)),
+        self._lib.orc_gradlag_cstep(self.h, _ptr(_f64(x)), _ptr(_f64(lam)), float(sigma), _ptr(_f64(dx)),
                                float(h), _ptr(out))
         return out
 
     def obj_textbook(self, x):
-        return float(_lib.orc_obj_textbook(self.h, _ptr(_f64(x))))
+        return float(self._lib.orc_obj_textbook(self.h, _ptr(_f64(x))))
 
     # -- COO -> CSC compression (Sec. III-A) ----------------------------------
     def csc(self, which, coo=None):
         """(colptr [n + 1], rowidx, vals or None) of J (which = 0) or the lower W
         (which = 1); duplicates summed in COO order."""
-        nnz = int(_lib.orc_csc_nnz(self.h, int(which)))
+        nnz = int(self._lib.orc_csc_nnz(self.h, int(which)))
         colptr = np.empty(self.n + 1, np.int64)
         rowidx = np.empty(nnz, np.int32)
         vals = None if coo is None else np.empty(nnz)
-        _lib.orc_csc(self.h, int(which), None if coo is None else _ptr(_f64(coo)), _ptr(colptr), _ptr(rowidx),
+        self._lib.orc_csc(self.h, int(which), None if coo is None else _ptr(_f64(coo)), _ptr(colptr), _ptr(rowidx),
                      None if vals is None else _ptr(vals))
         return colptr, rowidx, vals
 
@@ -244,21 +273,21 @@ class Oracle:
         """(Sigma_x, D, C, Sigma_s, recip) with recip = [rl_x, ru_x, rl_s, ru_s]."""
         sigx, dvec, cvec, sigs = np.empty(self.n), np.empty(self.m), np.empty(self.m), np.empty(self.m)
         recip = np.empty(2 * self.n + 2 * self.m)
-        _lib.orc_ipm_prepare(self.h, *[_ptr(_f64(a)) for a in (x, s, zlx, zux, zls, zus)], float(delta_w),
+        self._lib.orc_ipm_prepare(self.h, *[_ptr(_f64(a)) for a in (x, s, zlx, zux, zls, zus)], float(delta_w),
                              float(delta_c), float(eps), _ptr(sigx), _ptr(dvec), _ptr(cvec), _ptr(sigs),
                              _ptr(recip))
         return sigx, dvec, cvec, sigs, recip
 
     def ipm_rhs(self, x, s, y, zlx, zux, zls, zus, grad, c, mu, delta_w, delta_c, eps):
         rhs, w = np.empty(self.n), np.empty(self.m)
-        _lib.orc_ipm_rhs(self.h, *[_ptr(_f64(a)) for a in (x, s, y, zlx, zux, zls, zus, grad, c)], float(mu),
+        self._lib.orc_ipm_rhs(self.h, *[_ptr(_f64(a)) for a in (x, s, y, zlx, zux, zls, zus, grad, c)], float(mu),
                          float(delta_w), float(delta_c), float(eps), _ptr(rhs), _ptr(w))
         return rhs, w
 
     def ipm_recover(self, x, s, y, zlx, zux, zls, zus, c, dx, mu, delta_w, delta_c, eps):
         outs = [np.empty(self.m), np.empty(self.m), np.empty(self.n), np.empty(self.n), np.empty(self.m),
                 np.empty(self.m)]
-        _lib.orc_ipm_recover(self.h, *[_ptr(_f64(a)) for a in (x, s, y, zlx, zux, zls, zus, c, dx)], float(mu),
+        self._lib.orc_ipm_recover(self.h, *[_ptr(_f64(a)) for a in (x, s, y, zlx, zux, zls, zus, c, dx)], float(mu),
                              float(delta_w), float(delta_c), float(eps), *[_ptr(a) for a in outs])
         ds, dy, dzlx, dzux, dzls, dzus = outs
         return dict(ds=ds, dy=dy, dzlx=dzlx, dzux=dzux, dzls=dzls, dzus=dzus)
@@ -266,7 +295,7 @@ class Oracle:
     def branch_terms(self):
         L = self.inst.net.n_branch
         out = np.empty(8 * L)
-        _lib.orc_branch_terms(self.h, _ptr(out))
+        self._lib.orc_branch_terms(self.h, _ptr(out))
         return out.reshape(8, L)
 
 
