@@ -798,23 +798,29 @@ def run_ours(args, world, rank, local):
             "clocks": clk,
             "gpu_launches": launches * args.steps}
 
-    # end to end through the C-ABI with host buffers
-    if rank == 0:
-        pin = lambda k: torch.empty(k, dtype=torch.float64, pin_memory=True).numpy()
-        hx, hl, hs, hd = pin(n), pin(m), pin(n), pin(m)
-        hx[:], hl[:], hs[:], hd[:] = pt.x, pt.lam, pt.sigma_x, pt.dvec
-        hout = dict(f=pin(1), grad=pin(n), c=pin(m), jv=pin(h.nnz_jac), hv=pin(h.nnz_hess), kv=pin(h.nnz_kkt))
-        stream = torch.cuda.current_stream()
+    # end to end through the C-ABI with host buffers: every rank runs its own
+    # host-buffer sweeps at the same time (the ranks share the host's links)
+    pin = lambda k: torch.empty(k, dtype=torch.float64, pin_memory=True).numpy()
+    hx, hl, hs, hd = pin(n), pin(m), pin(n), pin(m)
+    hx[:], hl[:], hs[:], hd[:] = pt.x, pt.lam, pt.sigma_x, pt.dvec
+    hout = dict(f=pin(1), grad=pin(n), c=pin(m), jv=pin(h.nnz_jac), hv=pin(h.nnz_hess), kv=pin(h.nnz_kkt))
+    stream = torch.cuda.current_stream()
+    h.sweep_host(hx, hl, pt.sigma, hs, hd, pt.delta_w, hout, stream=stream)
+    ke = max(1, args.e2e_steps)
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    for _ in range(ke):
         h.sweep_host(hx, hl, pt.sigma, hs, hd, pt.delta_w, hout, stream=stream)
-        ke = max(1, args.e2e_steps)
-        t0 = time.perf_counter()
-        for _ in range(ke):
-            h.sweep_host(hx, hl, pt.sigma, hs, hd, pt.delta_w, hout, stream=stream)
-        el = time.perf_counter() - t0
-        h2d, d2h = 8 * (2 * n + 2 * m), 8 * (1 + n + m + h.nnz_jac + h.nnz_hess + h.nnz_kkt)
-        line["e2e"] = {"value": ke / el, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                       "d2h_gbs": d2h * ke / el / 1e9, "h2d_gbs": h2d * ke / el / 1e9,
-                       "steps": ke, "api": "mpopf_sweep_host (pinned host buffers, all inputs in, all outputs out)"}
+    el = max_over_ranks(time.perf_counter() - t0, world, dev)
+    h2d, d2h = 8 * (2 * n + 2 * m), 8 * (1 + n + m + h.nnz_jac + h.nnz_hess + h.nnz_kkt)
+    e2e = {"value": world * ke / el, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+           "d2h_gbs": world * d2h * ke / el / 1e9, "h2d_gbs": world * h2d * ke / el / 1e9,
+           "steps": ke, "ranks": world,
+           "api": "mpopf_sweep_host (pinned host buffers, all inputs in, all outputs out; every rank)"}
+    del hx, hl, hs, hd, hout
+    if rank == 0:
+        line["e2e"] = e2e
         if world == 1:
             line["cpu_baseline"] = cpu_baseline(inst, pt)
             line["adjoint"] = adjoint_comparison(torch)
