@@ -279,7 +279,8 @@ int mpopf_ipm_recover(mpopf_handle *h, const double *x, const double *jv, const 
  * mpopf_coo_to_csc: csc_vals [nnz] from coo_vals [nnz_jac or nnz_hess] (the
  *   values mpopf_eval_jac / mpopf_eval_hess write), device arrays, asynchronous
  *   on the stream; MPOPF_ERR_ARG if the pattern was not built first.
- * which: MPOPF_CSC_JAC or MPOPF_CSC_HESS (MPOPF_ERR_ARG otherwise). */
+ * which: MPOPF_CSC_JAC or MPOPF_CSC_HESS (MPOPF_ERR_ARG otherwise); a matrix
+ * with 2^31 or more COO entries gets MPOPF_ERR_SIZE. */
 enum { MPOPF_CSC_JAC = 0, MPOPF_CSC_HESS = 1 };
 typedef struct {
   int64_t nnz;

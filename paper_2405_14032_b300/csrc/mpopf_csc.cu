@@ -64,6 +64,8 @@ int build_csc(mpopf_handle *h, int which) {
   const mpopf_pattern &P = h->pat;
   const int64_t nnz = which == MPOPF_CSC_JAC ? P.nnz_jac : P.nnz_hess;
   const int64_t nrows = which == MPOPF_CSC_JAC ? P.m : P.n, ncols = P.n;
+  if (nnz >= ((int64_t)1 << 31))
+    return fail(MPOPF_ERR_SIZE, "mpopf_csc_pattern: 2^31 or more entries (32-bit entry numbers)");
   std::vector<int32_t> row(nnz), col(nnz);
   cudaError_t e = cudaSuccess;
   if (nnz > 0) {
