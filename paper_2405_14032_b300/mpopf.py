@@ -134,8 +134,8 @@ def exported_symbols():
             "mpopf_vjp_jv", "mpopf_jvp_jv", "mpopf_kkt_factor", "mpopf_kkt_solve", "mpopf_csc_pattern",
             "mpopf_coo_to_csc", "mpopf_ipm_prepare", "mpopf_ipm_rhs", "mpopf_ipm_recover", "mpopf_batch_create",
             "mpopf_batch_set_io", "mpopf_batch_sweep", "mpopf_batch_set_schedule", "mpopf_batch_get_schedule",
-            "mpopf_batch_tune", "mpopf_batch_status", "mpopf_batch_test_stall", "mpopf_batch_destroy", "mpopf_launch_count",
-            "mpopf_profile_start", "mpopf_profile_stop", "mpopf_destroy", "mpopf_last_error"]
+            "mpopf_batch_tune", "mpopf_batch_status", "mpopf_batch_test_stall", "mpopf_batch_destroy",
+            "mpopf_launch_count", "mpopf_profile_start", "mpopf_profile_stop", "mpopf_destroy", "mpopf_last_error"]
 
 
 class MpopfError(RuntimeError):
