@@ -144,3 +144,38 @@ def test_no_device_is_an_error_not_a_fallback():
         pytest.skip("a GPU is present")
     rc, msg = _setup_rc(synth.make_network(3, 10, 14, 2, 3))
     assert rc == -3 and "CUDA" in msg
+
+
+def test_last_error_is_per_thread():
+    """Threads that fail concurrently for different reasons each read their own
+    message (the error text is thread-local)."""
+    import threading
+    lib = mpopf.lib()
+    results = {}
+    barrier = threading.Barrier(8)
+
+    def worker(k):
+        net = synth.make_network(3, 10, 14, 2, 3)
+        if k % 2:
+            net.br_t = net.br_f.copy()  # self-loops
+            want = "self-loop"
+        else:
+            net.gen_bus = np.array([0, 99], np.int32)  # generator bus out of range
+            want = "generator bus"
+        barrier.wait()
+        for _ in range(50):
+            rc, msg = _setup_rc(net)
+            if rc != -1 or want not in msg:
+                results[k] = (rc, msg)
+                return
+            if want not in lib.mpopf_last_error().decode():
+                results[k] = ("reread", lib.mpopf_last_error().decode())
+                return
+        results[k] = "ok"
+
+    threads = [threading.Thread(target=worker, args=(k,)) for k in range(8)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert all(v == "ok" for v in results.values()), results
