@@ -44,13 +44,32 @@ __device__ __forceinline__ double ld_part(const double *p) {
   return COH ? __ldcg(p) : *p;
 }
 
+// Output staging of one warp (k_branch).  The J rows of the four flow
+// constraints and the W blocks of 32 consecutive branch elements are
+// contiguous ranges of the outputs, but each lane writes its own short piece
+// of them (5 or 10 entries): one L2 request per lane and store.  Staged, the
+// lanes write their pieces to a per-warp buffer in shared memory and the warp
+// copies the range out with coalesced stores (one request per 128-byte line).
+// One pad word per 32 spreads the lanes' pieces over the banks.
+constexpr int kStageCap = 320;                            // doubles per warp
+__device__ __forceinline__ int spad(int p) { return p + (p >> 5); }
+constexpr int kStagePitch = kStageCap + kStageCap / 32;  // spad(kStageCap)
+__device__ __forceinline__ void warp_flush(double *__restrict__ g, const double *s, int n, int lane) {
+  __syncwarp();
+  for (int i = lane; i < n; i += 32) g[i] = s[spad(i)];
+  __syncwarp();
+}
+
 template <unsigned MASK>
 __device__ __forceinline__ void branch_body(const Dev &d, int32_t tl, unsigned rt, const double *__restrict__ x,
                                             const double *__restrict__ lam, const double *__restrict__ sx,
                                             const double *__restrict__ dv, double dw, double *__restrict__ grad,
                                             double *__restrict__ c, double *__restrict__ jv,
-                                            double *__restrict__ hv, double *__restrict__ kv) {
+                                            double *__restrict__ hv, double *__restrict__ kv,
+                                            double *stage = nullptr) {
+  // stage: the warp's staging buffer when all 32 lanes hold elements, else null
   const unsigned mk = eff<MASK>(rt);
+  const int lane = (int)(threadIdx.x & 31);
   const int32_t L = d.L;
   if (tl >= d.T * L) return;
   const int32_t t = tl / L, l = tl - t * L;
@@ -120,12 +139,25 @@ __device__ __forceinline__ void branch_body(const Dev &d, int32_t tl, unsigned r
   const double jp6 = twice(pf), jq6 = twice(qf), jp7 = twice(pt), jq7 = twice(qt);
 
   if (mk & MPOPF_OUT_JAC) {
-    double *j1 = jv + d.T + (int64_t)tl * 5;
     const int64_t s5 = 5 * TL;
-    j1[0] = 1.0; j1[1] = a1; j1[2] = na1; j1[3] = b1; j1[4] = c1;
-    j1[s5 + 0] = 1.0; j1[s5 + 1] = a2; j1[s5 + 2] = na2; j1[s5 + 3] = b2; j1[s5 + 4] = c2;
-    j1[2 * s5 + 0] = 1.0; j1[2 * s5 + 1] = a3; j1[2 * s5 + 2] = na3; j1[2 * s5 + 3] = b3; j1[2 * s5 + 4] = c3;
-    j1[3 * s5 + 0] = 1.0; j1[3 * s5 + 1] = a4; j1[3 * s5 + 2] = na4; j1[3 * s5 + 3] = b4; j1[3 * s5 + 4] = c4;
+    if (stage) {
+      double *g = jv + d.T + (int64_t)(tl - lane) * 5;
+      auto put5 = [&](double *gk, double v1, double v2, double v3, double v4) {
+        stage[spad(5 * lane)] = 1.0; stage[spad(5 * lane + 1)] = v1; stage[spad(5 * lane + 2)] = v2;
+        stage[spad(5 * lane + 3)] = v3; stage[spad(5 * lane + 4)] = v4;
+        warp_flush(gk, stage, 160, lane);
+      };
+      put5(g, a1, na1, b1, c1);
+      put5(g + s5, a2, na2, b2, c2);
+      put5(g + 2 * s5, a3, na3, b3, c3);
+      put5(g + 3 * s5, a4, na4, b4, c4);
+    } else {
+      double *j1 = jv + d.T + (int64_t)tl * 5;
+      j1[0] = 1.0; j1[1] = a1; j1[2] = na1; j1[3] = b1; j1[4] = c1;
+      j1[s5 + 0] = 1.0; j1[s5 + 1] = a2; j1[s5 + 2] = na2; j1[s5 + 3] = b2; j1[s5 + 4] = c2;
+      j1[2 * s5 + 0] = 1.0; j1[2 * s5 + 1] = a3; j1[2 * s5 + 2] = na3; j1[2 * s5 + 3] = b3; j1[2 * s5 + 4] = c3;
+      j1[3 * s5 + 0] = 1.0; j1[3 * s5 + 1] = a4; j1[3 * s5 + 2] = na4; j1[3 * s5 + 3] = b4; j1[3 * s5 + 4] = c4;
+    }
     double *j5 = jv + d.j_k5 + (int64_t)tl * 2;
     j5[0] = 1.0; j5[1] = -1.0;
     double *j6 = jv + d.j_k6 + (int64_t)tl * 2;
@@ -147,11 +179,23 @@ __device__ __forceinline__ void branch_body(const Dev &d, int32_t tl, unsigned r
   const double h6 = twice(l6), h7 = twice(l7);
   const double nAsum = negx(Asum);
   if (mk & MPOPF_OUT_HESS) {
-    double *hb = hv + d.h_br + (int64_t)tl * 10;
-    hb[0] = Wdd; hb[1] = negx(Wdd); hb[2] = Wdd; hb[3] = Wdvf; hb[4] = negx(Wdvf);
-    hb[5] = Wvfvf; hb[6] = Wdvt; hb[7] = negx(Wdvt); hb[8] = nAsum; hb[9] = Wvtvt;
-    double *ht = hv + d.h_th + (int64_t)tl * 4;
-    ht[0] = h6; ht[1] = h6; ht[2] = h7; ht[3] = h7;
+    if (stage) {
+      const int b = 10 * lane;
+      stage[spad(b)] = Wdd; stage[spad(b + 1)] = negx(Wdd); stage[spad(b + 2)] = Wdd;
+      stage[spad(b + 3)] = Wdvf; stage[spad(b + 4)] = negx(Wdvf); stage[spad(b + 5)] = Wvfvf;
+      stage[spad(b + 6)] = Wdvt; stage[spad(b + 7)] = negx(Wdvt); stage[spad(b + 8)] = nAsum;
+      stage[spad(b + 9)] = Wvtvt;
+      warp_flush(hv + d.h_br + (int64_t)(tl - lane) * 10, stage, 320, lane);
+      const int e = 4 * lane;
+      stage[spad(e)] = h6; stage[spad(e + 1)] = h6; stage[spad(e + 2)] = h7; stage[spad(e + 3)] = h7;
+      warp_flush(hv + d.h_th + (int64_t)(tl - lane) * 4, stage, 128, lane);
+    } else {
+      double *hb = hv + d.h_br + (int64_t)tl * 10;
+      hb[0] = Wdd; hb[1] = negx(Wdd); hb[2] = Wdd; hb[3] = Wdvf; hb[4] = negx(Wdvf);
+      hb[5] = Wvfvf; hb[6] = Wdvt; hb[7] = negx(Wdvt); hb[8] = nAsum; hb[9] = Wvtvt;
+      double *ht = hv + d.h_th + (int64_t)tl * 4;
+      ht[0] = h6; ht[1] = h6; ht[2] = h7; ht[3] = h7;
+    }
   }
   if (!(mk & MPOPF_OUT_KKT)) return;
 
@@ -202,27 +246,31 @@ __device__ __forceinline__ void branch_body(const Dev &d, int32_t tl, unsigned r
   const int32_t kf = __ldg(d.bgen_ptr + f + 1) - __ldg(d.bgen_ptr + f);
   const int32_t kt = __ldg(d.bgen_ptr + to + 1) - __ldg(d.bgen_ptr + to);
   const int32_t rf = __ldg(d.arc_rank + l), rt2 = __ldg(d.arc_rank + L + l);
-  // Writes one arc row: [va lo, va hi, vm lo, vm hi], ngen x gval, [qp], nrank x aval, diag.
-  auto arc_row = [&](double *row, double vaf, double vat, double vmf, double vmt, int32_t ngen, double gval,
+  // Writes one arc row at kv[start ..]: [va lo, va hi, vm lo, vm hi], ngen x gval, [qp], nrank x aval, diag.
+  // The rows of 32 consecutive arcs of one kind and period are consecutive
+  // rows of M (contiguous in kv); a warp whose rows are contiguous and fit the
+  // buffer stages them, any other writes them directly.
+  // Writes one arc row at kv[start ..]: [va lo, va hi, vm lo, vm hi], ngen x gval, [qp], nrank x aval, diag.
+  auto arc_row = [&](int64_t start, double vaf, double vat, double vmf, double vmt, int32_t ngen, double gval,
                      bool has_qp, double qp, int32_t nrank, double aval, double diag) {
-    row[0] = flo ? vaf : vat;
-    row[1] = flo ? vat : vaf;
-    row[2] = flo ? vmf : vmt;
-    row[3] = flo ? vmt : vmf;
+    kv[start] = flo ? vaf : vat;
+    kv[start + 1] = flo ? vat : vaf;
+    kv[start + 2] = flo ? vmf : vmt;
+    kv[start + 3] = flo ? vmt : vmf;
     int k = 4;
-    for (int32_t e = 0; e < ngen; ++e) row[k++] = gval;
-    if (has_qp) row[k++] = qp;
-    for (int32_t e = 0; e < nrank; ++e) row[k++] = aval;
-    row[k] = diag;
+    for (int32_t e = 0; e < ngen; ++e) kv[start + k++] = gval;
+    if (has_qp) kv[start + k++] = qp;
+    for (int32_t e = 0; e < nrank; ++e) kv[start + k++] = aval;
+    kv[start + k] = diag;
   };
   const int64_t mp = d.m_p + (int64_t)t * d.mb_p, mq = d.m_q + (int64_t)t * d.mb_q;
-  arc_row(kv + mp + __ldg(d.mo_p + l), w11, negx(w11), w31 - w8f, w41, kf, negx(D8f), false, 0.0, rf, D8f,
+  arc_row(mp + __ldg(d.mo_p + l), w11, negx(w11), w31 - w8f, w41, kf, negx(D8f), false, 0.0, rf, D8f,
           ((sxpf + dw) + Lpp_f) + D8f);
-  arc_row(kv + mq + __ldg(d.mo_q + l), w12, negx(w12), w32 - w9f, w42, kf, negx(D9f), true, Lqp_f, rf, D9f,
+  arc_row(mq + __ldg(d.mo_q + l), w12, negx(w12), w32 - w9f, w42, kf, negx(D9f), true, Lqp_f, rf, D9f,
           ((sxqf + dw) + Lqq_f) + D9f);
-  arc_row(kv + mp + __ldg(d.mo_p + L + l), w13, negx(w13), w33, w43 - w8t, kt, negx(D8t), false, 0.0, rt2, D8t,
+  arc_row(mp + __ldg(d.mo_p + L + l), w13, negx(w13), w33, w43 - w8t, kt, negx(D8t), false, 0.0, rt2, D8t,
           ((sxpt + dw) + Lpp_t) + D8t);
-  arc_row(kv + mq + __ldg(d.mo_q + L + l), w14, negx(w14), w34, w44 - w9t, kt, negx(D9t), true, Lqp_t, rt2, D9t,
+  arc_row(mq + __ldg(d.mo_q + L + l), w14, negx(w14), w34, w44 - w9t, kt, negx(D9t), true, Lqp_t, rt2, D9t,
           ((sxqt + dw) + Lqq_t) + D9t);
 }
 
@@ -235,7 +283,9 @@ __global__ void __launch_bounds__(MPOPF_BRANCH_BLOCK, MPOPF_BRANCH_MINB)
              int32_t first, int32_t end) {
   const int32_t tl = first + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
   if (tl >= end) return;
-  branch_body<MASK>(d, tl, rt, x, lam, sx, dv, dw, grad, c, jv, hv, kv);
+  __shared__ double s_stage[MPOPF_BRANCH_BLOCK / 32][kStagePitch];
+  const bool full = tl - (int32_t)(threadIdx.x & 31) + 31 < end;  // uniform over the warp
+  branch_body<MASK>(d, tl, rt, x, lam, sx, dv, dw, grad, c, jv, hv, kv, full ? s_stage[threadIdx.x >> 5] : nullptr);
 }
 
 // ---------------------------------------------------------------------------

@@ -2,7 +2,11 @@
 resource report (no GPU needed).  The branch kernel is FP64-bound at three
 256-thread CTAs per SM (80 registers); its spills are sensitive to unrelated
 changes (a field inserted in the middle of the device descriptor once raised
-them from 32 to 72 bytes and the kernel time by 4%), so the budget is pinned."""
+them from 32 to 72 bytes and the kernel time by 4%), so the budget is pinned.
+The warp-staged stores of its J and W rows (shared memory, then coalesced
+copies) hold more values live and raise the static spill report from 32 to
+128 / 168 bytes of stores / loads; measured 0.868 ms against 0.961 ms without
+staging, so the budget is set just above that."""
 import os
 import re
 import shutil
@@ -30,4 +34,4 @@ def test_branch_kernel_register_and_spill_budget(tmp_path):
     spill = re.search(r"(\d+) bytes spill stores, (\d+) bytes spill loads", block)
     stores, loads = (int(spill.group(1)), int(spill.group(2))) if spill else (0, 0)
     assert regs <= 80, regs
-    assert stores <= 40 and loads <= 40, (stores, loads)
+    assert stores <= 136 and loads <= 176, (stores, loads)
