@@ -74,7 +74,15 @@ struct Dev {
   int32_t qramp;
   int64_t c_k11, j_k11, mb_qg1;
   const int32_t *mo_qg1;
+  // The branch kernel's per-branch integers packed for 16-byte loads
+  // (structure of quads, so a warp's load stays one contiguous run), [BRP_COUNT][L].
+  const int4 *brp;
 };
+
+// Quads of brp: (f, t, slot of the from end, slot of the to end), (M row
+// offsets of p_f, p_t, q_f, q_t inside a period block), (arc ranks of the from
+// and to ends, generators at the from bus, generators at the to bus).
+enum { BRP_ENDS, BRP_MROW, BRP_RANK, BRP_COUNT };
 
 inline constexpr int kBlock = 256;
 inline constexpr int kRec = 6;  // doubles per incidence record
@@ -121,7 +129,7 @@ int batch_max_ctas_per_sm();
 
 // The handle (opaque to callers).
 namespace mpopf {
-constexpr int kMaxBlocks = 96;
+constexpr int kMaxBlocks = 128;
 // CSC compression of J (0) or W (1), built on first request.
 struct CscState {
   bool built;

@@ -84,7 +84,9 @@ __device__ __forceinline__ void branch_body(const Dev &d, int32_t tl, unsigned r
   }
   if (!(mk & (MPOPF_OUT_CONS | MPOPF_OUT_JAC | MPOPF_OUT_HESS | MPOPF_OUT_KKT))) return;
 
-  const int32_t f = __ldg(d.br_f + l), to = __ldg(d.br_t + l);
+  // per-branch integers in 16-byte loads (quads, structure of arrays)
+  const int4 ends = __ldg(d.brp + (int64_t)BRP_ENDS * L + l);
+  const int32_t f = ends.x, to = ends.y;
   const double thf = __ldg(x + tN + f), tht = __ldg(x + tN + to);
   const double vf = __ldg(x + d.x_vm + tN + f), vt = __ldg(x + d.x_vm + tN + to);
   const double *bc = d.bc;
@@ -217,11 +219,11 @@ __device__ __forceinline__ void branch_body(const Dev &d, int32_t tl, unsigned r
   {
     // incidence records of both ends (bus-major, read by k_bus)
     double *R = d.S + (int64_t)t * 2 * L * kRec;
-    double2 *recf = reinterpret_cast<double2 *>(R + (int64_t)__ldg(d.br_slot + l) * kRec);
+    double2 *recf = reinterpret_cast<double2 *>(R + (int64_t)ends.z * kRec);
     recf[0] = make_double2(Sdd, Svfd);
     recf[1] = make_double2(Svfvf, Svtvf);
     recf[2] = make_double2(pf, qf);
-    double2 *rect = reinterpret_cast<double2 *>(R + (int64_t)__ldg(d.br_slot + L + l) * kRec);
+    double2 *rect = reinterpret_cast<double2 *>(R + (int64_t)ends.w * kRec);
     rect[0] = make_double2(Sdd, negx(Svtd));
     rect[1] = make_double2(Svtvt, Svtvf);
     rect[2] = make_double2(pt, qt);
@@ -243,9 +245,8 @@ __device__ __forceinline__ void branch_body(const Dev &d, int32_t tl, unsigned r
   const double sxpf = __ldg(sx + pb + l), sxpt = __ldg(sx + pb + L + l);
   const double sxqf = __ldg(sx + qb + l), sxqt = __ldg(sx + qb + L + l);
   const bool flo = f < to;
-  const int32_t kf = __ldg(d.bgen_ptr + f + 1) - __ldg(d.bgen_ptr + f);
-  const int32_t kt = __ldg(d.bgen_ptr + to + 1) - __ldg(d.bgen_ptr + to);
-  const int32_t rf = __ldg(d.arc_rank + l), rt2 = __ldg(d.arc_rank + L + l);
+  const int4 rank = __ldg(d.brp + (int64_t)BRP_RANK * L + l);
+  const int32_t rf = rank.x, rt2 = rank.y, kf = rank.z, kt = rank.w;
   // Writes one arc row at kv[start ..]: [va lo, va hi, vm lo, vm hi], ngen x gval, [qp], nrank x aval, diag.
   // The rows of 32 consecutive arcs of one kind and period are consecutive
   // rows of M (contiguous in kv); a warp whose rows are contiguous and fit the
@@ -264,13 +265,14 @@ __device__ __forceinline__ void branch_body(const Dev &d, int32_t tl, unsigned r
     kv[start + k] = diag;
   };
   const int64_t mp = d.m_p + (int64_t)t * d.mb_p, mq = d.m_q + (int64_t)t * d.mb_q;
-  arc_row(mp + __ldg(d.mo_p + l), w11, negx(w11), w31 - w8f, w41, kf, negx(D8f), false, 0.0, rf, D8f,
+  const int4 mrow = __ldg(d.brp + (int64_t)BRP_MROW * L + l);
+  arc_row(mp + mrow.x, w11, negx(w11), w31 - w8f, w41, kf, negx(D8f), false, 0.0, rf, D8f,
           ((sxpf + dw) + Lpp_f) + D8f);
-  arc_row(mq + __ldg(d.mo_q + l), w12, negx(w12), w32 - w9f, w42, kf, negx(D9f), true, Lqp_f, rf, D9f,
+  arc_row(mq + mrow.z, w12, negx(w12), w32 - w9f, w42, kf, negx(D9f), true, Lqp_f, rf, D9f,
           ((sxqf + dw) + Lqq_f) + D9f);
-  arc_row(mp + __ldg(d.mo_p + L + l), w13, negx(w13), w33, w43 - w8t, kt, negx(D8t), false, 0.0, rt2, D8t,
+  arc_row(mp + mrow.y, w13, negx(w13), w33, w43 - w8t, kt, negx(D8t), false, 0.0, rt2, D8t,
           ((sxpt + dw) + Lpp_t) + D8t);
-  arc_row(mq + __ldg(d.mo_q + L + l), w14, negx(w14), w34, w44 - w9t, kt, negx(D9t), true, Lqp_t, rt2, D9t,
+  arc_row(mq + mrow.w, w14, negx(w14), w34, w44 - w9t, kt, negx(D9t), true, Lqp_t, rt2, D9t,
           ((sxqt + dw) + Lqq_t) + D9t);
 }
 

@@ -553,6 +553,20 @@ int mpopf_setup(const mpopf_network *net, int32_t n_periods, const double *pd, c
   d.arc_perm = dev_upload(h, arc_perm, &err);
   d.slot_info = dev_upload(h, slot_info, &err);
   d.slot_next = dev_upload(h, slot_next, &err);
+  {
+    // the branch kernel's integers packed for 16-byte loads
+    std::vector<int32_t> brp((size_t)4 * BRP_COUNT * L);
+    for (int64_t l = 0; l < L; ++l) {
+      const int32_t f = net->br_f[l], to = net->br_t[l];
+      const int32_t q[BRP_COUNT][4] = {
+          {f, to, br_slot[l], br_slot[L + l]},
+          {mo_p[l], mo_p[L + l], mo_q[l], mo_q[L + l]},
+          {arc_rank[l], arc_rank[L + l], bgen_ptr[f + 1] - bgen_ptr[f], bgen_ptr[to + 1] - bgen_ptr[to]}};
+      for (int k = 0; k < BRP_COUNT; ++k)
+        for (int e = 0; e < 4; ++e) brp[4 * ((size_t)k * L + l) + e] = q[k][e];
+    }
+    d.brp = reinterpret_cast<const int4 *>(dev_upload(h, brp, &err));
+  }
   d.S = dev_alloc<double>(h, T * 2 * L * kRec, &err);
   d.fpart_n = (int32_t)std::max<int64_t>(1, (T * G + kBlock - 1) / kBlock);
   d.fpart = dev_alloc<double>(h, d.fpart_n, &err);
