@@ -70,6 +70,29 @@ def kernel_source_hash():
         return hashlib.sha256(fh.read()).hexdigest()[:16]
 
 
+def link_rates(torch, nbytes=1 << 30):
+    """The host link's rates for plain pinned copies of 1 GB (one direction at a
+    time, CUDA events on the current stream): the bound of the host-buffer
+    sweep, whose traffic is mostly device-to-host."""
+    k = nbytes // 8
+    d = torch.ones(k, dtype=torch.float64, device="cuda")
+    hbuf = torch.empty(k, dtype=torch.float64, pin_memory=True)
+    rates = {}
+    for name, fn in (("link_d2h_gbs", lambda: hbuf.copy_(d, non_blocking=True)),
+                     ("link_h2d_gbs", lambda: d.copy_(hbuf, non_blocking=True))):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        rates[name] = 3 * nbytes / (e0.elapsed_time(e1) * 1e-3) / 1e9
+    del d, hbuf
+    return rates
+
+
 def ncu_traffic():
     """DRAM bytes per launch of the dominant kernel from the committed ncu
     summary, or None when the kernel source changed since the capture."""
@@ -819,6 +842,9 @@ def run_ours(args, world, rank, local):
            "steps": ke, "ranks": world,
            "api": "mpopf_sweep_host (pinned host buffers, all inputs in, all outputs out; every rank)"}
     del hx, hl, hs, hd, hout
+    e2e.update(link_rates(torch))
+    if e2e.get("link_d2h_gbs"):
+        e2e["d2h_frac_of_link"] = (e2e["d2h_gbs"] / world) / e2e["link_d2h_gbs"]
     if rank == 0:
         line["e2e"] = e2e
         if world == 1:
