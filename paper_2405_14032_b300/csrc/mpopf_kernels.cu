@@ -932,15 +932,25 @@ int mpopf_sweep_host(mpopf_handle *h, const double *x, const double *lam, double
   // Periods in windows: inputs of window k go in on P.in, its branch and bus
   // work runs on the caller's stream, its outputs come out on P.out, so the
   // copies in both directions and the kernels overlap.  The generator work and
-  // the objective (whole horizon) and their outputs come last.
-  const int32_t per = (int32_t)((T + kHostWindows - 1) / kHostWindows);
-  const int32_t nw = (int32_t)((T + per - 1) / per);
+  // the objective (whole horizon) and their outputs come last.  A period's
+  // outputs are about 3.5 times its inputs, so the windows grow by 3 from a
+  // short first one (about T / 84 periods: outputs start moving early, and each
+  // window's inputs are in before the previous window's outputs are out) until
+  // an even split of the rest is smaller; the last window takes what is left.
+  int64_t wstart[kHostWindows + 1] = {0};
+  int32_t nw = 0;
+  for (int64_t size = std::max<int64_t>(1, T / 84); wstart[nw] < T; ++nw) {
+    const int64_t left = T - wstart[nw], wl = kHostWindows - nw;  // windows left, this one included
+    const int64_t take = wl == 1 ? left : std::min(size, (left + wl - 1) / wl);
+    wstart[nw + 1] = wstart[nw] + take;
+    size = 3 * take;
+  }
   Copier cp;
   cp.check(cudaEventRecord(P.start, s));
   cp.check(cudaStreamWaitEvent(P.in, P.start, 0));
   cp.check(cudaStreamWaitEvent(P.out, P.start, 0));
   for (int32_t k = 0; k < nw && cp.ok(); ++k) {
-    const int64_t t0 = (int64_t)k * per, t1 = std::min<int64_t>(T, t0 + per), tw = t1 - t0;
+    const int64_t t0 = wstart[k], t1 = wstart[k + 1], tw = t1 - t0;
     const int64_t r0 = std::max<int64_t>(t0, 1) - 1, r1 = t1 - 1;  // ramp rows (t - 1) G + g of these periods
     // inputs: x and Sigma_x by variable kind; lambda and D by row kind
     for (int v = 0; v < 2; ++v) {

@@ -177,11 +177,11 @@ def test_cfg2_full():
 
 HOST_CASES = {
     "cfg1": lambda: Case(synth.config_instance("cfg1"), 1),               # T = 4: four one-period windows
-    "ragged_T13": lambda: Case(synth.make_instance(52, 150, 240, 30, 90, 13), 52),  # windows of 2, last of 1
+    "ragged_T13": lambda: Case(synth.make_instance(52, 150, 240, 30, 90, 13), 52),  # windows 1, 2, 2, 2, 2, 2, 1, 1
     "edge_T1": lambda: Case(H.instance(_edge_network(), 1), 42),          # one window, no ramp rows
     "no_gens_no_loads": CASES["no_gens_no_loads"],
     "qramp_T3": CASES["qramp_T3"],
-    "cfg2": lambda: Case(synth.config_instance("cfg2"), 2),               # T = 24: eight windows of 3
+    "cfg2": lambda: Case(synth.config_instance("cfg2"), 2),               # T = 24: windows 1, 3, 4, 4, 3, 3, 3, 3
 }
 
 
