@@ -659,6 +659,7 @@ __global__ void __launch_bounds__(kBlock, MPOPF_BRANCH_MINB) k_batch(const Dev *
   // changes (the bodies read their fields many times).
   __shared__ __align__(16) unsigned char s_dev[sizeof(Dev)];
   __shared__ __align__(16) unsigned char s_io[sizeof(BatchIO)];
+  __shared__ double s_stage[kBlock / 32][kStagePitch];
   if (threadIdx.x == 0) s_inst = -1;
   const Dev &d = *reinterpret_cast<const Dev *>(s_dev);
   const BatchIO &b = *reinterpret_cast<const BatchIO *>(s_io);
@@ -698,10 +699,13 @@ __global__ void __launch_bounds__(kBlock, MPOPF_BRANCH_MINB) k_batch(const Dev *
     const int32_t end = I.first + I.count;
     switch (I.kind) {
       case ITEM_BRANCH:
-        for (int32_t c0 = I.first; c0 < end; c0 += kBlock)
+        for (int32_t c0 = I.first; c0 < end; c0 += kBlock) {
+          // warps whose 32 elements are all in the item stage their J and W rows
+          const bool full = c0 + (int32_t)(threadIdx.x & ~31u) + 31 < end;
           if (c0 + (int32_t)threadIdx.x < end)
             branch_body<MPOPF_OUT_ALL>(d, c0 + threadIdx.x, MPOPF_OUT_ALL, b.x, b.lam, b.sx, b.dv, b.dw, b.grad, b.c,
-                                       b.jv, b.hv, b.kv);
+                                       b.jv, b.hv, b.kv, full ? s_stage[threadIdx.x >> 5] : nullptr);
+        }
         break;
       case ITEM_GEN:
         for (int32_t c0 = I.first; c0 < end; c0 += kBlock)  // whole CTA: the objective tile tree
