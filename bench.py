@@ -65,9 +65,13 @@ def measured_peaks():
 
 
 def kernel_source_hash():
-    src = os.path.join(ROOT, "paper_2405_14032_b300", "csrc", "mpopf_kernels.cu")
-    with open(src, "rb") as fh:
-        return hashlib.sha256(fh.read()).hexdigest()[:16]
+    """Hash of the sources the sweep kernels are compiled from (the kernels,
+    their device helpers and the device descriptor's header)."""
+    h = hashlib.sha256()
+    for name in ("mpopf_kernels.cu", "mpopf_device.cuh", "mpopf_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2405_14032_b300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def link_rates(torch, nbytes=1 << 30):

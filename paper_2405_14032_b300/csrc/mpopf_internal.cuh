@@ -167,6 +167,14 @@ struct mpopf_handle {
 };
 
 namespace mpopf {
+// Branch and bus work of periods [t0, t1) of a full sweep, and the generator
+// work with the objective over the whole horizon; together, over a partition
+// of the horizon, exactly the launches of a full sweep (mpopf_kernels.cu).
+void launch_window(const Dev &d, int32_t t0, int32_t t1, const double *x, const double *lam, const double *sx,
+                   const double *dv, double dw, double *grad, double *c, double *jv, double *hv, double *kv,
+                   cudaStream_t s);
+void launch_gen_obj(const Dev &d, const double *x, double sigma, const double *sx, const double *dv, double dw,
+                    double *f, double *grad, double *c, double *jv, double *hv, double *kv, cudaStream_t s);
 void hostpipe_destroy(mpopf_handle *h);
 void kkt_solver_destroy(mpopf_handle *h);
 }  // namespace mpopf
