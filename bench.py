@@ -37,6 +37,8 @@ WORKLOAD = dict(n_bus=10000, n_branch=16000, n_gen=2000, n_load=6000, seed=3)
 # 14, Jacobian 8, W block 16, condensed-matrix contributions 75.  (Exact
 # doublings and sign flips are integer operations and are not counted.)
 FP64_OPS_PER_BRANCH_PERIOD = 147
+FP64_OPS_PER_BUS_PERIOD = 33   # hand counts of the bus and generator kernels (their
+FP64_OPS_PER_GEN_PERIOD = 17   # loops vary with the degree; these are averages)
 
 
 def parse():
@@ -380,7 +382,7 @@ def adjoint_comparison(torch, vectors=256):
     return res
 
 
-def batched_comparison(torch, reps=20):
+def batched_comparison(torch, reps=20, fp64_peak=None):
     """The batched workload: 64 instances (buses log-uniform in [500, 5000],
     L = 1.6 N, G = 0.2 N, D = 0.6 N, T in {12, 24, 48, 96}; instance k uses seed
     1000 + k) swept by one persistent launch (CUDA graph, autotuned schedule)
@@ -389,6 +391,8 @@ def batched_comparison(torch, reps=20):
     dev = lambda a: torch.as_tensor(a, dtype=torch.float64, device="cuda")
     hs, ios = [], []
     units = 0
+    alg_bytes = 0
+    fp64_ops = 0
     for s in synth.batch_shapes(64):
         inst = synth.make_instance(s["seed"], s["n_bus"], s["n_branch"], s["n_gen"], s["n_load"], s["T"])
         pt = synth.make_point(s["seed"], inst)
@@ -399,6 +403,9 @@ def batched_comparison(torch, reps=20):
         hs.append(h)
         ios.append(io)
         units += s["T"] * (s["n_bus"] + s["n_branch"] + s["n_gen"])
+        alg_bytes += algorithmic_bytes(h.n, h.m, h.nnz_jac, h.nnz_hess, h.nnz_kkt, s["n_load"], s["T"])
+        fp64_ops += s["T"] * (FP64_OPS_PER_BRANCH_PERIOD * s["n_branch"] + FP64_OPS_PER_BUS_PERIOD * s["n_bus"]
+                              + FP64_OPS_PER_GEN_PERIOD * s["n_gen"])
 
     def sequential():
         for h, io in zip(hs, ios):
@@ -430,7 +437,12 @@ def batched_comparison(torch, reps=20):
            "sequential_launches": 64 * hs[0].launch_count(), "batched_launches": 1,
            "speedup": seq_ms / bat_ms, "schedule": b.schedule(),
            "instance_sweeps_per_s_batched": 64 / (bat_ms * 1e-3),
-           "instance_sweeps_per_s_sequential": 64 / (seq_ms * 1e-3)}
+           "instance_sweeps_per_s_sequential": 64 / (seq_ms * 1e-3),
+           "algorithmic_bytes": alg_bytes, "gbs_batched": alg_bytes / (bat_ms * 1e-3) / 1e9,
+           "fp64_ops_hand_count": fp64_ops,
+           "fp64_gops_batched": fp64_ops / (bat_ms * 1e-3) / 1e9}
+    if fp64_peak:
+        res["fp64_frac_of_dgemm_rate"] = res["fp64_gops_batched"] / (fp64_peak / 1e9)
     b.close()
     for h in hs:
         h.close()
@@ -854,7 +866,7 @@ def run_ours(args, world, rank, local):
         if world == 1:
             line["cpu_baseline"] = cpu_baseline(inst, pt)
             line["adjoint"] = adjoint_comparison(torch)
-            line["batched"] = batched_comparison(torch)
+            line["batched"] = batched_comparison(torch, fp64_peak=fp64_peak)
             line["ipm"] = ipm_timing(torch, h)
             line["small_sweeps"] = graph_sweeps(torch)
             line["csc"] = csc_timing(torch, h, out)
