@@ -44,23 +44,46 @@ __device__ __forceinline__ double ld_part(const double *p) {
   return COH ? __ldcg(p) : *p;
 }
 
-// Output staging of one warp (k_branch).  The J rows of the four flow
-// constraints and the W blocks of 32 consecutive branch elements are
+// Output staging of one warp (k_branch, k_batch).  The J rows of the four
+// flow constraints and the W blocks of 32 consecutive branch elements are
 // contiguous ranges of the outputs, but each lane writes its own short piece
 // of them (5 or 10 entries): one L2 request per lane and store.  Staged, the
-// lanes write their pieces to a per-warp buffer in shared memory and the warp
-// copies the range out with coalesced stores (one request per 128-byte line).
-// One pad word per 32 spreads the lanes' pieces over the banks.
+// lanes write their pieces to a per-warp buffer in shared memory (in output
+// order) and the range goes out whole: in k_branch as coalesced warp stores
+// (one request per 128-byte line); in the persistent batch kernel as one
+// bulk copy (cp.async.bulk, shared to global, issued by one lane) when the
+// destination is 16-byte aligned, which measured faster there and slower in
+// k_branch.
+// Without the bulk copy, one pad word per 32 spreads the lanes' pieces over
+// the shared-memory banks; the bulk copy needs the range unpadded.
 constexpr int kStageCap = 320;                            // doubles per warp
-__device__ __forceinline__ int spad(int p) { return p + (p >> 5); }
-constexpr int kStagePitch = kStageCap + kStageCap / 32;  // spad(kStageCap)
-__device__ __forceinline__ void warp_flush(double *__restrict__ g, const double *s, int n, int lane) {
+constexpr int kStagePitch = kStageCap + kStageCap / 32;  // with the pad words
+template <bool BULK>
+__device__ __forceinline__ int spad(int p) { return BULK ? p : p + (p >> 5); }
+template <bool BULK>
+__device__ __forceinline__ void warp_flush(double *__restrict__ g, double *s, int n, int lane) {
+  if (BULK && (reinterpret_cast<uintptr_t>(g) & 15) == 0) {  // uniform over the warp
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the lanes' writes, to the copy engine
+    __syncwarp();
+    if (lane == 0) {
+      asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;"
+                   :: "l"(g), "r"((unsigned)__cvta_generic_to_shared(s)), "r"(n * 8) : "memory");
+      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+      asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");  // buffer free again
+    }
+    __syncwarp();
+    return;
+  }
   __syncwarp();
-  for (int i = lane; i < n; i += 32) g[i] = s[spad(i)];
+  for (int i = lane; i < n; i += 32) g[i] = s[spad<BULK>(i)];
   __syncwarp();
 }
+// Lane 0's bulk copies have completed their writes (before the warp exits).
+__device__ __forceinline__ void bulk_done(int lane) {
+  if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
 
-template <unsigned MASK>
+template <unsigned MASK, bool BULK = false>
 __device__ __forceinline__ void branch_body(const Dev &d, int32_t tl, unsigned rt, const double *__restrict__ x,
                                             const double *__restrict__ lam, const double *__restrict__ sx,
                                             const double *__restrict__ dv, double dw, double *__restrict__ grad,
@@ -145,9 +168,10 @@ __device__ __forceinline__ void branch_body(const Dev &d, int32_t tl, unsigned r
     if (stage) {
       double *g = jv + d.T + (int64_t)(tl - lane) * 5;
       auto put5 = [&](double *gk, double v1, double v2, double v3, double v4) {
-        stage[spad(5 * lane)] = 1.0; stage[spad(5 * lane + 1)] = v1; stage[spad(5 * lane + 2)] = v2;
-        stage[spad(5 * lane + 3)] = v3; stage[spad(5 * lane + 4)] = v4;
-        warp_flush(gk, stage, 160, lane);
+        stage[spad<BULK>(5 * lane)] = 1.0; stage[spad<BULK>(5 * lane + 1)] = v1;
+        stage[spad<BULK>(5 * lane + 2)] = v2; stage[spad<BULK>(5 * lane + 3)] = v3;
+        stage[spad<BULK>(5 * lane + 4)] = v4;
+        warp_flush<BULK>(gk, stage, 160, lane);
       };
       put5(g, a1, na1, b1, c1);
       put5(g + s5, a2, na2, b2, c2);
@@ -183,14 +207,15 @@ __device__ __forceinline__ void branch_body(const Dev &d, int32_t tl, unsigned r
   if (mk & MPOPF_OUT_HESS) {
     if (stage) {
       const int b = 10 * lane;
-      stage[spad(b)] = Wdd; stage[spad(b + 1)] = negx(Wdd); stage[spad(b + 2)] = Wdd;
-      stage[spad(b + 3)] = Wdvf; stage[spad(b + 4)] = negx(Wdvf); stage[spad(b + 5)] = Wvfvf;
-      stage[spad(b + 6)] = Wdvt; stage[spad(b + 7)] = negx(Wdvt); stage[spad(b + 8)] = nAsum;
-      stage[spad(b + 9)] = Wvtvt;
-      warp_flush(hv + d.h_br + (int64_t)(tl - lane) * 10, stage, 320, lane);
+      stage[spad<BULK>(b)] = Wdd; stage[spad<BULK>(b + 1)] = negx(Wdd); stage[spad<BULK>(b + 2)] = Wdd;
+      stage[spad<BULK>(b + 3)] = Wdvf; stage[spad<BULK>(b + 4)] = negx(Wdvf); stage[spad<BULK>(b + 5)] = Wvfvf;
+      stage[spad<BULK>(b + 6)] = Wdvt; stage[spad<BULK>(b + 7)] = negx(Wdvt); stage[spad<BULK>(b + 8)] = nAsum;
+      stage[spad<BULK>(b + 9)] = Wvtvt;
+      warp_flush<BULK>(hv + d.h_br + (int64_t)(tl - lane) * 10, stage, 320, lane);
       const int e = 4 * lane;
-      stage[spad(e)] = h6; stage[spad(e + 1)] = h6; stage[spad(e + 2)] = h7; stage[spad(e + 3)] = h7;
-      warp_flush(hv + d.h_th + (int64_t)(tl - lane) * 4, stage, 128, lane);
+      stage[spad<BULK>(e)] = h6; stage[spad<BULK>(e + 1)] = h6; stage[spad<BULK>(e + 2)] = h7;
+      stage[spad<BULK>(e + 3)] = h7;
+      warp_flush<BULK>(hv + d.h_th + (int64_t)(tl - lane) * 4, stage, 128, lane);
     } else {
       double *hb = hv + d.h_br + (int64_t)tl * 10;
       hb[0] = Wdd; hb[1] = negx(Wdd); hb[2] = Wdd; hb[3] = Wdvf; hb[4] = negx(Wdvf);
@@ -285,7 +310,7 @@ __global__ void __launch_bounds__(MPOPF_BRANCH_BLOCK, MPOPF_BRANCH_MINB)
              int32_t first, int32_t end) {
   const int32_t tl = first + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
   if (tl >= end) return;
-  __shared__ double s_stage[MPOPF_BRANCH_BLOCK / 32][kStagePitch];
+  __shared__ __align__(16) double s_stage[MPOPF_BRANCH_BLOCK / 32][kStagePitch];
   const bool full = tl - (int32_t)(threadIdx.x & 31) + 31 < end;  // uniform over the warp
   branch_body<MASK>(d, tl, rt, x, lam, sx, dv, dw, grad, c, jv, hv, kv, full ? s_stage[threadIdx.x >> 5] : nullptr);
 }
@@ -633,7 +658,7 @@ __global__ void __launch_bounds__(kBlock, MPOPF_BRANCH_MINB) k_batch(const Dev *
   // changes (the bodies read their fields many times).
   __shared__ __align__(16) unsigned char s_dev[sizeof(Dev)];
   __shared__ __align__(16) unsigned char s_io[sizeof(BatchIO)];
-  __shared__ double s_stage[kBlock / 32][kStagePitch];
+  __shared__ __align__(16) double s_stage[kBlock / 32][kStageCap];
   if (threadIdx.x == 0) s_inst = -1;
   const Dev &d = *reinterpret_cast<const Dev *>(s_dev);
   const BatchIO &b = *reinterpret_cast<const BatchIO *>(s_io);
@@ -642,7 +667,10 @@ __global__ void __launch_bounds__(kBlock, MPOPF_BRANCH_MINB) k_batch(const Dev *
     if (threadIdx.x == 0) s_item = atomicAdd(ctl, 1);
     __syncthreads();
     const int32_t it = s_item;
-    if (it >= n_items) return;
+    if (it >= n_items) {
+      bulk_done((int)(threadIdx.x & 31));
+      return;
+    }
     const BatchItem I = items[it];
     if (I.inst != s_inst) {
       const uint32_t *src = reinterpret_cast<const uint32_t *>(devs + I.inst);
@@ -677,8 +705,9 @@ __global__ void __launch_bounds__(kBlock, MPOPF_BRANCH_MINB) k_batch(const Dev *
           // warps whose 32 elements are all in the item stage their J and W rows
           const bool full = c0 + (int32_t)(threadIdx.x & ~31u) + 31 < end;
           if (c0 + (int32_t)threadIdx.x < end)
-            branch_body<MPOPF_OUT_ALL>(d, c0 + threadIdx.x, MPOPF_OUT_ALL, b.x, b.lam, b.sx, b.dv, b.dw, b.grad, b.c,
-                                       b.jv, b.hv, b.kv, full ? s_stage[threadIdx.x >> 5] : nullptr);
+            branch_body<MPOPF_OUT_ALL, true>(d, c0 + threadIdx.x, MPOPF_OUT_ALL, b.x, b.lam, b.sx, b.dv, b.dw,
+                                             b.grad, b.c, b.jv, b.hv, b.kv,
+                                             full ? s_stage[threadIdx.x >> 5] : nullptr);
         }
         break;
       case ITEM_GEN:
