@@ -51,8 +51,15 @@ def _check_all(b, ios, refs):
             assert torch.equal(io[k], ref[k]), (i, k)
 
 
+# Shapes cover both paths of the staged J and W ranges of the branch tiles
+# (one bulk copy when the destination is 16-byte aligned, warp stores when not):
+# T odd puts the K1 and K3 rows of J on an 8-byte boundary, and the K2 and K4
+# rows too unless L is odd; T G odd does so for the W blocks.  (57, 91, 11, 30,
+# 3) alternates the two paths within a warp, (161, 257, 33, 97, 2) takes only
+# bulk copies.
 SMALL = [(40, 64, 8, 20, 3), (73, 117, 15, 44, 2), (130, 208, 26, 78, 5), (31, 50, 6, 19, 1), (250, 400, 50, 150, 4),
-         (12, 20, 0, 5, 3), (600, 960, 120, 360, 7), (90, 140, 20, 50, 4, "qramp")]
+         (12, 20, 0, 5, 3), (600, 960, 120, 360, 7), (90, 140, 20, 50, 4, "qramp"), (57, 91, 11, 30, 3),
+         (161, 257, 33, 97, 2)]
 
 
 def test_batch_equals_individual_sweeps_every_schedule():
