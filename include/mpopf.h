@@ -17,7 +17,10 @@
  *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy default
  *     stream.  Work is enqueued asynchronously on it; nothing synchronises
  *     unless stated.  Calls on one handle must not overlap in time (they share
- *     the handle's scratch buffer).
+ *     the handle's scratch buffer).  The evaluation calls run their generator
+ *     kernels on a side stream of the handle, forked from `stream` and joined
+ *     back into it with events, so work enqueued on `stream` afterwards sees
+ *     every output (under stream capture the fork is a parallel graph branch).
  *   - Return value: MPOPF_OK (0) or a negative code; mpopf_last_error() gives a
  *     message (thread-local).  No call allocates device memory except
  *     mpopf_setup (and, once, mpopf_sweep_host for its staging buffers,
@@ -379,8 +382,9 @@ int mpopf_assemble_kkt_noalloc(mpopf_handle *h, const double *x, const double *l
 
 /* Per-kernel timing (instrumentation for benchmarks, not part of the paper's
  * method).  mpopf_profile_start creates 2 * max_launches CUDA events; every
- * later kernel launch of mpopf_eval (up to max_launches) is bracketed by an
- * event pair on its stream.  mpopf_profile_stop synchronises on those events,
+ * later kernel launch of mpopf_eval on the caller's stream (up to
+ * max_launches) is bracketed by an event pair on that stream; the generator
+ * kernels, when they run on the handle's side stream, are not timed.  mpopf_profile_stop synchronises on those events,
  * writes the summed milliseconds and launch counts per kernel kind
  * (ms_sum[4], launches[4]: 0 branch x period, 1 bus x period,
  * 2 generator x period, 3 objective reduction; either may be NULL) and

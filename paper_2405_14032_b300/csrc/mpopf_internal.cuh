@@ -95,10 +95,21 @@ struct Prof {
   int *kind = nullptr;        // [cap]
 };
 
-// Kernel launchers (mpopf_kernels.cu).
+// A side stream and two events of a handle: the generator work of an
+// evaluation runs on the side stream, forked from and joined back into the
+// caller's stream, alongside the branch and bus work (it reads none of their
+// outputs and writes disjoint ranges).
+struct Fork {
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+};
+
+// Kernel launchers (mpopf_kernels.cu).  With fork == nullptr every launch goes
+// to s in order.
 cudaError_t launch_eval(const Dev &d, unsigned outputs, const double *x, const double *lam, double sigma,
                         const double *sx, const double *dv, double dw, double *f, double *grad, double *c,
-                        double *jv, double *hv, double *kv, cudaStream_t s, Prof *prof);
+                        double *jv, double *hv, double *kv, cudaStream_t s, Prof *prof,
+                        const Fork *fork = nullptr);
 int eval_launch_count(const Dev &d, unsigned outputs);
 // Pattern expansion (mpopf_setup.cu).
 cudaError_t launch_patterns(const Dev &d, int32_t *jrow, int32_t *jcol, int32_t *hrow, int32_t *hcol,
@@ -164,6 +175,7 @@ struct mpopf_handle {
   mpopf::CscState csc[2];
   mpopf::HostPipe *pipe;
   mpopf::KktSolver *solver;  // library factorisation of M (built on first use)
+  mpopf::Fork fork;          // side stream of the evaluations (created at setup)
 };
 
 namespace mpopf {

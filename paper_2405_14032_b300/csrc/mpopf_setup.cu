@@ -267,6 +267,13 @@ T *dev_alloc(mpopf_handle *h, int64_t count, cudaError_t *err) {
   return static_cast<T *>(p);
 }
 
+void fork_destroy(mpopf_handle *h) {
+  if (h->fork.ev_join) cudaEventDestroy(h->fork.ev_join);
+  if (h->fork.ev_fork) cudaEventDestroy(h->fork.ev_fork);
+  if (h->fork.side) cudaStreamDestroy(h->fork.side);
+  h->fork = Fork();
+}
+
 void free_blocks(mpopf_handle *h) {
   for (int i = 0; i < h->nblocks; ++i) cudaFree(h->blocks[i]);
   h->nblocks = 0;
@@ -609,6 +616,17 @@ int mpopf_setup(const mpopf_network *net, int32_t n_periods, const double *pd, c
     cudaGetLastError();
     return fail(MPOPF_ERR_CUDA, msg);
   }
+  err = cudaStreamCreateWithFlags(&h->fork.side, cudaStreamNonBlocking);
+  if (err == cudaSuccess) err = cudaEventCreateWithFlags(&h->fork.ev_fork, cudaEventDisableTiming);
+  if (err == cudaSuccess) err = cudaEventCreateWithFlags(&h->fork.ev_join, cudaEventDisableTiming);
+  if (err != cudaSuccess) {
+    std::string msg = std::string("mpopf_setup: side stream: ") + cudaGetErrorString(err);
+    fork_destroy(h);
+    free_blocks(h);
+    delete h;
+    cudaGetLastError();
+    return fail(MPOPF_ERR_CUDA, msg);
+  }
   P.n = n; P.m = m; P.nnz_jac = d.nnz_jac; P.nnz_hess = d.nnz_hess; P.nnz_kkt = d.nnz_kkt;
   P.n_bus = d.N; P.n_branch = d.L; P.n_gen = d.G; P.n_load = d.D; P.n_periods = d.T;
   P.jac_row = jrow; P.jac_col = jcol; P.hess_row = hrow; P.hess_col = hcol;
@@ -638,6 +656,7 @@ int mpopf_set_loads(mpopf_handle *h, const double *d_pd, const double *d_qd, voi
 
 void mpopf_destroy(mpopf_handle *h) {
   if (!h) return;
+  fork_destroy(h);
   hostpipe_destroy(h);
   kkt_solver_destroy(h);
   free_blocks(h);
