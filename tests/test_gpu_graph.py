@@ -1,0 +1,65 @@
+"""Evaluations captured into a CUDA graph.  An evaluation forks its generator
+kernels onto the handle's side stream and joins them back with events; under
+stream capture that fork becomes a parallel branch of the graph.  Replaying
+the graph must give the plain sweep's outputs bit for bit, also for a graph of
+several sweeps at different iterates and for the callbacks one by one."""
+import numpy as np
+import pytest
+
+from paper_2405_14032_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+@pytest.mark.parametrize("shape", [(300, 480, 60, 180, 6), (57, 91, 11, 30, 3), (40, 64, 0, 20, 4)])
+def test_graph_replay_equals_plain(shape):
+    from paper_2405_14032_b300 import mpopf
+    N, L, G, D, T = shape
+    inst = synth.make_instance(71, N, L, G, D, T)
+    pt = synth.make_point(71, inst)
+    h = mpopf.Handle(inst)
+    x0, lam, sx, dv = _dev(pt.x), _dev(pt.lam), _dev(pt.sigma_x), _dev(pt.dvec)
+    gen = torch.Generator(device="cuda").manual_seed(5)
+    xs = [x0 + 1e-3 * torch.randn(h.n, generator=gen, device="cuda", dtype=torch.float64) for _ in range(3)]
+    refs = [h.sweep(x, lam, pt.sigma, sx, dv, pt.delta_w) for x in xs]
+    torch.cuda.synchronize()
+
+    outs = [h.new_outputs() for _ in xs]
+    st = torch.cuda.Stream()
+    st.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(st):
+        with torch.cuda.graph(g, stream=st):
+            for x, out in zip(xs, outs):
+                h.sweep(x, lam, pt.sigma, sx, dv, pt.delta_w, out=out, stream=st)
+    torch.cuda.synchronize()
+    for _ in range(2):
+        for out in outs:
+            for v in out.values():
+                v.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        for ref, out in zip(refs, outs):
+            for k in ref:
+                assert torch.equal(out[k], ref[k]), (shape, k)
+
+    # the callbacks one by one, captured the same way
+    single = {}
+    g2 = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(st):
+        with torch.cuda.graph(g2, stream=st):
+            single["f"] = h.eval(mpopf.OUT_OBJ, xs[0], stream=st)["f"]
+            single["c"] = h.eval(mpopf.OUT_CONS, xs[0], stream=st)["c"]
+            single["hv"] = h.eval(mpopf.OUT_HESS, xs[0], lam, pt.sigma, stream=st)["hv"]
+    g2.replay()
+    torch.cuda.synchronize()
+    for k in single:
+        assert torch.equal(single[k], refs[0][k]), (shape, k)
+    del g, g2
+    h.close()
