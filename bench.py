@@ -18,6 +18,7 @@ import hashlib
 import json
 import math
 import os
+import re
 import statistics
 import sys
 import threading
@@ -67,12 +68,16 @@ def measured_peaks():
 
 
 def kernel_source_hash():
-    """Hash of the sources the sweep kernels are compiled from (the kernels,
-    their device helpers and the device descriptor's header)."""
+    """Hash of the code the sweep kernels are compiled from (the kernels, their
+    device helpers and the device descriptor's header), comments and
+    whitespace removed, so that a comment edit keeps the counters valid."""
     h = hashlib.sha256()
     for name in ("mpopf_kernels.cu", "mpopf_device.cuh", "mpopf_internal.cuh"):
-        with open(os.path.join(ROOT, "paper_2405_14032_b300", "csrc", name), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2405_14032_b300", "csrc", name)) as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -10,7 +10,10 @@
 //                     values from S in a fixed order (no atomics);
 //   k_gen     (t, g): objective terms, gradient, objective W entry, ramp rows
 //                     and the pg/qg rows of M;
-//   k_fsum           : the objective's fixed-order tree reduction.
+//   k_fsum           : the objective's fixed-order tree reduction;
+//   k_batch          : all of the above for many instances, one persistent launch.
+// An evaluation runs k_branch and k_bus on the caller's stream and k_gen with
+// k_fsum on the handle's side stream (forked after k_branch, joined at the end).
 // Every value follows one fixed sequence of binary64 operations (explicit fma
 // where the definition has one; the build disables contraction), so results
 // are bitwise reproducible from run to run.
