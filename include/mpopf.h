@@ -330,7 +330,12 @@ int mpopf_kkt_solve(mpopf_handle *h, const double *rhs, double *dx, void *stream
  *   1..64), persistent CTAs per SM (0 = the occupancy maximum), periods per
  *   dependency chunk (0 = the whole horizon; with P > 0 the bus work of a chunk
  *   of P periods waits only for that chunk's branch work and overlaps the
- *   next chunk's); sched[4] = (order, tile, CTAs per SM, P).
+ *   next chunk's), and launches: 1 = one persistent launch (bus work waits
+ *   for its branch work), 2 = two persistent launches in the graph, the first
+ *   with every generator and branch tile, the second with every bus tile and
+ *   objective (no waits; the second runs at the bus work's own occupancy; P is
+ *   not used); sched[5] = (order, tile, CTAs per SM of the first launch, P,
+ *   launches).
  * mpopf_batch_tune: times candidate schedules (coordinate search; reps graph
  *   launches each, CUDA events on `stream`) and keeps the fastest; *best_ms its
  *   time per sweep.
@@ -347,12 +352,13 @@ int mpopf_batch_create(mpopf_handle *const *hs, int32_t k, mpopf_batch **out);
 int mpopf_batch_set_io(mpopf_batch *b, const mpopf_batch_io *io, void *stream);
 int mpopf_batch_sweep(mpopf_batch *b, void *stream);
 int mpopf_batch_set_schedule(mpopf_batch *b, int32_t order, int32_t tile_chunks, int32_t ctas_per_sm,
-                             int32_t chunk_periods);
-int mpopf_batch_get_schedule(const mpopf_batch *b, int32_t *sched /* [4] */, int32_t *grid, int32_t *n_items);
+                             int32_t chunk_periods, int32_t launches);
+int mpopf_batch_get_schedule(const mpopf_batch *b, int32_t *sched /* [5] */, int32_t *grid, int32_t *n_items);
 int mpopf_batch_tune(mpopf_batch *b, void *stream, int32_t reps, double *best_ms);
 int mpopf_batch_status(mpopf_batch *b);
-/* Failure-path test hook.  on != 0 raises the dependency target of the first
- * bus tile that waits, so that its wait can never be met: the next sweep waits
+/* Failure-path test hook (one-launch schedules; with two launches nothing
+ * waits and the hook returns MPOPF_ERR_ARG).  on != 0 raises the dependency
+ * target of the first bus tile that waits, so that its wait can never be met: the next sweep waits
  * out the bounded limit (about a second), sets the error flag, computes the
  * tile anyway and finishes; mpopf_batch_status then returns MPOPF_ERR_CUDA.
  * on == 0 restores the target (so do mpopf_batch_set_schedule and _tune).

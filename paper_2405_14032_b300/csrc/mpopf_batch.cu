@@ -9,8 +9,12 @@
 // sum) and come in the list one chunk behind them, so bus work overlaps branch
 // work.  The schedule decides the instance order (as given, or largest first),
 // the tile size (CTA-sized chunks per item), the persistent grid (CTAs per SM)
-// and P (0: the whole horizon).  Results do not depend on the schedule: each
-// value is computed by the same sequence of operations whichever CTA runs it.
+// and P (0: the whole horizon), and one launch or two: with two, the first
+// launch takes the generator and branch tiles and the second, the bus tiles and
+// the objective items, so the launch boundary replaces the dependency waits and
+// the bus work runs at its own occupancy.  Results do not depend on the
+// schedule: each value is computed by the same sequence of operations
+// whichever CTA runs it.
 #include <algorithm>
 #include <cstring>
 #include <numeric>
@@ -29,14 +33,20 @@ struct mpopf_batch {
   BatchIO *d_io = nullptr;
   BatchItem *d_items = nullptr;
   int32_t *d_need = nullptr;  // [n_counters]
-  int32_t *d_ctl = nullptr;   // [2 + n_counters]
-  int32_t n_items = 0, n_counters = 0, cap_counters = 0;
-  // order (0 given, 1 largest first), tile chunks, CTAs per SM (0 = max), periods per chunk (0 = all)
-  int32_t sched[4] = {0, 1, 0, 0};
+  int32_t *d_ctl = nullptr;   // [3 + n_counters]
+  int32_t n_items = 0, n_counters = 0, cap_ctl = 0;
+  // order (0 given, 1 largest first), tile chunks, CTAs per SM (0 = max),
+  // periods per chunk (0 = all), launches (1 or 2)
+  int32_t sched[5] = {0, 1, 0, 0, 1};
   int32_t grid = 0;
+  // two-launch schedule: items [0, n_items1) go to the first launch, the rest
+  // to the second (grid2 CTAs)
+  int32_t n_items1 = 0, n_items2 = 0, grid2 = 0;
+  BatchItem *d_items2 = nullptr;
+  int32_t *d_next2 = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  void *args[6];
+  void *args[7], *args2[7];
   bool io_set = false;
   std::vector<int32_t> need_host;  // dependency targets as built (the stall hook restores them)
   int32_t stall_counter = -1;      // counter whose target the stall hook raised, or -1
@@ -68,62 +78,90 @@ cudaError_t build_items(mpopf_batch *b) {
       if (signal >= 0) ++need[signal];
     }
   };
+  const bool two = b->sched[4] == 2;
   std::vector<int32_t> gen_counter(K, -1);
   for (int32_t k : order) {  // generator tiles first (no prerequisites)
     const Dev &d = b->hs[k]->d;
-    gen_counter[k] = (int32_t)need.size();
-    need.push_back(0);
-    add(ITEM_GEN, k, 0, (int64_t)d.T * d.G, -1, gen_counter[k]);
-  }
-  // Branch and bus tiles by period chunks, the bus tiles one chunk behind.
-  struct Chunk { int32_t k, t0, t1, counter; };
-  std::vector<std::vector<Chunk>> per(K);
-  int32_t rounds = 0;
-  for (int32_t k : order) {
-    const Dev &d = b->hs[k]->d;
-    const int32_t P = b->sched[3] > 0 ? b->sched[3] : d.T;
-    for (int32_t t0 = 0; t0 < d.T; t0 += P) {
-      per[k].push_back(Chunk{k, t0, std::min(d.T, t0 + P), (int32_t)need.size()});
+    if (!two) {
+      gen_counter[k] = (int32_t)need.size();
       need.push_back(0);
     }
-    rounds = std::max(rounds, (int32_t)per[k].size());
+    add(ITEM_GEN, k, 0, (int64_t)d.T * d.G, -1, gen_counter[k]);
   }
-  for (int32_t r = 0; r <= rounds; ++r)
+  int32_t n1 = 0;
+  if (two) {
+    // first launch: every branch tile; second: every bus tile, then the objectives
     for (int32_t k : order) {
       const Dev &d = b->hs[k]->d;
-      if (r < (int32_t)per[k].size()) {
-        const Chunk &c = per[k][r];
-        add(ITEM_BRANCH, k, (int64_t)c.t0 * d.L, (int64_t)c.t1 * d.L, -1, c.counter);
-      }
-      if (r >= 1 && r - 1 < (int32_t)per[k].size()) {
-        const Chunk &c = per[k][r - 1];
-        add(ITEM_BUS, k, (int64_t)c.t0 * d.N, (int64_t)c.t1 * d.N, d.L > 0 ? c.counter : -1, -1);
-      }
+      add(ITEM_BRANCH, k, 0, (int64_t)d.T * d.L, -1, -1);
     }
-  for (int32_t k : order) items.push_back(BatchItem{k, ITEM_FSUM, 0, 1, gen_counter[k], -1});
+    n1 = (int32_t)items.size();
+    for (int32_t k : order) {
+      const Dev &d = b->hs[k]->d;
+      add(ITEM_BUS, k, 0, (int64_t)d.T * d.N, -1, -1);
+    }
+    for (int32_t k : order) items.push_back(BatchItem{k, ITEM_FSUM, 0, 1, -1, -1});
+  } else {
+    // Branch and bus tiles by period chunks, the bus tiles one chunk behind.
+    struct Chunk { int32_t k, t0, t1, counter; };
+    std::vector<std::vector<Chunk>> per(K);
+    int32_t rounds = 0;
+    for (int32_t k : order) {
+      const Dev &d = b->hs[k]->d;
+      const int32_t P = b->sched[3] > 0 ? b->sched[3] : d.T;
+      for (int32_t t0 = 0; t0 < d.T; t0 += P) {
+        per[k].push_back(Chunk{k, t0, std::min(d.T, t0 + P), (int32_t)need.size()});
+        need.push_back(0);
+      }
+      rounds = std::max(rounds, (int32_t)per[k].size());
+    }
+    for (int32_t r = 0; r <= rounds; ++r)
+      for (int32_t k : order) {
+        const Dev &d = b->hs[k]->d;
+        if (r < (int32_t)per[k].size()) {
+          const Chunk &c = per[k][r];
+          add(ITEM_BRANCH, k, (int64_t)c.t0 * d.L, (int64_t)c.t1 * d.L, -1, c.counter);
+        }
+        if (r >= 1 && r - 1 < (int32_t)per[k].size()) {
+          const Chunk &c = per[k][r - 1];
+          add(ITEM_BUS, k, (int64_t)c.t0 * d.N, (int64_t)c.t1 * d.N, d.L > 0 ? c.counter : -1, -1);
+        }
+      }
+    for (int32_t k : order) items.push_back(BatchItem{k, ITEM_FSUM, 0, 1, gen_counter[k], -1});
+    n1 = (int32_t)items.size();
+  }
   cudaError_t e = cudaSuccess;
-  if ((int32_t)need.size() > b->cap_counters) {
+  const int32_t n_ctl = 3 + (int32_t)need.size();
+  if (n_ctl > b->cap_ctl) {
     cudaFree(b->d_need);
     cudaFree(b->d_ctl);
     b->d_need = nullptr;
     b->d_ctl = nullptr;
-    e = cudaMalloc(&b->d_need, need.size() * sizeof(int32_t));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_ctl, (2 + need.size()) * sizeof(int32_t));
-    b->cap_counters = (int32_t)need.size();
+    e = cudaMalloc(&b->d_need, std::max<size_t>(need.size(), 1) * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_ctl, n_ctl * sizeof(int32_t));
+    b->cap_ctl = n_ctl;
   }
   if (b->d_items) cudaFree(b->d_items);
   b->d_items = nullptr;
   if (e == cudaSuccess) e = cudaMalloc(&b->d_items, items.size() * sizeof(BatchItem));
   if (e == cudaSuccess) e = cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(b->d_need, need.data(), need.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !need.empty())
+    e = cudaMemcpy(b->d_need, need.data(), need.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
   b->n_items = (int32_t)items.size();
+  b->n_items1 = n1;
+  b->n_items2 = b->n_items - n1;
   b->n_counters = (int32_t)need.size();
+  b->d_items2 = b->d_items + n1;
+  b->d_next2 = b->d_ctl + 2 + b->n_counters;
   b->need_host = need;
   b->stall_counter = -1;
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
-  const int per_sm = b->sched[2] > 0 ? std::min(b->sched[2], batch_max_ctas_per_sm()) : batch_max_ctas_per_sm();
-  b->grid = std::max(1, std::min(sms * per_sm, b->n_items));
+  const int phase1 = two ? 1 : 0;
+  const int max1 = batch_max_ctas_per_sm(phase1);
+  const int per_sm = b->sched[2] > 0 ? std::min(b->sched[2], max1) : max1;
+  b->grid = std::max(1, std::min(sms * per_sm, std::max(1, b->n_items1)));
+  b->grid2 = two ? std::max(1, std::min(sms * batch_max_ctas_per_sm(2), std::max(1, b->n_items2))) : 0;
   return e;
 }
 
@@ -139,21 +177,35 @@ cudaError_t build_graph(mpopf_batch *b) {
   mp.dst = b->d_ctl;
   mp.value = 0;
   mp.elementSize = 4;
-  mp.width = (size_t)(2 + b->n_counters);
+  mp.width = (size_t)(3 + b->n_counters);
   mp.height = 1;
   mp.pitch = 0;
-  cudaGraphNode_t nmem = nullptr, nker = nullptr;
+  cudaGraphNode_t nmem = nullptr, nker = nullptr, nker2 = nullptr;
   e = cudaGraphAddMemsetNode(&nmem, b->graph, nullptr, 0, &mp);
   if (e != cudaSuccess) return e;
+  const bool two = b->sched[4] == 2;
   b->args[0] = &b->d_devs;
   b->args[1] = &b->d_io;
   b->args[2] = &b->d_items;
-  b->args[3] = &b->n_items;
+  b->args[3] = &b->n_items1;
   b->args[4] = &b->d_need;
   b->args[5] = &b->d_ctl;
+  b->args[6] = &b->d_ctl;  // the first launch counts items in ctl[0]
   cudaKernelNodeParams kp = {};
-  e = batch_kernel_node(&kp, b->args, b->grid);
+  e = batch_kernel_node(&kp, b->args, b->grid, two ? 1 : 0);
   if (e == cudaSuccess) e = cudaGraphAddKernelNode(&nker, b->graph, &nmem, 1, &kp);
+  if (e == cudaSuccess && two) {
+    b->args2[0] = &b->d_devs;
+    b->args2[1] = &b->d_io;
+    b->args2[2] = &b->d_items2;
+    b->args2[3] = &b->n_items2;
+    b->args2[4] = &b->d_need;
+    b->args2[5] = &b->d_ctl;
+    b->args2[6] = &b->d_next2;
+    cudaKernelNodeParams kp2 = {};
+    e = batch_kernel_node(&kp2, b->args2, b->grid2, 2);
+    if (e == cudaSuccess) e = cudaGraphAddKernelNode(&nker2, b->graph, &nker, 1, &kp2);
+  }
   if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
   return e;
 }
@@ -262,13 +314,15 @@ int mpopf_batch_test_stall(mpopf_batch *b, int32_t on) {
 }
 
 int mpopf_batch_set_schedule(mpopf_batch *b, int32_t order, int32_t tile_chunks, int32_t ctas_per_sm,
-                             int32_t chunk_periods) {
-  if (!b || order < 0 || order > 1 || tile_chunks < 1 || tile_chunks > 64 || ctas_per_sm < 0 || chunk_periods < 0)
+                             int32_t chunk_periods, int32_t launches) {
+  if (!b || order < 0 || order > 1 || tile_chunks < 1 || tile_chunks > 64 || ctas_per_sm < 0 || chunk_periods < 0 ||
+      launches < 1 || launches > 2)
     return fail(MPOPF_ERR_ARG, "mpopf_batch_set_schedule: bad argument");
   b->sched[0] = order;
   b->sched[1] = tile_chunks;
   b->sched[2] = ctas_per_sm;
   b->sched[3] = chunk_periods;
+  b->sched[4] = launches;
   cudaError_t e = cudaDeviceSynchronize();
   if (e == cudaSuccess) e = build_items(b);
   if (e == cudaSuccess) e = build_graph(b);
@@ -278,7 +332,7 @@ int mpopf_batch_set_schedule(mpopf_batch *b, int32_t order, int32_t tile_chunks,
 
 int mpopf_batch_get_schedule(const mpopf_batch *b, int32_t *sched, int32_t *grid, int32_t *n_items) {
   if (!b || !sched) return fail(MPOPF_ERR_ARG, "mpopf_batch_get_schedule: NULL argument");
-  std::memcpy(sched, b->sched, sizeof b->sched);  // [4]
+  std::memcpy(sched, b->sched, sizeof b->sched);  // [5]
   if (grid) *grid = b->grid;
   if (n_items) *n_items = b->n_items;
   return MPOPF_OK;
@@ -291,17 +345,17 @@ int mpopf_batch_tune(mpopf_batch *b, void *stream, int32_t reps, double *best_ms
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     return fail(MPOPF_ERR_CUDA, "mpopf_batch_tune: event creation failed");
-  const int maxc = batch_max_ctas_per_sm();
+  const int maxc = batch_max_ctas_per_sm(0);
   double best = 1e300;
-  int32_t best_s[4] = {b->sched[0], b->sched[1], b->sched[2], b->sched[3]};
+  int32_t best_s[5] = {b->sched[0], b->sched[1], b->sched[2], b->sched[3], b->sched[4]};
   int32_t maxT = 1;
   for (auto *h : b->hs) maxT = std::max(maxT, h->d.T);
   std::vector<int32_t> chunks = {0};
   for (int32_t P : {1, 2, 4, 8, 16}) if (P < maxT) chunks.push_back(P);
   int rc = MPOPF_OK;
-  auto trial = [&](int32_t order, int32_t tile, int32_t cps, int32_t P) {
+  auto trial = [&](int32_t order, int32_t tile, int32_t cps, int32_t P, int32_t launches) {
     if (rc != MPOPF_OK) return;
-    rc = mpopf_batch_set_schedule(b, order, tile, cps, P);
+    rc = mpopf_batch_set_schedule(b, order, tile, cps, P, launches);
     if (rc != MPOPF_OK) return;
     for (int w = 0; w < 2; ++w) cudaGraphLaunch(b->exec, st);
     cudaEventRecord(e0, st);
@@ -315,20 +369,22 @@ int mpopf_batch_tune(mpopf_batch *b, void *stream, int32_t reps, double *best_ms
     cudaEventElapsedTime(&ms, e0, e1);
     if (ms / reps < best) {
       best = ms / reps;
-      best_s[0] = order; best_s[1] = tile; best_s[2] = cps; best_s[3] = P;
+      best_s[0] = order; best_s[1] = tile; best_s[2] = cps; best_s[3] = P; best_s[4] = launches;
     }
   };
-  // coordinate search: grid and tile with whole-horizon chunks, then the chunk
-  // length, then the instance order
-  for (int32_t cps = 1; cps <= maxc; ++cps)
-    for (int32_t tile : {1, 2, 4}) trial(0, tile, cps, 0);
-  for (int32_t P : chunks) trial(0, best_s[1], best_s[2], P);
-  trial(1, best_s[1], best_s[2], best_s[3]);
+  // coordinate search: launches, grid and tile with whole-horizon chunks, then
+  // the chunk length (one launch), then the instance order
+  for (int32_t launches : {1, 2})
+    for (int32_t cps = 1; cps <= maxc; ++cps)
+      for (int32_t tile : {1, 2, 4}) trial(0, tile, cps, 0, launches);
+  if (best_s[4] == 1)
+    for (int32_t P : chunks) trial(0, best_s[1], best_s[2], P, 1);
+  trial(1, best_s[1], best_s[2], best_s[3], best_s[4]);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc != MPOPF_OK) return rc;
   if (best_ms) *best_ms = best;
-  return mpopf_batch_set_schedule(b, best_s[0], best_s[1], best_s[2], best_s[3]);
+  return mpopf_batch_set_schedule(b, best_s[0], best_s[1], best_s[2], best_s[3], best_s[4]);
 }
 
 void mpopf_batch_destroy(mpopf_batch *b) {

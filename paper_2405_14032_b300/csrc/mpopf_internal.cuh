@@ -131,10 +131,12 @@ struct BatchItem {
   int32_t inst, kind, first, count;  // units [first, first + count) of that kind of that instance
   int32_t wait, signal;              // dependency counter waited on / incremented when done (-1: none)
 };
-// ctl layout: [0] next item, [1] wait-limit flag, [2 + c] dependency counter c;
-// need[c] = number of items that signal counter c.
-cudaError_t batch_kernel_node(cudaKernelNodeParams *p, void **args, int32_t grid);
-int batch_max_ctas_per_sm();
+// ctl layout: [0] next item of the (first) launch, [1] wait-limit flag,
+// [2 + c] dependency counter c, [2 + n_counters] next item of the second
+// launch of a two-launch schedule; need[c] = number of items that signal
+// counter c.  phase: 0 one launch with every item, 1 / 2 the two launches.
+cudaError_t batch_kernel_node(cudaKernelNodeParams *p, void **args, int32_t grid, int phase);
+int batch_max_ctas_per_sm(int phase);
 
 }  // namespace mpopf
 

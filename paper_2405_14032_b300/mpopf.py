@@ -106,7 +106,7 @@ def lib():
             "mpopf_batch_create": (ctypes.c_int, [_P, _I32, ctypes.POINTER(_P)]),
             "mpopf_batch_set_io": (ctypes.c_int, [_P, _P, _P]),
             "mpopf_batch_sweep": (ctypes.c_int, [_P, _P]),
-            "mpopf_batch_set_schedule": (ctypes.c_int, [_P, _I32, _I32, _I32, _I32]),
+            "mpopf_batch_set_schedule": (ctypes.c_int, [_P, _I32, _I32, _I32, _I32, _I32]),
             "mpopf_batch_get_schedule": (ctypes.c_int, [_P, _P, _P, _P]),
             "mpopf_batch_tune": (ctypes.c_int, [_P, _P, _I32, _P]),
             "mpopf_batch_status": (ctypes.c_int, [_P]),
@@ -425,18 +425,18 @@ class Batch:
     def sweep(self, stream=None):
         _check(lib().mpopf_batch_sweep(self.b, _stream_ptr(stream)), "mpopf_batch_sweep")
 
-    def set_schedule(self, order, tile_chunks, ctas_per_sm, chunk_periods=0):
-        _check(lib().mpopf_batch_set_schedule(self.b, order, tile_chunks, ctas_per_sm, chunk_periods),
+    def set_schedule(self, order, tile_chunks, ctas_per_sm, chunk_periods=0, launches=1):
+        _check(lib().mpopf_batch_set_schedule(self.b, order, tile_chunks, ctas_per_sm, chunk_periods, launches),
                "mpopf_batch_set_schedule")
 
     def schedule(self):
-        s = np.zeros(4, np.int32)
+        s = np.zeros(5, np.int32)
         g = np.zeros(1, np.int32)
         k = np.zeros(1, np.int32)
         _check(lib().mpopf_batch_get_schedule(self.b, s.ctypes.data, g.ctypes.data, k.ctypes.data),
                "mpopf_batch_get_schedule")
         return dict(order=int(s[0]), tile_chunks=int(s[1]), ctas_per_sm=int(s[2]), chunk_periods=int(s[3]),
-                    grid=int(g[0]), items=int(k[0]))
+                    launches=int(s[4]), grid=int(g[0]), items=int(k[0]))
 
     def tune(self, reps=5, stream=None):
         best = np.zeros(1)

@@ -27,6 +27,8 @@ def main(argv=None) -> int:
     ap.add_argument("--buses", type=int, default=10000)
     ap.add_argument("--periods", type=int, default=24)
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--launches", type=int, default=1, choices=[1, 2],
+                    help="batch: one persistent launch or two (generator/branch, then bus/objective)")
     a = ap.parse_args(argv)
     dev = lambda v: torch.as_tensor(v, dtype=torch.float64, device="cuda")
 
@@ -44,6 +46,8 @@ def main(argv=None) -> int:
             ios.append(io)
         b = mpopf.Batch(hs)
         b.set_io(ios)
+        if a.launches == 2:
+            b.set_schedule(0, 1, 3, 0, 2)
         for _ in range(a.reps):
             b.sweep()
         b.status()

@@ -68,7 +68,8 @@ def test_batch_equals_individual_sweeps_every_schedule():
     b = mpopf.Batch(hs)
     b.set_io(ios)
     _check_all(b, ios, refs)
-    for sched in [(0, 1, 0, 0), (1, 1, 1, 1), (0, 2, 2, 2), (1, 4, 0, 3), (0, 4, 1, 0), (1, 2, 3, 1), (0, 1, 0, 2)]:
+    for sched in [(0, 1, 0, 0), (1, 1, 1, 1), (0, 2, 2, 2), (1, 4, 0, 3), (0, 4, 1, 0), (1, 2, 3, 1), (0, 1, 0, 2),
+                  (0, 1, 0, 0, 2), (1, 2, 1, 0, 2), (0, 4, 3, 0, 2)]:
         b.set_schedule(*sched)
         _check_all(b, ios, refs)
         _check_all(b, ios, refs)  # replay of the same graph
