@@ -314,7 +314,7 @@ int mpopf_kkt_factor(mpopf_handle *h, const double *kv, int64_t *zero_pivot, voi
 int mpopf_kkt_solve(mpopf_handle *h, const double *rhs, double *dx, void *stream);
 
 /* Batched full sweeps of many independent instances (uneven sizes and
- * horizons) in ONE persistent kernel launch, replayed as a CUDA graph.  The
+ * horizons) in one CUDA graph of one or two persistent kernel launches.  The
  * paper evaluates one model per solver; this runs many, e.g. scenario or
  * rolling-horizon instances, with the same values as mpopf_sweep on each.
  *
