@@ -120,4 +120,10 @@ def test_dependency_wait_timeout_is_reported_not_hung():
             assert torch.equal(io[k], ref[k]), k
     b.test_stall(False)
     _check_all(b, ios, refs)
+    # with two launches nothing waits: the hook has no wait to hold back
+    b.set_schedule(0, 1, 0, 0, 2)
+    assert b.schedule()["launches"] == 2
+    with pytest.raises(mpopf.MpopfError, match="no bus tile waits"):
+        b.test_stall(True)
+    _check_all(b, ios, refs)
     b.close()
