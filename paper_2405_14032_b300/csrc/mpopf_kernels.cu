@@ -29,12 +29,21 @@ template <unsigned MASK>
 __device__ __forceinline__ unsigned eff(unsigned rt) { return MASK ? MASK : rt; }
 
 // Branch kernel launch shape: threads per CTA and resident CTAs per SM (the
-// register cap follows from them); measured choice below.
+// register cap, 80, follows from them).  At that cap, 64-thread CTAs (12 per
+// SM) measured 0.830 ms at 10k buses x 168 against 0.833 ms for 128 x 6,
+// 0.839 ms for 192 x 4, 0.857 ms for 256 x 3 and 1.051 ms for 384 x 2; small
+// instances gain most (10k buses x 1: 33.5 -> 27.3 us per sweep).
 #ifndef MPOPF_BRANCH_MINB
-#define MPOPF_BRANCH_MINB 3
+#define MPOPF_BRANCH_MINB 12
 #endif
 #ifndef MPOPF_BRANCH_BLOCK
-#define MPOPF_BRANCH_BLOCK kBlock
+#define MPOPF_BRANCH_BLOCK 64
+#endif
+// Bus kernel CTA size (48 registers, so 1280 resident threads per SM whatever
+// the size): 128 measured 0.258 ms against 0.261 ms for 256 at 10k buses x 168,
+// and 26.3 against 27.3 us per sweep at 10k buses x 1.
+#ifndef MPOPF_BUS_BLOCK
+#define MPOPF_BUS_BLOCK 128
 #endif
 // Loads of values another CTA wrote in the same launch go through L2 (the
 // persistent batch kernel); separate launches may use the read-only path.
@@ -455,11 +464,9 @@ __device__ __forceinline__ void bus_body(const Dev &d, int32_t idx, unsigned rt,
   vm_row[(nd > 0 ? nd + 1 : 0) + ndlt] = Dvv;
 }
 
-// ---------------------------------------------------------------------------
-// Generator x period.
-// ---------------------------------------------------------------------------
+// Elements [first, end) of the bus x period range (t N + position).
 template <unsigned MASK>
-__global__ void __launch_bounds__(kBlock) k_bus(Dev d, unsigned rt, const double *__restrict__ x,
+__global__ void __launch_bounds__(MPOPF_BUS_BLOCK) k_bus(Dev d, unsigned rt, const double *__restrict__ x,
                                                 const double *__restrict__ lam, const double *__restrict__ sx,
                                                 const double *__restrict__ dv, double dw, double *__restrict__ grad,
                                                 double *__restrict__ c, double *__restrict__ jv,
@@ -649,7 +656,7 @@ cudaError_t launch_all(const Dev &d, unsigned rt, const double *x, const double 
   }
   if (mk & rest) {
     Timed tm(prof, s, KIND_BUS);
-    k_bus<MASK><<<grid_for((int64_t)d.T * d.N), kBlock, 0, s>>>(d, rt, x, lam, sx, dv, dw, grad, c, jv, hv, kv, 0,
+    k_bus<MASK><<<(unsigned)(((int64_t)d.T * d.N + MPOPF_BUS_BLOCK - 1) / MPOPF_BUS_BLOCK), MPOPF_BUS_BLOCK, 0, s>>>(d, rt, x, lam, sx, dv, dw, grad, c, jv, hv, kv, 0,
                                                              d.T * d.N);
   }
   if (side) {
@@ -697,9 +704,10 @@ __device__ __forceinline__ void batch_branch_item(const Dev &d, const BatchIO &b
 // boundary orders them, so nothing waits), at the bus work's own occupancy
 // (5 CTAs per SM instead of 3; the bus kernel alone runs 49% slower at 3).
 // `next` is the launch's work-item counter.
-constexpr int kBatchBusMinBlocks = 5;
+constexpr int kBatchMinBlocks = 3;     // 256-thread CTAs with branch work: 80 registers
+constexpr int kBatchBusMinBlocks = 5;  // bus and objective work only: 48 registers
 template <int PHASE>
-__global__ void __launch_bounds__(kBlock, PHASE == 2 ? kBatchBusMinBlocks : MPOPF_BRANCH_MINB)
+__global__ void __launch_bounds__(kBlock, PHASE == 2 ? kBatchBusMinBlocks : kBatchMinBlocks)
     k_batch(const Dev *__restrict__ devs, const BatchIO *__restrict__ io, const BatchItem *__restrict__ items,
             int32_t n_items, const int32_t *__restrict__ need, int32_t *__restrict__ ctl, int32_t *__restrict__ next) {
   __shared__ int32_t s_item;
@@ -793,7 +801,7 @@ void launch_window(const Dev &d, int32_t t0, int32_t t1, const double *x, const 
                   s>>>(d, A, x, lam, sx, dv, dw, grad, c, jv, hv, kv, first, end);
   }
   const int32_t first = t0 * d.N, end = t1 * d.N;
-  k_bus<A><<<grid_for((int64_t)end - first), kBlock, 0, s>>>(d, A, x, lam, sx, dv, dw, grad, c, jv, hv, kv, first,
+  k_bus<A><<<(unsigned)(((int64_t)end - first + MPOPF_BUS_BLOCK - 1) / MPOPF_BUS_BLOCK), MPOPF_BUS_BLOCK, 0, s>>>(d, A, x, lam, sx, dv, dw, grad, c, jv, hv, kv, first,
                                                              end);
 }
 
