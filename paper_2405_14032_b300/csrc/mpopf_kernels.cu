@@ -30,9 +30,10 @@ __device__ __forceinline__ unsigned eff(unsigned rt) { return MASK ? MASK : rt; 
 
 // Branch kernel launch shape: threads per CTA and resident CTAs per SM (the
 // register cap, 80, follows from them).  At that cap, 64-thread CTAs (12 per
-// SM) measured 0.830 ms at 10k buses x 168 against 0.833 ms for 128 x 6,
-// 0.839 ms for 192 x 4, 0.857 ms for 256 x 3 and 1.051 ms for 384 x 2; small
-// instances gain most (10k buses x 1: 33.5 -> 27.3 us per sweep).
+// SM) measured 0.830 ms at 10k buses x 168 against 0.831 ms for 96 x 8,
+// 0.833 ms for 128 x 6, 0.839 ms for 192 x 4, 0.857 ms for 256 x 3, 1.051 ms
+// for 384 x 2 and 0.863 ms for 32 x 24; small instances gain most (10k buses
+// x 1: 33.5 -> 27.3 us per sweep).
 #ifndef MPOPF_BRANCH_MINB
 #define MPOPF_BRANCH_MINB 12
 #endif
