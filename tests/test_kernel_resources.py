@@ -1,6 +1,6 @@
 """Register and spill budget of the dominant sweep kernel, from the compiler's
-resource report (no GPU needed).  The branch kernel is FP64-bound at three
-256-thread CTAs per SM (80 registers); its spills are sensitive to unrelated
+resource report (no GPU needed).  The branch kernel is FP64-bound at twelve
+64-thread CTAs per SM (80 registers); its spills are sensitive to unrelated
 changes (a field inserted in the middle of the device descriptor once raised
 them from 32 to 72 bytes and the kernel time by 4%), so the budget is pinned.
 The warp-staged stores of its J and W rows (shared memory, then coalesced
