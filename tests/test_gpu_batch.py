@@ -76,6 +76,10 @@ def test_batch_equals_individual_sweeps_every_schedule():
     best = b.tune(reps=2)
     assert best > 0
     _check_all(b, ios, refs)
+    for bad in [(0, 1, 0, 0, 0), (0, 1, 0, 0, 3), (2, 1, 0, 0, 1), (0, 0, 0, 0, 1), (0, 1, -1, 0, 1)]:
+        with pytest.raises(mpopf.MpopfError, match="bad argument"):
+            b.set_schedule(*bad)
+    _check_all(b, ios, refs)
     b.close()
 
 

@@ -63,3 +63,27 @@ def test_graph_replay_equals_plain(shape):
         assert torch.equal(single[k], refs[0][k]), (shape, k)
     del g, g2
     h.close()
+
+
+def test_profiling_times_the_callers_stream_kernels():
+    """Per-kernel profiling with the generator work on the side stream: the
+    branch and bus launches are timed, the side-stream launches are not, and
+    the outputs are those of an unprofiled sweep."""
+    from paper_2405_14032_b300 import mpopf
+    inst = synth.make_instance(72, 200, 320, 40, 120, 4)
+    pt = synth.make_point(72, inst)
+    h = mpopf.Handle(inst)
+    x, lam, sx, dv = _dev(pt.x), _dev(pt.lam), _dev(pt.sigma_x), _dev(pt.dvec)
+    ref = h.sweep(x, lam, pt.sigma, sx, dv, pt.delta_w)
+    out = h.new_outputs()
+    h.profile_start(4 * 3)
+    for _ in range(3):
+        h.sweep(x, lam, pt.sigma, sx, dv, pt.delta_w, out=out)
+    prof = h.profile_stop()
+    assert prof["branch"][1] == 3 and prof["bus"][1] == 3
+    assert prof["gen"][1] == 0 and prof["fsum"][1] == 0
+    assert prof["branch"][0] > 0 and prof["bus"][0] > 0
+    torch.cuda.synchronize()
+    for k in ref:
+        assert torch.equal(out[k], ref[k]), k
+    h.close()
