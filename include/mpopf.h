@@ -332,9 +332,10 @@ int mpopf_kkt_solve(mpopf_handle *h, const double *rhs, double *dx, void *stream
  *   of P periods waits only for that chunk's branch work and overlaps the
  *   next chunk's), and launches: 1 = one persistent launch (bus work waits
  *   for its branch work), 2 = two persistent launches in the graph, the first
- *   with every generator and branch tile, the second with every bus tile and
- *   objective (no waits; the second runs at the bus work's own occupancy; P is
- *   not used); sched[5] = (order, tile, CTAs per SM of the first launch, P,
+ *   with every branch tile (the sweep's 64-thread CTAs), the second with every
+ *   generator tile, bus tile and objective (bus tiles do not wait; objectives
+ *   wait for their generator tiles; run at the bus work's own occupancy; CTAs
+ *   per SM and P are not used); sched[5] = (order, tile, CTAs per SM, P,
  *   launches).
  * mpopf_batch_tune: times candidate schedules (coordinate search; reps graph
  *   launches each, CUDA events on `stream`) and keeps the fastest; *best_ms its

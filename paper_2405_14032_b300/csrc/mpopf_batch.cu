@@ -10,9 +10,10 @@
 // work.  The schedule decides the instance order (as given, or largest first),
 // the tile size (CTA-sized chunks per item), the persistent grid (CTAs per SM)
 // and P (0: the whole horizon), and one launch or two: with two, the first
-// launch takes the generator and branch tiles and the second, the bus tiles and
-// the objective items, so the launch boundary replaces the dependency waits and
-// the bus work runs at its own occupancy.  Results do not depend on the
+// launch takes the branch tiles (in the sweep kernel's 64-thread CTAs) and the
+// second the generator tiles, the bus tiles and the objective items, so the
+// launch boundary replaces the bus tiles' waits and the bus work runs at its
+// own occupancy.  Results do not depend on the
 // schedule: each value is computed by the same sequence of operations
 // whichever CTA runs it.
 #include <algorithm>
@@ -69,28 +70,24 @@ cudaError_t build_items(mpopf_batch *b) {
   if (b->sched[0] == 1)
     std::stable_sort(order.begin(), order.end(),
                      [&](int32_t a, int32_t c) { return work_of(b->hs[a]->d) > work_of(b->hs[c]->d); });
-  const int32_t tile = kBlock * std::max(1, b->sched[1]);
+  const bool two = b->sched[4] == 2;
+  // tiles are whole CTAs of the launch that runs them
+  const int32_t chunks = std::max(1, b->sched[1]);
+  const int32_t tile = kBlock * chunks, tile_branch = (two ? batch_block_threads(1) : kBlock) * chunks;
   std::vector<BatchItem> items;
   std::vector<int32_t> need;
   auto add = [&](int32_t kind, int32_t k, int64_t u0, int64_t u1, int32_t wait, int32_t signal) {
-    for (int64_t f = u0; f < u1; f += tile) {
-      items.push_back(BatchItem{k, kind, (int32_t)f, (int32_t)std::min<int64_t>(tile, u1 - f), wait, signal});
+    const int32_t t = kind == ITEM_BRANCH ? tile_branch : tile;
+    for (int64_t f = u0; f < u1; f += t) {
+      items.push_back(BatchItem{k, kind, (int32_t)f, (int32_t)std::min<int64_t>(t, u1 - f), wait, signal});
       if (signal >= 0) ++need[signal];
     }
   };
-  const bool two = b->sched[4] == 2;
   std::vector<int32_t> gen_counter(K, -1);
-  for (int32_t k : order) {  // generator tiles first (no prerequisites)
-    const Dev &d = b->hs[k]->d;
-    if (!two) {
-      gen_counter[k] = (int32_t)need.size();
-      need.push_back(0);
-    }
-    add(ITEM_GEN, k, 0, (int64_t)d.T * d.G, -1, gen_counter[k]);
-  }
   int32_t n1 = 0;
   if (two) {
-    // first launch: every branch tile; second: every bus tile, then the objectives
+    // first launch: every branch tile; second: the generator tiles, the bus
+    // tiles, then the objectives (each waits for its generator tiles)
     for (int32_t k : order) {
       const Dev &d = b->hs[k]->d;
       add(ITEM_BRANCH, k, 0, (int64_t)d.T * d.L, -1, -1);
@@ -98,10 +95,22 @@ cudaError_t build_items(mpopf_batch *b) {
     n1 = (int32_t)items.size();
     for (int32_t k : order) {
       const Dev &d = b->hs[k]->d;
+      gen_counter[k] = (int32_t)need.size();
+      need.push_back(0);
+      add(ITEM_GEN, k, 0, (int64_t)d.T * d.G, -1, gen_counter[k]);
+    }
+    for (int32_t k : order) {
+      const Dev &d = b->hs[k]->d;
       add(ITEM_BUS, k, 0, (int64_t)d.T * d.N, -1, -1);
     }
-    for (int32_t k : order) items.push_back(BatchItem{k, ITEM_FSUM, 0, 1, -1, -1});
+    for (int32_t k : order) items.push_back(BatchItem{k, ITEM_FSUM, 0, 1, gen_counter[k], -1});
   } else {
+    for (int32_t k : order) {  // generator tiles first (no prerequisites)
+      const Dev &d = b->hs[k]->d;
+      gen_counter[k] = (int32_t)need.size();
+      need.push_back(0);
+      add(ITEM_GEN, k, 0, (int64_t)d.T * d.G, -1, gen_counter[k]);
+    }
     // Branch and bus tiles by period chunks, the bus tiles one chunk behind.
     struct Chunk { int32_t k, t0, t1, counter; };
     std::vector<std::vector<Chunk>> per(K);
@@ -159,7 +168,9 @@ cudaError_t build_items(mpopf_batch *b) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
   const int phase1 = two ? 1 : 0;
   const int max1 = batch_max_ctas_per_sm(phase1);
-  const int per_sm = b->sched[2] > 0 ? std::min(b->sched[2], max1) : max1;
+  // CTAs per SM apply to the one-launch form; the two launches run at their
+  // occupancy maximum
+  const int per_sm = (!two && b->sched[2] > 0) ? std::min(b->sched[2], max1) : max1;
   b->grid = std::max(1, std::min(sms * per_sm, std::max(1, b->n_items1)));
   b->grid2 = two ? std::max(1, std::min(sms * batch_max_ctas_per_sm(2), std::max(1, b->n_items2))) : 0;
   return e;
@@ -372,11 +383,12 @@ int mpopf_batch_tune(mpopf_batch *b, void *stream, int32_t reps, double *best_ms
       best_s[0] = order; best_s[1] = tile; best_s[2] = cps; best_s[3] = P; best_s[4] = launches;
     }
   };
-  // coordinate search: launches, grid and tile with whole-horizon chunks, then
-  // the chunk length (one launch), then the instance order
-  for (int32_t launches : {1, 2})
-    for (int32_t cps = 1; cps <= maxc; ++cps)
-      for (int32_t tile : {1, 2, 4}) trial(0, tile, cps, 0, launches);
+  // coordinate search: grid and tile with whole-horizon chunks (one launch),
+  // tile (two launches), then the chunk length (one launch), then the instance
+  // order
+  for (int32_t cps = 1; cps <= maxc; ++cps)
+    for (int32_t tile : {1, 2, 4}) trial(0, tile, cps, 0, 1);
+  for (int32_t tile : {1, 2, 4, 8}) trial(0, tile, 0, 0, 2);
   if (best_s[4] == 1)
     for (int32_t P : chunks) trial(0, best_s[1], best_s[2], P, 1);
   trial(1, best_s[1], best_s[2], best_s[3], best_s[4]);

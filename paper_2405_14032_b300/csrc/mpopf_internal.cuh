@@ -137,6 +137,7 @@ struct BatchItem {
 // counter c.  phase: 0 one launch with every item, 1 / 2 the two launches.
 cudaError_t batch_kernel_node(cudaKernelNodeParams *p, void **args, int32_t grid, int phase);
 int batch_max_ctas_per_sm(int phase);
+int batch_block_threads(int phase);  // CTA size of each launch form
 
 }  // namespace mpopf
 

@@ -687,11 +687,13 @@ __device__ __forceinline__ int32_t ld_acquire(const int32_t *p) {
   return v;
 }
 
-// The branch items of the batch kernel (phases 0 and 1): warps whose 32
-// elements all lie in the item stage their J and W rows in shared memory.
+// The branch items of the batch kernel (phases 0 and 1, CTAs of B threads):
+// warps whose 32 elements all lie in the item stage their J and W rows in
+// shared memory.
+template <int B>
 __device__ __forceinline__ void batch_branch_item(const Dev &d, const BatchIO &b, int32_t first, int32_t end) {
-  __shared__ __align__(16) double s_stage[kBlock / 32][kStageCap];
-  for (int32_t c0 = first; c0 < end; c0 += kBlock) {
+  __shared__ __align__(16) double s_stage[B / 32][kStageCap];
+  for (int32_t c0 = first; c0 < end; c0 += B) {
     const bool full = c0 + (int32_t)(threadIdx.x & ~31u) + 31 < end;
     if (c0 + (int32_t)threadIdx.x < end)
       branch_body<MPOPF_OUT_ALL, true>(d, c0 + threadIdx.x, MPOPF_OUT_ALL, b.x, b.lam, b.sx, b.dv, b.dw, b.grad,
@@ -700,17 +702,24 @@ __device__ __forceinline__ void batch_branch_item(const Dev &d, const BatchIO &b
 }
 
 // PHASE 0: every kind of item in one persistent launch (bus and objective
-// items wait for their prerequisites); PHASE 1: generator and branch items;
-// PHASE 2: bus and objective items, launched after phase 1 (the launch
-// boundary orders them, so nothing waits), at the bus work's own occupancy
-// (5 CTAs per SM instead of 3; the bus kernel alone runs 49% slower at 3).
-// `next` is the launch's work-item counter.
-constexpr int kBatchMinBlocks = 3;     // 256-thread CTAs with branch work: 80 registers
-constexpr int kBatchBusMinBlocks = 5;  // bus and objective work only: 48 registers
+// items wait for their prerequisites), 256-thread CTAs, 3 per SM.
+// PHASE 1: the branch items, in the sweep kernel's shape (64-thread CTAs, 12
+// per SM).  PHASE 2, launched after phase 1 (the launch boundary orders the
+// bus items after the branch items, so they do not wait): the generator
+// items, the bus items and then the objective items, which wait for their
+// instance's generator items; 256-thread CTAs (the objective's tile tree),
+// 5 per SM at the bus work's 48 registers (the bus kernel alone is 49% slower
+// at 3 per SM).  `next` is the launch's work-item counter.
+__host__ __device__ constexpr int batch_block(int phase) { return phase == 1 ? MPOPF_BRANCH_BLOCK : kBlock; }
+__host__ __device__ constexpr int batch_minb(int phase) {
+  return phase == 1 ? MPOPF_BRANCH_MINB : phase == 2 ? 5 : 3;
+}
 template <int PHASE>
-__global__ void __launch_bounds__(kBlock, PHASE == 2 ? kBatchBusMinBlocks : kBatchMinBlocks)
+__global__ void __launch_bounds__(batch_block(PHASE), batch_minb(PHASE))
     k_batch(const Dev *__restrict__ devs, const BatchIO *__restrict__ io, const BatchItem *__restrict__ items,
             int32_t n_items, const int32_t *__restrict__ need, int32_t *__restrict__ ctl, int32_t *__restrict__ next) {
+  constexpr int B = batch_block(PHASE);
+  constexpr bool WAITS = PHASE != 1;  // phases whose items may wait or signal
   __shared__ int32_t s_item;
   __shared__ int32_t s_inst;
   // The instance's descriptors, copied to shared memory when the instance
@@ -732,16 +741,16 @@ __global__ void __launch_bounds__(kBlock, PHASE == 2 ? kBatchBusMinBlocks : kBat
     const BatchItem I = items[it];
     if (I.inst != s_inst) {
       const uint32_t *src = reinterpret_cast<const uint32_t *>(devs + I.inst);
-      for (int w = threadIdx.x; w < (int)(sizeof(Dev) / 4); w += kBlock)
+      for (int w = threadIdx.x; w < (int)(sizeof(Dev) / 4); w += B)
         reinterpret_cast<uint32_t *>(s_dev)[w] = src[w];
       const uint32_t *srci = reinterpret_cast<const uint32_t *>(io + I.inst);
-      for (int w = threadIdx.x; w < (int)(sizeof(BatchIO) / 4); w += kBlock)
+      for (int w = threadIdx.x; w < (int)(sizeof(BatchIO) / 4); w += B)
         reinterpret_cast<uint32_t *>(s_io)[w] = srci[w];
       __syncthreads();
       if (threadIdx.x == 0) s_inst = I.inst;
       // s_inst is read again only after the barrier at the top of the loop
     }
-    if (PHASE == 0 && I.wait >= 0) {
+    if (WAITS && I.wait >= 0) {
       if (threadIdx.x == 0) {
         const int32_t *cnt = ctl + 2 + I.wait;
         const int32_t target = need[I.wait];
@@ -758,27 +767,26 @@ __global__ void __launch_bounds__(kBlock, PHASE == 2 ? kBatchBusMinBlocks : kBat
     }
     const int32_t end = I.first + I.count;
     if constexpr (PHASE != 2) {
-      if (I.kind == ITEM_BRANCH) {
-        batch_branch_item(d, b, I.first, end);
-      } else if (I.kind == ITEM_GEN) {
+      if (I.kind == ITEM_BRANCH) batch_branch_item<B>(d, b, I.first, end);
+    }
+    if constexpr (PHASE != 1) {
+      static_assert(B == kBlock, "the generator and objective trees need kBlock-thread CTAs");
+      if (I.kind == ITEM_GEN) {
         for (int32_t c0 = I.first; c0 < end; c0 += kBlock)  // whole CTA: the objective tile tree
           gen_body<MPOPF_OUT_ALL>(d, c0 + threadIdx.x < end ? c0 + threadIdx.x : d.T * d.G, c0 / kBlock,
                                   MPOPF_OUT_ALL, b.x, b.sigma, b.sx, b.dv, b.dw, b.grad, b.c, b.jv, b.hv, b.kv);
-      }
-    }
-    if constexpr (PHASE != 1) {
-      // records and tile partials from the same launch (phase 0) are read
-      // through L2; from an earlier launch (phase 2), through the read-only path
-      if (I.kind == ITEM_BUS) {
+      } else if (I.kind == ITEM_BUS) {
+        // records from the same launch (phase 0) are read through L2; from
+        // the earlier launch (phase 2), through the read-only path
         for (int32_t c0 = I.first; c0 < end; c0 += kBlock)
           if (c0 + (int32_t)threadIdx.x < end)
             bus_body<MPOPF_OUT_ALL, PHASE == 0>(d, c0 + threadIdx.x, MPOPF_OUT_ALL, b.x, b.lam, b.sx, b.dv, b.dw,
                                                 b.grad, b.c, b.jv, b.hv, b.kv);
       } else if (I.kind == ITEM_FSUM) {
-        fsum_body<PHASE == 0>(d.fpart, d.G > 0 ? d.fpart_n : 0, b.f);
+        fsum_body<true>(d.fpart, d.G > 0 ? d.fpart_n : 0, b.f);  // partials of the same launch: through L2
       }
     }
-    if (PHASE == 0 && I.signal >= 0) {  // publish this item's writes, then count it done
+    if (WAITS && I.signal >= 0) {  // publish this item's writes, then count it done
       __threadfence();
       __syncthreads();
       if (threadIdx.x == 0) atomicAdd(ctl + 2 + I.signal, 1);
@@ -821,16 +829,19 @@ const void *batch_kernel(int phase) {
 }
 }  // namespace
 
+int batch_block_threads(int phase) { return batch_block(phase); }
+
 int batch_max_ctas_per_sm(int phase) {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel(phase), kBlock, 0) != cudaSuccess) return 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel(phase), batch_block(phase), 0) != cudaSuccess)
+    return 1;
   return n > 0 ? n : 1;
 }
 
 cudaError_t batch_kernel_node(cudaKernelNodeParams *p, void **args, int32_t grid, int phase) {
   p->func = const_cast<void *>(batch_kernel(phase));
   p->gridDim = dim3((unsigned)grid);
-  p->blockDim = dim3(kBlock);
+  p->blockDim = dim3(batch_block(phase));
   p->sharedMemBytes = 0;
   p->kernelParams = args;
   p->extra = nullptr;
