@@ -277,7 +277,8 @@ int mpopf_ipm_recover(mpopf_handle *h, const double *x, const double *jv, const 
  * first.  J has no duplicates, so its CSC values are a permutation.
  * mpopf_csc_pattern: fills *out with device pointers owned by the handle
  *   (valid until mpopf_destroy): colptr [n + 1] (int64), rowidx [nnz] (int32).
- *   The first call for a matrix builds the pattern (host counting sorts,
+ *   The first call for a matrix builds the pattern (on the device: column
+ *   counts, a scan, a scatter and a sort of each column by row and COO entry;
  *   device allocation, synchronous); later calls return it.
  * mpopf_coo_to_csc: csc_vals [nnz] from coo_vals [nnz_jac or nnz_hess] (the
  *   values mpopf_eval_jac / mpopf_eval_hess write), device arrays, asynchronous
