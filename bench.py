@@ -34,10 +34,10 @@ METRIC = "full derivative sweeps/s + HBM GB/s (10k-bus T=168); batched & adjoint
 UNIT = "sweeps/s"
 WORKLOAD = dict(n_bus=10000, n_branch=16000, n_gen=2000, n_load=6000, seed=3)
 # FP64 operations of one branch x period instance of the full sweep (k_branch,
-# ALL outputs): angle difference 1, sin/cos 19, flow terms 14, constraint values
+# ALL outputs): angle difference 1, sin/cos 15, flow terms 14, constraint values
 # 14, Jacobian 8, W block 16, condensed-matrix contributions 75.  (Exact
 # doublings and sign flips are integer operations and are not counted.)
-FP64_OPS_PER_BRANCH_PERIOD = 147
+FP64_OPS_PER_BRANCH_PERIOD = 143
 FP64_OPS_PER_BUS_PERIOD = 33   # hand counts of the bus and generator kernels (their
 FP64_OPS_PER_GEN_PERIOD = 17   # loops vary with the degree; these are averages)
 

@@ -8,10 +8,17 @@ namespace mpopf {
 
 // ---------------------------------------------------------------------------
 // sin and cos of the angle difference: Cody & Waite reduction by pi/2 in three
-// parts (Software Manual for the Elementary Functions, 1980), then the Taylor
-// series of sin (through r^17) and cos (through r^18), Horner in r^2, with
-// coefficients RN((-1)^k / k!).  |x| <= RN(pi/4) needs no reduction.  Outside
-// |x| < 2^30 (and for NaN/Inf) the CUDA library is used.
+// parts (Software Manual for the Elementary Functions, 1980), then, with
+// s = r^2, sin r = r + r^3 P(s) and cos r = 1 + s Q(s), Horner in s.  P (degree
+// 5) and Q (degree 6) are the Taylor series of (sin r - r)/r^3 through s^7 and
+// of (cos r - 1)/r^2 through s^8, economised by Chebyshev polynomials
+// (Lanczos's telescoping: each top term c_n s^n traded for the lower terms of
+// c_n T*_n(s) / lead(T*_n), T*_n(s) = T_n(16 s / 5 - 1) on [0, 5/8], which
+// covers |r| <= pi/4) in exact rational arithmetic, then rounded to nearest:
+// 15 FP64 instructions for both values (19 for the plain Taylor series through
+// r^17 and r^18), the polynomials within 2e-17 of sin and 1e-18 of cos.
+// |x| <= RN(pi/4) needs no reduction.  Outside |x| < 2^30 (and for NaN/Inf) the
+// CUDA library is used.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void sincos_cw(double x, double *sn, double *cs) {
   const unsigned long long ax = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffULL;
@@ -29,25 +36,21 @@ __device__ __forceinline__ void sincos_cw(double x, double *sn, double *cs) {
     q = (int)(__double2ll_rz(k) & 3);
   }
   const double r2 = r * r;
-  double p = 1.0 / 355687428096000.0;
-  p = fma(p, r2, -1.0 / 1307674368000.0);
-  p = fma(p, r2, 1.0 / 6227020800.0);
-  p = fma(p, r2, -1.0 / 39916800.0);
-  p = fma(p, r2, 1.0 / 362880.0);
-  p = fma(p, r2, -1.0 / 5040.0);
-  p = fma(p, r2, 1.0 / 120.0);
-  p = fma(p, r2, -1.0 / 6.0);
+  double p = 0x1.5e00b6cff8290p-33;
+  p = fma(p, r2, -0x1.ae5fedfda2660p-26);
+  p = fma(p, r2, 0x1.71de377a84b02p-19);
+  p = fma(p, r2, -0x1.a01a019e6dedep-13);
+  p = fma(p, r2, 0x1.1111111110b56p-7);
+  p = fma(p, r2, -0x1.5555555555555p-3);
   const double r3 = r2 * r;
   const double s = fma(r3, p, r);
-  double c = -1.0 / 6402373705728000.0;
-  c = fma(c, r2, 1.0 / 20922789888000.0);
-  c = fma(c, r2, -1.0 / 87178291200.0);
-  c = fma(c, r2, 1.0 / 479001600.0);
-  c = fma(c, r2, -1.0 / 3628800.0);
-  c = fma(c, r2, 1.0 / 40320.0);
-  c = fma(c, r2, -1.0 / 720.0);
-  c = fma(c, r2, 1.0 / 24.0);
-  c = fma(c, r2, -1.0 / 2.0);
+  double c = -0x1.8fedb35736fa4p-37;
+  c = fma(c, r2, 0x1.1eea6a6fdd11ap-29);
+  c = fma(c, r2, -0x1.27e4f8ca561dfp-22);
+  c = fma(c, r2, 0x1.a01a019dc2b7ep-16);
+  c = fma(c, r2, -0x1.6c16c16c15c7dp-10);
+  c = fma(c, r2, 0x1.5555555555550p-5);
+  c = fma(c, r2, -0x1.0000000000000p-1);
   const double co = fma(r2, c, 1.0);
   if (q == 0) { *sn = s; *cs = co; }
   else if (q == 1) { *sn = co; *cs = -s; }

@@ -4,7 +4,8 @@ Each test pins one part of the oracle to something other than itself: values
 printed in Table II, textbook complex-power flows, closed forms at flat start,
 the series-loss identity, invariances of the flow equations, complex-step and
 finite-difference derivatives of an independently written textbook c(x), dense
-brute force for the condensed matrix, and the C library for sin/cos.
+brute force for the condensed matrix, and the C library and exact rational
+and high-precision arithmetic for sin/cos.
 """
 import math
 import os
@@ -496,6 +497,93 @@ def test_sincos_special_values():
     assert abs(s[2] - 0.5) <= 2 * np.spacing(0.5)
     assert abs(c[3]) <= 1e-16 and s[3] == 1.0
     assert s[4] == 1e-300
+
+
+# The polynomial coefficients, recomputed here from their definition: the
+# Taylor series of (sin r - r)/r^3 through s^7 and of (cos r - 1)/r^2 through
+# s^8 (s = r^2), economised with shifted Chebyshev polynomials on [0, 5/8] down
+# to degrees 5 and 6, in exact rational arithmetic, then rounded to nearest.
+def _economised(coef, degree, a):
+    from fractions import Fraction as Fr
+
+    def times(p, q):
+        out = [Fr(0)] * (len(p) + len(q) - 1)
+        for i, u in enumerate(p):
+            for j, w in enumerate(q):
+                out[i + j] += u * w
+        return out
+
+    y = [Fr(-1), Fr(2) / a]  # maps [0, a] onto [-1, 1]
+    cheb = [[Fr(1)], y]
+    for k in range(1, len(coef)):
+        nxt = times([2 * u for u in y], cheb[k])
+        for i, u in enumerate(cheb[k - 1]):
+            nxt[i] -= u
+        cheb.append(nxt)
+    c = list(coef)
+    while len(c) - 1 > degree:
+        n = len(c) - 1
+        f = c[n] / cheb[n][n]
+        c = [c[i] - f * cheb[n][i] for i in range(n)]
+    return c
+
+
+def _sincos_polynomials():
+    from fractions import Fraction as Fr
+    a = Fr(5, 8)
+    P = _economised([Fr((-1) ** (k + 1), math.factorial(2 * k + 3)) for k in range(8)], 5, a)
+    Q = _economised([Fr((-1) ** (k + 1), math.factorial(2 * k + 2)) for k in range(9)], 6, a)
+    return P, Q
+
+
+def test_sincos_coefficients_are_the_economised_series():
+    """Both sincos implementations (the oracle's and the CUDA path's, written
+    separately) carry exactly the rounded economised coefficients, and the
+    economised polynomials stay within 2e-17 of sin and 1e-18 of cos."""
+    import re
+    import mpmath as mp
+    P, Q = _sincos_polynomials()
+    want_p, want_q = [float(c) for c in P], [float(c) for c in Q]
+    src = open(oracle._SRC).read()
+    got_p = [float.fromhex(re.search(r"kP%d = (-?0x[0-9a-fp.+-]+)" % i, src).group(1)) for i in range(6)]
+    got_q = [float.fromhex(re.search(r"kQ%d = (-?0x[0-9a-fp.+-]+)" % i, src).group(1)) for i in range(7)]
+    assert got_p == want_p and got_q == want_q
+    dev = open(os.path.join(HERE, "..", "paper_2405_14032_b300", "csrc", "mpopf_device.cuh")).read()
+    body = dev[dev.index("void sincos_cw"):]
+    body = body[:body.index("const double co")]
+    lits = [float.fromhex(h) for h in re.findall(r"(-?0x[0-9a-f]\.[0-9a-f]+p[+-]\d+)", body)]
+    # after the three Cody-Waite constants and 2/pi: P from the top down, then Q from the top down
+    assert lits[4:] == want_p[::-1] + want_q[::-1]
+    mp.mp.dps = 40
+    es = ec = mp.mpf(0)
+    for i in range(801):
+        r = mp.mpf(5) / 8 * i / 800
+        r = mp.sqrt(r)
+        s2 = r * r
+        ps = mp.mpf(0)
+        for c in reversed(P):
+            ps = ps * s2 + mp.mpf(c.numerator) / c.denominator
+        qs = mp.mpf(0)
+        for c in reversed(Q):
+            qs = qs * s2 + mp.mpf(c.numerator) / c.denominator
+        es = max(es, abs(r + r ** 3 * ps - mp.sin(r)))
+        ec = max(ec, abs(1 + s2 * qs - mp.cos(r)))
+    assert es < 2e-17 and ec < 1e-18, (es, ec)
+
+
+def test_sincos_within_one_ulp_of_high_precision():
+    """On the unreduced range (|x| <= pi/4, every angle difference of the
+    benchmark inputs) the oracle's sin and cos are within one ulp of the
+    correctly rounded values."""
+    import mpmath as mp
+    mp.mp.dps = 40
+    x = np.random.default_rng(7).uniform(-math.pi / 4, math.pi / 4, 3000)
+    x = np.concatenate([x, [math.pi / 4 * (1 - 2 ** -52), -0.6, 1e-9, 2.0 ** -30]])
+    s, c = oracle.sincos(x)
+    for xi, si, ci in zip(x, s, c):
+        S, C = mp.sin(mp.mpf(float(xi))), mp.cos(mp.mpf(float(xi)))
+        assert abs(mp.mpf(float(si)) - S) <= math.ulp(float(S)), xi
+        assert abs(mp.mpf(float(ci)) - C) <= math.ulp(float(C)), xi
 
 
 def test_jvp_load_tangent_finite_difference():
