@@ -38,6 +38,18 @@ WORKLOAD = dict(n_bus=10000, n_branch=16000, n_gen=2000, n_load=6000, seed=3)
 # 14, Jacobian 8, W block 16, condensed-matrix contributions 75.  (Exact
 # doublings and sign flips are integer operations and are not counted.)
 FP64_OPS_PER_BRANCH_PERIOD = 143
+# The FP64 pipe issues 2 thread-instructions (fma, add or mul) per cycle per SM
+# (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on.sum.peak_sustained = 296
+# for 148 SMs); with the maximum SM clock that is the ALU roofline of the path.
+FP64_PER_CYCLE_PER_SM = 2
+SM_MAX_MHZ = 2032.0
+
+
+def fp64_issue_peak(sms, sm_max_mhz):
+    """FP64 operations per second (in G) the GPU's FP64 pipes can issue."""
+    return FP64_PER_CYCLE_PER_SM * sms * sm_max_mhz * 1e6 / 1e9
+
+
 FP64_OPS_PER_BUS_PERIOD = 33   # hand counts of the bus and generator kernels (their
 FP64_OPS_PER_GEN_PERIOD = 17   # loops vary with the degree; these are averages)
 
@@ -446,6 +458,9 @@ def batched_comparison(torch, reps=20, fp64_peak=None):
            "algorithmic_bytes": alg_bytes, "gbs_batched": alg_bytes / (bat_ms * 1e-3) / 1e9,
            "fp64_ops_hand_count": fp64_ops,
            "fp64_gops_batched": fp64_ops / (bat_ms * 1e-3) / 1e9}
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    res["fp64_frac_of_issue_peak"] = res["fp64_gops_batched"] / fp64_issue_peak(
+        sms, measured_peaks().get("sm_max_mhz") or SM_MAX_MHZ)
     if fp64_peak:
         res["fp64_frac_of_dgemm_rate"] = res["fp64_gops_batched"] / (fp64_peak / 1e9)
     b.close()
@@ -818,14 +833,18 @@ def run_ours(args, world, rank, local):
     top = max(prof, key=lambda k: prof[k][0])
     top_ms = prof[top][0] / max(prof[top][1], 1)
     roof = None
-    if top == "branch" and fp64_peak:
+    if top == "branch":
         ops = FP64_OPS_PER_BRANCH_PERIOD * T * inst.net.n_branch
         achieved = ops / (top_ms * 1e-3) / 1e9
-        peak = fp64_peak / 1e9
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        peak = fp64_issue_peak(sms, measured_peaks().get("sm_max_mhz") or SM_MAX_MHZ)
         roof = {"bound": "alu", "kernel": "k_branch (branch x period)", "achieved": achieved, "peak": peak,
                 "unit": "Gop/s (FP64 fma/add/mul)", "frac": achieved / peak,
                 "traffic": ncu_traffic(), "ops_per_launch": ops, "avg_launch_ms": top_ms,
-                "peak_source": "measured: cuBLAS FP64 GEMM in this run (FMA count / time)"}
+                "peak_source": (f"derived: {FP64_PER_CYCLE_PER_SM} FP64 thread-instructions per cycle per SM x "
+                                f"{sms} SMs x max SM clock"),
+                "peak_measured_dgemm": fp64_peak / 1e9 if fp64_peak else None,
+                "frac_of_measured_dgemm": achieved / (fp64_peak / 1e9) if fp64_peak else None}
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs")
     gbs = alg / (ms_step * 1e-3) / 1e9
