@@ -29,11 +29,13 @@ def main(argv=None) -> int:
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--launches", type=int, default=1, choices=[1, 2],
                     help="batch: one persistent launch or two (generator/branch, then bus/objective)")
+    ap.add_argument("--instances", type=int, default=64,
+                    help="batch: the first INSTANCES of the 64 benchmark instances (a smaller capture)")
     a = ap.parse_args(argv)
     dev = lambda v: torch.as_tensor(v, dtype=torch.float64, device="cuda")
 
     if a.workload == "batch":
-        shapes = synth.batch_shapes(64)
+        shapes = synth.batch_shapes(64)[:max(1, min(64, a.instances))]
         hs, ios = [], []
         for s in shapes:
             inst = synth.make_instance(s["seed"], s["n_bus"], s["n_branch"], s["n_gen"], s["n_load"], s["T"])
@@ -52,7 +54,7 @@ def main(argv=None) -> int:
             b.sweep()
         b.status()
         torch.cuda.synchronize()
-        print(f"batch: {a.reps} batched sweeps of 64 instances")
+        print(f"batch: {a.reps} batched sweeps of {len(shapes)} instances")
         return 0
 
     inst = _instance(a.buses, a.periods)
