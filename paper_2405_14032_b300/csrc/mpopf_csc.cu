@@ -17,20 +17,37 @@
 namespace mpopf {
 namespace {
 
+// Each thread takes kStreams outputs a stride apart (u, u + stride, ...), so a
+// warp's index loads and stores stay coalesced and a thread has kStreams
+// independent gathers of COO values in flight.
+constexpr int kStreams = 4;
 template <bool SEG>
-__global__ void __launch_bounds__(kBlock) k_csc_values(int64_t nnz, const int64_t *__restrict__ seg,
+__global__ void __launch_bounds__(kBlock) k_csc_values(int64_t nnz, int64_t stride, const int64_t *__restrict__ seg,
                                                        const int32_t *__restrict__ src,
                                                        const double *__restrict__ coo, double *__restrict__ out) {
-  const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (u >= nnz) return;
-  if (!SEG) {
-    out[u] = coo[src[u]];
-    return;
+  const int64_t u0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (u0 >= stride) return;
+  if constexpr (!SEG) {
+    int32_t s[kStreams];
+    double v[kStreams];
+#pragma unroll
+    for (int k = 0; k < kStreams; ++k) s[k] = u0 + k * stride < nnz ? __ldg(src + u0 + k * stride) : 0;
+#pragma unroll
+    for (int k = 0; k < kStreams; ++k) v[k] = u0 + k * stride < nnz ? __ldg(coo + s[k]) : 0.0;
+#pragma unroll
+    for (int k = 0; k < kStreams; ++k)
+      if (u0 + k * stride < nnz) out[u0 + k * stride] = v[k];
+  } else {
+#pragma unroll
+    for (int k = 0; k < kStreams; ++k) {
+      const int64_t u = u0 + k * stride;
+      if (u >= nnz) break;
+      const int64_t p0 = seg[u], p1 = seg[u + 1];
+      double acc = coo[src[p0]];
+      for (int64_t p = p0 + 1; p < p1; ++p) acc = acc + coo[src[p]];
+      out[u] = acc;
+    }
   }
-  const int64_t p0 = seg[u], p1 = seg[u + 1];
-  double acc = coo[src[p0]];
-  for (int64_t p = p0 + 1; p < p1; ++p) acc = acc + coo[src[p]];
-  out[u] = acc;
 }
 
 int fail(int code, const std::string &msg) {
@@ -268,11 +285,12 @@ int mpopf_coo_to_csc(mpopf_handle *h, int32_t which, const double *coo_vals, dou
   if (!c.built) return fail(MPOPF_ERR_ARG, "mpopf_coo_to_csc: call mpopf_csc_pattern for this matrix first");
   if (c.nnz == 0) return MPOPF_OK;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const unsigned grid = (unsigned)((c.nnz + kBlock - 1) / kBlock);
+  const int64_t stride = (c.nnz + kStreams - 1) / kStreams;
+  const unsigned grid = (unsigned)((stride + kBlock - 1) / kBlock);
   if (c.seg)
-    k_csc_values<true><<<grid, kBlock, 0, st>>>(c.nnz, c.seg, c.src, coo_vals, csc_vals);
+    k_csc_values<true><<<grid, kBlock, 0, st>>>(c.nnz, stride, c.seg, c.src, coo_vals, csc_vals);
   else
-    k_csc_values<false><<<grid, kBlock, 0, st>>>(c.nnz, nullptr, c.src, coo_vals, csc_vals);
+    k_csc_values<false><<<grid, kBlock, 0, st>>>(c.nnz, stride, nullptr, c.src, coo_vals, csc_vals);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(MPOPF_ERR_CUDA, std::string("mpopf_coo_to_csc: ") + cudaGetErrorString(e));
   return MPOPF_OK;
