@@ -35,3 +35,11 @@ def test_reference_arm_other_ranks_print_nothing():
     r = _run({"WORLD_SIZE": "2", "RANK": "1", "LOCAL_RANK": "1"})
     assert r.returncode == 0, r.stderr[-2000:]
     assert not [l for l in r.stdout.splitlines() if l.startswith("{")]
+
+
+def test_fp64_issue_peak_from_unit_counts():
+    """The roofline peak of the FP64-bound kernel: 2 FP64 thread-instructions
+    per cycle per SM x 148 SMs x 2032 MHz."""
+    import bench
+    assert bench.FP64_PER_CYCLE_PER_SM == 2
+    assert abs(bench.fp64_issue_peak(148, 2032.0) - 601.472) < 1e-9
