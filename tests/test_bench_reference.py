@@ -1,6 +1,7 @@
 """bench.py's reference arm (the CPU oracle on the benchmark network) on the
 host: one JSON line with the contract's keys from rank 0, nothing from the
-other ranks.  A two-period horizon keeps it to seconds; no GPU."""
+other ranks.  A two-period horizon keeps it to seconds; no GPU.  Also the FP64
+issue peak that the GPU arm's roofline divides by."""
 import json
 import os
 import subprocess
