@@ -54,6 +54,15 @@ MUTATIONS = {
     "slack right-hand side sign": ("const double qs = std::fma(mu, r.ru - r.rl, y[i]);",
                                    "const double qs = std::fma(mu, r.rl - r.ru, y[i]);", 0,
                                    lambda: P.test_ipm_condensation_solves_full_lifted_system(1e-3, 1e-4)),
+    "reactive limits swapped": ("xl[v_qg(M, t, g)] = M.qmin[g]; xu[v_qg(M, t, g)] = M.qmax[g];",
+                                "xl[v_qg(M, t, g)] = M.qmax[g]; xu[v_qg(M, t, g)] = M.qmin[g];", 0,
+                                lambda: P.test_bounds_written_out_from_the_model(False, 2)),
+    "angle limits taken as symmetric": ("lo = M.angmin[comp]; hi = M.angmax[comp];",
+                                        "lo = -M.angmax[comp]; hi = M.angmax[comp];", 0,
+                                        lambda: P.test_bounds_written_out_from_the_model(False, 1)),
+    "reactive ramp limit from the P ramp": ("lo = -M.qramp[comp]; hi = M.qramp[comp];",
+                                            "lo = -M.ramp[comp]; hi = M.ramp[comp];", 0,
+                                            lambda: P.test_bounds_written_out_from_the_model(True, 3)),
     "CSC drops a duplicate": ("vals[k] = vals[k] + coo[v[p].e];", "vals[k] = coo[v[p].e];", 0,
                               lambda: P.test_csc_compression_matches_scipy_and_dense(1)),
 }

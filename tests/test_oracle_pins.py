@@ -702,3 +702,108 @@ def test_csc_compression_matches_scipy_and_dense(which):
         assert np.all(np.diff(colptr) >= 0)
         for j in range(o.n):
             assert np.all(np.diff(rowidx[colptr[j]:colptr[j + 1]]) > 0)
+
+
+# ---------------------------------------------------------------------------
+# Bounds of the standard form (Eq. 3) from the limits of Eq. 1f-1k
+# ---------------------------------------------------------------------------
+def _bounds_network(qramp):
+    """Three buses, three branches (one parallel pair), three generators on two
+    buses; every limit distinct and asymmetric, so that a swapped pair, a
+    borrowed limit or a dropped sign changes some bound."""
+    net = H.network(3, [0, 1, 0], [1, 2, 1], [0.01, 0.02, 0.03], [0.1, 0.12, 0.15], [0.01, 0.02, 0.0],
+                    gen_bus=[0, 2, 2], load_bus=[1, 2], ref=1)
+    net.bus_vmin[:] = [0.91, 0.93, 0.95]
+    net.bus_vmax[:] = [1.07, 1.08, 1.09]
+    net.br_angmin[:] = [-0.41, -0.52, -0.23]
+    net.br_angmax[:] = [0.37, 0.28, 0.19]
+    net.gen_pmin[:] = [0.1, 0.25, 0.0]
+    net.gen_pmax[:] = [2.5, 3.5, 1.5]
+    net.gen_qmin[:] = [-0.4, -0.9, -0.2]
+    net.gen_qmax[:] = [0.7, 1.1, 0.6]
+    net.gen_ramp[:] = [0.31, 0.47, 0.13]
+    if qramp:
+        net.gen_qramp = np.array([0.17, 0.29, 0.05])
+    return net
+
+
+@pytest.mark.parametrize("qramp", [False, True])
+@pytest.mark.parametrize("T", [1, 2, 3])
+def test_bounds_written_out_from_the_model(qramp, T):
+    """xl/xu/gl/gu row by row from the model, written out independently of the
+    oracle: vm in [vmin, vmax] (Eq. 1i), pg in [pmin, pmax] (Eq. 1g), qg in
+    [qmin, qmax] (Eq. 1h), va, p, q free; the reference row, the four flow
+    definitions and both balances are equalities (0, 0); the angle difference
+    in [angmin, angmax] (Eq. 1j); the squared thermal rows at both ends in
+    (-inf, 0] (Eq. 1f); the P ramp in [-ramp, ramp] for t >= 1 (Eq. 1k); the
+    reactive ramp, when present, in [-qramp, qramp]."""
+    net = _bounds_network(qramp)
+    N, L, G = net.n_bus, net.n_branch, net.n_gen
+    o = oracle.Oracle(H.instance(net, T))
+    xl, xu, gl, gu = o.bounds()
+    inf = math.inf
+    exl, exu = [], []
+    for _ in range(T):                       # va
+        exl += [-inf] * N; exu += [inf] * N
+    for _ in range(T):                       # vm
+        exl += list(net.bus_vmin); exu += list(net.bus_vmax)
+    for _ in range(T):                       # pg
+        exl += list(net.gen_pmin); exu += list(net.gen_pmax)
+    for _ in range(T):                       # qg
+        exl += list(net.gen_qmin); exu += list(net.gen_qmax)
+    for _ in range(2 * T):                   # p, q of both arcs of every branch
+        exl += [-inf] * (2 * L); exu += [inf] * (2 * L)
+    egl, egu = [0.0] * T, [0.0] * T          # K0 reference angle
+    for _ in range(4 * T):                   # K1..K4 flow definitions
+        egl += [0.0] * L; egu += [0.0] * L
+    for _ in range(T):                       # K5 angle difference
+        egl += list(net.br_angmin); egu += list(net.br_angmax)
+    for _ in range(2 * T):                   # K6, K7 thermal
+        egl += [-inf] * L; egu += [0.0] * L
+    for _ in range(2 * T):                   # K8, K9 balances
+        egl += [0.0] * N; egu += [0.0] * N
+    for _ in range(T - 1):                   # K10 ramp, t = 1 .. T-1
+        egl += [-r for r in net.gen_ramp]; egu += list(net.gen_ramp)
+    if qramp:
+        for _ in range(T - 1):               # K11 reactive ramp
+            egl += [-r for r in net.gen_qramp]; egu += list(net.gen_qramp)
+    assert (o.n, o.m) == (len(exl), len(egl))
+    for got, exp in ((xl, exl), (xu, exu), (gl, egl), (gu, egu)):
+        assert np.array_equal(got, np.array(exp)), np.nonzero(got != np.array(exp))[0][:8]
+    assert G == 3
+
+
+def test_bounds_match_the_network_arrays_cfg1():
+    """The same statement on cfg1 (with and without the reactive ramp), checked
+    by kind blocks against the network arrays."""
+    for qramp in (False, True):
+        inst = synth.config_instance("cfg1")
+        if qramp:
+            inst = synth.with_reactive_ramp(inst)
+        net, T = inst.net, inst.T
+        o = oracle.Oracle(inst)
+        xl, xu, gl, gu = o.bounds()
+        sl = H.var_slices(net, T)
+        assert np.all(xl[sl["va"]] == -np.inf) and np.all(xu[sl["va"]] == np.inf)
+        assert np.array_equal(xl[sl["vm"]], np.tile(net.bus_vmin, T))
+        assert np.array_equal(xu[sl["vm"]], np.tile(net.bus_vmax, T))
+        assert np.array_equal(xl[sl["pg"]], np.tile(net.gen_pmin, T))
+        assert np.array_equal(xu[sl["pg"]], np.tile(net.gen_pmax, T))
+        assert np.array_equal(xl[sl["qg"]], np.tile(net.gen_qmin, T))
+        assert np.array_equal(xu[sl["qg"]], np.tile(net.gen_qmax, T))
+        for k in ("p", "q"):
+            assert np.all(xl[sl[k]] == -np.inf) and np.all(xu[sl[k]] == np.inf)
+        ro = H.row_offsets(net, T)
+        eq = np.r_[ro[0]:ro[5], ro[8]:ro[10]]
+        assert np.all(gl[eq] == 0.0) and np.all(gu[eq] == 0.0)
+        assert np.array_equal(gl[ro[5]:ro[6]], np.tile(net.br_angmin, T))
+        assert np.array_equal(gu[ro[5]:ro[6]], np.tile(net.br_angmax, T))
+        assert np.all(gl[ro[6]:ro[8]] == -np.inf) and np.all(gu[ro[6]:ro[8]] == 0.0)
+        assert np.array_equal(gl[ro[10]:ro[11]], np.tile(-net.gen_ramp, T - 1))
+        assert np.array_equal(gu[ro[10]:ro[11]], np.tile(net.gen_ramp, T - 1))
+        if qramp:
+            assert o.m == ro[11] + (T - 1) * net.n_gen
+            assert np.array_equal(gl[ro[11]:], np.tile(-net.gen_qramp, T - 1))
+            assert np.array_equal(gu[ro[11]:], np.tile(net.gen_qramp, T - 1))
+        else:
+            assert o.m == ro[11]
