@@ -46,7 +46,10 @@ def _bind(lib):
         "orc_hess_pattern": (None, [_P, _P, _P]),
         "orc_jac_rowptr": (None, [_P, _P]),
         "orc_eval": (None, [_P, _I64, _I64, _P, _P, _D, _P, _P, _P, _P, _P]),
-        "orc_kkt": (_I64, [_P, _I64, _I64, _P, _P, _D, _P, _P, _D, _P, _P, _P, _P]),
+        "orc_kkt_new": (_P, [_P, _I64, _I64, _P, _P, _D, _P, _P, _D]),
+        "orc_kkt_sizes": (None, [_P, _P]),
+        "orc_kkt_copy": (None, [_P, _P, _P, _P, _P]),
+        "orc_kkt_free": (None, [_P]),
         "orc_window_rows": (_I64, [_P, _I64, _I64]),
         "orc_vjp": (None, [_P, _I64, _I64, _P, _P, _P, _P, _P]),
         "orc_hvp": (None, [_P, _I64, _I64, _P, _P, _D, _P, _P]),
@@ -188,15 +191,20 @@ class Oracle:
         (global row ids, row lengths, columns, values)."""
         t1 = self.T if t1 is None else t1
         x, lam, sx, dv = _f64(x), _f64(lam), _f64(sigma_x), _f64(dvec)
-        nr = self._lib.orc_window_rows(self.h, t0, t1)
-        rows = np.empty(nr, np.int64)
-        rowlen = np.empty(nr, np.int64)
-        nnz = self._lib.orc_kkt(self.h, t0, t1, _ptr(x), _ptr(lam), float(sigma), _ptr(sx), _ptr(dv),
-                           float(delta_w), _ptr(rows), _ptr(rowlen), None, None)
-        cols = np.empty(nnz, np.int32)
-        vals = np.empty(nnz, np.float64)
-        self._lib.orc_kkt(self.h, t0, t1, _ptr(x), _ptr(lam), float(sigma), _ptr(sx), _ptr(dv),
-                     float(delta_w), _ptr(rows), _ptr(rowlen), _ptr(cols), _ptr(vals))
+        res = self._lib.orc_kkt_new(self.h, t0, t1, _ptr(x), _ptr(lam), float(sigma), _ptr(sx), _ptr(dv),
+                                    float(delta_w))
+        try:
+            sizes = np.zeros(2, np.int64)
+            self._lib.orc_kkt_sizes(res, _ptr(sizes))
+            nr, nnz = int(sizes[0]), int(sizes[1])
+            assert nr == self._lib.orc_window_rows(self.h, t0, t1)
+            rows = np.empty(nr, np.int64)
+            rowlen = np.empty(nr, np.int64)
+            cols = np.empty(nnz, np.int32)
+            vals = np.empty(nnz, np.float64)
+            self._lib.orc_kkt_copy(res, _ptr(rows), _ptr(rowlen), _ptr(cols), _ptr(vals))
+        finally:
+            self._lib.orc_kkt_free(res)
         return rows, rowlen, cols, vals
 
     def kkt_csr(self, x, lam, sigma, sigma_x, dvec, delta_w):

@@ -659,22 +659,17 @@ void orc_eval(void* h, int64_t t0, int64_t t1, const double* x, const double* la
   }
 }
 
-// Condensed matrix rows for the variables of periods [t0, t1), in global row
-// order.  Returns the number of entries; fills rows_out (global row index of
-// each window row), rowlen, and (when cols/vals are not NULL) the sorted
-// columns and values of each row.  A call with cols == NULL computes and keeps
-// the result; the next call with the same arguments and cols != NULL copies it.
 }  // extern "C"
 
 namespace {
-struct KktCache {
-  const void* key[8] = {nullptr};
-  double dkey[2] = {0, 0};
+// Rows of the condensed matrix for the variables of a window of periods:
+// global row index and length of each row, then the columns (ascending) and
+// values of every row in turn.
+struct KktRows {
   std::vector<int64_t> rows, rowlen;
   std::vector<int32_t> cols;
   std::vector<double> vals;
 };
-thread_local KktCache g_kkt;
 
 // Local block of one element: (key, value) pairs, each key once, values
 // accumulated in the stated order.
@@ -689,7 +684,7 @@ struct Local {
 };
 
 void kkt_compute(const Model& M, int64_t t0, int64_t t1, const double* x, const double* lam, double sigma,
-                 const double* sigx, const double* dvec, double delta_w, KktCache* out) {
+                 const double* sigx, const double* dvec, double delta_w, KktRows* out) {
   // Contributions in the order they are added: diagonal terms first, then
   // every element's local values in element order.  A stable sort by key
   // keeps that order within each key; each key is then summed left to right.
@@ -746,27 +741,34 @@ void kkt_compute(const Model& M, int64_t t0, int64_t t1, const double* x, const 
 }
 }  // namespace
 
-extern "C" int64_t orc_kkt(void* h, int64_t t0, int64_t t1, const double* x, const double* lam, double sigma,
-                           const double* sigx, const double* dvec, double delta_w,
-                           int64_t* rows_out, int64_t* rowlen, int32_t* cols, double* vals) {
+// Condensed matrix rows for the variables of periods [t0, t1), in global row
+// order, in two explicit steps: orc_kkt_new computes them into a result object
+// that the caller owns; orc_kkt_sizes reports its row and entry counts;
+// orc_kkt_copy writes the global row index and length of each row and the
+// columns and values of all rows; orc_kkt_free releases it.
+extern "C" void* orc_kkt_new(void* h, int64_t t0, int64_t t1, const double* x, const double* lam, double sigma,
+                             const double* sigx, const double* dvec, double delta_w) {
   const Model& M = *static_cast<Model*>(h);
-  KktCache& C = g_kkt;
-  const void* key[8] = {h, (const void*)(intptr_t)t0, (const void*)(intptr_t)t1, x, lam, sigx, dvec, nullptr};
-  const bool hit = cols && std::memcmp(C.key, key, sizeof key) == 0 && C.dkey[0] == sigma && C.dkey[1] == delta_w;
-  if (!hit) {
-    kkt_compute(M, t0, t1, x, lam, sigma, sigx, dvec, delta_w, &C);
-    std::memcpy(C.key, key, sizeof key);
-    C.dkey[0] = sigma;
-    C.dkey[1] = delta_w;
-  }
-  for (size_t r = 0; r < C.rows.size(); ++r) { rows_out[r] = C.rows[r]; rowlen[r] = C.rowlen[r]; }
-  if (cols) {
-    std::memcpy(cols, C.cols.data(), C.cols.size() * sizeof(int32_t));
-    std::memcpy(vals, C.vals.data(), C.vals.size() * sizeof(double));
-    std::memset(C.key, 0, sizeof C.key);
-  }
-  return (int64_t)C.cols.size();
+  KktRows* out = new KktRows();
+  kkt_compute(M, t0, t1, x, lam, sigma, sigx, dvec, delta_w, out);
+  return out;
 }
+
+// sizes[0] = number of rows, sizes[1] = number of entries.
+extern "C" void orc_kkt_sizes(const void* res, int64_t* sizes) {
+  const KktRows& R = *static_cast<const KktRows*>(res);
+  sizes[0] = (int64_t)R.rows.size();
+  sizes[1] = (int64_t)R.cols.size();
+}
+
+extern "C" void orc_kkt_copy(const void* res, int64_t* rows_out, int64_t* rowlen, int32_t* cols, double* vals) {
+  const KktRows& R = *static_cast<const KktRows*>(res);
+  for (size_t r = 0; r < R.rows.size(); ++r) { rows_out[r] = R.rows[r]; rowlen[r] = R.rowlen[r]; }
+  std::memcpy(cols, R.cols.data(), R.cols.size() * sizeof(int32_t));
+  std::memcpy(vals, R.vals.data(), R.vals.size() * sizeof(double));
+}
+
+extern "C" void orc_kkt_free(void* res) { delete static_cast<KktRows*>(res); }
 
 extern "C" {
 
