@@ -373,18 +373,22 @@ int mpopf_launch_count(const mpopf_handle *h, unsigned outputs);
 
 /* Condensed-matrix assembly that allocates nothing (the paper has no
  * counterpart: this is a deployment variant of mpopf_assemble_kkt).  For
- * callers that cannot call cudaMalloc while they run -- work recorded inside a
- * CUDA stream capture, processes that reserve all device memory up front and
- * forbid later allocation (real-time controllers, pooled serving processes).
+ * callers that cannot call cudaMalloc once they are running: processes that
+ * reserve all device memory up front and forbid later allocation (real-time
+ * controllers, serving processes with pooled memory) and plugins inside a host
+ * application that owns the device's memory.
  * Same inputs, output and values as mpopf_assemble_kkt; the per-branch scratch
  * it needs lives in a fixed 32 MiB array inside the library's device image
  * (held by every GPU that loads the library until exit) instead of the
  * handle.  Limit: 12 T L <= 4 Mi doubles (T x L <= 349525 branch-periods);
- * larger problems return MPOPF_ERR_SIZE.  The first call on each device looks
- * up the array's address (cudaGetSymbolAddress, no allocation): make it
- * outside any stream capture.  All calls on a device share the array, which
- * keeps the last call's contents (every record read is first rewritten, so no
- * clearing is needed); calls that overlap on the GPU race on it. */
+ * larger problems return MPOPF_ERR_SIZE.  The handle's device must be current
+ * (MPOPF_ERR_ARG otherwise).  The first call on each device looks up the
+ * array's address (cudaGetSymbolAddress, no allocation) and must come before
+ * any stream capture; later calls look it up again, except on a capturing
+ * stream, where the address found earlier on that device is used.  All calls
+ * on a device share the array, which keeps the last call's contents (every
+ * record read is first rewritten, so no clearing is needed); calls that
+ * overlap on the GPU race on it. */
 int mpopf_assemble_kkt_noalloc(mpopf_handle *h, const double *x, const double *lam, double sigma,
                                const double *sigma_x, const double *dvec, double delta_w, double *kv, void *stream);
 

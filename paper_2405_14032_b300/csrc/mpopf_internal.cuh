@@ -179,6 +179,7 @@ struct mpopf_handle {
   mpopf::HostPipe *pipe;
   mpopf::KktSolver *solver;  // library factorisation of M (built on first use)
   mpopf::Fork fork;          // side stream of the evaluations (created at setup)
+  int device;                // CUDA device current at setup (holds every allocation above)
 };
 
 namespace mpopf {

@@ -500,6 +500,11 @@ int mpopf_setup(const mpopf_network *net, int32_t n_periods, const double *pd, c
 
   mpopf_handle *h = new mpopf_handle();
   std::memset(h, 0, sizeof(*h));
+  if (cudaGetDevice(&h->device) != cudaSuccess) {
+    delete h;
+    cudaGetLastError();
+    return fail(MPOPF_ERR_CUDA, "mpopf_setup: no current CUDA device");
+  }
   Dev &d = h->d;
   d.N = (int32_t)N; d.L = (int32_t)L; d.G = (int32_t)G; d.D = (int32_t)D; d.T = (int32_t)T; d.ref = net->ref_bus;
   d.n = n; d.m = m;

@@ -1,8 +1,8 @@
 """The allocation-free condensed-matrix entry point, through the C-ABI.
 
-mpopf_assemble_kkt_noalloc serves callers that cannot call cudaMalloc while
-they run (work recorded in a stream capture, processes that reserve all device
-memory up front).  Its scratch is a fixed array inside the library, shared by
+mpopf_assemble_kkt_noalloc serves callers that cannot call cudaMalloc once
+they are running (processes that reserve all device memory up front, plugins
+inside an application that owns the device's memory).  Its scratch is a fixed array inside the library, shared by
 every call, so this test checks two calls in a row against the regular
 mpopf_assemble_kkt, with the tolerance the parity tests use.  It sits in a file
 of its own that pytest collects last.
