@@ -7,9 +7,13 @@ COO) and the condensed KKT matrix M = W + diag(Sigma_x + delta_w) + J^T D J
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-One JSON line on rank 0.  Under torchrun (N > 1) every rank evaluates its own
-copy of the instance (independent problems, no data-path collective; weak
-scaling); the timing is the max over ranks.
+One JSON line on rank 0.  Under torchrun (N > 1) the horizon is split into N
+contiguous blocks of periods, one per GPU (strong scaling): before each sweep
+every rank exchanges two G-vectors with its neighbours (pg of the period
+before its block, D of the ramp rows after it; NCCL point-to-point) and after
+it the partial objectives are summed (all-reduce); --mode replicas instead
+evaluates one independent copy per rank (weak scaling).  The timing is the max
+over ranks.
 """
 from __future__ import annotations
 
@@ -62,6 +66,12 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--periods", type=int, default=168, help="horizon T (168 is the benchmark workload)")
     ap.add_argument("--e2e-steps", type=int, default=8)
+    ap.add_argument("--dist-backend", choices=["nccl", "gloo"], default="nccl",
+                    help="process-group backend for N > 1 (gloo stages the halo through host memory)")
+    ap.add_argument("--mode", choices=["single", "replicas", "shards"], default=None,
+                    help="N > 1: 'shards' (default; the horizon split into contiguous period blocks, one per "
+                         "GPU, halo exchange and f all-reduce; strong scaling) or 'replicas' (one independent "
+                         "copy of the instance per GPU; weak scaling)")
     return ap.parse_args()
 
 
@@ -116,9 +126,11 @@ def link_rates(torch, nbytes=1 << 30):
     return rates
 
 
-def ncu_traffic():
-    """DRAM bytes per launch of the dominant kernel from the committed ncu
-    summary, or None when the kernel source changed since the capture."""
+def ncu_traffic(periods):
+    """DRAM bytes of one launch of the dominant kernel over `periods` periods,
+    scaled from the committed ncu capture of a shorter horizon (the kernel's
+    traffic is proportional to the branch x period elements it processes), or
+    None when the kernel source changed since the capture."""
     p = os.path.join(ROOT, "profiles", "k_branch_traffic.json")
     try:
         with open(p) as fh:
@@ -127,7 +139,10 @@ def ncu_traffic():
         return None
     if rec.get("kernel_source_sha256_16") != kernel_source_hash():
         return None
-    return rec.get("dram_bytes_per_launch_full_workload")
+    per = rec.get("dram_bytes_per_launch")
+    if per is None or not rec.get("captured_periods"):
+        return None
+    return per * periods / rec["captured_periods"]
 
 
 # ---------------------------------------------------------------------------
@@ -140,7 +155,7 @@ class ClockSampler:
         "hw_power_brake_slowdown": 0x80, "display_clock_setting": 0x100,
     }
 
-    def __init__(self, index, period_s=0.01):
+    def __init__(self, index, period_s=0.002):
         self.index, self.period = index, period_s
         self.samples, self.reasons = [], 0
         self.max_mhz = None
@@ -185,7 +200,7 @@ class ClockSampler:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def _start_smi(self):
-        """Fallback without the NVML Python module: nvidia-smi every 50 ms."""
+        """Fallback when NVML cannot be used from Python: nvidia-smi every 50 ms."""
         import subprocess
         sel = []
         try:
@@ -222,7 +237,8 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": self.max_mhz,
                 "samples": len(mhz), "reasons": sorted(reasons),
-                "source": "nvidia-smi every 50 ms during the timed region"}
+                "source": "nvidia-smi every 50 ms during the timed region",
+                "nvml_error": self.error}
 
     def _run(self):
         nv = self._nv
@@ -245,7 +261,7 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(self.samples) if self.samples else None,
                 "sm_max_mhz": self.max_mhz, "samples": len(self.samples),
                 "reasons": [k for k, v in self.REASONS.items() if self.reasons & v],
-                "source": "NVML, read-only, every 10 ms during the timed region"}
+                "source": "NVML, read-only, every 2 ms during the timed region"}
 
 
 # ---------------------------------------------------------------------------
@@ -263,6 +279,8 @@ def max_over_ranks(value, world, device=None):
         return value
     import torch
     import torch.distributed as dist
+    if dist.get_backend() == "gloo":
+        device = None  # gloo reduces host tensors
     t = torch.tensor([value], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
@@ -584,7 +602,9 @@ def ipm_step_timing(torch, reps=5):
         for k, a, b in zip(parts, marks[:-1], marks[1:]):
             parts[k] += (b - a) * 1e3 / reps
     h.close()
-    return {"workload": "2000-bus / 3200-branch / 400-gen / 1200-load network, T = 24 (n = 422,400)",
+    return {"kind": ("functional check of one whole interior-point step through the library factorisation "
+                     "(a stand-in for the paper's cuDSS), not a performance figure of this library's kernels"),
+            "workload": "2000-bus / 3200-branch / 400-gen / 1200-load network, T = 24 (n = 422,400)",
             "ordering_and_analysis_s": first_s, "ms": parts, "step_ms": sum(parts.values()),
             "timing": "host clock around each synchronised call (the factorisation synchronises itself)",
             "factorisation": "cuSOLVER sparse Cholesky (csrchol), METIS nested-dissection ordering"}
@@ -776,127 +796,159 @@ def run_reference(args, world, rank):
     return 0
 
 
+def fp64_ops_per_sweep(N, L, G, T):
+    """Hand count of the FP64 operations of one full sweep over T periods."""
+    return FP64_OPS_PER_BRANCH_PERIOD * T * L + FP64_OPS_PER_BUS_PERIOD * T * N + FP64_OPS_PER_GEN_PERIOD * T * G
+
+
 def run_ours(args, world, rank, local):
     import torch
+    local = local % max(torch.cuda.device_count(), 1)  # ranks beyond the visible GPUs share them
     if world > 1:
         import torch.distributed as dist
         torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+        dist.init_process_group(args.dist_backend)
     dev = torch.device("cuda", local)
-    from paper_2405_14032_b300 import mpopf, synth
+    from paper_2405_14032_b300 import mpopf, shard, synth
 
+    mode = (args.mode or "shards") if world > 1 else "single"
     T = args.periods
     inst = synth.make_instance(WORKLOAD["seed"], WORKLOAD["n_bus"], WORKLOAD["n_branch"], WORKLOAD["n_gen"],
                                WORKLOAD["n_load"], T)
     pt = synth.make_point(WORKLOAD["seed"], inst)
+    span = shard.split(T, world)[rank] if mode == "shards" else None
+    plan = mpopf.shard_plan(inst.net, T, *span) if span else None
     torch.cuda.synchronize()
     t_setup = time.perf_counter()
-    h = mpopf.Handle(inst)
+    h = mpopf.Handle(inst, shard=span)
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t_setup
     n, m = h.n, h.m
     D = inst.net.n_load
     todev = lambda a: torch.as_tensor(a, dtype=torch.float64, device=dev)
     # two perturbed iterates, alternated step by step
-    xs = [todev(pt.x), todev(synth.perturb(WORKLOAD["seed"], pt.x, 0))]
-    lam, sx, dv = todev(pt.lam), todev(pt.sigma_x), todev(pt.dvec)
+    xs_whole = [pt.x, synth.perturb(WORKLOAD["seed"], pt.x, 0)]
+    if plan:
+        local = lambda a, what, k: shard.scatter(plan, what, a, np.zeros(k))
+        xs = [todev(local(x, "x", n)) for x in xs_whole]
+        lam, sx, dv = todev(local(pt.lam, "rows", m)), todev(local(pt.sigma_x, "x", n)), todev(local(pt.dvec, "rows", m))
+    else:
+        xs = [todev(x) for x in xs_whole]
+        lam, sx, dv = todev(pt.lam), todev(pt.sigma_x), todev(pt.dvec)
     out = h.new_outputs()
     launches = h.launch_count()
-    alg = algorithmic_bytes(n, m, h.nnz_jac, h.nnz_hess, h.nnz_kkt, D, T)
+    W = (span[1] - span[0]) if span else T   # periods this rank evaluates
+    whole = mpopf.shard_plan(inst.net, T, 0, T)  # sizes of the whole-horizon model (host only)
+    alg_whole = algorithmic_bytes(whole["n"], whole["m"], whole["nnz_jac"], whole["nnz_hess"], whole["nnz_kkt"], D, T)
+
+    def step(k):
+        x = xs[k % 2]
+        if plan:
+            shard.exchange_halos(plan, x, dv, rank, world)
+        h.sweep(x, lam, pt.sigma, sx, dv, pt.delta_w, out=out)
+        if plan:
+            shard.reduce_objective(out["f"])
 
     fp64_peak = fp64_gemm_peak(torch) if rank == 0 else None
+    probe_rate, _ = mpopf.fp64_issue_rate(16384)
 
     for k in range(args.warmup):
-        h.sweep(xs[k % 2], lam, pt.sigma, sx, dv, pt.delta_w, out=out)
+        step(k)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks = ClockSampler(local).start()
-    h.profile_start(args.steps * launches)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for k in range(args.steps):
-        h.sweep(xs[k % 2], lam, pt.sigma, sx, dv, pt.delta_w, out=out)
+        step(k)
     e1.record()
     torch.cuda.synchronize()
     clk = clocks.stop()
-    prof = h.profile_stop()
     if world > 1:
         torch.distributed.barrier()
     ms = e0.elapsed_time(e1)
     ms = max_over_ranks(ms, world, dev)
     ms_step = ms / args.steps
-    value = world * args.steps / (ms * 1e-3)
+    # whole-job sweeps per second: N replicas make N sweeps per step; N shards
+    # make one sweep of the whole horizon per step
+    value = (world if mode == "replicas" else 1) * args.steps / (ms * 1e-3)
+
+    # per-kernel times: a separate pass with a CUDA-event pair around every
+    # launch on the caller's stream (not inside the timed region)
+    h.profile_start(args.steps * launches)
+    for k in range(args.steps):
+        h.sweep(xs[k % 2], lam, pt.sigma, sx, dv, pt.delta_w, out=out)
+    torch.cuda.synchronize()
+    prof = h.profile_stop()
 
     # dominant kernel and its roofline
     top = max(prof, key=lambda k: prof[k][0])
     top_ms = prof[top][0] / max(prof[top][1], 1)
     roof = None
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    derived = fp64_issue_peak(sms, measured_peaks().get("sm_max_mhz") or SM_MAX_MHZ)
+    peak = probe_rate / 1e9
     if top == "branch":
-        ops = FP64_OPS_PER_BRANCH_PERIOD * T * inst.net.n_branch
+        ops = FP64_OPS_PER_BRANCH_PERIOD * W * inst.net.n_branch
         achieved = ops / (top_ms * 1e-3) / 1e9
-        sms = torch.cuda.get_device_properties(dev).multi_processor_count
-        peak = fp64_issue_peak(sms, measured_peaks().get("sm_max_mhz") or SM_MAX_MHZ)
         roof = {"bound": "alu", "kernel": "k_branch (branch x period)", "achieved": achieved, "peak": peak,
                 "unit": "Gop/s (FP64 fma/add/mul)", "frac": achieved / peak,
-                "traffic": ncu_traffic(), "ops_per_launch": ops, "avg_launch_ms": top_ms,
-                "peak_source": (f"derived: {FP64_PER_CYCLE_PER_SM} FP64 thread-instructions per cycle per SM x "
-                                f"{sms} SMs x max SM clock"),
+                "traffic": ncu_traffic(W), "ops_per_launch": ops, "avg_launch_ms": top_ms,
+                "peak_source": ("measured: the library's DFMA-chain probe (mpopf_fp64_issue_rate), "
+                                "FP64 thread-instructions per second, same run"),
+                "peak_derived": derived,
+                "peak_derived_source": (f"{FP64_PER_CYCLE_PER_SM} FP64 thread-instructions per cycle per SM x "
+                                        f"{sms} SMs x max SM clock"),
                 "peak_measured_dgemm": fp64_peak / 1e9 if fp64_peak else None,
                 "frac_of_measured_dgemm": achieved / (fp64_peak / 1e9) if fp64_peak else None}
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs")
-    gbs = alg / (ms_step * 1e-3) / 1e9
+    gbs = alg_whole / (ms_step * 1e-3) / 1e9 * (world if mode == "replicas" else 1)
+    floor_ms = fp64_ops_per_sweep(inst.net.n_bus, inst.net.n_branch, inst.net.n_gen, W) / probe_rate * 1e3
+    hbm = {"algorithmic_bytes_per_sweep": alg_whole, "gbs": gbs, "peak_gbs": hbm_peak,
+           "frac": gbs / hbm_peak if hbm_peak else None, "peak_source": "MEASURED_PEAKS.json",
+           "nominal_gbs": 7700.0, "frac_nominal": gbs / 7700.0}
+    if mode != "shards":
+        # the FP64 work alone bounds the sweep from below; at that floor the
+        # algorithmic bytes would move at this fraction of the HBM peak
+        hbm.update({"fp64_ops_per_sweep": fp64_ops_per_sweep(inst.net.n_bus, inst.net.n_branch, inst.net.n_gen, T),
+                    "fp64_floor_ms": floor_ms,
+                    "attainable_frac": (alg_whole / (floor_ms * 1e-3) / 1e9) / hbm_peak if hbm_peak else None,
+                    "frac_of_fp64_floor": floor_ms / ms_step})
 
+    par = {"single": "single", "replicas": f"replicas{world}", "shards": f"period-shards{world} (halo + f all-reduce)"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "strong" if mode == "shards" else "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"mpopf_sweep_10k_bus_T{T}", **WORKLOAD, "n_periods": T,
-                       "n": n, "m": m, "nnz_jac": h.nnz_jac, "nnz_hess": h.nnz_hess, "nnz_kkt": h.nnz_kkt,
-                       "parallelism": f"replicas{world}" if world > 1 else "single",
+                       "n": whole["n"], "m": whole["m"], "nnz_jac": whole["nnz_jac"],
+                       "nnz_hess": whole["nnz_hess"], "nnz_kkt": whole["nnz_kkt"],
+                       "parallelism": par[mode],
                        "l2": "inputs + outputs 2.7 GB per step > 126 MB L2; no flush",
                        "iterates": "two perturbed iterates alternated"},
-            "hbm": {"algorithmic_bytes_per_sweep": alg, "gbs": gbs, "peak_gbs": hbm_peak,
-                    "frac": gbs / hbm_peak if hbm_peak else None, "peak_source": "MEASURED_PEAKS.json",
-                    "nominal_gbs": 7700.0, "frac_nominal": gbs / 7700.0},
+            "hbm": hbm,
             "roofline": roof,
             "kernels_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1] > 0},
-            "kernels_note": ("CUDA events on the caller's stream; k_gen and k_fsum run on the handle's side "
-                             "stream, overlapped with k_bus, and are not timed per kernel (see the ncu launch "
-                             "list for their serialised durations)"),
+            "kernels_note": ("a separate pass after the timed region, CUDA events around every launch on the "
+                             "caller's stream; k_gen and k_fsum run on the handle's side stream, overlapped with "
+                             "k_bus, and are not timed per kernel (see the ncu launch list for their serialised "
+                             "durations)"),
             "clocks": clk,
             "gpu_launches": launches * args.steps,
             "setup": {"seconds": setup_s,
                       "what": ("mpopf_setup once per handle: layout, templates and incidence lists on the host, "
                                "the J / W / M patterns and bounds expanded on the GPU")}}
+    if plan:
+        line["shards"] = {"periods_per_rank": [b - a for a, b in shard.split(T, world)],
+                          "halo_doubles_each_way": plan["halo_len"] * plan["halo_blocks"],
+                          "exchange": "torch.distributed batch_isend_irecv (NCCL) before each sweep; "
+                                      "f summed by all_reduce after it"}
 
-    # end to end through the C-ABI with host buffers: every rank runs its own
-    # host-buffer sweeps at the same time (the ranks share the host's links)
-    pin = lambda k: torch.empty(k, dtype=torch.float64, pin_memory=True).numpy()
-    hx, hl, hs, hd = pin(n), pin(m), pin(n), pin(m)
-    hx[:], hl[:], hs[:], hd[:] = pt.x, pt.lam, pt.sigma_x, pt.dvec
-    hout = dict(f=pin(1), grad=pin(n), c=pin(m), jv=pin(h.nnz_jac), hv=pin(h.nnz_hess), kv=pin(h.nnz_kkt))
-    stream = torch.cuda.current_stream()
-    h.sweep_host(hx, hl, pt.sigma, hs, hd, pt.delta_w, hout, stream=stream)
-    ke = max(1, args.e2e_steps)
-    if world > 1:
-        torch.distributed.barrier()
-    t0 = time.perf_counter()
-    for _ in range(ke):
-        h.sweep_host(hx, hl, pt.sigma, hs, hd, pt.delta_w, hout, stream=stream)
-    el = max_over_ranks(time.perf_counter() - t0, world, dev)
-    h2d, d2h = 8 * (2 * n + 2 * m), 8 * (1 + n + m + h.nnz_jac + h.nnz_hess + h.nnz_kkt)
-    e2e = {"value": world * ke / el, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-           "d2h_gbs": world * d2h * ke / el / 1e9, "h2d_gbs": world * h2d * ke / el / 1e9,
-           "steps": ke, "ranks": world,
-           "api": "mpopf_sweep_host (pinned host buffers, all inputs in, all outputs out; every rank)"}
-    del hx, hl, hs, hd, hout
-    e2e.update(link_rates(torch))
-    if e2e.get("link_d2h_gbs"):
-        e2e["d2h_frac_of_link"] = (e2e["d2h_gbs"] / world) / e2e["link_d2h_gbs"]
+    line["e2e"] = e2e_host(torch, args, world, rank, dev, h, plan, pt, inst, mode)
     if rank == 0:
-        line["e2e"] = e2e
         if world == 1:
             line["cpu_baseline"] = cpu_baseline(inst, pt)
             line["adjoint"] = adjoint_comparison(torch)
@@ -913,6 +965,67 @@ def run_ours(args, world, rank, local):
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def e2e_host(torch, args, world, rank, dev, h, plan, pt, inst, mode):
+    """End to end through the public API with host buffers: every step copies
+    that step's inputs in from pinned host memory and all outputs back.  One
+    rank (or replicas): mpopf_sweep_host (pipelined copies inside the call).
+    Shards: each rank copies its local inputs in, exchanges the halo, sweeps
+    its shard (mpopf_sweep), sums f and copies its owned outputs out."""
+    from paper_2405_14032_b300 import shard
+    pin = lambda k: torch.empty(k, dtype=torch.float64, pin_memory=True)
+    n, m = h.n, h.m
+    stream = torch.cuda.current_stream()
+    hout = dict(f=pin(1), grad=pin(n), c=pin(m), jv=pin(h.nnz_jac), hv=pin(h.nnz_hess), kv=pin(h.nnz_kkt))
+    if plan is None:
+        hx, hl, hs, hd = pin(n), pin(m), pin(n), pin(m)
+        hx.numpy()[:], hl.numpy()[:], hs.numpy()[:], hd.numpy()[:] = pt.x, pt.lam, pt.sigma_x, pt.dvec
+        hostnp = {k: v.numpy() for k, v in hout.items()}
+        run = lambda: h.sweep_host(hx.numpy(), hl.numpy(), pt.sigma, hs.numpy(), hd.numpy(), pt.delta_w, hostnp,
+                                   stream=stream)
+        h2d, d2h = 8 * (2 * n + 2 * m), 8 * (1 + n + m + h.nnz_jac + h.nnz_hess + h.nnz_kkt)
+        api = "mpopf_sweep_host (pinned host buffers, all inputs in, all outputs out; every rank)"
+    else:
+        loc = lambda a, what, k: torch.from_numpy(shard.scatter(plan, what, a, np.zeros(k)))
+        hx, hl, hs, hd = (loc(pt.x, "x", n), loc(pt.lam, "rows", m), loc(pt.sigma_x, "x", n),
+                          loc(pt.dvec, "rows", m))
+        hx, hl, hs, hd = (t.pin_memory() for t in (hx, hl, hs, hd))
+        dx, dl, ds, dd = (torch.empty(t.numel(), dtype=torch.float64, device=dev) for t in (hx, hl, hs, hd))
+        dout = h.new_outputs()
+
+        def run():
+            for d_, h_ in ((dx, hx), (dl, hl), (ds, hs), (dd, hd)):
+                d_.copy_(h_, non_blocking=True)
+            shard.exchange_halos(plan, dx, dd, rank, world)
+            h.sweep(dx, dl, pt.sigma, ds, dd, pt.delta_w, out=dout)
+            shard.reduce_objective(dout["f"])
+            for k, v in dout.items():
+                hout[k].copy_(v, non_blocking=True)
+            torch.cuda.synchronize()
+        h2d = 8 * (2 * n + 2 * m)
+        d2h = 8 * (1 + n + m + h.nnz_jac + h.nnz_hess + h.nnz_kkt)
+        api = ("shard handle: pinned host -> device copies of the shard's inputs, halo exchange, mpopf_sweep, "
+               "f all-reduce, device -> pinned host copies of its outputs; every rank")
+    run()
+    torch.cuda.synchronize()
+    ke = max(1, args.e2e_steps)
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        run()
+    el = max_over_ranks(time.perf_counter() - t0, world, dev)
+    per = world if mode == "replicas" else 1
+    e2e = {"value": per * ke / el, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+           "d2h_gbs": d2h * ke / el / 1e9, "h2d_gbs": h2d * ke / el / 1e9,
+           "bytes_note": "per rank" if world > 1 else "",
+           "steps": ke, "ranks": world, "api": api}
+    del hout
+    e2e.update(link_rates(torch))
+    if e2e.get("link_d2h_gbs"):
+        e2e["d2h_frac_of_link"] = e2e["d2h_gbs"] / e2e["link_d2h_gbs"]
+    return e2e
 
 
 def main():

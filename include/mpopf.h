@@ -140,6 +140,78 @@ typedef struct mpopf_handle mpopf_handle;
 int mpopf_setup(const mpopf_network *net, int32_t n_periods, const double *pd, const double *qd,
                 mpopf_handle **out, mpopf_pattern *pat);
 
+/* Period shards: the horizon split into contiguous blocks of periods, one per
+ * GPU (Sec. II: only the ramp rows, Eq. 1k, couple periods).
+ *
+ * A shard owning periods [t0, t1) of a T-period model is the local model of
+ * periods [t0 - h0, t1 + h1), h0 = (t0 > 0), h1 = (t1 < T): one halo period
+ * before and / or after the owned ones.  Its handle (mpopf_shard_setup)
+ * evaluates the owned periods only, with the same kernels and arithmetic as a
+ * whole-horizon handle, so every owned output entry equals the whole-horizon
+ * model's entry bit for bit, except f, which is the sum over the owned
+ * periods only (the whole f is the sum over the shards, a scalar
+ * all-reduce).  Inputs and outputs of a shard handle use the local model's
+ * layout (T_loc = t1 - t0 + h0 + h1 periods; sizes in the layout below);
+ * entries of the halo periods are inputs only (two of them are read, see
+ * below) and are never written.  The handle's pattern (mpopf_pattern) is the
+ * local model's.  Only mpopf_eval, the callbacks built on it, mpopf_sweep,
+ * the schedule, launch-count and profiling calls, mpopf_set_loads and
+ * mpopf_get_pattern accept a shard handle; every other entry point returns
+ * MPOPF_ERR_ARG for it.
+ *
+ * The halo exchange of one evaluation (before it; G doubles per block, block
+ * 0 = P, block 1 = Q with the reactive ramp K11):
+ *   x[x_recv[b] ..] <- the previous shard's x[x_send[b] ..]:  pg (qg) of
+ *     period t0 - 1, read by the ramp rows at t0;
+ *   dvec[d_recv[b] ..] <- the next shard's dvec[d_send[b] ..]:  D of the ramp
+ *     rows at t1, the last term of the pg (qg) diagonals of M at t1 - 1 (the
+ *     (pg[t1-1], pg[t1-1]) contribution D * 1 * 1 of those rows);
+ * an offset is -1 where the neighbour does not exist.  Nothing else crosses a
+ * shard boundary.
+ *
+ * Ranges map local entries to the whole-horizon model's (count entries from
+ * `local` in the shard's array correspond to count entries from `global` in
+ * the whole model's array): MPOPF_RANGE_X the owned variables (x, grad,
+ * sigma_x), MPOPF_RANGE_XALL every local variable, halo periods included (for
+ * mapping pattern columns), MPOPF_RANGE_ROWS the owned rows (c, lam, dvec),
+ * MPOPF_RANGE_JAC / _HESS / _KKT the owned values of J, W and M. */
+enum {
+  MPOPF_RANGE_X = 0,
+  MPOPF_RANGE_XALL = 1,
+  MPOPF_RANGE_ROWS = 2,
+  MPOPF_RANGE_JAC = 3,
+  MPOPF_RANGE_HESS = 4,
+  MPOPF_RANGE_KKT = 5
+};
+#define MPOPF_SHARD_MAX_RANGES 64
+typedef struct {
+  int32_t what;     /* MPOPF_RANGE_* */
+  int32_t reserved; /* 0 */
+  int64_t local, global, count;
+} mpopf_range;
+typedef struct {
+  int32_t n_periods, t0, t1;       /* whole horizon T; owned periods [t0, t1) */
+  int32_t local_periods;           /* T_loc */
+  int32_t own0, own1;              /* owned periods in local numbering: [h0, h0 + t1 - t0) */
+  int32_t halo_len, halo_blocks;   /* G; 1, or 2 with the reactive ramp */
+  int64_t n, m, nnz_jac, nnz_hess, nnz_kkt;  /* sizes of the local model's arrays */
+  int64_t x_recv[2], x_send[2];    /* halo offsets into the local x (-1: none) */
+  int64_t d_recv[2], d_send[2];    /* halo offsets into the local dvec (-1: none) */
+  int32_t n_ranges;
+  int32_t reserved;
+  mpopf_range ranges[MPOPF_SHARD_MAX_RANGES];
+} mpopf_shard_layout;
+
+/* Layout of the shard [t0, t1) of a T-period model: host computation only (no
+ * device needed), validates the network like mpopf_setup.  MPOPF_ERR_ARG
+ * unless 0 <= t0 < t1 <= n_periods. */
+int mpopf_shard_plan(const mpopf_network *net, int32_t n_periods, int32_t t0, int32_t t1, mpopf_shard_layout *plan);
+/* Handle of the shard [t0, t1): like mpopf_setup for the local model; pd, qd
+ * are the loads of the WHOLE horizon (host [n_periods][D]), of which the
+ * local periods' rows are copied. */
+int mpopf_shard_setup(const mpopf_network *net, int32_t n_periods, int32_t t0, int32_t t1, const double *pd,
+                      const double *qd, mpopf_handle **out, mpopf_pattern *pat);
+
 /* Pattern of an existing handle. */
 int mpopf_get_pattern(const mpopf_handle *h, mpopf_pattern *pat);
 
@@ -371,6 +443,27 @@ void mpopf_batch_destroy(mpopf_batch *b);
 /* Number of kernel launches one mpopf_eval call with these output bits makes. */
 int mpopf_launch_count(const mpopf_handle *h, unsigned outputs);
 
+/* Launch schedule of the evaluation calls of a handle (a performance setting;
+ * the outputs are the same bit for bit under every schedule).
+ * chunk_periods = 0: one branch x period launch, then one bus x period launch
+ * on `stream` (the generator work on the handle's side stream).  P > 0: the
+ * horizon is cut into chunks of P periods (at most 64 chunks; P grows when T
+ * needs more); the branch kernel of each chunk runs on `stream` and the bus
+ * kernel of the same chunk on a second internal stream, behind an event
+ * recorded after that branch launch, so the bus work of one chunk overlaps
+ * the branch work of the next while the chunk's intermediate per-branch
+ * records are still in L2.  flags: MPOPF_SCHED_BUS_PRIORITY puts the second
+ * stream at the device's highest stream priority (its CTAs are dispatched
+ * first as SMs free up); MPOPF_SCHED_GEN_FIRST forks the generator work
+ * before the first branch chunk instead of after the last.  Both streams join
+ * `stream` before the call returns, so work enqueued on `stream` afterwards
+ * sees every output (under stream capture they are parallel graph branches).
+ * Per-kernel profiling (mpopf_profile_start) times unchunked launches.
+ * MPOPF_ERR_ARG for P < 0 or unknown flags. */
+enum { MPOPF_SCHED_BUS_PRIORITY = 1, MPOPF_SCHED_GEN_FIRST = 2 };
+int mpopf_set_sweep_schedule(mpopf_handle *h, int32_t chunk_periods, int32_t flags);
+int mpopf_get_sweep_schedule(const mpopf_handle *h, int32_t *chunk_periods, int32_t *flags);
+
 /* Condensed-matrix assembly that allocates nothing (the paper has no
  * counterpart: this is a deployment variant of mpopf_assemble_kkt).  For
  * callers that cannot call cudaMalloc once they are running: processes that
@@ -391,6 +484,16 @@ int mpopf_launch_count(const mpopf_handle *h, unsigned outputs);
  * overlap on the GPU race on it. */
 int mpopf_assemble_kkt_noalloc(mpopf_handle *h, const double *x, const double *lam, double sigma,
                                const double *sigma_x, const double *dvec, double delta_w, double *kv, void *stream);
+
+/* FP64 issue-rate probe (instrumentation for the roofline of the FP64-bound
+ * kernels, not part of the paper's method): a kernel of eight independent
+ * chains of fused multiply-adds per thread, eight 256-thread CTAs per SM, each
+ * thread running `iters` iterations (8 fma each) on the current device.  One
+ * warm-up launch, then the best of three timed with CUDA events.  Writes
+ * *inst_per_s = FP64 thread-instructions (fma) per second and, if not NULL,
+ * *seconds = the best launch's duration.  Allocates (and frees) a small output
+ * buffer and a stream; synchronous.  MPOPF_ERR_ARG for iters < 1. */
+int mpopf_fp64_issue_rate(int32_t iters, double *inst_per_s, double *seconds);
 
 /* Per-kernel timing (instrumentation for benchmarks, not part of the paper's
  * method).  mpopf_profile_start creates 2 * max_launches CUDA events; every

@@ -363,6 +363,7 @@ extern "C" {
 int mpopf_vjp_jv(mpopf_handle *h, const double *x, const double *jv, const double *y, double *gx, double *gpd,
                  double *gqd, void *stream) {
   if (!h || !x || !y || !gx) return fail(MPOPF_ERR_ARG, "mpopf_vjp: NULL argument");
+  if (mpopf::is_shard(h->d)) return fail(MPOPF_ERR_ARG, "mpopf_vjp: not available on a period shard");
   if ((gpd == nullptr) != (gqd == nullptr)) return fail(MPOPF_ERR_ARG, "mpopf_vjp: give both gpd and gqd or neither");
   const Dev &d = h->d;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -384,6 +385,7 @@ int mpopf_vjp(mpopf_handle *h, const double *x, const double *y, double *gx, dou
 int mpopf_jvp_jv(mpopf_handle *h, const double *x, const double *jv, const double *v, const double *dpd,
                  const double *dqd, double *jv_out, void *stream) {
   if (!h || !x || !v || !jv_out) return fail(MPOPF_ERR_ARG, "mpopf_jvp: NULL argument");
+  if (mpopf::is_shard(h->d)) return fail(MPOPF_ERR_ARG, "mpopf_jvp: not available on a period shard");
   if ((dpd == nullptr) != (dqd == nullptr)) return fail(MPOPF_ERR_ARG, "mpopf_jvp: give both dpd and dqd or neither");
   const Dev &d = h->d;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -406,6 +408,7 @@ int mpopf_jvp(mpopf_handle *h, const double *x, const double *v, const double *d
 int mpopf_hvp(mpopf_handle *h, const double *x, const double *lam, double sigma, const double *v, double *hv,
               void *stream) {
   if (!h || !x || !lam || !v || !hv) return fail(MPOPF_ERR_ARG, "mpopf_hvp: NULL argument");
+  if (mpopf::is_shard(h->d)) return fail(MPOPF_ERR_ARG, "mpopf_hvp: not available on a period shard");
   const Dev &d = h->d;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (d.L > 0) k_hvp_branch<<<grid_for((int64_t)d.T * d.L), kAdjBlock, 0, s>>>(d, x, lam, v, hv);

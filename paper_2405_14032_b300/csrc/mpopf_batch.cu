@@ -240,6 +240,8 @@ int mpopf_batch_create(mpopf_handle *const *hs, int32_t k, mpopf_batch **out) {
   *out = nullptr;
   for (int32_t i = 0; i < k; ++i)
     if (!hs[i]) return fail(MPOPF_ERR_ARG, "mpopf_batch_create: NULL handle");
+  for (int32_t i = 0; i < k; ++i)
+    if (mpopf::is_shard(hs[i]->d)) return fail(MPOPF_ERR_ARG, "mpopf_batch_create: not available on a period shard");
   mpopf_batch *b = new mpopf_batch();
   b->K = k;
   b->hs.assign(hs, hs + k);

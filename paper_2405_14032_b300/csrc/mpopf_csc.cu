@@ -264,6 +264,7 @@ extern "C" {
 
 int mpopf_csc_pattern(mpopf_handle *h, int32_t which, mpopf_csc *out) {
   if (!h || !out) return fail(MPOPF_ERR_ARG, "mpopf_csc_pattern: NULL argument");
+  if (mpopf::is_shard(h->d)) return fail(MPOPF_ERR_ARG, "mpopf_csc_pattern: not available on a period shard");
   if (which != MPOPF_CSC_JAC && which != MPOPF_CSC_HESS)
     return fail(MPOPF_ERR_ARG, "mpopf_csc_pattern: which must be MPOPF_CSC_JAC or MPOPF_CSC_HESS");
   if (!h->csc[which].built) {
@@ -279,6 +280,7 @@ int mpopf_csc_pattern(mpopf_handle *h, int32_t which, mpopf_csc *out) {
 
 int mpopf_coo_to_csc(mpopf_handle *h, int32_t which, const double *coo_vals, double *csc_vals, void *stream) {
   if (!h || !coo_vals || !csc_vals) return fail(MPOPF_ERR_ARG, "mpopf_coo_to_csc: NULL argument");
+  if (mpopf::is_shard(h->d)) return fail(MPOPF_ERR_ARG, "mpopf_coo_to_csc: not available on a period shard");
   if (which != MPOPF_CSC_JAC && which != MPOPF_CSC_HESS)
     return fail(MPOPF_ERR_ARG, "mpopf_coo_to_csc: which must be MPOPF_CSC_JAC or MPOPF_CSC_HESS");
   const CscState &c = h->csc[which];

@@ -83,6 +83,7 @@ int mpopf_sweep_host(mpopf_handle *h, const double *x, const double *lam, double
                      const double *dvec, double delta_w, double *f, double *grad, double *c, double *jv, double *hv,
                      double *kv, void *stream) {
   if (!h) return fail(MPOPF_ERR_ARG, "mpopf_sweep_host: NULL handle");
+  if (mpopf::is_shard(h->d)) return fail(MPOPF_ERR_ARG, "mpopf_sweep_host: not available on a period shard");
   if (!x || !lam || !sigma_x || !dvec || !f || !grad || !c || !jv || !hv || !kv)
     return fail(MPOPF_ERR_ARG, "mpopf_sweep_host: NULL buffer");
   const Dev &d = h->d;

@@ -77,7 +77,14 @@ struct Dev {
   // The branch kernel's per-branch integers packed for 16-byte loads
   // (structure of quads, so a warp's load stays one contiguous run), [BRP_COUNT][L].
   const int4 *brp;
+  // Owned periods [w0, w1) that the evaluation launches cover: [0, T) for a
+  // model of its own; a period shard's local model has a halo period before
+  // (w0 = 1) and / or after (w1 = T - 1) the periods it owns.
+  int32_t w0, w1;
 };
+
+// A period shard's handle evaluates only the periods it owns.
+inline bool is_shard(const Dev &d) { return d.w0 != 0 || d.w1 != d.T; }
 
 // Quads of brp: (f, t, slot of the from end, slot of the to end), (M row
 // offsets of p_f, p_t, q_f, q_t inside a period block), (arc ranks of the from
@@ -99,9 +106,21 @@ struct Prof {
 // evaluation runs on the side stream, forked from and joined back into the
 // caller's stream, alongside the branch and bus work (it reads none of their
 // outputs and writes disjoint ranges).
+// Period chunks (chunk > 0): the branch kernel runs chunk by chunk on the
+// caller's stream and the bus kernel of each chunk on a second stream `bus`,
+// after an event recorded behind that chunk's branch launch, so that the bus
+// work of chunk c overlaps the branch work of chunk c + 1 while the chunk's
+// incidence records are still in L2.
+constexpr int kMaxChunks = 64;
+enum { SCHED_BUS_PRIORITY = MPOPF_SCHED_BUS_PRIORITY, SCHED_GEN_FIRST = MPOPF_SCHED_GEN_FIRST };
 struct Fork {
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaStream_t bus = nullptr;          // bus kernels of a chunked evaluation
+  cudaEvent_t ev_bus = nullptr;        // end of the bus stream's work
+  cudaEvent_t ev_chunk[kMaxChunks] = {};
+  int32_t chunk = 0;                   // periods per chunk; 0: one launch per kernel
+  int32_t flags = 0;                   // SCHED_*: bus stream at the highest priority; generator work forked first
 };
 
 // Kernel launchers (mpopf_kernels.cu).  With fork == nullptr every launch goes
@@ -110,7 +129,10 @@ cudaError_t launch_eval(const Dev &d, unsigned outputs, const double *x, const d
                         const double *sx, const double *dv, double dw, double *f, double *grad, double *c,
                         double *jv, double *hv, double *kv, cudaStream_t s, Prof *prof,
                         const Fork *fork = nullptr);
-int eval_launch_count(const Dev &d, unsigned outputs);
+int eval_launch_count(const Dev &d, unsigned outputs, const Fork *fork = nullptr);
+// Creates (or re-creates, for a new priority) the bus stream and the chunk
+// events of a fork (mpopf_kernels.cu).
+cudaError_t fork_bus_stream(Fork *fork, bool high_priority);
 // Pattern expansion (mpopf_setup.cu).
 cudaError_t launch_patterns(const Dev &d, int32_t *jrow, int32_t *jcol, int32_t *hrow, int32_t *hcol,
                             int64_t *krowptr, int32_t *kcol, double *xl, double *xu, double *gl, double *gu,

@@ -163,6 +163,7 @@ int mpopf_ipm_prepare(mpopf_handle *h, const double *x, const double *s, const d
                       double *sigma_x, double *dvec, double *cvec, double *recip, void *stream) {
   if (!h || !x || !s || !zl_x || !zu_x || !zl_s || !zu_s || !sigma_x || !dvec || !cvec || !recip)
     return fail(MPOPF_ERR_ARG, "mpopf_ipm_prepare: NULL argument");
+  if (mpopf::is_shard(h->d)) return fail(MPOPF_ERR_ARG, "mpopf_ipm_prepare: not available on a period shard");
   const Dev &d = h->d;
   const mpopf_pattern &P = h->pat;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -186,6 +187,7 @@ int mpopf_ipm_rhs(mpopf_handle *h, const double *x, const double *jv, const doub
                   double mu, double *rhs, void *stream) {
   if (!h || !x || !s || !y || !grad || !c || !recip || !dvec || !cvec || !rhs)
     return fail(MPOPF_ERR_ARG, "mpopf_ipm_rhs: NULL argument");
+  if (mpopf::is_shard(h->d)) return fail(MPOPF_ERR_ARG, "mpopf_ipm_rhs: not available on a period shard");
   const Dev &d = h->d;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int64_t n = d.n, m = d.m;
@@ -208,6 +210,7 @@ int mpopf_ipm_recover(mpopf_handle *h, const double *x, const double *jv, const 
   if (!h || !x || !s || !y || !zl_x || !zu_x || !zl_s || !zu_s || !c || !recip || !cvec || !dx || !ds || !dy ||
       !dzl_x || !dzu_x || !dzl_s || !dzu_s)
     return fail(MPOPF_ERR_ARG, "mpopf_ipm_recover: NULL argument");
+  if (mpopf::is_shard(h->d)) return fail(MPOPF_ERR_ARG, "mpopf_ipm_recover: not available on a period shard");
   const Dev &d = h->d;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int64_t n = d.n, m = d.m;

@@ -483,14 +483,15 @@ __global__ void __launch_bounds__(MPOPF_BUS_BLOCK) k_bus(Dev d, unsigned rt, con
 // blk = index of the CTA-sized tile, where the tile's partial sum is stored.
 // ---------------------------------------------------------------------------
 template <unsigned MASK>
-__device__ __forceinline__ void gen_body(const Dev &d, int32_t tg, int32_t blk, unsigned rt,
+__device__ __forceinline__ void gen_body(const Dev &d, int32_t tg, int32_t end, int32_t blk, unsigned rt,
                                          const double *__restrict__ x, double sigma, const double *__restrict__ sx,
                                          const double *__restrict__ dv, double dw, double *__restrict__ grad,
                                          double *__restrict__ c, double *__restrict__ jv, double *__restrict__ hv,
                                          double *__restrict__ kv) {
+  // tg: element t G + g; elements at or past `end` only add 0 to the tile sum
   const unsigned mk = eff<MASK>(rt);
   const int32_t G = d.G;
-  const bool live = tg < d.T * G;
+  const bool live = tg < end;
   const int32_t t = live ? tg / G : 0, g = live ? tg - t * G : 0;
   double pg = 0.0;
   if (live) pg = __ldg(x + d.x_pg + tg);
@@ -564,14 +565,16 @@ __device__ __forceinline__ void gen_body(const Dev &d, int32_t tg, int32_t blk, 
   qr[k] = qdiag;
 }
 
+// Elements [first, end) of the generator x period range (t G + g); tile k's
+// partial objective goes to fpart[k].
 template <unsigned MASK>
 __global__ void __launch_bounds__(kBlock) k_gen(Dev d, unsigned rt, const double *__restrict__ x, double sigma,
                                                 const double *__restrict__ sx, const double *__restrict__ dv, double dw,
                                                 double *__restrict__ grad, double *__restrict__ c,
                                                 double *__restrict__ jv, double *__restrict__ hv,
-                                                double *__restrict__ kv) {
-  gen_body<MASK>(d, (int32_t)(blockIdx.x * blockDim.x + threadIdx.x), (int32_t)blockIdx.x, rt, x, sigma, sx, dv, dw,
-                 grad, c, jv, hv, kv);
+                                                double *__restrict__ kv, int32_t first, int32_t end) {
+  gen_body<MASK>(d, first + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x), end, (int32_t)blockIdx.x, rt, x, sigma,
+                 sx, dv, dw, grad, c, jv, hv, kv);
 }
 
 // Objective: fixed-order reduction of the per-tile partial sums by one CTA of
@@ -620,13 +623,16 @@ template <unsigned MASK>
 void launch_gen_part(const Dev &d, unsigned rt, unsigned mk, const double *x, double sigma, const double *sx,
                      const double *dv, double dw, double *f, double *grad, double *c, double *jv, double *hv,
                      double *kv, cudaStream_t g, Prof *prof) {
+  // the owned periods' elements; the objective sums exactly the tiles launched
+  const int32_t first = d.w0 * d.G, end = d.w1 * d.G;
+  const unsigned tiles = grid_for((int64_t)end - first);
   if (mk && d.G > 0) {
     Timed tm(prof, g, KIND_GEN);
-    k_gen<MASK><<<grid_for((int64_t)d.T * d.G), kBlock, 0, g>>>(d, rt, x, sigma, sx, dv, dw, grad, c, jv, hv, kv);
+    k_gen<MASK><<<tiles, kBlock, 0, g>>>(d, rt, x, sigma, sx, dv, dw, grad, c, jv, hv, kv, first, end);
   }
   if (mk & MPOPF_OUT_OBJ) {
     Timed tm(prof, g, KIND_FSUM);
-    k_fsum<<<1, kBlock, 0, g>>>(d.fpart, d.G > 0 ? d.fpart_n : 0, f);
+    k_fsum<<<1, kBlock, 0, g>>>(d.fpart, d.G > 0 ? (int32_t)tiles : 0, f);
   }
 }
 
@@ -637,6 +643,61 @@ void launch_gen_part(const Dev &d, unsigned rt, unsigned mk, const double *x, do
 // shared the SMs with the dominant kernel instead).  The side-stream
 // launches are not bracketed by profiling events: their durations would
 // include the wait for SMs held by the bus kernel.
+// Number of period chunks of a chunked evaluation (0: not chunked).  At most
+// kMaxChunks; the chunk length grows when the horizon needs more.
+int chunk_count(const Dev &d, const Fork *fork, int32_t *per) {
+  const int32_t W = d.w1 - d.w0;  // owned periods
+  if (!fork || !fork->bus || fork->chunk <= 0 || d.L == 0 || W <= fork->chunk) return 0;
+  int32_t P = fork->chunk;
+  if ((W + P - 1) / P > kMaxChunks) P = (W + kMaxChunks - 1) / kMaxChunks;
+  *per = P;
+  return (W + P - 1) / P;
+}
+
+// Chunked evaluation: the branch kernel of each chunk of periods on s, the bus
+// kernel of that chunk on the fork's bus stream behind an event recorded after
+// it, the generator work on the side stream (forked before the first branch
+// chunk or after the last); both streams join s at the end.  Every element is
+// computed by the same code as in launch_all, so the outputs are the same bit
+// for bit.
+template <unsigned MASK>
+cudaError_t launch_chunked(const Dev &d, unsigned rt, unsigned mk, const double *x, const double *lam, double sigma,
+                           const double *sx, const double *dv, double dw, double *f, double *grad, double *c,
+                           double *jv, double *hv, double *kv, cudaStream_t s, const Fork *fork, int32_t P,
+                           int nch, bool side) {
+  cudaError_t e = cudaEventRecord(fork->ev_fork, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(fork->bus, fork->ev_fork, 0);
+  const bool gen_first = fork->flags & SCHED_GEN_FIRST;
+  if (e == cudaSuccess && side && gen_first) {
+    e = cudaStreamWaitEvent(fork->side, fork->ev_fork, 0);
+    if (e == cudaSuccess) launch_gen_part<MASK>(d, rt, mk, x, sigma, sx, dv, dw, f, grad, c, jv, hv, kv, fork->side, nullptr);
+  }
+  for (int k = 0; k < nch && e == cudaSuccess; ++k) {
+    const int32_t t0 = d.w0 + k * P, t1 = std::min(d.w1, t0 + P);
+    const int32_t bf = t0 * d.L, be = t1 * d.L;
+    k_branch<MASK><<<(unsigned)((be - bf + MPOPF_BRANCH_BLOCK - 1) / MPOPF_BRANCH_BLOCK), MPOPF_BRANCH_BLOCK, 0,
+                     s>>>(d, rt, x, lam, sx, dv, dw, grad, c, jv, hv, kv, bf, be);
+    e = cudaEventRecord(fork->ev_chunk[k], s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(fork->bus, fork->ev_chunk[k], 0);
+    if (e != cudaSuccess) break;
+    const int32_t nf = t0 * d.N, ne = t1 * d.N;
+    k_bus<MASK><<<(unsigned)((ne - nf + MPOPF_BUS_BLOCK - 1) / MPOPF_BUS_BLOCK), MPOPF_BUS_BLOCK, 0, fork->bus>>>(
+        d, rt, x, lam, sx, dv, dw, grad, c, jv, hv, kv, nf, ne);
+  }
+  if (e == cudaSuccess && side && !gen_first) {
+    e = cudaStreamWaitEvent(fork->side, fork->ev_chunk[nch - 1], 0);
+    if (e == cudaSuccess) launch_gen_part<MASK>(d, rt, mk, x, sigma, sx, dv, dw, f, grad, c, jv, hv, kv, fork->side, nullptr);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(fork->ev_bus, fork->bus);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, fork->ev_bus, 0);
+  if (e == cudaSuccess && side) {
+    e = cudaEventRecord(fork->ev_join, fork->side);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, fork->ev_join, 0);
+  }
+  if (e == cudaSuccess && !side) launch_gen_part<MASK>(d, rt, mk, x, sigma, sx, dv, dw, f, grad, c, jv, hv, kv, s, nullptr);
+  return e;
+}
+
 template <unsigned MASK>
 cudaError_t launch_all(const Dev &d, unsigned rt, const double *x, const double *lam, double sigma, const double *sx,
                        const double *dv, double dw, double *f, double *grad, double *c, double *jv, double *hv,
@@ -644,10 +705,16 @@ cudaError_t launch_all(const Dev &d, unsigned rt, const double *x, const double 
   const unsigned mk = MASK ? MASK : rt;
   const unsigned rest = MPOPF_OUT_GRAD | MPOPF_OUT_CONS | MPOPF_OUT_JAC | MPOPF_OUT_HESS | MPOPF_OUT_KKT;
   const bool side = fork && (mk & rest) && (mk && d.G > 0);  // both parts have work
+  int32_t P = 0;
+  const int nch = prof ? 0 : chunk_count(d, fork, &P);  // per-kernel profiling times whole launches
+  if (nch > 0 && (mk & rest))
+    return launch_chunked<MASK>(d, rt, mk, x, lam, sigma, sx, dv, dw, f, grad, c, jv, hv, kv, s, fork, P, nch, side);
+  const int32_t W = d.w1 - d.w0;  // owned periods
   if ((mk & rest) && d.L > 0) {
     Timed tm(prof, s, KIND_BRANCH);
-    k_branch<MASK><<<(unsigned)(((int64_t)d.T * d.L + MPOPF_BRANCH_BLOCK - 1) / MPOPF_BRANCH_BLOCK),
-                     MPOPF_BRANCH_BLOCK, 0, s>>>(d, rt, x, lam, sx, dv, dw, grad, c, jv, hv, kv, 0, d.T * d.L);
+    k_branch<MASK><<<(unsigned)(((int64_t)W * d.L + MPOPF_BRANCH_BLOCK - 1) / MPOPF_BRANCH_BLOCK),
+                     MPOPF_BRANCH_BLOCK, 0, s>>>(d, rt, x, lam, sx, dv, dw, grad, c, jv, hv, kv, d.w0 * d.L,
+                                                 d.w1 * d.L);
   }
   if (side) {
     cudaError_t e = cudaEventRecord(fork->ev_fork, s);
@@ -657,8 +724,8 @@ cudaError_t launch_all(const Dev &d, unsigned rt, const double *x, const double 
   }
   if (mk & rest) {
     Timed tm(prof, s, KIND_BUS);
-    k_bus<MASK><<<(unsigned)(((int64_t)d.T * d.N + MPOPF_BUS_BLOCK - 1) / MPOPF_BUS_BLOCK), MPOPF_BUS_BLOCK, 0, s>>>(d, rt, x, lam, sx, dv, dw, grad, c, jv, hv, kv, 0,
-                                                             d.T * d.N);
+    k_bus<MASK><<<(unsigned)(((int64_t)W * d.N + MPOPF_BUS_BLOCK - 1) / MPOPF_BUS_BLOCK), MPOPF_BUS_BLOCK, 0, s>>>(
+        d, rt, x, lam, sx, dv, dw, grad, c, jv, hv, kv, d.w0 * d.N, d.w1 * d.N);
   }
   if (side) {
     cudaError_t e = cudaEventRecord(fork->ev_join, fork->side);
@@ -773,8 +840,8 @@ __global__ void __launch_bounds__(batch_block(PHASE), batch_minb(PHASE))
       static_assert(B == kBlock, "the generator and objective trees need kBlock-thread CTAs");
       if (I.kind == ITEM_GEN) {
         for (int32_t c0 = I.first; c0 < end; c0 += kBlock)  // whole CTA: the objective tile tree
-          gen_body<MPOPF_OUT_ALL>(d, c0 + threadIdx.x < end ? c0 + threadIdx.x : d.T * d.G, c0 / kBlock,
-                                  MPOPF_OUT_ALL, b.x, b.sigma, b.sx, b.dv, b.dw, b.grad, b.c, b.jv, b.hv, b.kv);
+          gen_body<MPOPF_OUT_ALL>(d, c0 + threadIdx.x, end, c0 / kBlock, MPOPF_OUT_ALL, b.x, b.sigma, b.sx, b.dv,
+                                  b.dw, b.grad, b.c, b.jv, b.hv, b.kv);
       } else if (I.kind == ITEM_BUS) {
         // records from the same launch (phase 0) are read through L2; from
         // the earlier launch (phase 2), through the read-only path
@@ -818,7 +885,8 @@ void launch_gen_obj(const Dev &d, const double *x, double sigma, const double *s
                     double *f, double *grad, double *c, double *jv, double *hv, double *kv, cudaStream_t s) {
   constexpr unsigned A = MPOPF_OUT_ALL;
   if (d.G > 0)
-    k_gen<A><<<grid_for((int64_t)d.T * d.G), kBlock, 0, s>>>(d, A, x, sigma, sx, dv, dw, grad, c, jv, hv, kv);
+    k_gen<A><<<grid_for((int64_t)d.T * d.G), kBlock, 0, s>>>(d, A, x, sigma, sx, dv, dw, grad, c, jv, hv, kv, 0,
+                                                             d.T * d.G);
   k_fsum<<<1, kBlock, 0, s>>>(d.fpart, d.G > 0 ? d.fpart_n : 0, f);
 }
 
@@ -848,11 +916,28 @@ cudaError_t batch_kernel_node(cudaKernelNodeParams *p, void **args, int32_t grid
   return cudaSuccess;
 }
 
-int eval_launch_count(const Dev &d, unsigned mk) {
+cudaError_t fork_bus_stream(Fork *fork, bool high_priority) {
+  if (fork->bus) cudaStreamDestroy(fork->bus);
+  fork->bus = nullptr;
+  int lo = 0, hi = 0;
+  cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);  // hi: numerically lowest = highest priority
+  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&fork->bus, cudaStreamNonBlocking, high_priority ? hi : lo);
+  if (e == cudaSuccess && !fork->ev_bus) e = cudaEventCreateWithFlags(&fork->ev_bus, cudaEventDisableTiming);
+  for (int k = 0; k < kMaxChunks && e == cudaSuccess; ++k)
+    if (!fork->ev_chunk[k]) e = cudaEventCreateWithFlags(&fork->ev_chunk[k], cudaEventDisableTiming);
+  return e;
+}
+
+int eval_launch_count(const Dev &d, unsigned mk, const Fork *fork) {
   const unsigned rest = MPOPF_OUT_GRAD | MPOPF_OUT_CONS | MPOPF_OUT_JAC | MPOPF_OUT_HESS | MPOPF_OUT_KKT;
+  int32_t P = 0;
+  const int nch = chunk_count(d, fork, &P);
   int k = 0;
-  if ((mk & rest) && d.L > 0) ++k;
-  if (mk & rest) ++k;
+  if ((mk & rest) && nch > 0) k += 2 * nch;  // a branch and a bus launch per chunk
+  else {
+    if ((mk & rest) && d.L > 0) ++k;
+    if (mk & rest) ++k;
+  }
   if (mk && d.G > 0) ++k;
   if (mk & MPOPF_OUT_OBJ) ++k;
   return k;
@@ -893,7 +978,30 @@ extern "C" {
 
 int mpopf_launch_count(const mpopf_handle *h, unsigned outputs) {
   if (!h) return fail(MPOPF_ERR_ARG, "mpopf_launch_count: NULL handle");
-  return eval_launch_count(h->d, outputs & MPOPF_OUT_ALL);
+  return eval_launch_count(h->d, outputs & MPOPF_OUT_ALL, &h->fork);
+}
+
+int mpopf_set_sweep_schedule(mpopf_handle *h, int32_t chunk_periods, int32_t flags) {
+  if (!h) return fail(MPOPF_ERR_ARG, "mpopf_set_sweep_schedule: NULL handle");
+  if (chunk_periods < 0 || (flags & ~(SCHED_BUS_PRIORITY | SCHED_GEN_FIRST)))
+    return fail(MPOPF_ERR_ARG, "mpopf_set_sweep_schedule: bad argument");
+  if ((flags ^ h->fork.flags) & SCHED_BUS_PRIORITY) {
+    const cudaError_t e = fork_bus_stream(&h->fork, flags & SCHED_BUS_PRIORITY);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(MPOPF_ERR_CUDA, std::string("mpopf_set_sweep_schedule: ") + cudaGetErrorString(e));
+    }
+  }
+  h->fork.chunk = chunk_periods;
+  h->fork.flags = flags;
+  return MPOPF_OK;
+}
+
+int mpopf_get_sweep_schedule(const mpopf_handle *h, int32_t *chunk_periods, int32_t *flags) {
+  if (!h) return fail(MPOPF_ERR_ARG, "mpopf_get_sweep_schedule: NULL handle");
+  if (chunk_periods) *chunk_periods = h->fork.chunk;
+  if (flags) *flags = h->fork.flags;
+  return MPOPF_OK;
 }
 
 int mpopf_eval(mpopf_handle *h, unsigned outputs, const double *x, const double *lam, double sigma,

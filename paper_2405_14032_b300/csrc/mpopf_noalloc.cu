@@ -64,6 +64,7 @@ extern "C" int mpopf_assemble_kkt_noalloc(mpopf_handle *h, const double *x, cons
                                           const double *sigma_x, const double *dvec, double delta_w, double *kv,
                                           void *stream) {
   if (!h) return fail(MPOPF_ERR_ARG, "mpopf_assemble_kkt_noalloc: NULL handle");
+  if (mpopf::is_shard(h->d)) return fail(MPOPF_ERR_ARG, "mpopf_assemble_kkt_noalloc: not available on a period shard");
   if (!x || !lam || !sigma_x || !dvec || !kv) return fail(MPOPF_ERR_ARG, "mpopf_assemble_kkt_noalloc: NULL array");
   const long long need = 2LL * mpopf::kRec * h->d.T * h->d.L;
   if (need > kScratchDoubles)

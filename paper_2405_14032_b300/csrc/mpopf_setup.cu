@@ -271,6 +271,10 @@ void fork_destroy(mpopf_handle *h) {
   if (h->fork.ev_join) cudaEventDestroy(h->fork.ev_join);
   if (h->fork.ev_fork) cudaEventDestroy(h->fork.ev_fork);
   if (h->fork.side) cudaStreamDestroy(h->fork.side);
+  for (cudaEvent_t e : h->fork.ev_chunk)
+    if (e) cudaEventDestroy(e);
+  if (h->fork.ev_bus) cudaEventDestroy(h->fork.ev_bus);
+  if (h->fork.bus) cudaStreamDestroy(h->fork.bus);
   h->fork = Fork();
 }
 
@@ -288,60 +292,79 @@ int fail(int code, const std::string &msg) {
 
 }  // namespace
 
-extern "C" {
+namespace {
+// Everything setup computes on the host for a network over T periods:
+// validated sizes, per-branch constants, adjacency, incidence slots and the
+// per-period templates of the J and M patterns (period-invariant).
+struct HostModel {
+  int64_t N, L, G, D, T, n, m;
+  bool qramp;
+  std::vector<double> bc, m2gs, p2bs, mgs, bsv;
+  std::vector<uint8_t> sym;
+  std::vector<int32_t> bgen_ptr, bgen_idx, barc_ptr, barc_idx, bload_ptr, bload_idx, gen_rank, arc_rank;
+  std::vector<int32_t> bus_order, inc_ptr, inc_code, nbr_ptr, nbr_bus, nbr_grp, grp_code, bus_nd, bus_ndlt;
+  std::vector<int32_t> br_slot, slot_info, slot_next, arc_perm, jk8_off;
+  std::vector<int32_t> mo_va, mo_vm, mo_pg0, mo_pg1, mo_qg, mo_qg1, mo_p, mo_q;
+  int64_t jk8_per, mb_va, mb_vm, mb_pg0, mb_pg1, mb_qg, mb_qg1, mb_p, mb_q;
+};
 
-const char *mpopf_last_error(void) { return g_err.c_str(); }
-
-int mpopf_setup(const mpopf_network *net, int32_t n_periods, const double *pd, const double *qd, mpopf_handle **out,
-                mpopf_pattern *pat) {
-  if (!net || !out) return fail(MPOPF_ERR_ARG, "mpopf_setup: NULL network or output handle");
-  *out = nullptr;
+// Validation and the host model (no device work).  `who` prefixes messages.
+int host_model(const mpopf_network *net, int64_t n_periods, const char *who, HostModel *out) {
+  HostModel &hm = *out;
+  if (!net) return fail(MPOPF_ERR_ARG, std::string(who) + ": NULL network");
   const int64_t N = net->n_bus, L = net->n_branch, G = net->n_gen, D = net->n_load, T = n_periods;
-  if (N < 1 || L < 0 || G < 0 || D < 0) return fail(MPOPF_ERR_ARG, "mpopf_setup: need n_bus >= 1 and counts >= 0");
-  if (T < 1) return fail(MPOPF_ERR_ARG, "mpopf_setup: need n_periods >= 1");
-  if (net->ref_bus < 0 || net->ref_bus >= N) return fail(MPOPF_ERR_ARG, "mpopf_setup: ref_bus out of range");
+  if (N < 1 || L < 0 || G < 0 || D < 0) return fail(MPOPF_ERR_ARG, std::string(who) + ": need n_bus >= 1 and counts >= 0");
+  if (T < 1) return fail(MPOPF_ERR_ARG, std::string(who) + ": need n_periods >= 1");
+  if (net->ref_bus < 0 || net->ref_bus >= N) return fail(MPOPF_ERR_ARG, std::string(who) + ": ref_bus out of range");
   // Sizes first (before touching any array), so oversized problems fail cleanly.
   const int64_t n = T * (2 * N + 2 * G + 4 * L);
   const bool qramp = G > 0 && net->gen_qramp != nullptr;
   const int64_t m = T * (1 + 7 * L + 2 * N) + G * (T - 1) * (qramp ? 2 : 1);
   if (n >= ((int64_t)1 << 31) || m >= ((int64_t)1 << 31) || T * L >= ((int64_t)1 << 31))
-    return fail(MPOPF_ERR_SIZE, "mpopf_setup: n or m >= 2^31 (32-bit pattern indices)");
+    return fail(MPOPF_ERR_SIZE, std::string(who) + ": n or m >= 2^31 (32-bit pattern indices)");
   if (N > 0 && (!net->bus_gs || !net->bus_bs || !net->bus_vmin || !net->bus_vmax))
-    return fail(MPOPF_ERR_ARG, "mpopf_setup: NULL bus array");
+    return fail(MPOPF_ERR_ARG, std::string(who) + ": NULL bus array");
   if (L > 0 && (!net->br_f || !net->br_t || !net->br_r || !net->br_x || !net->br_b || !net->br_tap ||
                 !net->br_shift || !net->br_smax || !net->br_angmin || !net->br_angmax))
-    return fail(MPOPF_ERR_ARG, "mpopf_setup: NULL branch array");
+    return fail(MPOPF_ERR_ARG, std::string(who) + ": NULL branch array");
   if (G > 0 && (!net->gen_bus || !net->gen_c2 || !net->gen_c1 || !net->gen_c0 || !net->gen_pmin ||
                 !net->gen_pmax || !net->gen_qmin || !net->gen_qmax || !net->gen_ramp))
-    return fail(MPOPF_ERR_ARG, "mpopf_setup: NULL generator array");
-  if (D > 0 && (!net->load_bus || !pd || !qd)) return fail(MPOPF_ERR_ARG, "mpopf_setup: NULL load array");
+    return fail(MPOPF_ERR_ARG, std::string(who) + ": NULL generator array");
+  if (D > 0 && !net->load_bus) return fail(MPOPF_ERR_ARG, std::string(who) + ": NULL load array");
   for (int64_t l = 0; l < L; ++l) {
     const int32_t f = net->br_f[l], t = net->br_t[l];
-    if (f < 0 || f >= N || t < 0 || t >= N) return fail(MPOPF_ERR_ARG, "mpopf_setup: branch end out of range");
-    if (f == t) return fail(MPOPF_ERR_ARG, "mpopf_setup: self-loop branch");
+    if (f < 0 || f >= N || t < 0 || t >= N) return fail(MPOPF_ERR_ARG, std::string(who) + ": branch end out of range");
+    if (f == t) return fail(MPOPF_ERR_ARG, std::string(who) + ": self-loop branch");
     const double r = net->br_r[l], x = net->br_x[l];
-    if (!(r * r + x * x > 0.0)) return fail(MPOPF_ERR_ARG, "mpopf_setup: branch with r = x = 0");
+    if (!(r * r + x * x > 0.0)) return fail(MPOPF_ERR_ARG, std::string(who) + ": branch with r = x = 0");
     if (!(net->br_tap[l] != 0.0) || !std::isfinite(net->br_tap[l]))
-      return fail(MPOPF_ERR_ARG, "mpopf_setup: branch tap must be finite and nonzero");
+      return fail(MPOPF_ERR_ARG, std::string(who) + ": branch tap must be finite and nonzero");
   }
   for (int64_t g = 0; g < G; ++g)
-    if (net->gen_bus[g] < 0 || net->gen_bus[g] >= N) return fail(MPOPF_ERR_ARG, "mpopf_setup: generator bus out of range");
+    if (net->gen_bus[g] < 0 || net->gen_bus[g] >= N) return fail(MPOPF_ERR_ARG, std::string(who) + ": generator bus out of range");
   if (qramp)
     for (int64_t g = 0; g < G; ++g)
-      if (!(net->gen_qramp[g] >= 0.0)) return fail(MPOPF_ERR_ARG, "mpopf_setup: reactive ramp limit must be >= 0");
+      if (!(net->gen_qramp[g] >= 0.0)) return fail(MPOPF_ERR_ARG, std::string(who) + ": reactive ramp limit must be >= 0");
   for (int64_t k = 0; k < D; ++k)
-    if (net->load_bus[k] < 0 || net->load_bus[k] >= N) return fail(MPOPF_ERR_ARG, "mpopf_setup: load bus out of range");
+    if (net->load_bus[k] < 0 || net->load_bus[k] >= N) return fail(MPOPF_ERR_ARG, std::string(who) + ": load bus out of range");
 
-  int ndev = 0;
-  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
-    cudaGetLastError();
-    return fail(MPOPF_ERR_CUDA, "mpopf_setup: no CUDA device");
-  }
-
+  auto &bc = hm.bc; auto &sym = hm.sym;
+  auto &m2gs = hm.m2gs; auto &p2bs = hm.p2bs; auto &mgs = hm.mgs; auto &bsv = hm.bsv;
+  auto &bgen_ptr = hm.bgen_ptr; auto &bgen_idx = hm.bgen_idx; auto &barc_ptr = hm.barc_ptr;
+  auto &barc_idx = hm.barc_idx; auto &bload_ptr = hm.bload_ptr; auto &bload_idx = hm.bload_idx;
+  auto &gen_rank = hm.gen_rank; auto &arc_rank = hm.arc_rank; auto &bus_order = hm.bus_order;
+  auto &inc_ptr = hm.inc_ptr; auto &inc_code = hm.inc_code; auto &nbr_ptr = hm.nbr_ptr; auto &nbr_bus = hm.nbr_bus;
+  auto &nbr_grp = hm.nbr_grp; auto &grp_code = hm.grp_code; auto &bus_nd = hm.bus_nd; auto &bus_ndlt = hm.bus_ndlt;
+  auto &br_slot = hm.br_slot; auto &slot_info = hm.slot_info; auto &slot_next = hm.slot_next;
+  auto &arc_perm = hm.arc_perm; auto &jk8_off = hm.jk8_off; auto &jk8_per = hm.jk8_per;
+  auto &mo_va = hm.mo_va; auto &mo_vm = hm.mo_vm; auto &mo_pg0 = hm.mo_pg0; auto &mo_pg1 = hm.mo_pg1;
+  auto &mo_qg = hm.mo_qg; auto &mo_qg1 = hm.mo_qg1; auto &mo_p = hm.mo_p; auto &mo_q = hm.mo_q;
+  auto &mb_va = hm.mb_va; auto &mb_vm = hm.mb_vm; auto &mb_pg0 = hm.mb_pg0; auto &mb_pg1 = hm.mb_pg1;
+  auto &mb_qg = hm.mb_qg; auto &mb_qg1 = hm.mb_qg1; auto &mb_p = hm.mb_p; auto &mb_q = hm.mb_q;
   // ---- pi-model terms (textbook: y = 1/(r + jx), Y_ff = (y + jb/2)/tau^2,
   // Y_ft = -y/(tau e^{-j phi}), Y_tf = -y/(tau e^{j phi}), Y_tt = y + jb/2) ----
-  std::vector<double> bc((size_t)BC_COUNT * L);
-  std::vector<uint8_t> sym(L);
+  bc.assign((size_t)BC_COUNT * L, 0.0);
+  sym.assign(L, 0);
   for (int64_t l = 0; l < L; ++l) {
     const double r = net->br_r[l], x = net->br_x[l], chg = net->br_b[l];
     const double den = r * r + x * x;
@@ -358,7 +381,7 @@ int mpopf_setup(const mpopf_network *net, int32_t n_periods, const double *pd, c
     for (int k = 0; k < BC_COUNT; ++k) bc[(size_t)k * L + l] = vals[k];
     sym[l] = (std::memcmp(&gtf, &gft, 8) == 0 && std::memcmp(&btf, &bft, 8) == 0) ? 1 : 0;
   }
-  std::vector<double> m2gs(N), p2bs(N), mgs(N), bsv(N);
+  m2gs.assign(N, 0.0); p2bs.assign(N, 0.0); mgs.assign(N, 0.0); bsv.assign(N, 0.0);
   for (int64_t i = 0; i < N; ++i) {
     m2gs[i] = -(2.0 * net->bus_gs[i]);
     p2bs[i] = 2.0 * net->bus_bs[i];
@@ -375,11 +398,10 @@ int mpopf_setup(const mpopf_network *net, int32_t n_periods, const double *pd, c
     std::vector<int32_t> fill(ptr->begin(), ptr->end() - 1);
     for (int64_t e = 0; e < nitems; ++e) (*idx)[fill[key(e)]++] = (int32_t)e;  // ascending e
   };
-  std::vector<int32_t> bgen_ptr, bgen_idx, barc_ptr, barc_idx, bload_ptr, bload_idx;
   csr(G, [&](int64_t g) { return (int64_t)net->gen_bus[g]; }, &bgen_ptr, &bgen_idx);
   csr(2 * L, [&](int64_t a) { return (int64_t)(a < L ? net->br_f[a] : net->br_t[a - L]); }, &barc_ptr, &barc_idx);
   csr(D, [&](int64_t k) { return (int64_t)net->load_bus[k]; }, &bload_ptr, &bload_idx);
-  std::vector<int32_t> gen_rank(G), arc_rank(2 * L);
+  gen_rank.assign(G, 0); arc_rank.assign(2 * L, 0);
   for (int64_t i = 0; i < N; ++i) {
     for (int32_t q = bgen_ptr[i]; q < bgen_ptr[i + 1]; ++q) gen_rank[bgen_idx[q]] = q - bgen_ptr[i];
     for (int32_t q = barc_ptr[i]; q < barc_ptr[i + 1]; ++q) arc_rank[barc_idx[q]] = q - barc_ptr[i];
@@ -393,11 +415,11 @@ int mpopf_setup(const mpopf_network *net, int32_t n_periods, const double *pd, c
   // Buses in the order the bus kernel processes them.  Natural order: sorting
   // by degree (equal loop trip counts in a warp) was measured slower because
   // the per-bus loads and stores then scatter.
-  std::vector<int32_t> bus_order(N);
+  bus_order.assign(N, 0);
   for (int64_t i = 0; i < N; ++i) bus_order[i] = (int32_t)i;
   // Incidence slots numbered in that order (a warp's records are contiguous);
   // inc_ptr is indexed by position in bus_order, each bus's slots in branch order.
-  std::vector<int32_t> inc_ptr(N + 1, 0), inc_code;
+  inc_ptr.assign(N + 1, 0);
   inc_code.reserve(2 * L);
   std::vector<int32_t> slot_start(N);
   for (int64_t pos = 0; pos < N; ++pos) {
@@ -406,7 +428,7 @@ int mpopf_setup(const mpopf_network *net, int32_t n_periods, const double *pd, c
     inc_code.insert(inc_code.end(), inc[i].begin(), inc[i].end());  // ascending in l
     inc_ptr[pos + 1] = (int32_t)inc_code.size();
   }
-  std::vector<int32_t> nbr_ptr(N + 1, 0), nbr_bus, nbr_grp, grp_code, bus_nd(N), bus_ndlt(N);
+  nbr_ptr.assign(N + 1, 0); bus_nd.assign(N, 0); bus_ndlt.assign(N, 0);
   for (int64_t i = 0; i < N; ++i) {
     std::vector<int32_t> &v = inc[i];
     std::vector<std::pair<int32_t, int32_t>> nb;  // (neighbour, code)
@@ -432,7 +454,7 @@ int mpopf_setup(const mpopf_network *net, int32_t n_periods, const double *pd, c
   nbr_grp.push_back((int32_t)grp_code.size());
   // Per slot: neighbour position and group links; per branch end: its slot;
   // per bus: its slots in ascending arc index (from ends, then to ends).
-  std::vector<int32_t> br_slot(2 * L), slot_info(2 * L), slot_next(2 * L, -1), arc_perm(2 * L);
+  br_slot.assign(2 * L, 0); slot_info.assign(2 * L, 0); slot_next.assign(2 * L, -1); arc_perm.assign(2 * L, 0);
   for (int64_t i = 0; i < N; ++i) {
     std::vector<int32_t> nbs;  // distinct neighbours ascending
     for (int32_t q = nbr_ptr[i]; q < nbr_ptr[i + 1]; ++q) nbs.push_back(nbr_bus[q]);
@@ -458,13 +480,13 @@ int mpopf_setup(const mpopf_network *net, int32_t n_periods, const double *pd, c
   }
 
   // ---- templates ----
-  std::vector<int32_t> jk8_off(N);
+  jk8_off.assign(N, 0);
   int64_t acc = 0;
   for (int64_t i = 0; i < N; ++i) {
     jk8_off[i] = (int32_t)acc;
     acc += 1 + (bgen_ptr[i + 1] - bgen_ptr[i]) + (barc_ptr[i + 1] - barc_ptr[i]);
   }
-  const int64_t jk8_per = acc;  // = N + G + 2L
+  jk8_per = acc;  // = N + G + 2L
   auto prefix = [](const std::vector<int64_t> &len, std::vector<int32_t> *off) {
     off->assign(len.size(), 0);
     int64_t s = 0;
@@ -489,42 +511,97 @@ int mpopf_setup(const mpopf_network *net, int32_t n_periods, const double *pd, c
     len_p[a] = 4 + kb + arc_rank[a] + 1;
     len_q[a] = 4 + kb + 1 + arc_rank[a] + 1;
   }
-  std::vector<int32_t> mo_va, mo_vm, mo_pg0, mo_pg1, mo_qg, mo_qg1, mo_p, mo_q;
-  const int64_t mb_va = prefix(len_va, &mo_va), mb_vm = prefix(len_vm, &mo_vm);
-  const int64_t mb_pg0 = prefix(len_pg0, &mo_pg0), mb_pg1 = prefix(len_pg1, &mo_pg1);
-  const int64_t mb_qg = prefix(len_qg, &mo_qg), mb_qg1 = prefix(len_qg1, &mo_qg1);
-  const int64_t mb_p = prefix(len_p, &mo_p), mb_q = prefix(len_q, &mo_q);
+  mb_va = prefix(len_va, &mo_va); mb_vm = prefix(len_vm, &mo_vm);
+  mb_pg0 = prefix(len_pg0, &mo_pg0); mb_pg1 = prefix(len_pg1, &mo_pg1);
+  mb_qg = prefix(len_qg, &mo_qg); mb_qg1 = prefix(len_qg1, &mo_qg1);
+  mb_p = prefix(len_p, &mo_p); mb_q = prefix(len_q, &mo_q);
   const int64_t big = (int64_t)1 << 31;
   if (mb_vm >= big || mb_p >= big || mb_q >= big || jk8_per * 1 >= big)
-    return fail(MPOPF_ERR_SIZE, "mpopf_setup: one period of M exceeds 32-bit offsets");
+    return fail(MPOPF_ERR_SIZE, std::string(who) + ": one period of M exceeds 32-bit offsets");
 
+  hm.N = N; hm.L = L; hm.G = G; hm.D = D; hm.T = T; hm.n = n; hm.m = m; hm.qramp = qramp;
+  return MPOPF_OK;
+}
+
+// Offsets of every variable, row, J, W and M block of a T-period layout, from
+// d.N, d.L, d.G, d.qramp, d.jk8_per and the per-period M block sizes d.mb_*.
+void set_offsets(Dev &d, int64_t T) {
+  const int64_t N = d.N, L = d.L, G = d.G;
+  d.T = (int32_t)T;
+  d.n = T * (2 * N + 2 * G + 4 * L);
+  d.m = T * (1 + 7 * L + 2 * N) + G * (T - 1) * (d.qramp ? 2 : 1);
+  d.x_vm = T * N; d.x_pg = 2 * T * N; d.x_qg = 2 * T * N + T * G; d.x_p = 2 * T * N + 2 * T * G;
+  d.x_q = d.x_p + 2 * T * L;
+  d.c_k8 = T + 7 * T * L; d.c_k9 = d.c_k8 + T * N; d.c_k10 = d.c_k9 + T * N; d.c_k11 = d.c_k10 + (T - 1) * G;
+  d.j_k5 = T + 20 * T * L; d.j_k6 = d.j_k5 + 2 * T * L; d.j_k7 = d.j_k6 + 2 * T * L; d.j_k8 = d.j_k7 + 2 * T * L;
+  d.j_k9 = d.j_k8 + T * d.jk8_per; d.j_k10 = d.j_k9 + T * d.jk8_per;
+  d.j_k11 = d.j_k10 + 2 * (T - 1) * G;
+  d.nnz_jac = d.j_k11 + (d.qramp ? 2 * (T - 1) * G : 0);
+  d.h_br = T * G; d.h_th = d.h_br + 10 * T * L; d.h_sh = d.h_th + 4 * T * L; d.nnz_hess = d.h_sh + 2 * T * N;
+  d.m_va = 0;
+  d.m_vm = d.m_va + T * d.mb_va;
+  d.m_pg = d.m_vm + T * d.mb_vm;
+  d.m_qg = d.m_pg + d.mb_pg0 + (T - 1) * d.mb_pg1;
+  d.m_p = d.m_qg + d.mb_qg + (T - 1) * d.mb_qg1;
+  d.m_q = d.m_p + T * d.mb_p;
+  d.nnz_kkt = d.m_q + T * d.mb_q;
+  d.w0 = 0;
+  d.w1 = (int32_t)T;
+}
+
+// Template sizes of a host model into a device descriptor.
+void set_templates(Dev &d, const HostModel &hm) {
+  d.N = (int32_t)hm.N; d.L = (int32_t)hm.L; d.G = (int32_t)hm.G; d.D = (int32_t)hm.D;
+  d.qramp = hm.qramp ? 1 : 0;
+  d.jk8_per = hm.jk8_per;
+  d.mb_va = hm.mb_va; d.mb_vm = hm.mb_vm; d.mb_pg0 = hm.mb_pg0; d.mb_pg1 = hm.mb_pg1; d.mb_qg = hm.mb_qg;
+  d.mb_qg1 = hm.mb_qg1; d.mb_p = hm.mb_p; d.mb_q = hm.mb_q;
+}
+
+}  // namespace
+
+namespace {
+// The handle of a T-period model (mpopf_setup; a period shard's local model).
+int setup_model(const mpopf_network *net, int32_t n_periods, const double *pd, const double *qd, const char *who,
+                mpopf_handle **out, mpopf_pattern *pat) {
+  if (!out) return fail(MPOPF_ERR_ARG, std::string(who) + ": NULL output handle");
+  *out = nullptr;
+  HostModel hm;
+  const int rc = host_model(net, n_periods, who, &hm);
+  if (rc != MPOPF_OK) return rc;
+  const int64_t N = hm.N, L = hm.L, G = hm.G, D = hm.D, T = hm.T, n = hm.n, m = hm.m;
+  const bool qramp = hm.qramp;
+  if (D > 0 && (!pd || !qd)) return fail(MPOPF_ERR_ARG, std::string(who) + ": NULL load array");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return fail(MPOPF_ERR_CUDA, std::string(who) + ": no CUDA device");
+  }
+
+  const auto &bc = hm.bc; const auto &sym = hm.sym;
+  const auto &m2gs = hm.m2gs; const auto &p2bs = hm.p2bs; const auto &mgs = hm.mgs; const auto &bsv = hm.bsv;
+  const auto &bgen_ptr = hm.bgen_ptr; const auto &bgen_idx = hm.bgen_idx; const auto &barc_ptr = hm.barc_ptr;
+  const auto &barc_idx = hm.barc_idx; const auto &bload_ptr = hm.bload_ptr; const auto &bload_idx = hm.bload_idx;
+  const auto &gen_rank = hm.gen_rank; const auto &arc_rank = hm.arc_rank; const auto &bus_order = hm.bus_order;
+  const auto &inc_ptr = hm.inc_ptr; const auto &inc_code = hm.inc_code; const auto &nbr_ptr = hm.nbr_ptr;
+  const auto &nbr_bus = hm.nbr_bus; const auto &nbr_grp = hm.nbr_grp; const auto &grp_code = hm.grp_code;
+  const auto &bus_nd = hm.bus_nd; const auto &bus_ndlt = hm.bus_ndlt; const auto &br_slot = hm.br_slot;
+  const auto &slot_info = hm.slot_info; const auto &slot_next = hm.slot_next; const auto &arc_perm = hm.arc_perm;
+  const auto &jk8_off = hm.jk8_off;
+  const auto &mo_va = hm.mo_va; const auto &mo_vm = hm.mo_vm; const auto &mo_pg0 = hm.mo_pg0;
+  const auto &mo_pg1 = hm.mo_pg1; const auto &mo_qg = hm.mo_qg; const auto &mo_qg1 = hm.mo_qg1;
+  const auto &mo_p = hm.mo_p; const auto &mo_q = hm.mo_q;
   mpopf_handle *h = new mpopf_handle();
   std::memset(h, 0, sizeof(*h));
   if (cudaGetDevice(&h->device) != cudaSuccess) {
     delete h;
     cudaGetLastError();
-    return fail(MPOPF_ERR_CUDA, "mpopf_setup: no current CUDA device");
+    return fail(MPOPF_ERR_CUDA, std::string(who) + ": no current CUDA device");
   }
   Dev &d = h->d;
-  d.N = (int32_t)N; d.L = (int32_t)L; d.G = (int32_t)G; d.D = (int32_t)D; d.T = (int32_t)T; d.ref = net->ref_bus;
-  d.n = n; d.m = m;
-  d.x_vm = T * N; d.x_pg = 2 * T * N; d.x_qg = 2 * T * N + T * G; d.x_p = 2 * T * N + 2 * T * G;
-  d.x_q = d.x_p + 2 * T * L;
-  d.c_k8 = T + 7 * T * L; d.c_k9 = d.c_k8 + T * N; d.c_k10 = d.c_k9 + T * N; d.c_k11 = d.c_k10 + (T - 1) * G;
-  d.qramp = qramp ? 1 : 0;
-  d.j_k5 = T + 20 * T * L; d.j_k6 = d.j_k5 + 2 * T * L; d.j_k7 = d.j_k6 + 2 * T * L; d.j_k8 = d.j_k7 + 2 * T * L;
-  d.jk8_per = jk8_per; d.j_k9 = d.j_k8 + T * jk8_per; d.j_k10 = d.j_k9 + T * jk8_per;
-  d.j_k11 = d.j_k10 + 2 * (T - 1) * G;
-  d.nnz_jac = d.j_k11 + (qramp ? 2 * (T - 1) * G : 0);
-  d.h_br = T * G; d.h_th = d.h_br + 10 * T * L; d.h_sh = d.h_th + 4 * T * L; d.nnz_hess = d.h_sh + 2 * T * N;
-  d.mb_va = mb_va; d.mb_vm = mb_vm; d.mb_pg0 = mb_pg0; d.mb_pg1 = mb_pg1; d.mb_qg = mb_qg; d.mb_qg1 = mb_qg1; d.mb_p = mb_p; d.mb_q = mb_q;
-  d.m_va = 0;
-  d.m_vm = d.m_va + T * mb_va;
-  d.m_pg = d.m_vm + T * mb_vm;
-  d.m_qg = d.m_pg + mb_pg0 + (T - 1) * mb_pg1;
-  d.m_p = d.m_qg + mb_qg + (T - 1) * mb_qg1;
-  d.m_q = d.m_p + T * mb_p;
-  d.nnz_kkt = d.m_q + T * mb_q;
+  set_templates(d, hm);
+  set_offsets(d, T);
+  d.ref = net->ref_bus;
 
   cudaError_t err = cudaSuccess;
   std::vector<int32_t> brf(net->br_f, net->br_f + L), brt(net->br_t, net->br_t + L);
@@ -601,7 +678,7 @@ int mpopf_setup(const mpopf_network *net, int32_t n_periods, const double *pd, c
   double *src = dev_upload(h, tmp_src, &err);
   if (err != cudaSuccess) {
     const bool oom = err == cudaErrorMemoryAllocation;
-    std::string msg = std::string("mpopf_setup: ") + cudaGetErrorString(err);
+    std::string msg = std::string(who) + ": " + cudaGetErrorString(err);
     free_blocks(h);
     delete h;
     cudaGetLastError();
@@ -615,7 +692,7 @@ int mpopf_setup(const mpopf_network *net, int32_t n_periods, const double *pd, c
                         angmin, angmax, ramp, qramp_src, 0);
   if (err == cudaSuccess) err = cudaDeviceSynchronize();
   if (err != cudaSuccess) {
-    std::string msg = std::string("mpopf_setup: pattern expansion: ") + cudaGetErrorString(err);
+    std::string msg = std::string(who) + ": pattern expansion: " + cudaGetErrorString(err);
     free_blocks(h);
     delete h;
     cudaGetLastError();
@@ -624,8 +701,9 @@ int mpopf_setup(const mpopf_network *net, int32_t n_periods, const double *pd, c
   err = cudaStreamCreateWithFlags(&h->fork.side, cudaStreamNonBlocking);
   if (err == cudaSuccess) err = cudaEventCreateWithFlags(&h->fork.ev_fork, cudaEventDisableTiming);
   if (err == cudaSuccess) err = cudaEventCreateWithFlags(&h->fork.ev_join, cudaEventDisableTiming);
+  if (err == cudaSuccess) err = fork_bus_stream(&h->fork, false);
   if (err != cudaSuccess) {
-    std::string msg = std::string("mpopf_setup: side stream: ") + cudaGetErrorString(err);
+    std::string msg = std::string(who) + ": side stream: " + cudaGetErrorString(err);
     fork_destroy(h);
     free_blocks(h);
     delete h;
@@ -640,6 +718,123 @@ int mpopf_setup(const mpopf_network *net, int32_t n_periods, const double *pd, c
   *out = h;
   return MPOPF_OK;
 }
+}  // namespace
+
+extern "C" {
+
+const char *mpopf_last_error(void) { return g_err.c_str(); }
+
+int mpopf_setup(const mpopf_network *net, int32_t n_periods, const double *pd, const double *qd, mpopf_handle **out,
+                mpopf_pattern *pat) {
+  return setup_model(net, n_periods, pd, qd, "mpopf_setup", out, pat);
+}
+
+// ---------------------------------------------------------------------------
+// Period shards.  Only the ramp rows (Eq. 1k) couple periods, so the horizon
+// splits into contiguous blocks of periods.  A shard owning [t0, t1) is the
+// model of periods [t0 - h0, t1 + h1) (h0 = 1 if t0 > 0, h1 = 1 if t1 < T),
+// evaluated on its owned periods only: every owned entry is then computed by
+// exactly the arithmetic of the whole-horizon model.  The halo periods carry
+// the two values an owned entry reads from a neighbour: pg (and qg with the
+// reactive ramp) of period t0 - 1, read by the ramp rows at t0, and D of the
+// ramp rows at t1, added last to the pg (qg) diagonals of M at t1 - 1.
+// ---------------------------------------------------------------------------
+int mpopf_shard_plan(const mpopf_network *net, int32_t n_periods, int32_t t0, int32_t t1, mpopf_shard_layout *plan) {
+  if (!plan) return fail(MPOPF_ERR_ARG, "mpopf_shard_plan: NULL layout");
+  if (!(n_periods >= 1 && t0 >= 0 && t1 > t0 && t1 <= n_periods))
+    return fail(MPOPF_ERR_ARG, "mpopf_shard_plan: need 0 <= t0 < t1 <= n_periods");
+  HostModel hm;
+  const int rc = host_model(net, n_periods, "mpopf_shard_plan", &hm);
+  if (rc != MPOPF_OK) return rc;
+  const int64_t T = n_periods, N = hm.N, L = hm.L, G = hm.G;
+  const int32_t h0 = t0 > 0 ? 1 : 0, h1 = t1 < T ? 1 : 0;
+  const int64_t W = t1 - t0, Tl = W + h0 + h1;
+  Dev g, l;
+  std::memset(&g, 0, sizeof g);
+  set_templates(g, hm);
+  l = g;
+  set_offsets(g, T);
+  set_offsets(l, Tl);
+  mpopf_shard_layout &P = *plan;
+  std::memset(&P, 0, sizeof P);
+  P.n_periods = (int32_t)T; P.t0 = t0; P.t1 = t1; P.local_periods = (int32_t)Tl;
+  P.own0 = h0; P.own1 = (int32_t)(h0 + W);
+  P.halo_len = (int32_t)G; P.halo_blocks = hm.qramp ? 2 : 1;
+  P.n = l.n; P.m = l.m; P.nnz_jac = l.nnz_jac; P.nnz_hess = l.nnz_hess; P.nnz_kkt = l.nnz_kkt;
+  const int64_t o0 = P.own0, o1 = P.own1;
+  for (int b = 0; b < 2; ++b) {
+    const bool on = b == 0 || hm.qramp;
+    const int64_t xb = b == 0 ? l.x_pg : l.x_qg, rb = b == 0 ? l.c_k10 : l.c_k11;
+    P.x_recv[b] = on && h0 ? xb + (o0 - 1) * G : -1;
+    P.x_send[b] = on && h1 ? xb + (o1 - 1) * G : -1;
+    P.d_recv[b] = on && h1 ? rb + (o1 - 1) * G : -1;  // ramp rows of local period o1
+    P.d_send[b] = on && h0 ? rb + (o0 - 1) * G : -1;  // ramp rows of local period o0
+  }
+  auto add = [&](int32_t what, int64_t loc, int64_t glob, int64_t cnt) {
+    if (cnt <= 0 || P.n_ranges >= MPOPF_SHARD_MAX_RANGES) return;
+    P.ranges[P.n_ranges++] = mpopf_range{what, 0, loc, glob, cnt};
+  };
+  // variables: owned periods, and every local period (halos included)
+  const int64_t cnt[6] = {N, N, G, G, 2 * L, 2 * L};
+  const int64_t lx[6] = {0, l.x_vm, l.x_pg, l.x_qg, l.x_p, l.x_q}, gx[6] = {0, g.x_vm, g.x_pg, g.x_qg, g.x_p, g.x_q};
+  for (int k = 0; k < 6; ++k) add(MPOPF_RANGE_X, lx[k] + o0 * cnt[k], gx[k] + t0 * cnt[k], W * cnt[k]);
+  for (int k = 0; k < 6; ++k) add(MPOPF_RANGE_XALL, lx[k], gx[k] + (t0 - h0) * cnt[k], Tl * cnt[k]);
+  // rows of the owned periods (a ramp row (t, g) belongs to period t >= 1)
+  const int64_t ta = t0 > 1 ? t0 : 1, lta = ta - t0 + h0, nr = (t1 - ta) * G;
+  add(MPOPF_RANGE_ROWS, o0, t0, W);
+  for (int k = 1; k <= 7; ++k) add(MPOPF_RANGE_ROWS, Tl + (k - 1) * Tl * L + o0 * L, T + (k - 1) * T * L + t0 * L, W * L);
+  add(MPOPF_RANGE_ROWS, l.c_k8 + o0 * N, g.c_k8 + t0 * N, W * N);
+  add(MPOPF_RANGE_ROWS, l.c_k9 + o0 * N, g.c_k9 + t0 * N, W * N);
+  add(MPOPF_RANGE_ROWS, l.c_k10 + (lta - 1) * G, g.c_k10 + (ta - 1) * G, nr);
+  if (hm.qramp) add(MPOPF_RANGE_ROWS, l.c_k11 + (lta - 1) * G, g.c_k11 + (ta - 1) * G, nr);
+  // J entries of those rows
+  add(MPOPF_RANGE_JAC, o0, t0, W);
+  for (int k = 1; k <= 4; ++k)
+    add(MPOPF_RANGE_JAC, Tl + 5 * (k - 1) * Tl * L + o0 * 5 * L, T + 5 * (k - 1) * T * L + t0 * 5 * L, 5 * W * L);
+  add(MPOPF_RANGE_JAC, l.j_k5 + o0 * 2 * L, g.j_k5 + t0 * 2 * L, 2 * W * L);
+  add(MPOPF_RANGE_JAC, l.j_k6 + o0 * 2 * L, g.j_k6 + t0 * 2 * L, 2 * W * L);
+  add(MPOPF_RANGE_JAC, l.j_k7 + o0 * 2 * L, g.j_k7 + t0 * 2 * L, 2 * W * L);
+  add(MPOPF_RANGE_JAC, l.j_k8 + o0 * l.jk8_per, g.j_k8 + t0 * g.jk8_per, W * g.jk8_per);
+  add(MPOPF_RANGE_JAC, l.j_k9 + o0 * l.jk8_per, g.j_k9 + t0 * g.jk8_per, W * g.jk8_per);
+  add(MPOPF_RANGE_JAC, l.j_k10 + 2 * (lta - 1) * G, g.j_k10 + 2 * (ta - 1) * G, 2 * nr);
+  if (hm.qramp) add(MPOPF_RANGE_JAC, l.j_k11 + 2 * (lta - 1) * G, g.j_k11 + 2 * (ta - 1) * G, 2 * nr);
+  // W entries of the owned periods' elements
+  add(MPOPF_RANGE_HESS, o0 * G, t0 * G, W * G);
+  add(MPOPF_RANGE_HESS, l.h_br + o0 * 10 * L, g.h_br + t0 * 10 * L, 10 * W * L);
+  add(MPOPF_RANGE_HESS, l.h_th + o0 * 4 * L, g.h_th + t0 * 4 * L, 4 * W * L);
+  add(MPOPF_RANGE_HESS, l.h_sh + o0 * 2 * N, g.h_sh + t0 * 2 * N, 2 * W * N);
+  // M values of the owned variables' rows (each kind's rows are contiguous)
+  auto off1 = [](int64_t t, int64_t b0, int64_t b1) { return t == 0 ? 0 : b0 + (t - 1) * b1; };
+  add(MPOPF_RANGE_KKT, l.m_va + o0 * l.mb_va, g.m_va + t0 * g.mb_va, W * g.mb_va);
+  add(MPOPF_RANGE_KKT, l.m_vm + o0 * l.mb_vm, g.m_vm + t0 * g.mb_vm, W * g.mb_vm);
+  const int64_t pg_l = off1(o1, l.mb_pg0, l.mb_pg1) - off1(o0, l.mb_pg0, l.mb_pg1);
+  const int64_t pg_g = off1(t1, g.mb_pg0, g.mb_pg1) - off1(t0, g.mb_pg0, g.mb_pg1);
+  const int64_t qg_l = off1(o1, l.mb_qg, l.mb_qg1) - off1(o0, l.mb_qg, l.mb_qg1);
+  const int64_t qg_g = off1(t1, g.mb_qg, g.mb_qg1) - off1(t0, g.mb_qg, g.mb_qg1);
+  if (pg_l != pg_g || qg_l != qg_g) return fail(MPOPF_ERR_ARG, "mpopf_shard_plan: inconsistent generator rows");
+  add(MPOPF_RANGE_KKT, l.m_pg + off1(o0, l.mb_pg0, l.mb_pg1), g.m_pg + off1(t0, g.mb_pg0, g.mb_pg1), pg_g);
+  add(MPOPF_RANGE_KKT, l.m_qg + off1(o0, l.mb_qg, l.mb_qg1), g.m_qg + off1(t0, g.mb_qg, g.mb_qg1), qg_g);
+  add(MPOPF_RANGE_KKT, l.m_p + o0 * l.mb_p, g.m_p + t0 * g.mb_p, W * g.mb_p);
+  add(MPOPF_RANGE_KKT, l.m_q + o0 * l.mb_q, g.m_q + t0 * g.mb_q, W * g.mb_q);
+  return MPOPF_OK;
+}
+
+int mpopf_shard_setup(const mpopf_network *net, int32_t n_periods, int32_t t0, int32_t t1, const double *pd,
+                      const double *qd, mpopf_handle **out, mpopf_pattern *pat) {
+  if (!out) return fail(MPOPF_ERR_ARG, "mpopf_shard_setup: NULL output handle");
+  *out = nullptr;
+  mpopf_shard_layout plan;
+  int rc = mpopf_shard_plan(net, n_periods, t0, t1, &plan);  // validates the whole-horizon model too
+  if (rc != MPOPF_OK) return rc;
+  const int64_t D = net->n_load, first = t0 - plan.own0;  // loads of periods [t0 - h0, t1 + h1)
+  rc = setup_model(net, plan.local_periods, pd ? pd + first * D : nullptr, qd ? qd + first * D : nullptr,
+                   "mpopf_shard_setup", out, pat);
+  if (rc != MPOPF_OK) return rc;
+  (*out)->d.w0 = plan.own0;
+  (*out)->d.w1 = plan.own1;
+  return MPOPF_OK;
+}
+
 
 int mpopf_get_pattern(const mpopf_handle *h, mpopf_pattern *pat) {
   if (!h || !pat) return fail(MPOPF_ERR_ARG, "mpopf_get_pattern: NULL argument");

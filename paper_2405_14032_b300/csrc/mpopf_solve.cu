@@ -199,6 +199,7 @@ extern "C" {
 
 int mpopf_kkt_factor(mpopf_handle *h, const double *kv, int64_t *zero_pivot, void *stream) {
   if (!h || !kv) return fail(MPOPF_ERR_ARG, "mpopf_kkt_factor: NULL argument");
+  if (mpopf::is_shard(h->d)) return fail(MPOPF_ERR_ARG, "mpopf_kkt_factor: not available on a period shard");
   if (zero_pivot) *zero_pivot = -1;
   if (!h->solver) {
     h->solver = new KktSolver();
@@ -235,6 +236,7 @@ int mpopf_kkt_factor(mpopf_handle *h, const double *kv, int64_t *zero_pivot, voi
 
 int mpopf_kkt_solve(mpopf_handle *h, const double *rhs, double *dx, void *stream) {
   if (!h || !rhs || !dx) return fail(MPOPF_ERR_ARG, "mpopf_kkt_solve: NULL argument");
+  if (mpopf::is_shard(h->d)) return fail(MPOPF_ERR_ARG, "mpopf_kkt_solve: not available on a period shard");
   if (!h->solver || !h->solver->factored)
     return fail(MPOPF_ERR_ARG, "mpopf_kkt_solve: call mpopf_kkt_factor successfully first");
   KktSolver &S = *h->solver;

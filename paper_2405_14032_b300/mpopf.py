@@ -46,6 +46,25 @@ class _Pattern(ctypes.Structure):
                                 "xl", "xu", "gl", "gu")]
 
 
+class _Range(ctypes.Structure):
+    _fields_ = [("what", _I32), ("reserved", _I32), ("local", ctypes.c_int64), ("global_", ctypes.c_int64),
+                ("count", ctypes.c_int64)]
+
+
+SHARD_MAX_RANGES = 64
+RANGE_X, RANGE_XALL, RANGE_ROWS, RANGE_JAC, RANGE_HESS, RANGE_KKT = 0, 1, 2, 3, 4, 5
+RANGE_NAMES = {RANGE_X: "x", RANGE_XALL: "xall", RANGE_ROWS: "rows", RANGE_JAC: "jac", RANGE_HESS: "hess",
+               RANGE_KKT: "kkt"}
+
+
+class _ShardLayout(ctypes.Structure):
+    _fields_ = [(k, _I32) for k in ("n_periods", "t0", "t1", "local_periods", "own0", "own1", "halo_len",
+                                    "halo_blocks")] + \
+               [(k, ctypes.c_int64) for k in ("n", "m", "nnz_jac", "nnz_hess", "nnz_kkt")] + \
+               [(k, ctypes.c_int64 * 2) for k in ("x_recv", "x_send", "d_recv", "d_send")] + \
+               [("n_ranges", _I32), ("reserved", _I32), ("ranges", _Range * SHARD_MAX_RANGES)]
+
+
 class _BatchIO(ctypes.Structure):
     _fields_ = [("x", _P), ("lam", _P), ("sigma_x", _P), ("dvec", _P), ("sigma", _D), ("delta_w", _D),
                 ("f", _P), ("grad", _P), ("c", _P), ("jv", _P), ("hv", _P), ("kv", _P)]
@@ -79,6 +98,10 @@ def lib():
         sig = {
             "mpopf_setup": (ctypes.c_int, [ctypes.POINTER(_Network), _I32, _P, _P, ctypes.POINTER(_P),
                                            ctypes.POINTER(_Pattern)]),
+            "mpopf_shard_plan": (ctypes.c_int, [ctypes.POINTER(_Network), _I32, _I32, _I32,
+                                                ctypes.POINTER(_ShardLayout)]),
+            "mpopf_shard_setup": (ctypes.c_int, [ctypes.POINTER(_Network), _I32, _I32, _I32, _P, _P,
+                                                 ctypes.POINTER(_P), ctypes.POINTER(_Pattern)]),
             "mpopf_get_pattern": (ctypes.c_int, [_P, ctypes.POINTER(_Pattern)]),
             "mpopf_set_loads": (ctypes.c_int, [_P, _P, _P, _P]),
             "mpopf_eval": (ctypes.c_int, [_P, _U, _P, _P, _D, _P, _P, _D, _P, _P, _P, _P, _P, _P, _P]),
@@ -113,6 +136,9 @@ def lib():
             "mpopf_batch_test_stall": (ctypes.c_int, [_P, _I32]),
             "mpopf_batch_destroy": (None, [_P]),
             "mpopf_launch_count": (ctypes.c_int, [_P, _U]),
+            "mpopf_set_sweep_schedule": (ctypes.c_int, [_P, _I32, _I32]),
+            "mpopf_get_sweep_schedule": (ctypes.c_int, [_P, _P, _P]),
+            "mpopf_fp64_issue_rate": (ctypes.c_int, [_I32, _P, _P]),
             "mpopf_profile_start": (ctypes.c_int, [_P, _I32]),
             "mpopf_profile_stop": (ctypes.c_int, [_P, _P, _P]),
             "mpopf_destroy": (None, [_P]),
@@ -128,18 +154,28 @@ def lib():
 
 def exported_symbols():
     """Names the header declares (for the load/export check)."""
-    return ["mpopf_setup", "mpopf_get_pattern", "mpopf_set_loads", "mpopf_eval", "mpopf_eval_obj",
+    return ["mpopf_setup", "mpopf_shard_plan", "mpopf_shard_setup", "mpopf_get_pattern", "mpopf_set_loads", "mpopf_eval", "mpopf_eval_obj",
             "mpopf_eval_grad", "mpopf_eval_cons", "mpopf_eval_jac", "mpopf_eval_hess", "mpopf_assemble_kkt",
             "mpopf_sweep", "mpopf_sweep_host", "mpopf_assemble_kkt_noalloc", "mpopf_vjp", "mpopf_jvp", "mpopf_hvp",
             "mpopf_vjp_jv", "mpopf_jvp_jv", "mpopf_kkt_factor", "mpopf_kkt_solve", "mpopf_csc_pattern",
             "mpopf_coo_to_csc", "mpopf_ipm_prepare", "mpopf_ipm_rhs", "mpopf_ipm_recover", "mpopf_batch_create",
             "mpopf_batch_set_io", "mpopf_batch_sweep", "mpopf_batch_set_schedule", "mpopf_batch_get_schedule",
             "mpopf_batch_tune", "mpopf_batch_status", "mpopf_batch_test_stall", "mpopf_batch_destroy",
-            "mpopf_launch_count", "mpopf_profile_start", "mpopf_profile_stop", "mpopf_destroy", "mpopf_last_error"]
+            "mpopf_launch_count", "mpopf_set_sweep_schedule", "mpopf_get_sweep_schedule",
+            "mpopf_fp64_issue_rate", "mpopf_profile_start", "mpopf_profile_stop", "mpopf_destroy", "mpopf_last_error"]
 
 
 class MpopfError(RuntimeError):
     pass
+
+
+def fp64_issue_rate(iters=4096, stream=None):
+    """(FP64 thread-instructions per second, seconds) of the library's DFMA-chain
+    probe on the current device (mpopf_fp64_issue_rate; synchronous)."""
+    rate = np.zeros(1)
+    secs = np.zeros(1)
+    _check(lib().mpopf_fp64_issue_rate(int(iters), rate.ctypes.data, secs.ctypes.data), "mpopf_fp64_issue_rate")
+    return float(rate[0]), float(secs[0])
 
 
 def _check(rc, what):
@@ -169,40 +205,76 @@ def _stream_ptr(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-class Handle:
-    """A multi-period AC OPF model on the GPU (``mpopf_setup`` once)."""
+def _network_struct(net, keep):
+    """The C network descriptor of a synth.Network; `keep` holds the arrays
+    it points to."""
 
-    def __init__(self, inst):
+    def arr(a, dt):
+        a = np.ascontiguousarray(a, dtype=dt)
+        keep.append(a)
+        return a.ctypes.data if a.size else None
+
+    f64, i32 = np.float64, np.int32
+    return _Network(
+        n_bus=net.n_bus, n_branch=net.n_branch, n_gen=net.n_gen, n_load=net.n_load, ref_bus=net.ref_bus,
+        bus_gs=arr(net.bus_gs, f64), bus_bs=arr(net.bus_bs, f64), bus_vmin=arr(net.bus_vmin, f64),
+        bus_vmax=arr(net.bus_vmax, f64), br_f=arr(net.br_f, i32), br_t=arr(net.br_t, i32),
+        br_r=arr(net.br_r, f64), br_x=arr(net.br_x, f64), br_b=arr(net.br_b, f64), br_tap=arr(net.br_tap, f64),
+        br_shift=arr(net.br_shift, f64), br_smax=arr(net.br_smax, f64), br_angmin=arr(net.br_angmin, f64),
+        br_angmax=arr(net.br_angmax, f64), gen_bus=arr(net.gen_bus, i32), gen_c2=arr(net.gen_c2, f64),
+        gen_c1=arr(net.gen_c1, f64), gen_c0=arr(net.gen_c0, f64), gen_pmin=arr(net.gen_pmin, f64),
+        gen_pmax=arr(net.gen_pmax, f64), gen_qmin=arr(net.gen_qmin, f64), gen_qmax=arr(net.gen_qmax, f64),
+        gen_ramp=arr(net.gen_ramp, f64), load_bus=arr(net.load_bus, i32),
+        gen_qramp=None if net.gen_qramp is None else arr(net.gen_qramp, f64))
+
+
+def shard_plan(net, T, t0, t1):
+    """Layout of the period shard [t0, t1) of a T-period model (host only, no
+    device): dict with the local sizes, the halo offsets (x_recv, x_send,
+    d_recv, d_send: lists per block, -1 where there is no neighbour) and the
+    local <-> global ranges {name: [(local, global, count), ...]}."""
+    keep = []
+    c = _network_struct(net, keep)
+    lay = _ShardLayout()
+    _check(lib().mpopf_shard_plan(ctypes.byref(c), int(T), int(t0), int(t1), ctypes.byref(lay)), "mpopf_shard_plan")
+    out = {k: int(getattr(lay, k)) for k in ("n_periods", "t0", "t1", "local_periods", "own0", "own1", "halo_len",
+                                             "halo_blocks", "n", "m", "nnz_jac", "nnz_hess", "nnz_kkt")}
+    for k in ("x_recv", "x_send", "d_recv", "d_send"):
+        out[k] = [int(v) for v in getattr(lay, k)][:out["halo_blocks"]]
+    ranges = {name: [] for name in RANGE_NAMES.values()}
+    for i in range(lay.n_ranges):
+        r = lay.ranges[i]
+        ranges[RANGE_NAMES[r.what]].append((int(r.local), int(r.global_), int(r.count)))
+    out["ranges"] = ranges
+    return out
+
+
+class Handle:
+    """A multi-period AC OPF model on the GPU (``mpopf_setup`` once); with
+    shard=(t0, t1) the period shard [t0, t1) of it (``mpopf_shard_setup``)."""
+
+    def __init__(self, inst, shard=None):
         net = inst.net
         self._keep = []
-
-        def arr(a, dt):
-            a = np.ascontiguousarray(a, dtype=dt)
-            self._keep.append(a)
-            return a.ctypes.data if a.size else None
-
-        f64, i32 = np.float64, np.int32
-        c = _Network(
-            n_bus=net.n_bus, n_branch=net.n_branch, n_gen=net.n_gen, n_load=net.n_load, ref_bus=net.ref_bus,
-            bus_gs=arr(net.bus_gs, f64), bus_bs=arr(net.bus_bs, f64), bus_vmin=arr(net.bus_vmin, f64),
-            bus_vmax=arr(net.bus_vmax, f64), br_f=arr(net.br_f, i32), br_t=arr(net.br_t, i32),
-            br_r=arr(net.br_r, f64), br_x=arr(net.br_x, f64), br_b=arr(net.br_b, f64), br_tap=arr(net.br_tap, f64),
-            br_shift=arr(net.br_shift, f64), br_smax=arr(net.br_smax, f64), br_angmin=arr(net.br_angmin, f64),
-            br_angmax=arr(net.br_angmax, f64), gen_bus=arr(net.gen_bus, i32), gen_c2=arr(net.gen_c2, f64),
-            gen_c1=arr(net.gen_c1, f64), gen_c0=arr(net.gen_c0, f64), gen_pmin=arr(net.gen_pmin, f64),
-            gen_pmax=arr(net.gen_pmax, f64), gen_qmin=arr(net.gen_qmin, f64), gen_qmax=arr(net.gen_qmax, f64),
-            gen_ramp=arr(net.gen_ramp, f64), load_bus=arr(net.load_bus, i32),
-            gen_qramp=None if net.gen_qramp is None else arr(net.gen_qramp, f64))
-        pd = arr(inst.pd, f64)
-        qd = arr(inst.qd, f64)
+        c = _network_struct(net, self._keep)
+        pd = np.ascontiguousarray(inst.pd, dtype=np.float64)
+        qd = np.ascontiguousarray(inst.qd, dtype=np.float64)
+        pdp = pd.ctypes.data if pd.size else None
+        qdp = qd.ctypes.data if qd.size else None
         h = ctypes.c_void_p()
         pat = _Pattern()
-        _check(lib().mpopf_setup(ctypes.byref(c), int(inst.T), pd, qd, ctypes.byref(h), ctypes.byref(pat)),
-               "mpopf_setup")
+        if shard is None:
+            _check(lib().mpopf_setup(ctypes.byref(c), int(inst.T), pdp, qdp, ctypes.byref(h), ctypes.byref(pat)),
+                   "mpopf_setup")
+        else:
+            t0, t1 = (int(v) for v in shard)
+            _check(lib().mpopf_shard_setup(ctypes.byref(c), int(inst.T), t0, t1, pdp, qdp, ctypes.byref(h),
+                                           ctypes.byref(pat)), "mpopf_shard_setup")
         self._keep = []
         self.h = h
         self.pat = pat
-        self.T = int(inst.T)
+        self.shard = None if shard is None else (t0, t1)
+        self.T = int(pat.n_periods)
         self.n_load = int(inst.net.n_load)
         self.n, self.m = int(pat.n), int(pat.m)
         self.nnz_jac, self.nnz_hess, self.nnz_kkt = int(pat.nnz_jac), int(pat.nnz_hess), int(pat.nnz_kkt)
@@ -232,6 +304,19 @@ class Handle:
 
     def launch_count(self, outputs=OUT_ALL):
         return int(lib().mpopf_launch_count(self.h, outputs))
+
+    SCHED_BUS_PRIORITY, SCHED_GEN_FIRST = 1, 2
+
+    def set_sweep_schedule(self, chunk_periods, flags=0):
+        """Period chunks of the evaluation launches (0: one launch per kernel);
+        flags SCHED_BUS_PRIORITY, SCHED_GEN_FIRST (see mpopf_set_sweep_schedule)."""
+        _check(lib().mpopf_set_sweep_schedule(self.h, int(chunk_periods), int(flags)), "mpopf_set_sweep_schedule")
+
+    def sweep_schedule(self):
+        p = np.zeros(1, np.int32)
+        f = np.zeros(1, np.int32)
+        _check(lib().mpopf_get_sweep_schedule(self.h, p.ctypes.data, f.ctypes.data), "mpopf_get_sweep_schedule")
+        return int(p[0]), int(f[0])
 
     KERNEL_KINDS = ("branch", "bus", "gen", "fsum")
 
@@ -281,8 +366,9 @@ class Handle:
     def assemble_kkt_noalloc(self, x, lam, sigma, sigma_x, dvec, delta_w, kv, stream=None):
         """M values into the caller's `kv` with no device allocation by the
         call: the scratch is a fixed array inside the library (for callers
-        that cannot allocate while they run, e.g. inside a stream capture).
-        Raises MpopfError (code -2) when 12 T L exceeds that array."""
+        that cannot allocate once they are running, e.g. processes that
+        reserve all device memory up front).  Raises MpopfError (code -2)
+        when 12 T L exceeds that array."""
         _check(lib().mpopf_assemble_kkt_noalloc(self.h, _ptr(x), _ptr(lam), float(sigma), _ptr(sigma_x),
                                                 _ptr(dvec), float(delta_w), _ptr(kv), _stream_ptr(stream)),
                "mpopf_assemble_kkt_noalloc")

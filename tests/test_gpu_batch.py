@@ -1,9 +1,14 @@
 """Batched sweeps: many uneven instances in one persistent launch (CUDA graph)
 give, for every instance, the same outputs bit for bit as mpopf_sweep on that
-instance alone, whatever the schedule; the autotuner keeps that property."""
+instance alone, whatever the schedule; the autotuner keeps that property.  The
+batched outputs are also compared with the CPU oracle directly: every output
+of every small instance, and sampled periods of the smallest, the largest, a
+T = 12 and a T = 96 instance of the 64-instance workload, with the parity
+tolerance |gpu - ref| <= max(1e-12 |ref|, 1e-14)."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_2405_14032_b300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -17,15 +22,20 @@ def _dev(a):
     return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
 
 
-def _setup(shapes):
+def _setup(shapes, seeds=None, keep=None):
+    """Handles, batch I/O and per-instance reference sweeps; with `keep` (a
+    list) the (instance, point) pairs are appended to it."""
     from paper_2405_14032_b300 import mpopf
     hs, ios, refs = [], [], []
     for k, shape in enumerate(shapes):
         N, L, G, D, T = shape[:5]
-        inst = synth.make_instance(100 + k, N, L, G, D, T)
+        seed = 100 + k if seeds is None else seeds[k]
+        inst = synth.make_instance(seed, N, L, G, D, T)
         if len(shape) > 5 and shape[5] == "qramp":
             inst = synth.with_reactive_ramp(inst)
-        pt = synth.make_point(100 + k, inst)
+        pt = synth.make_point(seed, inst)
+        if keep is not None:
+            keep.append((inst, pt))
         h = mpopf.Handle(inst)
         io = dict(x=_dev(pt.x), lam=_dev(pt.lam), sigma=pt.sigma, sigma_x=_dev(pt.sigma_x), dvec=_dev(pt.dvec),
                   delta_w=pt.delta_w)
@@ -37,6 +47,42 @@ def _setup(shapes):
         refs.append(ref)
     torch.cuda.synchronize()
     return hs, ios, refs
+
+
+def _within(name, got, ref):
+    err = np.abs(got - ref)
+    ok = err <= np.maximum(1e-12 * np.abs(ref), 1e-14)
+    assert ok.all(), (name, int((~ok).sum()), np.nonzero(~ok)[0][:5])
+
+
+def _check_oracle(inst, pt, h, io, periods=None):
+    """The batched outputs of one instance against the oracle: every output
+    (periods None) or every entry of the sampled periods."""
+    o = oracle.Oracle(inst)
+    got = {k: io[k].cpu().numpy() for k in KEYS}
+    pat = {k: v.cpu().numpy() for k, v in h.pattern().items()}
+    if periods is None:
+        ref = o.eval(pt.x, pt.lam, pt.sigma)
+        for key, gkey in (("c", "c"), ("g", "grad"), ("jv", "jv"), ("hv", "hv")):
+            _within(gkey, got[gkey], ref[key])
+        rp, cols, vals = o.kkt_csr(pt.x, pt.lam, pt.sigma, pt.sigma_x, pt.dvec, pt.delta_w)
+        assert np.array_equal(pat["kkt_rowptr"], rp) and np.array_equal(pat["kkt_col"], cols)
+        _within("kv", got["kv"], vals)
+    else:
+        for t in periods:
+            ref = o.eval(pt.x, pt.lam, pt.sigma, t0=t, t1=t + 1)
+            for key, gkey in (("c", "c"), ("g", "grad"), ("jv", "jv"), ("hv", "hv")):
+                mask = ~np.isnan(ref[key])
+                assert mask.sum() > 0, (t, key)
+                _within((t, gkey), got[gkey][mask], ref[key][mask])
+            rows, rowlen, cols, vals = o.kkt(pt.x, pt.lam, pt.sigma, pt.sigma_x, pt.dvec, pt.delta_w, t0=t, t1=t + 1)
+            rp = pat["kkt_rowptr"]
+            assert np.array_equal(rp[rows + 1] - rp[rows], rowlen), t
+            pos = np.concatenate([np.arange(rp[r], rp[r + 1]) for r in rows])
+            assert np.array_equal(pat["kkt_col"][pos], cols), t
+            _within((t, "kv"), got["kv"][pos], vals)
+    f_ref = o.obj_textbook(pt.x)
+    assert abs(float(got["f"][0]) - f_ref) <= 1e-12 * abs(f_ref) + 1e-14
 
 
 def _check_all(b, ios, refs):
@@ -64,10 +110,13 @@ SMALL = [(40, 64, 8, 20, 3), (73, 117, 15, 44, 2), (130, 208, 26, 78, 5), (31, 5
 
 def test_batch_equals_individual_sweeps_every_schedule():
     from paper_2405_14032_b300 import mpopf
-    hs, ios, refs = _setup(SMALL)
+    kept = []
+    hs, ios, refs = _setup(SMALL, keep=kept)
     b = mpopf.Batch(hs)
     b.set_io(ios)
     _check_all(b, ios, refs)
+    for (inst, pt), h, io in zip(kept, hs, ios):  # the batched outputs against the oracle, in full
+        _check_oracle(inst, pt, h, io)
     for sched in [(0, 1, 0, 0), (1, 1, 1, 1), (0, 2, 2, 2), (1, 4, 0, 3), (0, 4, 1, 0), (1, 2, 3, 1), (0, 1, 0, 2),
                   (0, 1, 0, 0, 2), (1, 2, 1, 0, 2), (0, 4, 3, 0, 2)]:
         b.set_schedule(*sched)
@@ -87,13 +136,26 @@ def test_batch_64_uneven_instances():
     """The batched workload: 64 instances, buses log-uniform in [500, 5000],
     L = 1.6 N, G = 0.2 N, D = 0.6 N, T in {12, 24, 48, 96}."""
     from paper_2405_14032_b300 import mpopf
-    shapes = [(s["n_bus"], s["n_branch"], s["n_gen"], s["n_load"], s["T"]) for s in synth.batch_shapes(64)]
-    hs, ios, refs = _setup(shapes)
+    spec = synth.batch_shapes(64)
+    shapes = [(s["n_bus"], s["n_branch"], s["n_gen"], s["n_load"], s["T"]) for s in spec]
+    kept = []
+    hs, ios, refs = _setup(shapes, seeds=[s["seed"] for s in spec], keep=kept)
     b = mpopf.Batch(hs)
     b.set_io(ios)
     _check_all(b, ios, refs)
     b.tune(reps=2)
     _check_all(b, ios, refs)
+    # the tuned batch's outputs against the oracle: the smallest and the
+    # largest instance, and one with T = 12 and one with T = 96 (sampled
+    # periods: both ends of the horizon, with their ramp rows, and the middle)
+    sizes = [s["n_bus"] * s["T"] for s in spec]
+    pick = [int(np.argmin(sizes)), int(np.argmax(sizes))]
+    for T in (12, 96):
+        pick.append(next(k for k, s in enumerate(spec) if s["T"] == T and k not in pick))
+    for k in pick:
+        T = spec[k]["T"]
+        inst, pt = kept[k]
+        _check_oracle(inst, pt, hs[k], ios[k], periods=sorted({0, 1, T // 2, T - 2, T - 1}))
     b.close()
 
 

@@ -17,8 +17,11 @@ def _dev(a):
     return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
 
 
+@pytest.mark.parametrize("sched", [(0, 0), (2, 1), (1, 2)])
 @pytest.mark.parametrize("shape", [(300, 480, 60, 180, 6), (57, 91, 11, 30, 3), (40, 64, 0, 20, 4)])
-def test_graph_replay_equals_plain(shape):
+def test_graph_replay_equals_plain(shape, sched):
+    """sched: the launch schedule (period chunks with the bus kernels on a
+    second stream, itself a parallel branch of the captured graph)."""
     from paper_2405_14032_b300 import mpopf
     N, L, G, D, T = shape
     inst = synth.make_instance(71, N, L, G, D, T)
@@ -27,8 +30,9 @@ def test_graph_replay_equals_plain(shape):
     x0, lam, sx, dv = _dev(pt.x), _dev(pt.lam), _dev(pt.sigma_x), _dev(pt.dvec)
     gen = torch.Generator(device="cuda").manual_seed(5)
     xs = [x0 + 1e-3 * torch.randn(h.n, generator=gen, device="cuda", dtype=torch.float64) for _ in range(3)]
-    refs = [h.sweep(x, lam, pt.sigma, sx, dv, pt.delta_w) for x in xs]
+    refs = [h.sweep(x, lam, pt.sigma, sx, dv, pt.delta_w) for x in xs]  # plain schedule
     torch.cuda.synchronize()
+    h.set_sweep_schedule(*sched)
 
     outs = [h.new_outputs() for _ in xs]
     st = torch.cuda.Stream()

@@ -200,3 +200,50 @@ def test_sweep_host_matches_device(name):
         cs.h.sweep_host(pt.x, pt.lam, pt.sigma, pt.sigma_x, pt.dvec, pt.delta_w, out)
         for k in out:
             assert np.array_equal(out[k], dev[k]), (name, k)
+
+
+SCHEDULES = [(1, 0), (2, 1), (3, 2), (4, 3), (5, 0)]
+
+
+def test_chunked_schedules_equal_plain(case):
+    """Every launch schedule (period chunks, the bus kernel of each chunk on a
+    second stream, with and without its priority raised, the generator work
+    forked first or last) gives the plain sweep's outputs bit for bit, for
+    every output and for the callbacks alone; the plain sweep matches the
+    oracle (test_values_match_oracle), so these do too."""
+    name, cs = case
+    full = cs.run()
+    try:
+        for P, flags in SCHEDULES:
+            cs.h.set_sweep_schedule(P, flags)
+            assert cs.h.sweep_schedule() == (P, flags)
+            got = cs.run()
+            for k in full:
+                assert np.array_equal(got[k], full[k]), (name, P, flags, k)
+            for bit, key in ((4, "c"), (32, "kv")):
+                assert np.array_equal(cs.run(bit)[key], full[key]), (name, P, flags, key)
+    finally:
+        cs.h.set_sweep_schedule(0, 0)
+
+
+def test_chunked_schedule_cfg2_and_launch_count():
+    """2,000 buses x 24 periods in chunks of 5 (the last one shorter): the
+    outputs equal the oracle's; the launch count reports two launches per
+    chunk plus the generator kernels."""
+    import paper_2405_14032_b300.mpopf as mp
+    cs = Case(synth.config_instance("cfg2"), 2)
+    plain = cs.h.launch_count()
+    cs.h.set_sweep_schedule(5, mp.Handle.SCHED_BUS_PRIORITY)
+    assert cs.h.launch_count() == plain - 2 + 2 * 5
+    pt, o = cs.pt, cs.o
+    out = cs.run()
+    ref = o.eval(pt.x, pt.lam, pt.sigma)
+    _, _, kv = o.kkt_csr(pt.x, pt.lam, pt.sigma, pt.sigma_x, pt.dvec, pt.delta_w)
+    for k, r in (("grad", ref["g"]), ("c", ref["c"]), ("jv", ref["jv"]), ("hv", ref["hv"]), ("kv", kv)):
+        assert_close(f"cfg2 chunked:{k}", out[k], r)
+    assert abs(out["f"][0] - ref["f"]) <= 1e-12 * abs(ref["f"])
+    with pytest.raises(mp.MpopfError, match="bad argument"):
+        cs.h.set_sweep_schedule(-1, 0)
+    with pytest.raises(mp.MpopfError, match="bad argument"):
+        cs.h.set_sweep_schedule(4, 8)
+    cs.h.close()
