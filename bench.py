@@ -542,6 +542,54 @@ def graph_sweeps(torch, count=1000):
     return res
 
 
+def batched_iterates(torch, k=8, launches=125):
+    """Throughput of many independent sweeps of the 2,000-bus, T = 24 network
+    (seed 2): k handles of the same network at k perturbed iterates, one
+    batched sweep (mpopf_batch_sweep, tuned schedule) evaluating all k;
+    `launches` batched sweeps = k x launches sweeps.  For evaluations that do
+    not depend on each other (scenarios, line searches over several trial
+    points); an interior-point iteration's sweeps are sequential and are the
+    graph-replayed figures of small_sweeps."""
+    from paper_2405_14032_b300 import mpopf, synth
+    dev = lambda a: torch.as_tensor(a, dtype=torch.float64, device="cuda")
+    inst = synth.config_instance("cfg2")
+    pt = synth.make_point(2, inst)
+    gen = torch.Generator(device="cuda").manual_seed(2)
+    hs, ios = [], []
+    for j in range(k):
+        h = mpopf.Handle(inst)
+        x = dev(pt.x) + 1e-3 * torch.randn(h.n, generator=gen, device="cuda", dtype=torch.float64)
+        io = dict(x=x, lam=dev(pt.lam), sigma=pt.sigma, sigma_x=dev(pt.sigma_x), dvec=dev(pt.dvec),
+                  delta_w=pt.delta_w)
+        io.update(h.new_outputs())
+        hs.append(h)
+        ios.append(io)
+    b = mpopf.Batch(hs)
+    b.set_io(ios)
+    b.tune(reps=5)
+    for _ in range(3):
+        b.sweep()
+    torch.cuda.synchronize()
+    e0, e1 = _events(torch)
+    e0.record()
+    for _ in range(launches):
+        b.sweep()
+    e1.record()
+    torch.cuda.synchronize()
+    b.status()
+    ms = e0.elapsed_time(e1)
+    h = hs[0]
+    alg = algorithmic_bytes(h.n, h.m, h.nnz_jac, h.nnz_hess, h.nnz_kkt, inst.net.n_load, inst.T)
+    res = {"workload": f"2,000-bus network, T = 24: {k} iterates per batched sweep, {launches} batched sweeps",
+           "sweeps": k * launches, "ms_per_sweep": ms / (k * launches), "sweeps_per_s": k * launches / (ms * 1e-3),
+           "algorithmic_bytes_per_sweep": alg, "gbs": alg * k * launches / (ms * 1e-3) / 1e9,
+           "schedule": b.schedule()}
+    b.close()
+    for h in hs:
+        h.close()
+    return res
+
+
 def ipm_step_timing(torch, reps=5):
     """One whole interior-point step on the 2,000-bus, T = 24 network (seed 2)
     at an interior point (interval midpoints, unit duals, delta_w = 50 so that M
@@ -955,6 +1003,7 @@ def run_ours(args, world, rank, local):
             line["batched"] = batched_comparison(torch, fp64_peak=fp64_peak)
             line["ipm"] = ipm_timing(torch, h)
             line["small_sweeps"] = graph_sweeps(torch)
+            line["small_sweeps"]["2000_bus_T24_batched_iterates"] = batched_iterates(torch)
             line["csc"] = csc_timing(torch, h, out)
             line["unfused"] = unfused_timing(torch, h, xs[0], lam, pt.sigma, sx, dv, pt.delta_w, out)
             line["unfused"]["fused_ms"] = ms_step

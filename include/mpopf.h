@@ -458,9 +458,15 @@ int mpopf_launch_count(const mpopf_handle *h, unsigned outputs);
  * before the first branch chunk instead of after the last.  Both streams join
  * `stream` before the call returns, so work enqueued on `stream` afterwards
  * sees every output (under stream capture they are parallel graph branches).
- * Per-kernel profiling (mpopf_profile_start) times unchunked launches.
+ * MPOPF_SCHED_PDL (with P = 0): the bus kernel is launched with
+ * programmatic stream serialization, so its CTAs may be scheduled while the
+ * branch kernel's last CTAs run; it waits (griddepcontrol.wait) for the
+ * branch kernel's completion before reading its records; the generator work
+ * is forked before the branch kernel.
+ * Per-kernel profiling (mpopf_profile_start) times unchunked launches without
+ * programmatic dependencies.
  * MPOPF_ERR_ARG for P < 0 or unknown flags. */
-enum { MPOPF_SCHED_BUS_PRIORITY = 1, MPOPF_SCHED_GEN_FIRST = 2 };
+enum { MPOPF_SCHED_BUS_PRIORITY = 1, MPOPF_SCHED_GEN_FIRST = 2, MPOPF_SCHED_PDL = 4 };
 int mpopf_set_sweep_schedule(mpopf_handle *h, int32_t chunk_periods, int32_t flags);
 int mpopf_get_sweep_schedule(const mpopf_handle *h, int32_t *chunk_periods, int32_t *flags);
 

@@ -112,7 +112,8 @@ struct Prof {
 // work of chunk c overlaps the branch work of chunk c + 1 while the chunk's
 // incidence records are still in L2.
 constexpr int kMaxChunks = 64;
-enum { SCHED_BUS_PRIORITY = MPOPF_SCHED_BUS_PRIORITY, SCHED_GEN_FIRST = MPOPF_SCHED_GEN_FIRST };
+enum { SCHED_BUS_PRIORITY = MPOPF_SCHED_BUS_PRIORITY, SCHED_GEN_FIRST = MPOPF_SCHED_GEN_FIRST,
+       SCHED_PDL = MPOPF_SCHED_PDL };
 struct Fork {
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;

@@ -321,6 +321,10 @@ __global__ void __launch_bounds__(MPOPF_BRANCH_BLOCK, MPOPF_BRANCH_MINB)
              const double *__restrict__ sx, const double *__restrict__ dv, double dw, double *__restrict__ grad,
              double *__restrict__ c, double *__restrict__ jv, double *__restrict__ hv, double *__restrict__ kv,
              int32_t first, int32_t end) {
+  // a bus launch behind this one (programmatic dependent launch) may be
+  // scheduled once every CTA of this grid has started; it waits for this
+  // grid's completion before it reads the records
+  asm volatile("griddepcontrol.launch_dependents;");
   const int32_t tl = first + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
   if (tl >= end) return;
   __shared__ __align__(16) double s_stage[MPOPF_BRANCH_BLOCK / 32][kStagePitch];
@@ -331,7 +335,12 @@ __global__ void __launch_bounds__(MPOPF_BRANCH_BLOCK, MPOPF_BRANCH_MINB)
 // ---------------------------------------------------------------------------
 // Bus x period.
 // ---------------------------------------------------------------------------
-template <unsigned MASK, bool COH>
+// Waits (griddepcontrol.wait) until the grids this launch depends on
+// programmatically have completed and their writes are visible; returns at
+// once for a launch without such a dependency.
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <unsigned MASK, bool COH, bool WAIT = false>
 __device__ __forceinline__ void bus_body(const Dev &d, int32_t idx, unsigned rt, const double *__restrict__ x,
                                          const double *__restrict__ lam, const double *__restrict__ sx,
                                          const double *__restrict__ dv, double dw, double *__restrict__ grad,
@@ -362,6 +371,9 @@ __device__ __forceinline__ void bus_body(const Dev &d, int32_t idx, unsigned rt,
   // Incidence records of this bus (written by k_branch when M is assembled).
   const double *R = d.S + (int64_t)t * 2 * L * kRec;
   const bool have_rec = mk & MPOPF_OUT_KKT;
+  // a bus launch that may start before the branch launch has finished waits
+  // here, before its first read of the records
+  if (WAIT && have_rec) grid_dependency_wait();
   if (mk & MPOPF_OUT_CONS) {
     const double vm2 = vm * vm;
     double aP = 0.0, aQ = 0.0;
@@ -475,7 +487,7 @@ __global__ void __launch_bounds__(MPOPF_BUS_BLOCK) k_bus(Dev d, unsigned rt, con
                                                 int32_t end) {
   const int32_t idx = first + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
   if (idx >= end) return;
-  bus_body<MASK, false>(d, idx, rt, x, lam, sx, dv, dw, grad, c, jv, hv, kv);
+  bus_body<MASK, false, true>(d, idx, rt, x, lam, sx, dv, dw, grad, c, jv, hv, kv);
 }
 
 // ---------------------------------------------------------------------------
@@ -710,22 +722,52 @@ cudaError_t launch_all(const Dev &d, unsigned rt, const double *x, const double 
   if (nch > 0 && (mk & rest))
     return launch_chunked<MASK>(d, rt, mk, x, lam, sigma, sx, dv, dw, f, grad, c, jv, hv, kv, s, fork, P, nch, side);
   const int32_t W = d.w1 - d.w0;  // owned periods
+  // Programmatic dependent launch: the bus kernel may start while the branch
+  // kernel finishes (it waits before reading the records); the generator work
+  // is then forked before the branch kernel, so that nothing is enqueued
+  // between the two launches.
+  const bool pdl = fork && (fork->flags & SCHED_PDL) && !prof && (mk & rest) && d.L > 0;
+  auto fork_gen = [&]() -> cudaError_t {
+    cudaError_t e = cudaEventRecord(fork->ev_fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(fork->side, fork->ev_fork, 0);
+    if (e != cudaSuccess) return e;
+    launch_gen_part<MASK>(d, rt, mk, x, sigma, sx, dv, dw, f, grad, c, jv, hv, kv, fork->side, nullptr);
+    return cudaSuccess;
+  };
+  if (side && pdl) {
+    const cudaError_t e = fork_gen();
+    if (e != cudaSuccess) return e;
+  }
   if ((mk & rest) && d.L > 0) {
     Timed tm(prof, s, KIND_BRANCH);
     k_branch<MASK><<<(unsigned)(((int64_t)W * d.L + MPOPF_BRANCH_BLOCK - 1) / MPOPF_BRANCH_BLOCK),
                      MPOPF_BRANCH_BLOCK, 0, s>>>(d, rt, x, lam, sx, dv, dw, grad, c, jv, hv, kv, d.w0 * d.L,
                                                  d.w1 * d.L);
   }
-  if (side) {
-    cudaError_t e = cudaEventRecord(fork->ev_fork, s);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(fork->side, fork->ev_fork, 0);
+  if (side && !pdl) {
+    const cudaError_t e = fork_gen();
     if (e != cudaSuccess) return e;
-    launch_gen_part<MASK>(d, rt, mk, x, sigma, sx, dv, dw, f, grad, c, jv, hv, kv, fork->side, nullptr);
   }
   if (mk & rest) {
     Timed tm(prof, s, KIND_BUS);
-    k_bus<MASK><<<(unsigned)(((int64_t)W * d.N + MPOPF_BUS_BLOCK - 1) / MPOPF_BUS_BLOCK), MPOPF_BUS_BLOCK, 0, s>>>(
-        d, rt, x, lam, sx, dv, dw, grad, c, jv, hv, kv, d.w0 * d.N, d.w1 * d.N);
+    const unsigned grid = (unsigned)(((int64_t)W * d.N + MPOPF_BUS_BLOCK - 1) / MPOPF_BUS_BLOCK);
+    const int32_t bf = d.w0 * d.N, be = d.w1 * d.N;
+    if (pdl) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(grid);
+      cfg.blockDim = dim3(MPOPF_BUS_BLOCK);
+      cfg.stream = s;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      at[0].val.programmaticStreamSerializationAllowed = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      const cudaError_t e = cudaLaunchKernelEx(&cfg, k_bus<MASK>, d, rt, x, lam, sx, dv, dw, grad, c, jv, hv, kv,
+                                               bf, be);
+      if (e != cudaSuccess) return e;
+    } else {
+      k_bus<MASK><<<grid, MPOPF_BUS_BLOCK, 0, s>>>(d, rt, x, lam, sx, dv, dw, grad, c, jv, hv, kv, bf, be);
+    }
   }
   if (side) {
     cudaError_t e = cudaEventRecord(fork->ev_join, fork->side);
@@ -983,7 +1025,7 @@ int mpopf_launch_count(const mpopf_handle *h, unsigned outputs) {
 
 int mpopf_set_sweep_schedule(mpopf_handle *h, int32_t chunk_periods, int32_t flags) {
   if (!h) return fail(MPOPF_ERR_ARG, "mpopf_set_sweep_schedule: NULL handle");
-  if (chunk_periods < 0 || (flags & ~(SCHED_BUS_PRIORITY | SCHED_GEN_FIRST)))
+  if (chunk_periods < 0 || (flags & ~(SCHED_BUS_PRIORITY | SCHED_GEN_FIRST | SCHED_PDL)))
     return fail(MPOPF_ERR_ARG, "mpopf_set_sweep_schedule: bad argument");
   if ((flags ^ h->fork.flags) & SCHED_BUS_PRIORITY) {
     const cudaError_t e = fork_bus_stream(&h->fork, flags & SCHED_BUS_PRIORITY);
