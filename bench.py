@@ -148,6 +148,54 @@ def ncu_traffic(periods):
 # ---------------------------------------------------------------------------
 # Clocks (NVML, read-only) sampled during the timed region.
 # ---------------------------------------------------------------------------
+class NvmlLite:
+    """The few read-only NVML queries the clock sampler makes, through ctypes
+    on the driver's libnvidia-ml.so.1 (for hosts without the pynvml module).
+    Same names as pynvml's."""
+    NVML_CLOCK_SM = 1
+
+    def __init__(self):
+        import ctypes
+        self._c = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+
+    def _check(self, rc, what):
+        if rc != 0:
+            raise RuntimeError(f"NVML {what}: error {rc}")
+
+    def nvmlInit(self):
+        self._check(self.lib.nvmlInit_v2(), "init")
+
+    def nvmlDeviceGetHandleByUUID(self, uuid):
+        h = self._c.c_void_p()
+        uuid = uuid if isinstance(uuid, bytes) else uuid.encode()
+        self._check(self.lib.nvmlDeviceGetHandleByUUID(self._c.c_char_p(uuid), self._c.byref(h)), "handle by UUID")
+        return h
+
+    def nvmlDeviceGetHandleByIndex(self, i):
+        h = self._c.c_void_p()
+        self._check(self.lib.nvmlDeviceGetHandleByIndex_v2(self._c.c_uint(i), self._c.byref(h)), "handle by index")
+        return h
+
+    def _uint(self, fn, h, *args):
+        v = self._c.c_uint()
+        self._check(fn(h, *args, self._c.byref(v)), fn.__name__)
+        return v.value
+
+    def nvmlDeviceGetMaxClockInfo(self, h, kind):
+        return self._uint(self.lib.nvmlDeviceGetMaxClockInfo, h, self._c.c_int(kind))
+
+    def nvmlDeviceGetClockInfo(self, h, kind):
+        return self._uint(self.lib.nvmlDeviceGetClockInfo, h, self._c.c_int(kind))
+
+    def nvmlDeviceGetCurrentClocksEventReasons(self, h):
+        v = self._c.c_ulonglong()
+        fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        self._check(fn(h, self._c.byref(v)), "clock event reasons")
+        return v.value
+
+
 class ClockSampler:
     REASONS = {
         "gpu_idle": 0x1, "applications_clocks_setting": 0x2, "sw_power_cap": 0x4, "hw_slowdown": 0x8,
@@ -182,11 +230,16 @@ class ClockSampler:
 
     def start(self):
         try:
-            import pynvml
-            pynvml.nvmlInit()
-            self._nv = pynvml
-            self._h = self._handle(pynvml)
-            self.max_mhz = pynvml.nvmlDeviceGetMaxClockInfo(self._h, pynvml.NVML_CLOCK_SM)
+            try:
+                import pynvml as nv
+                self.api = "pynvml"
+            except ImportError:
+                nv = NvmlLite()
+                self.api = "libnvidia-ml.so.1 via ctypes"
+            nv.nvmlInit()
+            self._nv = nv
+            self._h = self._handle(nv)
+            self.max_mhz = nv.nvmlDeviceGetMaxClockInfo(self._h, nv.NVML_CLOCK_SM)
             self.ok = True
         except Exception as exc:
             self.error = repr(exc)[:200]
@@ -261,7 +314,7 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(self.samples) if self.samples else None,
                 "sm_max_mhz": self.max_mhz, "samples": len(self.samples),
                 "reasons": [k for k, v in self.REASONS.items() if self.reasons & v],
-                "source": "NVML, read-only, every 2 ms during the timed region"}
+                "source": f"NVML ({self.api}), read-only, every 2 ms during the timed region"}
 
 
 # ---------------------------------------------------------------------------
