@@ -595,7 +595,7 @@ def graph_sweeps(torch, count=1000):
     return res
 
 
-def batched_iterates(torch, k=8, launches=125):
+def batched_iterates(torch, k=32, launches=32):
     """Throughput of many independent sweeps of the 2,000-bus, T = 24 network
     (seed 2): k handles of the same network at k perturbed iterates, one
     batched sweep (mpopf_batch_sweep, tuned schedule) evaluating all k;

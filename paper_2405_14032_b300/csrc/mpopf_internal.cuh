@@ -81,6 +81,10 @@ struct Dev {
   // model of its own; a period shard's local model has a halo period before
   // (w0 = 1) and / or after (w1 = T - 1) the periods it owns.
   int32_t w0, w1;
+  // 1 if every branch is symmetric (br_sym all 1: no tap ratio or phase
+  // shift asymmetry); the branch kernel then runs an instantiation without the
+  // per-branch test
+  int32_t all_sym;
 };
 
 // A period shard's handle evaluates only the periods it owns.

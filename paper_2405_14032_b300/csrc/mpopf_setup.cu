@@ -609,6 +609,7 @@ int setup_model(const mpopf_network *net, int32_t n_periods, const double *pd, c
   d.br_t = dev_upload(h, brt, &err);
   d.bc = dev_upload(h, bc, &err);
   d.br_sym = dev_upload(h, sym, &err);
+  d.all_sym = std::all_of(sym.begin(), sym.end(), [](uint8_t v) { return v != 0; }) ? 1 : 0;
   d.bus_m2gs = dev_upload(h, m2gs, &err);
   d.bus_p2bs = dev_upload(h, p2bs, &err);
   d.bus_mgs = dev_upload(h, mgs, &err);

@@ -26,12 +26,15 @@ def test_branch_kernel_register_and_spill_budget(tmp_path):
     cmd = [NVCC, *flags, "-Xptxas", "-v", "-I", os.path.join(build.ROOT, "include"), "-c", src,
            "-o", str(tmp_path / "k.o")]
     out = subprocess.run(cmd, capture_output=True, text=True, check=True).stderr
-    # the report block of the full-sweep instantiation k_branch<63>
-    m = re.search(r"Compiling entry function '[^']*k_branchILj63E[^']*'.*?Used (\d+) registers", out, re.S)
-    assert m, "no resource report for k_branch<63>"
-    block = out[m.start():m.end()]
-    regs = int(m.group(1))
-    spill = re.search(r"(\d+) bytes spill stores, (\d+) bytes spill loads", block)
-    stores, loads = (int(spill.group(1)), int(spill.group(2))) if spill else (0, 0)
-    assert regs <= 80, regs
-    assert stores <= 136 and loads <= 176, (stores, loads)
+    # the report blocks of the full-sweep instantiations k_branch<63, SYM>
+    # (with and without the per-branch symmetry test)
+    blocks = list(re.finditer(r"Compiling entry function '[^']*k_branchILj63E[^']*'.*?Used (\d+) registers", out,
+                              re.S))
+    assert len(blocks) == 2, "no resource report for both k_branch<63, SYM> instantiations"
+    for m in blocks:
+        block = out[m.start():m.end()]
+        regs = int(m.group(1))
+        spill = re.search(r"(\d+) bytes spill stores, (\d+) bytes spill loads", block)
+        stores, loads = (int(spill.group(1)), int(spill.group(2))) if spill else (0, 0)
+        assert regs <= 80, regs
+        assert stores <= 136 and loads <= 176, (stores, loads)
