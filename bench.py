@@ -857,6 +857,21 @@ def lib_vjp(h, x, y, gx, gpd, gqd):
 
 
 # ---------------------------------------------------------------------------
+PARALLELISM = {"single": "single", "replicas": "replicas{n}", "shards": "period-shards{n} (halo + f all-reduce)"}
+L2_NOTE = "inputs + outputs 2.7 GB per step > 126 MB L2; no flush"
+
+
+def workload_config(T, world, mode):
+    """The `config` object of both arms: the workload and how it is spread over
+    the GPUs."""
+    return {"workload": f"mpopf_sweep_10k_bus_T{T}", **WORKLOAD, "n_periods": T,
+            "parallelism": PARALLELISM[mode].format(n=world), "l2": L2_NOTE}
+
+
+def run_mode(args, world):
+    return (args.mode or "shards") if world > 1 else "single"
+
+
 def run_reference(args, world, rank):
     """The reference arm: the CPU oracle on this workload, timed on the host
     cores; each step evaluates every callback and the M rows of one period
@@ -886,10 +901,10 @@ def run_reference(args, world, rank):
     value = sweeps / el
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": True, "scaling": "strong" if run_mode(args, world) == "shards" else "weak",
+            "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "mpopf_sweep_10k_bus_T168", **{k: v for k, v in WORKLOAD.items()},
-                       "n_periods": inst.T},
+            "config": workload_config(inst.T, world, run_mode(args, world)),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": "per step: all callbacks + M rows of one period of the horizon"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -912,7 +927,7 @@ def run_ours(args, world, rank, local):
     dev = torch.device("cuda", local)
     from paper_2405_14032_b300 import mpopf, shard, synth
 
-    mode = (args.mode or "shards") if world > 1 else "single"
+    mode = run_mode(args, world)
     T = args.periods
     inst = synth.make_instance(WORKLOAD["seed"], WORKLOAD["n_bus"], WORKLOAD["n_branch"], WORKLOAD["n_gen"],
                                WORKLOAD["n_load"], T)
@@ -1019,17 +1034,14 @@ def run_ours(args, world, rank, local):
                     "attainable_frac": (alg_whole / (floor_ms * 1e-3) / 1e9) / hbm_peak if hbm_peak else None,
                     "frac_of_fp64_floor": floor_ms / ms_step})
 
-    par = {"single": "single", "replicas": f"replicas{world}", "shards": f"period-shards{world} (halo + f all-reduce)"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "strong" if mode == "shards" else "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"mpopf_sweep_10k_bus_T{T}", **WORKLOAD, "n_periods": T,
-                       "n": whole["n"], "m": whole["m"], "nnz_jac": whole["nnz_jac"],
-                       "nnz_hess": whole["nnz_hess"], "nnz_kkt": whole["nnz_kkt"],
-                       "parallelism": par[mode],
-                       "l2": "inputs + outputs 2.7 GB per step > 126 MB L2; no flush",
-                       "iterates": "two perturbed iterates alternated"},
+            "config": workload_config(T, world, mode),
+            "sizes": {"n": whole["n"], "m": whole["m"], "nnz_jac": whole["nnz_jac"], "nnz_hess": whole["nnz_hess"],
+                      "nnz_kkt": whole["nnz_kkt"]},
+            "inputs": "two perturbed iterates alternated step by step, resident in HBM",
             "hbm": hbm,
             "roofline": roof,
             "kernels_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1] > 0},
