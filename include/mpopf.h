@@ -458,11 +458,11 @@ int mpopf_launch_count(const mpopf_handle *h, unsigned outputs);
  * before the first branch chunk instead of after the last.  Both streams join
  * `stream` before the call returns, so work enqueued on `stream` afterwards
  * sees every output (under stream capture they are parallel graph branches).
- * MPOPF_SCHED_PDL (with P = 0): the bus kernel is launched with
- * programmatic stream serialization, so its CTAs may be scheduled while the
- * branch kernel's last CTAs run; it waits (griddepcontrol.wait) for the
- * branch kernel's completion before reading its records; the generator work
- * is forked before the branch kernel.
+ * MPOPF_SCHED_PDL (with P = 0; the default schedule is P = 0 with this flag):
+ * the bus kernel is launched with programmatic stream serialization, so its
+ * CTAs may be scheduled while the branch kernel's last CTAs run; it waits
+ * (griddepcontrol.wait) for the branch kernel's completion before reading its
+ * records.
  * Per-kernel profiling (mpopf_profile_start) times unchunked launches without
  * programmatic dependencies.
  * MPOPF_ERR_ARG for P < 0 or unknown flags. */

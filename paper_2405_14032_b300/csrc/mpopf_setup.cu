@@ -703,6 +703,7 @@ int setup_model(const mpopf_network *net, int32_t n_periods, const double *pd, c
   if (err == cudaSuccess) err = cudaEventCreateWithFlags(&h->fork.ev_fork, cudaEventDisableTiming);
   if (err == cudaSuccess) err = cudaEventCreateWithFlags(&h->fork.ev_join, cudaEventDisableTiming);
   if (err == cudaSuccess) err = fork_bus_stream(&h->fork, false);
+  h->fork.flags = SCHED_PDL;  // the default launch schedule
   if (err != cudaSuccess) {
     std::string msg = std::string(who) + ": side stream: " + cudaGetErrorString(err);
     fork_destroy(h);

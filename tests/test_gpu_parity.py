@@ -202,7 +202,7 @@ def test_sweep_host_matches_device(name):
             assert np.array_equal(out[k], dev[k]), (name, k)
 
 
-SCHEDULES = [(1, 0), (2, 1), (3, 2), (4, 3), (5, 0), (0, 4), (0, 6)]
+SCHEDULES = [(1, 0), (2, 1), (3, 2), (4, 3), (5, 0), (0, 0), (0, 2), (0, 6)]
 
 
 def test_chunked_schedules_equal_plain(case):
@@ -213,6 +213,8 @@ def test_chunked_schedules_equal_plain(case):
     every output and for the callbacks alone; the plain sweep matches the
     oracle (test_values_match_oracle), so these do too."""
     name, cs = case
+    default = cs.h.sweep_schedule()
+    assert default == (0, 4)  # one launch per kernel, the bus kernel a programmatic dependent launch
     full = cs.run()
     try:
         for P, flags in SCHEDULES:
@@ -224,7 +226,7 @@ def test_chunked_schedules_equal_plain(case):
             for bit, key in ((4, "c"), (32, "kv")):
                 assert np.array_equal(cs.run(bit)[key], full[key]), (name, P, flags, key)
     finally:
-        cs.h.set_sweep_schedule(0, 0)
+        cs.h.set_sweep_schedule(*default)
 
 
 def test_chunked_schedule_cfg2_and_launch_count():
