@@ -468,6 +468,17 @@ int mpopf_launch_count(const mpopf_handle *h, unsigned outputs);
  * MPOPF_ERR_ARG for P < 0 or unknown flags. */
 enum { MPOPF_SCHED_BUS_PRIORITY = 1, MPOPF_SCHED_GEN_FIRST = 2, MPOPF_SCHED_PDL = 4 };
 int mpopf_set_sweep_schedule(mpopf_handle *h, int32_t chunk_periods, int32_t flags);
+
+/* An extra dependency of the generator work (generator x period kernel and
+ * objective) of later evaluations of this handle: it also waits for `event`
+ * (a cudaEvent_t passed as void*, owned and recorded by the caller; NULL
+ * removes the dependency).  Only the generator work reads a period shard's
+ * halo values (pg of period t0 - 1 and D of the ramp rows at t1), so a caller
+ * can run the halo exchange on a stream of its own, record the event after it
+ * and enqueue the evaluation at once: the branch and bus work then overlap
+ * the exchange.  The event must be recorded before each evaluation is
+ * enqueued; it is not meant for work recorded in a stream capture. */
+int mpopf_set_gen_dependency(mpopf_handle *h, void *event);
 int mpopf_get_sweep_schedule(const mpopf_handle *h, int32_t *chunk_periods, int32_t *flags);
 
 /* Condensed-matrix assembly that allocates nothing (the paper has no

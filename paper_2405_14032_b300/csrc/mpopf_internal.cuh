@@ -126,6 +126,7 @@ struct Fork {
   cudaEvent_t ev_chunk[kMaxChunks] = {};
   int32_t chunk = 0;                   // periods per chunk; 0: one launch per kernel
   int32_t flags = 0;                   // SCHED_*: bus stream at the highest priority; generator work forked first
+  cudaEvent_t gen_after = nullptr;     // the caller's event the generator work also waits for (or none)
 };
 
 // Kernel launchers (mpopf_kernels.cu).  With fork == nullptr every launch goes

@@ -649,10 +649,13 @@ struct Timed {
 
 // The generator kernel (and the objective sum after it) on stream g, which is
 // the caller's stream s or the handle's side stream.
+// `after`, when not null, is an event the generator work also waits for (a
+// caller's halo exchange of a period shard).
 template <unsigned MASK>
 void launch_gen_part(const Dev &d, unsigned rt, unsigned mk, const double *x, double sigma, const double *sx,
                      const double *dv, double dw, double *f, double *grad, double *c, double *jv, double *hv,
-                     double *kv, cudaStream_t g, Prof *prof) {
+                     double *kv, cudaStream_t g, Prof *prof, cudaEvent_t after = nullptr) {
+  if (after && mk) cudaStreamWaitEvent(g, after, 0);
   // the owned periods' elements; the objective sums exactly the tiles launched
   const int32_t first = d.w0 * d.G, end = d.w1 * d.G;
   const unsigned tiles = grid_for((int64_t)end - first);
@@ -700,7 +703,9 @@ cudaError_t launch_chunked(const Dev &d, unsigned rt, unsigned mk, const double 
   const bool gen_first = fork->flags & SCHED_GEN_FIRST;
   if (e == cudaSuccess && side && gen_first) {
     e = cudaStreamWaitEvent(fork->side, fork->ev_fork, 0);
-    if (e == cudaSuccess) launch_gen_part<MASK>(d, rt, mk, x, sigma, sx, dv, dw, f, grad, c, jv, hv, kv, fork->side, nullptr);
+    if (e == cudaSuccess)
+      launch_gen_part<MASK>(d, rt, mk, x, sigma, sx, dv, dw, f, grad, c, jv, hv, kv, fork->side, nullptr,
+                            fork->gen_after);
   }
   for (int k = 0; k < nch && e == cudaSuccess; ++k) {
     const int32_t t0 = d.w0 + k * P, t1 = std::min(d.w1, t0 + P);
@@ -715,7 +720,9 @@ cudaError_t launch_chunked(const Dev &d, unsigned rt, unsigned mk, const double 
   }
   if (e == cudaSuccess && side && !gen_first) {
     e = cudaStreamWaitEvent(fork->side, fork->ev_chunk[nch - 1], 0);
-    if (e == cudaSuccess) launch_gen_part<MASK>(d, rt, mk, x, sigma, sx, dv, dw, f, grad, c, jv, hv, kv, fork->side, nullptr);
+    if (e == cudaSuccess)
+      launch_gen_part<MASK>(d, rt, mk, x, sigma, sx, dv, dw, f, grad, c, jv, hv, kv, fork->side, nullptr,
+                            fork->gen_after);
   }
   if (e == cudaSuccess) e = cudaEventRecord(fork->ev_bus, fork->bus);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s, fork->ev_bus, 0);
@@ -723,7 +730,8 @@ cudaError_t launch_chunked(const Dev &d, unsigned rt, unsigned mk, const double 
     e = cudaEventRecord(fork->ev_join, fork->side);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, fork->ev_join, 0);
   }
-  if (e == cudaSuccess && !side) launch_gen_part<MASK>(d, rt, mk, x, sigma, sx, dv, dw, f, grad, c, jv, hv, kv, s, nullptr);
+  if (e == cudaSuccess && !side)
+    launch_gen_part<MASK>(d, rt, mk, x, sigma, sx, dv, dw, f, grad, c, jv, hv, kv, s, nullptr, fork->gen_after);
   return e;
 }
 
@@ -751,7 +759,8 @@ cudaError_t launch_all(const Dev &d, unsigned rt, const double *x, const double 
     cudaError_t e = cudaEventRecord(fork->ev_fork, s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(fork->side, fork->ev_fork, 0);
     if (e != cudaSuccess) return e;
-    launch_gen_part<MASK>(d, rt, mk, x, sigma, sx, dv, dw, f, grad, c, jv, hv, kv, fork->side, nullptr);
+    launch_gen_part<MASK>(d, rt, mk, x, sigma, sx, dv, dw, f, grad, c, jv, hv, kv, fork->side, nullptr,
+                          fork->gen_after);
     return cudaSuccess;
   };
   if ((mk & rest) && d.L > 0) {
@@ -789,7 +798,8 @@ cudaError_t launch_all(const Dev &d, unsigned rt, const double *x, const double 
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, fork->ev_join, 0);
     return e;
   }
-  launch_gen_part<MASK>(d, rt, mk, x, sigma, sx, dv, dw, f, grad, c, jv, hv, kv, s, prof);
+  launch_gen_part<MASK>(d, rt, mk, x, sigma, sx, dv, dw, f, grad, c, jv, hv, kv, s, prof,
+                        fork ? fork->gen_after : nullptr);
   return cudaSuccess;
 }
 
@@ -1050,6 +1060,12 @@ int mpopf_set_sweep_schedule(mpopf_handle *h, int32_t chunk_periods, int32_t fla
   }
   h->fork.chunk = chunk_periods;
   h->fork.flags = flags;
+  return MPOPF_OK;
+}
+
+int mpopf_set_gen_dependency(mpopf_handle *h, void *event) {
+  if (!h) return fail(MPOPF_ERR_ARG, "mpopf_set_gen_dependency: NULL handle");
+  h->fork.gen_after = static_cast<cudaEvent_t>(event);
   return MPOPF_OK;
 }
 

@@ -138,6 +138,7 @@ def lib():
             "mpopf_launch_count": (ctypes.c_int, [_P, _U]),
             "mpopf_set_sweep_schedule": (ctypes.c_int, [_P, _I32, _I32]),
             "mpopf_get_sweep_schedule": (ctypes.c_int, [_P, _P, _P]),
+            "mpopf_set_gen_dependency": (ctypes.c_int, [_P, _P]),
             "mpopf_fp64_issue_rate": (ctypes.c_int, [_I32, _P, _P]),
             "mpopf_profile_start": (ctypes.c_int, [_P, _I32]),
             "mpopf_profile_stop": (ctypes.c_int, [_P, _P, _P]),
@@ -161,7 +162,7 @@ def exported_symbols():
             "mpopf_coo_to_csc", "mpopf_ipm_prepare", "mpopf_ipm_rhs", "mpopf_ipm_recover", "mpopf_batch_create",
             "mpopf_batch_set_io", "mpopf_batch_sweep", "mpopf_batch_set_schedule", "mpopf_batch_get_schedule",
             "mpopf_batch_tune", "mpopf_batch_status", "mpopf_batch_test_stall", "mpopf_batch_destroy",
-            "mpopf_launch_count", "mpopf_set_sweep_schedule", "mpopf_get_sweep_schedule",
+            "mpopf_launch_count", "mpopf_set_sweep_schedule", "mpopf_get_sweep_schedule", "mpopf_set_gen_dependency",
             "mpopf_fp64_issue_rate", "mpopf_profile_start", "mpopf_profile_stop", "mpopf_destroy", "mpopf_last_error"]
 
 
@@ -311,6 +312,14 @@ class Handle:
         """Period chunks of the evaluation launches (0: one launch per kernel);
         flags SCHED_BUS_PRIORITY, SCHED_GEN_FIRST, SCHED_PDL (see mpopf_set_sweep_schedule)."""
         _check(lib().mpopf_set_sweep_schedule(self.h, int(chunk_periods), int(flags)), "mpopf_set_sweep_schedule")
+
+    def set_gen_dependency(self, event):
+        """Later evaluations' generator work also waits for `event` (a
+        torch.cuda.Event recorded by the caller before each evaluation, e.g.
+        after a shard's halo exchange on another stream); None removes it."""
+        self._gen_event = event  # kept alive while the handle may use it
+        _check(lib().mpopf_set_gen_dependency(self.h, None if event is None else ctypes.c_void_p(event.cuda_event)),
+               "mpopf_set_gen_dependency")
 
     def sweep_schedule(self):
         p = np.zeros(1, np.int32)

@@ -111,6 +111,19 @@ def exchange_halos(plan: dict, x, dvec, rank: int, world: int, group=None):
                 t.copy_(b)
 
 
+def exchange_halos_async(plan: dict, x, dvec, rank: int, world: int, stream, event, group=None):
+    """The halo exchange on its own CUDA `stream` (ordered after the work
+    enqueued on the current stream so far), with `event` recorded on that
+    stream after it.  A shard handle whose generator work waits for `event`
+    (Handle.set_gen_dependency) can be evaluated right away: its branch and
+    bus kernels, which read no halo value, overlap the exchange."""
+    import torch
+    stream.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(stream):
+        exchange_halos(plan, x, dvec, rank, world, group)
+        event.record(stream)
+
+
 def reduce_objective(f, group=None):
     """The whole objective from the ranks' partial objectives (sum, in place;
     staged through host memory for a device tensor under gloo)."""

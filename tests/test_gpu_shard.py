@@ -163,3 +163,50 @@ def test_benchmark_workload_in_three_shards():
     assert abs(f - float(ref["f"][0])) <= 1e-12 * abs(float(ref["f"][0]))
     for x in hs + [h]:
         x.close()
+
+
+def test_halo_exchange_on_another_stream_is_waited_for():
+    """The halo copies run on a stream of their own, held back by a delay on
+    that stream, while the shards are evaluated at once; the generator work
+    waits for the exchange through the handle's dependency event
+    (mpopf_set_gen_dependency), so the stitched outputs are still exact (a
+    generator kernel that ran early would read the NaN halo slots)."""
+    from paper_2405_14032_b300 import mpopf
+    inst = synth.with_reactive_ramp(synth.make_instance(64, 300, 480, 60, 180, 9))
+    pt = synth.make_point(9, inst)
+    h = mpopf.Handle(inst)
+    ref = h.sweep(_dev(pt.x), _dev(pt.lam), pt.sigma, _dev(pt.sigma_x), _dev(pt.dvec), pt.delta_w)
+    torch.cuda.synchronize()
+    spans = shard.split(inst.T, 3)
+    plans = [mpopf.shard_plan(inst.net, inst.T, t0, t1) for t0, t1 in spans]
+    hs = [mpopf.Handle(inst, shard=sp) for sp in spans]
+    ins = []
+    for p in plans:
+        nan = lambda k: torch.full((k,), float("nan"), dtype=torch.float64, device="cuda")
+        x, sx, lam, dv = nan(p["n"]), nan(p["n"]), nan(p["m"]), nan(p["m"])
+        shard.scatter(p, "x", _dev(pt.x), x)
+        shard.scatter(p, "x", _dev(pt.sigma_x), sx)
+        shard.scatter(p, "rows", _dev(pt.lam), lam)
+        shard.scatter(p, "rows", _dev(pt.dvec), dv)
+        ins.append((x, lam, sx, dv))
+    halo = torch.cuda.Stream()
+    ev = torch.cuda.Event()
+    halo.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(halo):
+        torch.cuda._sleep(50_000_000)  # holds the copies back (a bounded busy loop on this stream)
+        _exchange(plans, [i[0] for i in ins], [i[3] for i in ins])
+        ev.record(halo)
+    outs = []
+    for hs_, (x, lam, sx, dv) in zip(hs, ins):
+        hs_.set_gen_dependency(ev)
+        outs.append(hs_.sweep(x, lam, pt.sigma, sx, dv, pt.delta_w))
+    torch.cuda.synchronize()
+    for key, what in KEYS:
+        whole = torch.full_like(ref[key], float("nan"))
+        for p, out in zip(plans, outs):
+            shard.gather(p, what, out[key], whole)
+        assert torch.equal(whole, ref[key]), key
+    for hs_ in hs:
+        hs_.set_gen_dependency(None)
+        hs_.close()
+    h.close()
