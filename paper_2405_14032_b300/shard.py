@@ -124,6 +124,25 @@ def exchange_halos_async(plan: dict, x, dvec, rank: int, world: int, stream, eve
         event.record(stream)
 
 
+def reduce_objective_async(f, buf, stream, group=None):
+    """The whole objective into `buf` (a one-element tensor on f's device):
+    f is copied into buf and buf summed over the ranks on `stream`, ordered
+    after the work enqueued on the current stream so far; later work on
+    `stream` is ordered after the sum, while the current stream goes on (the
+    next evaluation, which rewrites f, does not wait for it).  Under gloo the
+    sum is taken synchronously (host-staged)."""
+    import torch
+    import torch.distributed as dist
+    stream.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(stream):
+        buf.copy_(f)
+        if dist.get_backend(group) == "gloo":
+            reduce_objective(buf, group)
+        else:
+            dist.all_reduce(buf, op=dist.ReduceOp.SUM, group=group, async_op=True).wait()
+    return buf
+
+
 def reduce_objective(f, group=None):
     """The whole objective from the ranks' partial objectives (sum, in place;
     staged through host memory for a device tensor under gloo)."""
