@@ -16,14 +16,15 @@ from paper_2405_14032_b300 import build, synth
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "c", "sweep_host_example.c")
+SHARD_SRC = os.path.join(HERE, "c", "shard_plan_example.c")
 GCC = shutil.which("gcc")
 
 
-def _compile(tmp_path):
-    exe = str(tmp_path / "sweep_host_example")
+def _compile(tmp_path, src=SRC):
+    exe = str(tmp_path / os.path.splitext(os.path.basename(src))[0])
     build.build()
     subprocess.run([GCC, "-std=c99", "-Wall", "-Wextra", "-Werror", "-ffp-contract=off", "-I",
-                    os.path.join(build.ROOT, "include"), SRC, "-o", exe, "-L", build.HERE, "-lmpopf",
+                    os.path.join(build.ROOT, "include"), src, "-o", exe, "-L", build.HERE, "-lmpopf",
                     "-Wl,-rpath," + build.HERE], check=True, capture_output=True, text=True)
     return exe
 
@@ -81,3 +82,30 @@ def test_c_caller_outputs_equal_the_reference(tmp_path):
     parts = np.split(rest, np.cumsum([n, m, nj, nh]))
     for got, want in zip(parts, (ref["g"], ref["c"], ref["jv"], ref["hv"], kv)):
         assert np.array_equal(got, want)
+
+
+@pytest.mark.skipif(GCC is None, reason="gcc not available")
+def test_shard_plan_from_c_matches_the_binding(tmp_path):
+    """tests/c/shard_plan_example.c asks for the layout of three period
+    shards (no device needed); sizes, halo offsets and ranges equal the
+    Python binding's, and a split with t0 = t1 is refused."""
+    from paper_2405_14032_b300 import mpopf
+    r = subprocess.run([_compile(tmp_path, SHARD_SRC)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    lines = [list(map(int, ln.split())) for ln in r.stdout.split("\n") if ln.strip()]
+    inst = _instance()
+    net = inst.net
+    pos = 0
+    for t0, t1 in ((0, 2), (2, 3), (3, 5)):
+        head = lines[pos]
+        p = mpopf.shard_plan(net, 5, t0, t1)
+        assert head[:5] == [t0, t1, p["local_periods"], p["own0"], p["own1"]]
+        assert head[5:10] == [p["n"], p["m"], p["nnz_jac"], p["nnz_hess"], p["nnz_kkt"]]
+        assert head[10:14] == [p["x_recv"][0], p["x_send"][0], p["d_recv"][0], p["d_send"][0]]
+        n = head[14]
+        got = {}
+        for what, lo, gl, cnt in lines[pos + 1:pos + 1 + n]:
+            got.setdefault(mpopf.RANGE_NAMES[what], []).append((lo, gl, cnt))
+        assert got == {k: v for k, v in p["ranges"].items() if v}
+        pos += 1 + n
+    assert pos == len(lines)
