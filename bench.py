@@ -593,7 +593,9 @@ def graph_sweeps(torch, count=1000):
         torch.cuda.synchronize()
         graph_ms = e0.elapsed_time(e1)
         alg = algorithmic_bytes(h.n, h.m, h.nnz_jac, h.nnz_hess, h.nnz_kkt, D, T)
+        cpu = cpu_baseline(inst, pt, budget_s=4.0)
         res[name] = {"sweeps": count, "n": h.n, "m": h.m, "graph_ms_per_sweep": graph_ms / count,
+                     "cpu_oracle": cpu,
                      "plain_ms_per_sweep": plain_ms / count, "sweeps_per_s_graph": count / (graph_ms * 1e-3),
                      "sweeps_per_s_plain": count / (plain_ms * 1e-3),
                      "algorithmic_bytes_per_sweep": alg, "gbs_graph": alg * count / (graph_ms * 1e-3) / 1e9}
