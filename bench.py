@@ -652,6 +652,51 @@ def batched_iterates(torch, k=32, launches=32):
     return res
 
 
+# Synthetic networks with the sizes of the benchmark cases of the paper's
+# Table II (bus counts from the case names; branch and generator counts the
+# commonly reported sizes of those public cases; loads at 0.6 of the buses, as
+# in every synthetic network here) and the horizons the paper runs them with.
+TABLE2_SHAPES = [("case30", 30, 41, 6, 30), ("case118", 118, 186, 54, 168), ("case118", 118, 186, 54, 10080),
+                 ("case1354", 1354, 1991, 260, 30), ("case9241", 9241, 16049, 1445, 30),
+                 ("case9241", 9241, 16049, 1445, 180)]
+
+
+def table2_shapes(torch, reps=10):
+    """The full sweep on seeded synthetic networks shaped like the paper's
+    Table II cases (the case files themselves are not available): time per
+    sweep (CUDA events, mean of `reps` after 3 warm-ups) and algorithmic
+    bandwidth."""
+    from paper_2405_14032_b300 import mpopf, synth
+    dev = lambda a: torch.as_tensor(a, dtype=torch.float64, device="cuda")
+    peak = measured_peaks().get("hbm_gbs")
+    out = {}
+    for k, (case, N, L, G, T) in enumerate(TABLE2_SHAPES):
+        D = round(0.6 * N)
+        inst = synth.make_instance(50 + k, N, L, G, D, T)
+        pt = synth.make_point(50 + k, inst)
+        h = mpopf.Handle(inst)
+        x, lam, sx, dv = dev(pt.x), dev(pt.lam), dev(pt.sigma_x), dev(pt.dvec)
+        res = h.new_outputs()
+        for _ in range(3):
+            h.sweep(x, lam, pt.sigma, sx, dv, pt.delta_w, out=res)
+        torch.cuda.synchronize()
+        e0, e1 = _events(torch)
+        e0.record()
+        for _ in range(reps):
+            h.sweep(x, lam, pt.sigma, sx, dv, pt.delta_w, out=res)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        alg = algorithmic_bytes(h.n, h.m, h.nnz_jac, h.nnz_hess, h.nnz_kkt, D, T)
+        gbs = alg / (ms * 1e-3) / 1e9
+        out[f"{case}_T{T}"] = {"n_bus": N, "n_branch": L, "n_gen": G, "n_load": D, "T": T, "n": h.n, "m": h.m,
+                               "ms_per_sweep": ms, "sweeps_per_s": 1e3 / ms, "gbs": gbs,
+                               "hbm_frac": gbs / peak if peak else None}
+        del res, x, lam, sx, dv
+        h.close()
+    return out
+
+
 def ipm_step_timing(torch, reps=5):
     """One whole interior-point step on the 2,000-bus, T = 24 network (seed 2)
     at an interior point (interval midpoints, unit duals, delta_w = 50 so that M
@@ -1101,6 +1146,7 @@ def run_ours(args, world, rank, local):
             line["unfused"]["fused_ms"] = ms_step
             line["unfused"]["speedup_fused"] = line["unfused"]["unfused_ms"] / ms_step
             line["ipm_step"] = ipm_step_timing(torch)
+            line["table2_shapes"] = table2_shapes(torch)
         print(json.dumps(line), flush=True)
     h.close()
     if world > 1:
