@@ -90,20 +90,25 @@ def measured_peaks():
 
 
 BRANCH_KERNEL_END = "// The branch kernel over elements [first, end) on stream s"
+DESCRIPTOR_END = "// Optional per-kernel CUDA-event timing of the evaluation launches."
 
 
 def kernel_source_hash():
     """Hash of the code the branch kernel is compiled from: the device
-    descriptor's header, the device helpers, and the kernels file up to the end
-    of k_branch (its helpers, branch_body and the kernel itself; the launchers
-    and the other kernels follow), comments and whitespace removed, so that a
-    comment edit or a change elsewhere keeps the counters valid."""
+    descriptor and constants of the internal header (up to the launch-side
+    declarations that follow them), the device helpers, and the kernels file
+    up to the end of k_branch (its helpers, branch_body and the kernel itself;
+    the launchers and the other kernels follow), comments and whitespace
+    removed, so that a comment edit or a change elsewhere keeps the counters
+    valid."""
     h = hashlib.sha256()
     for name in ("mpopf_internal.cuh", "mpopf_device.cuh", "mpopf_kernels.cu"):
         with open(os.path.join(ROOT, "paper_2405_14032_b300", "csrc", name)) as fh:
             text = fh.read()
         if name == "mpopf_kernels.cu":
             text = text[:text.index(BRANCH_KERNEL_END)]
+        if name == "mpopf_internal.cuh":
+            text = text[:text.index(DESCRIPTOR_END)]
         text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
         text = re.sub(r"//[^\n]*", " ", text)
         h.update(" ".join(text.split()).encode())
