@@ -90,3 +90,48 @@ def test_halo_exchange_gloo(world):
     order = np.lexsort((cols, rows))
     assert np.array_equal(rows[order], np.repeat(np.arange(o.n), np.diff(rp)))
     assert np.array_equal(cols[order], rc) and np.array_equal(vals[order], rv)
+
+
+def _lost_peer_worker(rank, world, port, q):
+    import datetime
+    import time
+
+    import torch
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=10))
+    from paper_2405_14032_b300 import mpopf, shard
+    inst = _instance()
+    t0, t1 = shard.split(inst.T, world)[rank]
+    plan = mpopf.shard_plan(inst.net, inst.T, t0, t1)
+    if rank == 1:
+        q.put((rank, "left"))
+        q.close()
+        q.join_thread()  # the message is sent before the process goes
+        os._exit(0)  # leaves before its first exchange, without a goodbye
+    x = torch.zeros(plan["n"], dtype=torch.float64)
+    dv = torch.zeros(plan["m"], dtype=torch.float64)
+    start = time.perf_counter()
+    try:
+        shard.exchange_halos(plan, x, dv, rank, world)
+        q.put((rank, "no error"))
+    except Exception as exc:  # the lost peer surfaces as an error, not a hang
+        q.put((rank, f"error after {time.perf_counter() - start:.1f}s: {type(exc).__name__}"))
+
+
+def test_lost_peer_is_an_error_not_a_hang():
+    """A rank that leaves before a halo exchange: its neighbour's exchange
+    ends with an error (the closed connection, or the process group's
+    10-second timeout) instead of waiting forever."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_lost_peer_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = dict(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+    assert res[1] == "left"
+    assert res[0].startswith("error after"), res[0]
+    assert float(res[0].split()[2].rstrip("s:")) < 60.0
