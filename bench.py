@@ -983,6 +983,7 @@ def run_ours(args, world, rank, local):
         import torch.distributed as dist
         torch.cuda.set_device(local)
         dist.init_process_group(args.dist_backend)
+        dist.barrier()  # a collective of every rank first: the halo exchanges' batched P2P calls never are
     dev = torch.device("cuda", local)
     from paper_2405_14032_b300 import mpopf, shard, synth
 
