@@ -63,6 +63,28 @@ MUTATIONS = {
     "reactive ramp limit from the P ramp": ("lo = -M.qramp[comp]; hi = M.qramp[comp];",
                                             "lo = -M.ramp[comp]; hi = M.ramp[comp];", 0,
                                             lambda: P.test_bounds_written_out_from_the_model(True, 3)),
+    "condensed-matrix diagonal without delta_w": ("contrib.push_back({{j, j}, sigx[j] + delta_w});",
+                                                  "contrib.push_back({{j, j}, sigx[j]});", 0,
+                                                  lambda: P.test_kkt_dense_brute_force(_cfg1())),
+    "W v with a transposed entry": ("b = std::fma(e.v, v[e.r], b);", "b = std::fma(e.v, v[e.c], b);", 0,
+                                    lambda: P.test_vjp_jvp_hvp(_cfg1())),
+    "load tangent sign": ("acc = acc - dl[t * M.D + d];", "acc = acc + dl[t * M.D + d];", 0,
+                          lambda: P.test_jvp_load_tangent_finite_difference()),
+    "load adjoint sign": ("if (gpd) gpd[t * M.D + d] = -y[r_k8(M, t, M.lbus[d])];",
+                          "if (gpd) gpd[t * M.D + d] = y[r_k8(M, t, M.lbus[d])];", 0,
+                          lambda: P.test_load_adjoint_complex_step()),
+    "Sigma with the bound reciprocals swapped": ("return std::fma(zl, r.rl, zu * r.ru);",
+                                                "return std::fma(zl, r.ru, zu * r.rl);", 0,
+                                                lambda: P.test_ipm_condensation_solves_full_lifted_system(1e-3, 1e-4)),
+    "multiplier step without delta_w": ("dy[i] = std::fma(sg + delta_w, d, -qs);", "dy[i] = std::fma(sg, d, -qs);", 0,
+                                        lambda: P.test_ipm_condensation_solves_full_lifted_system(0.3, 0.7)),
+    "cost constant dropped": ("acc = acc + std::fma(std::fma(M.c2[g], pg, M.c1[g]), pg, M.c0[g]);",
+                              "acc = acc + std::fma(std::fma(M.c2[g], pg, M.c1[g]), pg, 0.0);", 0,
+                              lambda: P.test_objective_with_constant_cost()),
+    "ramp rows of a window's first period skipped": (
+        "const int64_t a = std::max<int64_t>(t0, 1), b = std::max<int64_t>(t1, 1);",
+        "const int64_t a = t0 + 1, b = std::max<int64_t>(t1, 1);", 0,
+        lambda: P.test_windowed_outputs_agree_with_full()),
     "CSC drops a duplicate": ("vals[k] = vals[k] + coo[v[p].e];", "vals[k] = coo[v[p].e];", 0,
                               lambda: P.test_csc_compression_matches_scipy_and_dense(1)),
 }

@@ -460,12 +460,14 @@ def test_windowed_outputs_agree_with_full():
     full = o.eval(pt.x, pt.lam, pt.sigma)
     rows, rowlen, cols, vals = o.kkt(pt.x, pt.lam, pt.sigma, pt.sigma_x, pt.dvec, pt.delta_w)
     rowptr = np.concatenate([[0], np.cumsum(rowlen)])
+    covered = {k: np.zeros(full[k].size, np.int32) for k in ("g", "c", "jv", "hv")}
     for t0, t1 in ((0, 2), (2, 5), (5, 6)):
         w = o.eval(pt.x, pt.lam, pt.sigma, t0, t1)
         for k in ("g", "c", "jv", "hv"):
             ok = ~np.isnan(w[k])
             assert ok.any()
             assert np.array_equal(w[k][ok], full[k][ok])
+            covered[k] += ok
         wr, wl, wc, wv = o.kkt(pt.x, pt.lam, pt.sigma, pt.sigma_x, pt.dvec, pt.delta_w, t0, t1)
         pos = np.concatenate([np.arange(rowptr[r], rowptr[r + 1]) for r in wr])
         assert np.array_equal(cols[pos], wc) and np.array_equal(vals[pos], wv)
@@ -473,6 +475,31 @@ def test_windowed_outputs_agree_with_full():
         gxf, _, _ = o.vjp(pt.x, pt.lam)
         ok = ~np.isnan(gx)
         assert np.array_equal(gx[ok], gxf[ok])
+    # the windows partition the horizon: every entry (the ramp rows of the
+    # first period of each window included) is written by exactly one window
+    for k, cnt in covered.items():
+        assert np.all(cnt == 1), (k, np.nonzero(cnt != 1)[0][:5])
+
+
+def test_objective_with_constant_cost():
+    """f = sum over periods and generators of c2 pg^2 + c1 pg + c0 (Eq. 1a with
+    the quadratic cost), written out, with every coefficient nonzero (the
+    synthetic networks have c0 = 0)."""
+    net = H.network(4, [0, 1, 2], [1, 2, 3], [0.01] * 3, [0.1] * 3, [0.0] * 3, gen_bus=[0, 2, 3], load_bus=[1],
+                    c2=[0.02, 0.05, 0.08], c1=[11.0, 17.0, 23.0])
+    net.gen_c0[:] = [3.5, -1.25, 7.0]
+    T = 3
+    o = oracle.Oracle(H.instance(net, T))
+    sl = H.var_slices(net, T)
+    x = np.zeros(o.n)
+    x[sl["pg"]] = [0.5, 1.5, 2.5, 0.25, 1.0, 2.0, 0.75, 1.25, 1.75]
+    f = o.eval(x, np.zeros(o.m), 1.0)["f"]
+    want = 0.0
+    for t in range(T):
+        for g in range(3):
+            pg = x[sl["pg"].start + t * 3 + g]
+            want += net.gen_c2[g] * pg * pg + net.gen_c1[g] * pg + net.gen_c0[g]
+    assert abs(f - want) <= 1e-13 * abs(want)
 
 
 # ---------------------------------------------------------------------------
