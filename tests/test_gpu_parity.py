@@ -61,7 +61,8 @@ class Case:
 
 def _edge_network():
     """Parallel branches, an isolated bus, several generators on one bus, a bus
-    with no generator or load, tap/shift branches (asymmetric pi-model)."""
+    with no generator or load, tap/shift branches (asymmetric pi-model),
+    nonzero cost constants."""
     f = [0, 1, 1, 2, 3, 0, 4, 2, 5]
     t = [1, 2, 2, 3, 4, 4, 5, 0, 6]
     L = len(f)
@@ -71,11 +72,13 @@ def _edge_network():
     tap[3], shift[3] = 1.04, 0.05
     tap[6] = 0.97
     shift[8] = -0.08
-    return H.network(8, f, t, rng.uniform(0.005, 0.05, L), rng.uniform(0.02, 0.2, L), rng.uniform(0, 0.05, L),
-                     gen_bus=[1, 1, 1, 4, 6, 0], load_bus=[2, 2, 3, 6, 7], ref=3, tap=tap, shift=shift,
-                     gs=rng.uniform(0, 0.05, 8) * (rng.uniform(size=8) < 0.5),
-                     bs=rng.uniform(0, 0.3, 8) * (rng.uniform(size=8) < 0.5),
-                     c2=rng.uniform(0.01, 0.1, 6), c1=rng.uniform(10, 40, 6))
+    net = H.network(8, f, t, rng.uniform(0.005, 0.05, L), rng.uniform(0.02, 0.2, L), rng.uniform(0, 0.05, L),
+                    gen_bus=[1, 1, 1, 4, 6, 0], load_bus=[2, 2, 3, 6, 7], ref=3, tap=tap, shift=shift,
+                    gs=rng.uniform(0, 0.05, 8) * (rng.uniform(size=8) < 0.5),
+                    bs=rng.uniform(0, 0.3, 8) * (rng.uniform(size=8) < 0.5),
+                    c2=rng.uniform(0.01, 0.1, 6), c1=rng.uniform(10, 40, 6))
+    net.gen_c0[:] = rng.uniform(-5.0, 5.0, 6)  # the synthetic networks have c0 = 0
+    return net
 
 
 def _cases():
