@@ -463,10 +463,14 @@ int mpopf_launch_count(const mpopf_handle *h, unsigned outputs);
  * CTAs may be scheduled while the branch kernel's last CTAs run; it waits
  * (griddepcontrol.wait) for the branch kernel's completion before reading its
  * records.
- * Per-kernel profiling (mpopf_profile_start) times unchunked launches without
- * programmatic dependencies.
+ * MPOPF_SCHED_SPLIT_BUS (with P = 0): the bus work as two kernels after the
+ * branch kernel, side by side: the balance rows with their J rows, the shunt W
+ * entries, the gradient zeros and the reference row on the internal second
+ * stream, the va / vm rows of M on `stream`.
+ * Per-kernel profiling (mpopf_profile_start) times unchunked, unsplit launches
+ * without programmatic dependencies.
  * MPOPF_ERR_ARG for P < 0 or unknown flags. */
-enum { MPOPF_SCHED_BUS_PRIORITY = 1, MPOPF_SCHED_GEN_FIRST = 2, MPOPF_SCHED_PDL = 4 };
+enum { MPOPF_SCHED_BUS_PRIORITY = 1, MPOPF_SCHED_GEN_FIRST = 2, MPOPF_SCHED_PDL = 4, MPOPF_SCHED_SPLIT_BUS = 8 };
 int mpopf_set_sweep_schedule(mpopf_handle *h, int32_t chunk_periods, int32_t flags);
 
 /* An extra dependency of the generator work (generator x period kernel and

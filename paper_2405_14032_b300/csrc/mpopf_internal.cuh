@@ -117,7 +117,7 @@ struct Prof {
 // incidence records are still in L2.
 constexpr int kMaxChunks = 64;
 enum { SCHED_BUS_PRIORITY = MPOPF_SCHED_BUS_PRIORITY, SCHED_GEN_FIRST = MPOPF_SCHED_GEN_FIRST,
-       SCHED_PDL = MPOPF_SCHED_PDL };
+       SCHED_PDL = MPOPF_SCHED_PDL, SCHED_SPLIT_BUS = MPOPF_SCHED_SPLIT_BUS };
 struct Fork {
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;

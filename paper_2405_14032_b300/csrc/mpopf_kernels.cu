@@ -358,7 +358,10 @@ void launch_branch(const Dev &d, unsigned rt, const double *x, const double *lam
 // once for a launch without such a dependency.
 __device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
-template <unsigned MASK, bool COH, bool WAIT = false>
+// PART: 0 everything; 1 the balance rows, their J rows, the shunt W entries,
+// the gradient zeros and the reference row; 2 the va / vm rows of M (the two
+// halves of a split schedule, run side by side).
+template <unsigned MASK, bool COH, bool WAIT = false, int PART = 0>
 __device__ __forceinline__ void bus_body(const Dev &d, int32_t idx, unsigned rt, const double *__restrict__ x,
                                          const double *__restrict__ lam, const double *__restrict__ sx,
                                          const double *__restrict__ dv, double dw, double *__restrict__ grad,
@@ -373,11 +376,11 @@ __device__ __forceinline__ void bus_body(const Dev &d, int32_t idx, unsigned rt,
   const int32_t tn = t * N + n;  // (period, bus) position of every per-bus array
   const int64_t tN = (int64_t)t * N;
   const int64_t L = d.L, G = d.G;
-  if (mk & MPOPF_OUT_GRAD) {
+  if (PART != 2 && (mk & MPOPF_OUT_GRAD)) {
     grad[tn] = 0.0;
     grad[d.x_vm + tn] = 0.0;
   }
-  if (n == d.ref) {
+  if (PART != 2 && n == d.ref) {
     if (mk & MPOPF_OUT_CONS) c[t] = __ldg(x + tN + n);
     if (mk & MPOPF_OUT_JAC) jv[t] = 1.0;
   }
@@ -392,7 +395,7 @@ __device__ __forceinline__ void bus_body(const Dev &d, int32_t idx, unsigned rt,
   // a bus launch that may start before the branch launch has finished waits
   // here, before its first read of the records
   if (WAIT && have_rec) grid_dependency_wait();
-  if (mk & MPOPF_OUT_CONS) {
+  if (PART != 2 && (mk & MPOPF_OUT_CONS)) {
     const double vm2 = vm * vm;
     double aP = 0.0, aQ = 0.0;
     const int64_t pgb = d.x_pg + (int64_t)t * G, qgb = d.x_qg + (int64_t)t * G;
@@ -433,7 +436,7 @@ __device__ __forceinline__ void bus_body(const Dev &d, int32_t idx, unsigned rt,
     c[d.c_k9 + tn] = aQ;
   }
   const double J8 = m2gs * vm, J9 = p2bs * vm;
-  if (mk & MPOPF_OUT_JAC) {
+  if (PART != 2 && (mk & MPOPF_OUT_JAC)) {
     double *r8 = jv + d.j_k8 + (int64_t)t * d.jk8_per + __ldg(d.jk8_off + n);
     double *r9 = r8 + (d.j_k9 - d.j_k8);
     r8[0] = J8;
@@ -444,11 +447,11 @@ __device__ __forceinline__ void bus_body(const Dev &d, int32_t idx, unsigned rt,
   }
   if (!(mk & (MPOPF_OUT_HESS | MPOPF_OUT_KKT))) return;
   const double WP = __ldg(lam + d.c_k8 + tn) * m2gs, WQ = __ldg(lam + d.c_k9 + tn) * p2bs;
-  if (mk & MPOPF_OUT_HESS) {
+  if (PART != 2 && (mk & MPOPF_OUT_HESS)) {
     hv[d.h_sh + 2 * (int64_t)tn] = WP;
     hv[d.h_sh + 2 * (int64_t)tn + 1] = WQ;
   }
-  if (!(mk & MPOPF_OUT_KKT)) return;
+  if (PART == 1 || !(mk & MPOPF_OUT_KKT)) return;
 
   const int32_t nd = __ldg(d.bus_nd + n), ndlt = __ldg(d.bus_ndlt + n);
   double *va_row = kv + d.m_va + (int64_t)t * d.mb_va + __ldg(d.mo_va + n);
@@ -496,7 +499,7 @@ __device__ __forceinline__ void bus_body(const Dev &d, int32_t idx, unsigned rt,
 }
 
 // Elements [first, end) of the bus x period range (t N + position).
-template <unsigned MASK>
+template <unsigned MASK, int PART = 0>
 __global__ void __launch_bounds__(MPOPF_BUS_BLOCK) k_bus(Dev d, unsigned rt, const double *__restrict__ x,
                                                 const double *__restrict__ lam, const double *__restrict__ sx,
                                                 const double *__restrict__ dv, double dw, double *__restrict__ grad,
@@ -505,7 +508,7 @@ __global__ void __launch_bounds__(MPOPF_BUS_BLOCK) k_bus(Dev d, unsigned rt, con
                                                 int32_t end) {
   const int32_t idx = first + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
   if (idx >= end) return;
-  bus_body<MASK, false, true>(d, idx, rt, x, lam, sx, dv, dw, grad, c, jv, hv, kv);
+  bus_body<MASK, false, true, PART>(d, idx, rt, x, lam, sx, dv, dw, grad, c, jv, hv, kv);
 }
 
 // ---------------------------------------------------------------------------
@@ -772,7 +775,22 @@ cudaError_t launch_all(const Dev &d, unsigned rt, const double *x, const double 
     const cudaError_t e = fork_gen();
     if (e != cudaSuccess) return e;
   }
-  if (mk & rest) {
+  // Split bus work (SCHED_SPLIT_BUS): the balance part on the fork's bus
+  // stream and the M part on s, side by side after the branch kernel.
+  const bool split = fork && (fork->flags & SCHED_SPLIT_BUS) && fork->bus && !prof && (mk & MPOPF_OUT_KKT) &&
+                     (mk & (MPOPF_OUT_GRAD | MPOPF_OUT_CONS | MPOPF_OUT_JAC | MPOPF_OUT_HESS));
+  if (split) {
+    const unsigned grid = (unsigned)(((int64_t)W * d.N + MPOPF_BUS_BLOCK - 1) / MPOPF_BUS_BLOCK);
+    const int32_t bf = d.w0 * d.N, be = d.w1 * d.N;
+    cudaError_t e = cudaEventRecord(fork->ev_chunk[0], s);  // after the branch kernel
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(fork->bus, fork->ev_chunk[0], 0);
+    if (e != cudaSuccess) return e;
+    k_bus<MASK, 1><<<grid, MPOPF_BUS_BLOCK, 0, fork->bus>>>(d, rt, x, lam, sx, dv, dw, grad, c, jv, hv, kv, bf, be);
+    k_bus<MASK, 2><<<grid, MPOPF_BUS_BLOCK, 0, s>>>(d, rt, x, lam, sx, dv, dw, grad, c, jv, hv, kv, bf, be);
+    e = cudaEventRecord(fork->ev_bus, fork->bus);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, fork->ev_bus, 0);
+    if (e != cudaSuccess) return e;
+  } else if (mk & rest) {
     Timed tm(prof, s, KIND_BUS);
     const unsigned grid = (unsigned)(((int64_t)W * d.N + MPOPF_BUS_BLOCK - 1) / MPOPF_BUS_BLOCK);
     const int32_t bf = d.w0 * d.N, be = d.w1 * d.N;
@@ -1049,7 +1067,7 @@ int mpopf_launch_count(const mpopf_handle *h, unsigned outputs) {
 
 int mpopf_set_sweep_schedule(mpopf_handle *h, int32_t chunk_periods, int32_t flags) {
   if (!h) return fail(MPOPF_ERR_ARG, "mpopf_set_sweep_schedule: NULL handle");
-  if (chunk_periods < 0 || (flags & ~(SCHED_BUS_PRIORITY | SCHED_GEN_FIRST | SCHED_PDL)))
+  if (chunk_periods < 0 || (flags & ~(SCHED_BUS_PRIORITY | SCHED_GEN_FIRST | SCHED_PDL | SCHED_SPLIT_BUS)))
     return fail(MPOPF_ERR_ARG, "mpopf_set_sweep_schedule: bad argument");
   if ((flags ^ h->fork.flags) & SCHED_BUS_PRIORITY) {
     const cudaError_t e = fork_bus_stream(&h->fork, flags & SCHED_BUS_PRIORITY);

@@ -17,7 +17,7 @@ def _dev(a):
     return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
 
 
-@pytest.mark.parametrize("sched", [(0, 4), (0, 0), (2, 1), (1, 2)])
+@pytest.mark.parametrize("sched", [(0, 4), (0, 0), (2, 1), (1, 2), (0, 8)])
 @pytest.mark.parametrize("shape", [(300, 480, 60, 180, 6), (57, 91, 11, 30, 3), (40, 64, 0, 20, 4)])
 def test_graph_replay_equals_plain(shape, sched):
     """sched: the launch schedule (period chunks with the bus kernels on a

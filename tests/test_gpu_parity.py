@@ -205,14 +205,15 @@ def test_sweep_host_matches_device(name):
             assert np.array_equal(out[k], dev[k]), (name, k)
 
 
-SCHEDULES = [(1, 0), (2, 1), (3, 2), (4, 3), (5, 0), (0, 0), (0, 2), (0, 6)]
+SCHEDULES = [(1, 0), (2, 1), (3, 2), (4, 3), (5, 0), (0, 0), (0, 2), (0, 6), (0, 8), (0, 12)]
 
 
 def test_chunked_schedules_equal_plain(case):
     """Every launch schedule (period chunks, the bus kernel of each chunk on a
     second stream, with and without its priority raised, the generator work
-    forked first or last; the bus kernel as a programmatic dependent launch)
-    gives the plain sweep's outputs bit for bit, for
+    forked first or last; the bus kernel as a programmatic dependent launch;
+    the bus work split in two kernels side by side) gives the plain sweep's
+    outputs bit for bit, for
     every output and for the callbacks alone; the plain sweep matches the
     oracle (test_values_match_oracle), so these do too."""
     name, cs = case
