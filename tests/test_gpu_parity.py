@@ -252,5 +252,5 @@ def test_chunked_schedule_cfg2_and_launch_count():
     with pytest.raises(mp.MpopfError, match="bad argument"):
         cs.h.set_sweep_schedule(-1, 0)
     with pytest.raises(mp.MpopfError, match="bad argument"):
-        cs.h.set_sweep_schedule(4, 8)
+        cs.h.set_sweep_schedule(4, 16)
     cs.h.close()
