@@ -609,6 +609,47 @@ def graph_sweeps(torch, count=1000):
     return res
 
 
+def point_sweeps(torch, k=40, launches=25):
+    """Many sweeps of one network at independent points through
+    mpopf_sweep_points: k perturbed iterates (x_j = x + 1e-3 N(0, 1), drawn on
+    the device from a seeded generator; lam, sigma_x and dvec the same at every
+    point) per call, `launches` calls = k x launches sweeps, for the 2,000-bus
+    T = 24 network (1,000 sweeps at the default k and launches) and the 10k-bus
+    T = 1 network.  Each call launches the sweep's four kernels once over all
+    k points."""
+    from paper_2405_14032_b300 import mpopf, synth
+    dev = lambda a: torch.as_tensor(a, dtype=torch.float64, device="cuda")
+    res = {}
+    for name, (N, L, G, D, T, seed) in (("2000_bus_T24", (2000, 3200, 400, 1200, 24, 2)),
+                                         ("10k_bus_T1", (10000, 16000, 2000, 6000, 1, 3))):
+        inst = synth.make_instance(seed, N, L, G, D, T)
+        pt = synth.make_point(seed, inst)
+        h = mpopf.Handle(inst)
+        gen = torch.Generator(device="cuda").manual_seed(seed)
+        X = dev(pt.x) + 1e-3 * torch.randn((k, h.n), generator=gen, device="cuda", dtype=torch.float64)
+        rep = lambda a: dev(a).unsqueeze(0).repeat(k, 1).contiguous()
+        lam, sx, dv = rep(pt.lam), rep(pt.sigma_x), rep(pt.dvec)
+        out = h.new_point_outputs(k)
+        sweep = lambda: h.sweep_points(X, lam, pt.sigma, sx, dv, pt.delta_w, out=out)
+        for _ in range(3):
+            sweep()
+        torch.cuda.synchronize()
+        e0, e1 = _events(torch)
+        e0.record()
+        for _ in range(launches):
+            sweep()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        alg = algorithmic_bytes(h.n, h.m, h.nnz_jac, h.nnz_hess, h.nnz_kkt, D, T)
+        res[name] = {"points_per_call": k, "calls": launches, "sweeps": k * launches,
+                     "ms_per_sweep": ms / (k * launches), "sweeps_per_s": k * launches / (ms * 1e-3),
+                     "algorithmic_bytes_per_sweep": alg, "gbs": alg * k * launches / (ms * 1e-3) / 1e9}
+        del X, lam, sx, dv, out
+        h.close()
+    return res
+
+
 def batched_iterates(torch, k=32, launches=32):
     """Throughput of many independent sweeps of the 2,000-bus, T = 24 network
     (seed 2): k handles of the same network at k perturbed iterates, one
@@ -1147,6 +1188,7 @@ def run_ours(args, world, rank, local):
             line["ipm"] = ipm_timing(torch, h)
             line["small_sweeps"] = graph_sweeps(torch)
             line["small_sweeps"]["2000_bus_T24_batched_iterates"] = batched_iterates(torch)
+            line["small_sweeps"]["points"] = point_sweeps(torch)
             line["csc"] = csc_timing(torch, h, out)
             line["unfused"] = unfused_timing(torch, h, xs[0], lam, pt.sigma, sx, dv, pt.delta_w, out)
             line["unfused"]["fused_ms"] = ms_step

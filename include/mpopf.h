@@ -248,6 +248,25 @@ int mpopf_sweep(mpopf_handle *h, const double *x, const double *lam, double sigm
                 const double *dvec, double delta_w, double *f, double *grad, double *c, double *jv, double *hv,
                 double *kv, void *stream);
 
+/* Full sweeps of one network at k points (iterates: a line search's trial
+ * points, perturbed iterates, scenarios of the same network) in one launch of
+ * each sweep kernel over all k points (Eq. 3, 4, 6 at every point).  Point j's
+ * inputs and outputs are the j-th of k consecutive arrays of mpopf_sweep's
+ * sizes, all on the device: x [k][n], lam [k][m], sigma_x [k][n], dvec [k][m];
+ * f [k], grad [k][n], c [k][m], jv [k][nnz_jac], hv [k][nnz_hess],
+ * kv [k][nnz_kkt]; sigma and delta_w are shared by the k points.  Each point's
+ * outputs equal mpopf_sweep's at that point bit for bit.  1 <= k <= 65535.
+ * Scratch for the points' incidence records and objective partials
+ * (k x (2 L T x 48 + 8 ceil(T G / 256)) bytes) is allocated by the first
+ * call that needs more than the handle holds (after a device-wide
+ * synchronisation when it replaces a smaller one) and kept by the handle;
+ * calls on one handle must not overlap.  MPOPF_ERR_ARG for a NULL buffer, k
+ * outside the range or a shard handle; MPOPF_ERR_ALLOC when the scratch
+ * cannot be allocated. */
+int mpopf_sweep_points(mpopf_handle *h, int32_t k, const double *x, const double *lam, double sigma,
+                       const double *sigma_x, const double *dvec, double delta_w, double *f, double *grad, double *c,
+                       double *jv, double *hv, double *kv, void *stream);
+
 /* Full sweep from HOST buffers: copies x, lam, sigma_x, dvec to the device,
  * runs the sweep and copies all six outputs back to the host buffers; returns
  * when the outputs are in the host buffers.  The horizon is processed in up to

@@ -208,6 +208,9 @@ struct mpopf_handle {
   mpopf::KktSolver *solver;  // library factorisation of M (built on first use)
   mpopf::Fork fork;          // side stream of the evaluations (created at setup)
   int device;                // CUDA device current at setup (holds every allocation above)
+  // incidence records and objective partials of mpopf_sweep_points (grown on use)
+  double *pts;
+  size_t pts_bytes;
 };
 
 namespace mpopf {

@@ -97,7 +97,9 @@ __device__ __forceinline__ void bulk_done(int lane) {
 }
 
 // SYM: every branch of the model is symmetric (the per-branch test is known).
-template <unsigned MASK, bool BULK = false, bool SYM = false>
+// PTS: the element belongs to point blockIdx.y of a sweep over several points,
+// whose incidence records follow the earlier points' (T periods each).
+template <unsigned MASK, bool BULK = false, bool SYM = false, bool PTS = false>
 __device__ __forceinline__ void branch_body(const Dev &d, int32_t tl, unsigned rt, const double *__restrict__ x,
                                             const double *__restrict__ lam, const double *__restrict__ sx,
                                             const double *__restrict__ dv, double dw, double *__restrict__ grad,
@@ -258,6 +260,7 @@ __device__ __forceinline__ void branch_body(const Dev &d, int32_t tl, unsigned r
   {
     // incidence records of both ends (bus-major, read by k_bus)
     double *R = d.S + (int64_t)t * 2 * L * kRec;
+    if (PTS) R += (int64_t)blockIdx.y * d.T * 2 * L * kRec;
     double2 *recf = reinterpret_cast<double2 *>(R + (int64_t)ends.z * kRec);
     recf[0] = make_double2(Sdd, Svfd);
     recf[1] = make_double2(Svfvf, Svtvf);
@@ -316,7 +319,22 @@ __device__ __forceinline__ void branch_body(const Dev &d, int32_t tl, unsigned r
 }
 
 // Elements [first, end) of the branch x period range (t L + l).
-template <unsigned MASK, bool SYM>
+// The point offsets of a sweep over several points: point j = blockIdx.y
+// reads and writes the j-th of consecutive arrays of the single-point sizes.
+#define MPOPF_POINT_OFFSETS(d)                                        \
+  do {                                                                \
+    const int64_t j_ = blockIdx.y;                                    \
+    x += j_ * (d).n;                                                  \
+    sx += j_ * (d).n;                                                 \
+    dv += j_ * (d).m;                                                 \
+    grad += j_ * (d).n;                                               \
+    c += j_ * (d).m;                                                  \
+    jv += j_ * (d).nnz_jac;                                           \
+    hv += j_ * (d).nnz_hess;                                          \
+    kv += j_ * (d).nnz_kkt;                                           \
+  } while (0)
+
+template <unsigned MASK, bool SYM, bool PTS = false>
 __global__ void __launch_bounds__(MPOPF_BRANCH_BLOCK, MPOPF_BRANCH_MINB)
     k_branch(Dev d, unsigned rt, const double *__restrict__ x, const double *__restrict__ lam,
              const double *__restrict__ sx, const double *__restrict__ dv, double dw, double *__restrict__ grad,
@@ -328,26 +346,31 @@ __global__ void __launch_bounds__(MPOPF_BRANCH_BLOCK, MPOPF_BRANCH_MINB)
   asm volatile("griddepcontrol.launch_dependents;");
   const int32_t tl = first + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
   if (tl >= end) return;
+  if (PTS) {
+    MPOPF_POINT_OFFSETS(d);
+    lam += (int64_t)blockIdx.y * d.m;
+  }
   __shared__ __align__(16) double s_stage[MPOPF_BRANCH_BLOCK / 32][kStagePitch];
   const bool full = tl - (int32_t)(threadIdx.x & 31) + 31 < end;  // uniform over the warp
-  branch_body<MASK, false, SYM>(d, tl, rt, x, lam, sx, dv, dw, grad, c, jv, hv, kv,
-                                full ? s_stage[threadIdx.x >> 5] : nullptr);
+  branch_body<MASK, false, SYM, PTS>(d, tl, rt, x, lam, sx, dv, dw, grad, c, jv, hv, kv,
+                                     full ? s_stage[threadIdx.x >> 5] : nullptr);
 }
 
 // The branch kernel over elements [first, end) on stream s; the instantiation
 // without the per-branch symmetry test when every branch is symmetric
 // (measured 0.798 against 0.810 ms at 10k buses x 168; the same values).
-template <unsigned MASK>
+// With PTS, `points` points (grid y).
+template <unsigned MASK, bool PTS = false>
 void launch_branch(const Dev &d, unsigned rt, const double *x, const double *lam, const double *sx,
                    const double *dv, double dw, double *grad, double *c, double *jv, double *hv, double *kv,
-                   int32_t first, int32_t end, cudaStream_t s) {
-  const unsigned grid = (unsigned)(((int64_t)end - first + MPOPF_BRANCH_BLOCK - 1) / MPOPF_BRANCH_BLOCK);
+                   int32_t first, int32_t end, cudaStream_t s, unsigned points = 1) {
+  const dim3 grid((unsigned)(((int64_t)end - first + MPOPF_BRANCH_BLOCK - 1) / MPOPF_BRANCH_BLOCK), PTS ? points : 1);
   if (d.all_sym)
-    k_branch<MASK, true><<<grid, MPOPF_BRANCH_BLOCK, 0, s>>>(d, rt, x, lam, sx, dv, dw, grad, c, jv, hv, kv, first,
-                                                              end);
+    k_branch<MASK, true, PTS><<<grid, MPOPF_BRANCH_BLOCK, 0, s>>>(d, rt, x, lam, sx, dv, dw, grad, c, jv, hv, kv,
+                                                                   first, end);
   else
-    k_branch<MASK, false><<<grid, MPOPF_BRANCH_BLOCK, 0, s>>>(d, rt, x, lam, sx, dv, dw, grad, c, jv, hv, kv, first,
-                                                               end);
+    k_branch<MASK, false, PTS><<<grid, MPOPF_BRANCH_BLOCK, 0, s>>>(d, rt, x, lam, sx, dv, dw, grad, c, jv, hv, kv,
+                                                                    first, end);
 }
 
 // ---------------------------------------------------------------------------
@@ -361,7 +384,8 @@ __device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepco
 // PART: 0 everything; 1 the balance rows, their J rows, the shunt W entries,
 // the gradient zeros and the reference row; 2 the va / vm rows of M (the two
 // halves of a split schedule, run side by side).
-template <unsigned MASK, bool COH, bool WAIT = false, int PART = 0>
+// PTS: as in branch_body.
+template <unsigned MASK, bool COH, bool WAIT = false, int PART = 0, bool PTS = false>
 __device__ __forceinline__ void bus_body(const Dev &d, int32_t idx, unsigned rt, const double *__restrict__ x,
                                          const double *__restrict__ lam, const double *__restrict__ sx,
                                          const double *__restrict__ dv, double dw, double *__restrict__ grad,
@@ -391,6 +415,7 @@ __device__ __forceinline__ void bus_body(const Dev &d, int32_t idx, unsigned rt,
   const double m2gs = __ldg(d.bus_m2gs + n), p2bs = __ldg(d.bus_p2bs + n);
   // Incidence records of this bus (written by k_branch when M is assembled).
   const double *R = d.S + (int64_t)t * 2 * L * kRec;
+  if (PTS) R += (int64_t)blockIdx.y * d.T * 2 * L * kRec;
   const bool have_rec = mk & MPOPF_OUT_KKT;
   // a bus launch that may start before the branch launch has finished waits
   // here, before its first read of the records
@@ -499,7 +524,7 @@ __device__ __forceinline__ void bus_body(const Dev &d, int32_t idx, unsigned rt,
 }
 
 // Elements [first, end) of the bus x period range (t N + position).
-template <unsigned MASK, int PART = 0>
+template <unsigned MASK, int PART = 0, bool PTS = false>
 __global__ void __launch_bounds__(MPOPF_BUS_BLOCK) k_bus(Dev d, unsigned rt, const double *__restrict__ x,
                                                 const double *__restrict__ lam, const double *__restrict__ sx,
                                                 const double *__restrict__ dv, double dw, double *__restrict__ grad,
@@ -508,7 +533,11 @@ __global__ void __launch_bounds__(MPOPF_BUS_BLOCK) k_bus(Dev d, unsigned rt, con
                                                 int32_t end) {
   const int32_t idx = first + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
   if (idx >= end) return;
-  bus_body<MASK, false, true, PART>(d, idx, rt, x, lam, sx, dv, dw, grad, c, jv, hv, kv);
+  if (PTS) {
+    MPOPF_POINT_OFFSETS(d);
+    lam += (int64_t)blockIdx.y * d.m;
+  }
+  bus_body<MASK, false, true, PART, PTS>(d, idx, rt, x, lam, sx, dv, dw, grad, c, jv, hv, kv);
 }
 
 // ---------------------------------------------------------------------------
@@ -599,15 +628,18 @@ __device__ __forceinline__ void gen_body(const Dev &d, int32_t tg, int32_t end, 
 }
 
 // Elements [first, end) of the generator x period range (t G + g); tile k's
-// partial objective goes to fpart[k].
-template <unsigned MASK>
+// partial objective goes to fpart[k] (with PTS, point blockIdx.y's tiles
+// follow the earlier points').
+template <unsigned MASK, bool PTS = false>
 __global__ void __launch_bounds__(kBlock) k_gen(Dev d, unsigned rt, const double *__restrict__ x, double sigma,
                                                 const double *__restrict__ sx, const double *__restrict__ dv, double dw,
                                                 double *__restrict__ grad, double *__restrict__ c,
                                                 double *__restrict__ jv, double *__restrict__ hv,
                                                 double *__restrict__ kv, int32_t first, int32_t end) {
-  gen_body<MASK>(d, first + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x), end, (int32_t)blockIdx.x, rt, x, sigma,
-                 sx, dv, dw, grad, c, jv, hv, kv);
+  if (PTS) MPOPF_POINT_OFFSETS(d);
+  const int32_t blk = PTS ? (int32_t)(blockIdx.y * gridDim.x + blockIdx.x) : (int32_t)blockIdx.x;
+  gen_body<MASK>(d, first + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x), end, blk, rt, x, sigma, sx, dv, dw,
+                 grad, c, jv, hv, kv);
 }
 
 // Objective: fixed-order reduction of the per-tile partial sums by one CTA of
@@ -629,6 +661,13 @@ __device__ __forceinline__ void fsum_body(const double *part, int32_t count, dou
 __global__ void __launch_bounds__(kBlock) k_fsum(const double *__restrict__ part, int32_t count,
                                                  double *__restrict__ f) {
   fsum_body<false>(part, count, f);
+}
+
+// The objectives of a sweep over several points: CTA j sums point j's
+// `count` partials into f[j].
+__global__ void __launch_bounds__(kBlock) k_fsum_points(const double *__restrict__ part, int32_t count,
+                                                        double *__restrict__ f) {
+  fsum_body<false>(part + (int64_t)blockIdx.x * count, count, f + blockIdx.x);
 }
 
 unsigned grid_for(int64_t count) { return (unsigned)((count + kBlock - 1) / kBlock); }
@@ -819,6 +858,53 @@ cudaError_t launch_all(const Dev &d, unsigned rt, const double *x, const double 
   launch_gen_part<MASK>(d, rt, mk, x, sigma, sx, dv, dw, f, grad, c, jv, hv, kv, s, prof,
                         fork ? fork->gen_after : nullptr);
   return cudaSuccess;
+}
+
+// A full sweep at `points` points of one network (the sweep's kernels once
+// each, over every point: grid y): the branch kernel on s, the generator work
+// and the objectives forked onto the side stream after it, the bus kernel as
+// a programmatic dependent launch when the schedule has SCHED_PDL.  S and
+// fpart hold the points' incidence records (points x 2 L T kRec doubles) and
+// objective partials (points x tiles).  A point's elements run the code of a
+// single sweep's, so its outputs are launch_all's at that point bit for bit.
+cudaError_t launch_points(const Dev &d0, int32_t points, double *S, double *fpart, const double *x,
+                          const double *lam, double sigma, const double *sx, const double *dv, double dw, double *f,
+                          double *grad, double *c, double *jv, double *hv, double *kv, cudaStream_t s,
+                          const Fork *fork) {
+  constexpr unsigned A = MPOPF_OUT_ALL;
+  Dev d = d0;
+  d.S = S;
+  d.fpart = fpart;
+  const unsigned P = (unsigned)points;
+  if (d.L > 0) launch_branch<A, true>(d, A, x, lam, sx, dv, dw, grad, c, jv, hv, kv, 0, d.T * d.L, s, P);
+  cudaError_t e = cudaEventRecord(fork->ev_fork, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(fork->side, fork->ev_fork, 0);
+  if (e != cudaSuccess) return e;
+  const int32_t tg = d.T * d.G;
+  const unsigned tiles = grid_for(tg);
+  if (d.G > 0)
+    k_gen<A, true><<<dim3(tiles, P), kBlock, 0, fork->side>>>(d, A, x, sigma, sx, dv, dw, grad, c, jv, hv, kv, 0, tg);
+  k_fsum_points<<<P, kBlock, 0, fork->side>>>(fpart, d.G > 0 ? (int32_t)tiles : 0, f);
+  const dim3 grid((unsigned)(((int64_t)d.T * d.N + MPOPF_BUS_BLOCK - 1) / MPOPF_BUS_BLOCK), P);
+  const int32_t be = d.T * d.N;
+  if ((fork->flags & SCHED_PDL) && d.L > 0) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(MPOPF_BUS_BLOCK);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, k_bus<A, 0, true>, d, A, x, lam, sx, dv, dw, grad, c, jv, hv, kv, 0, be);
+    if (e != cudaSuccess) return e;
+  } else {
+    k_bus<A, 0, true><<<grid, MPOPF_BUS_BLOCK, 0, s>>>(d, A, x, lam, sx, dv, dw, grad, c, jv, hv, kv, 0, be);
+  }
+  e = cudaEventRecord(fork->ev_join, fork->side);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, fork->ev_join, 0);
+  return e;
 }
 
 // ---------------------------------------------------------------------------
@@ -1145,6 +1231,44 @@ int mpopf_sweep(mpopf_handle *h, const double *x, const double *lam, double sigm
                 double *kv, void *stream) {
   if (!f || !grad || !c || !jv || !hv || !kv) return fail(MPOPF_ERR_ARG, "mpopf_sweep: NULL output");
   return mpopf_eval(h, MPOPF_OUT_ALL, x, lam, sigma, sigma_x, dvec, delta_w, f, grad, c, jv, hv, kv, stream);
+}
+
+int mpopf_sweep_points(mpopf_handle *h, int32_t points, const double *x, const double *lam, double sigma,
+                       const double *sigma_x, const double *dvec, double delta_w, double *f, double *grad, double *c,
+                       double *jv, double *hv, double *kv, void *stream) {
+  if (!h) return fail(MPOPF_ERR_ARG, "mpopf_sweep_points: NULL handle");
+  if (is_shard(h->d)) return fail(MPOPF_ERR_ARG, "mpopf_sweep_points: not available on a period shard");
+  if (points < 1 || points > 65535) return fail(MPOPF_ERR_ARG, "mpopf_sweep_points: points outside [1, 65535]");
+  if (!x || !lam || !sigma_x || !dvec || !f || !grad || !c || !jv || !hv || !kv)
+    return fail(MPOPF_ERR_ARG, "mpopf_sweep_points: NULL buffer");
+  const Dev &d = h->d;
+  const size_t rec = (size_t)2 * d.L * d.T * kRec;  // record doubles of one point
+  const size_t tiles = grid_for((int64_t)d.T * d.G);
+  const size_t need = (size_t)points * (rec + tiles) * sizeof(double);
+  if (need > h->pts_bytes) {
+    if (h->pts) {
+      // an earlier call's kernels may still read the old scratch
+      cudaError_t e = cudaDeviceSynchronize();
+      if (e == cudaSuccess) e = cudaFree(h->pts);
+      h->pts = nullptr;
+      h->pts_bytes = 0;
+      if (e != cudaSuccess) return fail(MPOPF_ERR_CUDA, std::string("mpopf_sweep_points: ") + cudaGetErrorString(e));
+    }
+    void *p = nullptr;
+    const cudaError_t e = cudaMalloc(&p, need);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(MPOPF_ERR_ALLOC, std::string("mpopf_sweep_points: scratch: ") + cudaGetErrorString(e));
+    }
+    h->pts = static_cast<double *>(p);
+    h->pts_bytes = need;
+  }
+  cudaError_t e = launch_points(d, points, h->pts, h->pts + (size_t)points * rec, x, lam, sigma, sigma_x, dvec,
+                                delta_w, f, grad, c, jv, hv, kv, static_cast<cudaStream_t>(stream), &h->fork);
+  const cudaError_t l = cudaGetLastError();
+  if (e == cudaSuccess) e = l;
+  if (e != cudaSuccess) return fail(MPOPF_ERR_CUDA, std::string("mpopf_sweep_points: ") + cudaGetErrorString(e));
+  return MPOPF_OK;
 }
 
 int mpopf_profile_start(mpopf_handle *h, int32_t max_launches) {

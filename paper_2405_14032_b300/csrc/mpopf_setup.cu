@@ -283,6 +283,9 @@ void free_blocks(mpopf_handle *h) {
   h->nblocks = 0;
   if (h->stage) cudaFree(h->stage);
   h->stage = nullptr;
+  if (h->pts) cudaFree(h->pts);
+  h->pts = nullptr;
+  h->pts_bytes = 0;
 }
 
 int fail(int code, const std::string &msg) {

@@ -113,6 +113,7 @@ def lib():
             "mpopf_assemble_kkt": (ctypes.c_int, [_P, _P, _P, _D, _P, _P, _D, _P, _P]),
             "mpopf_sweep": (ctypes.c_int, [_P, _P, _P, _D, _P, _P, _D, _P, _P, _P, _P, _P, _P, _P]),
             "mpopf_sweep_host": (ctypes.c_int, [_P, _P, _P, _D, _P, _P, _D, _P, _P, _P, _P, _P, _P, _P]),
+            "mpopf_sweep_points": (ctypes.c_int, [_P, _I32, _P, _P, _D, _P, _P, _D, _P, _P, _P, _P, _P, _P, _P]),
             "mpopf_assemble_kkt_noalloc": (ctypes.c_int, [_P, _P, _P, _D, _P, _P, _D, _P, _P]),
             "mpopf_vjp": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
             "mpopf_jvp": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
@@ -157,7 +158,7 @@ def exported_symbols():
     """Names the header declares (for the load/export check)."""
     return ["mpopf_setup", "mpopf_shard_plan", "mpopf_shard_setup", "mpopf_get_pattern", "mpopf_set_loads", "mpopf_eval", "mpopf_eval_obj",
             "mpopf_eval_grad", "mpopf_eval_cons", "mpopf_eval_jac", "mpopf_eval_hess", "mpopf_assemble_kkt",
-            "mpopf_sweep", "mpopf_sweep_host", "mpopf_assemble_kkt_noalloc", "mpopf_vjp", "mpopf_jvp", "mpopf_hvp",
+            "mpopf_sweep", "mpopf_sweep_host", "mpopf_sweep_points", "mpopf_assemble_kkt_noalloc", "mpopf_vjp", "mpopf_jvp", "mpopf_hvp",
             "mpopf_vjp_jv", "mpopf_jvp_jv", "mpopf_kkt_factor", "mpopf_kkt_solve", "mpopf_csc_pattern",
             "mpopf_coo_to_csc", "mpopf_ipm_prepare", "mpopf_ipm_rhs", "mpopf_ipm_recover", "mpopf_batch_create",
             "mpopf_batch_set_io", "mpopf_batch_sweep", "mpopf_batch_set_schedule", "mpopf_batch_get_schedule",
@@ -363,6 +364,30 @@ class Handle:
         _check(lib().mpopf_sweep(self.h, _ptr(x), _ptr(lam), float(sigma), _ptr(sigma_x), _ptr(dvec),
                                  float(delta_w), _ptr(out["f"]), _ptr(out["grad"]), _ptr(out["c"]), _ptr(out["jv"]),
                                  _ptr(out["hv"]), _ptr(out["kv"]), _stream_ptr(stream)), "mpopf_sweep")
+        return out
+
+    def new_point_outputs(self, k):
+        """Outputs of mpopf_sweep_points at k points: [k, size] tensors."""
+        import torch
+        kw = dict(dtype=torch.float64, device="cuda")
+        return dict(f=torch.empty(k, **kw), grad=torch.empty(k, self.n, **kw), c=torch.empty(k, self.m, **kw),
+                    jv=torch.empty(k, self.nnz_jac, **kw), hv=torch.empty(k, self.nnz_hess, **kw),
+                    kv=torch.empty(k, self.nnz_kkt, **kw))
+
+    def sweep_points(self, x, lam, sigma, sigma_x, dvec, delta_w, out=None, stream=None):
+        """Full sweeps at k points in one launch per kernel (mpopf_sweep_points):
+        x, sigma_x [k, n] and lam, dvec [k, m] contiguous device tensors;
+        sigma and delta_w shared.  Returns [k, size] outputs (f [k])."""
+        k = int(x.shape[0])
+        for name, a, w in (("x", x, self.n), ("lam", lam, self.m), ("sigma_x", sigma_x, self.n),
+                           ("dvec", dvec, self.m)):
+            if tuple(a.shape) != (k, w) or not a.is_contiguous():
+                raise ValueError(f"sweep_points: {name} must be a contiguous [{k}, {w}] tensor")
+        out = self.new_point_outputs(k) if out is None else out
+        _check(lib().mpopf_sweep_points(self.h, k, _ptr(x), _ptr(lam), float(sigma), _ptr(sigma_x), _ptr(dvec),
+                                        float(delta_w), _ptr(out["f"]), _ptr(out["grad"]), _ptr(out["c"]),
+                                        _ptr(out["jv"]), _ptr(out["hv"]), _ptr(out["kv"]), _stream_ptr(stream)),
+               "mpopf_sweep_points")
         return out
 
     def sweep_host(self, x, lam, sigma, sigma_x, dvec, delta_w, out, stream=None):

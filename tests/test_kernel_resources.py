@@ -26,15 +26,17 @@ def test_branch_kernel_register_and_spill_budget(tmp_path):
     cmd = [NVCC, *flags, "-Xptxas", "-v", "-I", os.path.join(build.ROOT, "include"), "-c", src,
            "-o", str(tmp_path / "k.o")]
     out = subprocess.run(cmd, capture_output=True, text=True, check=True).stderr
-    # the report blocks of the full-sweep instantiations k_branch<63, SYM>
-    # (with and without the per-branch symmetry test)
-    blocks = list(re.finditer(r"Compiling entry function '[^']*k_branchILj63E[^']*'.*?Used (\d+) registers", out,
-                              re.S))
-    assert len(blocks) == 2, "no resource report for both k_branch<63, SYM> instantiations"
-    for m in blocks:
-        block = out[m.start():m.end()]
-        regs = int(m.group(1))
-        spill = re.search(r"(\d+) bytes spill stores, (\d+) bytes spill loads", block)
-        stores, loads = (int(spill.group(1)), int(spill.group(2))) if spill else (0, 0)
-        assert regs <= 80, regs
-        assert stores <= 136 and loads <= 176, (stores, loads)
+    # the report blocks of the full-sweep instantiations k_branch<63, SYM, PTS>
+    # (with and without the per-branch symmetry test; one point, or several
+    # points with their pointer offsets, which hold more values live)
+    for pts, budget in (("0", (136, 176)), ("1", (184, 224))):
+        blocks = list(re.finditer(r"Compiling entry function '[^']*k_branchILj63ELb[01]ELb" + pts +
+                                  r"E[^']*'.*?Used (\d+) registers", out, re.S))
+        assert len(blocks) == 2, f"no resource report for both k_branch<63, SYM, {pts}> instantiations"
+        for m in blocks:
+            block = out[m.start():m.end()]
+            regs = int(m.group(1))
+            spill = re.search(r"(\d+) bytes spill stores, (\d+) bytes spill loads", block)
+            stores, loads = (int(spill.group(1)), int(spill.group(2))) if spill else (0, 0)
+            assert regs <= 80, regs
+            assert stores <= budget[0] and loads <= budget[1], (pts, stores, loads)
