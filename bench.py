@@ -478,6 +478,40 @@ def adjoint_comparison(torch, vectors=256):
     }
     res["vjp_speedup_vs_fresh"] = res["vjp_plain_fresh_ms"] / res["vjp_matrix_free_ms"]
     res["hvp_speedup_vs_fresh"] = res["hvp_plain_fresh_ms"] / res["hvp_matrix_free_ms"]
+
+    # All 256 vectors at once: mpopf_vjp_many / mpopf_hvp_many (branch rows
+    # recomputed, or read from the J / W the sweep wrote at this point) against
+    # the plain form's sparse-times-dense product (J or W formed once,
+    # torch.sparse.mm over the 256 columns).
+    def timed_once(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = _events(torch)
+        e0.record()
+        for _ in range(10):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 10 / vectors
+
+    out = h.sweep(x, lam, pt.sigma, dev(pt.sigma_x), dev(pt.dvec), pt.delta_w)
+    A_j = torch.sparse_csr_tensor(jt_crow, jt_col, out["jv"][order], size=(h.n, h.m))
+    A_w = torch.sparse_csr_tensor(w_crow, w_col, out["hv"][w_src], size=(h.n, h.n))
+    YT, VT = Y.t().contiguous(), V.t().contiguous()
+    err_many = max(float((h.vjp_many(x, Y, loads=False)[0][5] - h.vjp(x, Y[5], loads=False)[0]).abs().max()),
+                   float((h.hvp_many(x, lam, pt.sigma, V)[9] - h.hvp(x, lam, pt.sigma, V[9])).abs().max()))
+    res["many"] = {
+        "what": "all 256 vectors in one call at one point; ms per vector",
+        "vjp_ms": timed_once(lambda: h.vjp_many(x, Y)),
+        "vjp_stored_j_ms": timed_once(lambda: h.vjp_many(x, Y, jv=out["jv"])),
+        "hvp_ms": timed_once(lambda: h.hvp_many(x, lam, pt.sigma, V)),
+        "hvp_stored_w_ms": timed_once(lambda: h.hvp_many(x, lam, pt.sigma, V, hw=out["hv"])),
+        "vjp_plain_spmm_ms": timed_once(lambda: torch.sparse.mm(A_j, YT)),
+        "hvp_plain_spmm_ms": timed_once(lambda: torch.sparse.mm(A_w, VT)),
+        "max_abs_diff_vs_single_products": err_many,
+        "plain": "J / W formed once (untimed), cuSPARSE SpMM over the 256 columns via torch.sparse.mm",
+    }
     h.close()
     return res
 

@@ -307,6 +307,27 @@ int mpopf_jvp(mpopf_handle *h, const double *x, const double *v, const double *d
               void *stream);
 int mpopf_hvp(mpopf_handle *h, const double *x, const double *lam, double sigma, const double *v, double *hv,
               void *stream);
+/* The same products for k vectors at one point, each kernel launched once
+ * over all k (1 <= k <= 65535).  Vector j's input and output are the j-th of
+ * k consecutive arrays of the single product's sizes, all on the device:
+ *   mpopf_vjp_many: y [k][m] -> gx [k][n], gpd, gqd [k][T][D] (both or NULL);
+ *   mpopf_jvp_many: v [k][n], dpd, dqd [k][T][D] (both or NULL) -> out [k][m];
+ *   mpopf_hvp_many: v [k][n] -> hv [k][n].
+ * jv [nnz_jac] / hw [nnz_hess] (NULL: recompute): J's / W's values at the
+ * same x (and lam, sigma) as mpopf_eval_jac / _hess or mpopf_sweep wrote
+ * them, read by the branch elements instead of recomputed.  Each vector's
+ * result equals the single product's (mpopf_vjp_jv, mpopf_jvp_jv, mpopf_hvp)
+ * bit for bit.  mpopf_vjp_many and mpopf_hvp_many keep their incidence
+ * records (k x 2 L T x 16 bytes) in the handle's scratch, grown like
+ * mpopf_sweep_points's (shared with it); calls on one handle must not
+ * overlap.  MPOPF_ERR_ARG for a NULL argument, k outside the range or a shard
+ * handle; MPOPF_ERR_ALLOC when the scratch cannot be allocated. */
+int mpopf_vjp_many(mpopf_handle *h, int32_t k, const double *x, const double *jv, const double *y, double *gx,
+                   double *gpd, double *gqd, void *stream);
+int mpopf_jvp_many(mpopf_handle *h, int32_t k, const double *x, const double *jv, const double *v,
+                   const double *dpd, const double *dqd, double *out, void *stream);
+int mpopf_hvp_many(mpopf_handle *h, int32_t k, const double *x, const double *lam, double sigma, const double *hw,
+                   const double *v, double *hv, void *stream);
 
 /* Interior-point algebra around the condensed matrix (Sec. III-B, Eq. 5).
  * x [n] is the point, s [m] the slacks of the rows g(x) - s = 0, y [m] the

@@ -21,6 +21,21 @@ namespace {
 #endif
 constexpr int kAdjBlock = MPOPF_ADJ_BLOCK;
 
+// MANY: the kernels of the products for several vectors at one point (vector
+// j = blockIdx.y reads and writes the j-th of consecutive arrays of the
+// single product's sizes).  Incidence records: one double2 per branch end;
+// a single product writes them into the sweep's record array (kRec doubles
+// apart), several vectors into their own packed array (vector j's T periods
+// after the earlier vectors').
+template <bool MANY>
+__device__ __forceinline__ double *prod_rec(const Dev &d, int32_t t) {
+  return d.S + ((MANY ? (int64_t)blockIdx.y * d.T : 0) + t) * 2 * d.L * (MANY ? 2 : kRec);
+}
+template <bool MANY>
+__host__ __device__ constexpr int rec_stride() {
+  return MANY ? 2 : kRec;
+}
+
 // ---------------------------------------------------------------------------
 // J^T y.  Branch element local sums over its rows K1..K7:
 //   va_f: a1 y1, + a2 y2, + a3 y3, + a4 y4, + y5   (va_t: the exact negation)
@@ -28,11 +43,16 @@ constexpr int kAdjBlock = MPOPF_ADJ_BLOCK;
 //   p_f: fma(2pf, y6, y1);  q_f: fma(2qf, y6, y2);  p_t: fma(2pt, y7, y3);
 //   q_t: fma(2qt, y7, y4); then the bus element adds -y8 (p) or -y9 (q).
 // ---------------------------------------------------------------------------
+template <bool MANY>
 __global__ void __launch_bounds__(kAdjBlock) k_vjp_branch(Dev d, const double *__restrict__ x,
                                                        const double *__restrict__ y, double *__restrict__ gx) {
   const int32_t L = d.L;
   const int32_t tl = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
   if (tl >= d.T * L) return;
+  if (MANY) {
+    y += (int64_t)blockIdx.y * d.m;
+    gx += (int64_t)blockIdx.y * d.n;
+  }
   const int32_t t = tl / L, l = tl - t * L;
   const int64_t TL = (int64_t)d.T * L, tN = (int64_t)t * d.N;
   const int64_t pb = d.x_p + 2 * (int64_t)t * L, qb = d.x_q + 2 * (int64_t)t * L;
@@ -54,28 +74,39 @@ __global__ void __launch_bounds__(kAdjBlock) k_vjp_branch(Dev d, const double *_
   gx[qb + l] = fma(twice(qf), y6, y2) - __ldg(y + r8f + d89);
   gx[pb + L + l] = fma(twice(pt), y7, y3) - __ldg(y + r8t);
   gx[qb + L + l] = fma(twice(qt), y7, y4) - __ldg(y + r8t + d89);
-  double *R = d.S + (int64_t)t * 2 * L * kRec;
-  *reinterpret_cast<double2 *>(R + (int64_t)__ldg(d.br_slot + l) * kRec) = make_double2(Ld, Lvf);
-  *reinterpret_cast<double2 *>(R + (int64_t)__ldg(d.br_slot + L + l) * kRec) = make_double2(negx(Ld), Lvt);
+  double *R = prod_rec<MANY>(d, t);
+  *reinterpret_cast<double2 *>(R + (int64_t)__ldg(d.br_slot + l) * rec_stride<MANY>()) = make_double2(Ld, Lvf);
+  *reinterpret_cast<double2 *>(R + (int64_t)__ldg(d.br_slot + L + l) * rec_stride<MANY>()) =
+      make_double2(negx(Ld), Lvt);
 }
 
+template <bool MANY>
 __global__ void __launch_bounds__(kAdjBlock) k_vjp_bus(Dev d, const double *__restrict__ x,
                                                     const double *__restrict__ y, double *__restrict__ gx,
                                                     double *__restrict__ gpd, double *__restrict__ gqd) {
   const int32_t N = d.N;
   const int32_t idx = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
   if (idx >= d.T * N) return;
+  if (MANY) {
+    const int64_t j = blockIdx.y;
+    y += j * d.m;
+    gx += j * d.n;
+    if (gpd) {
+      gpd += j * d.T * d.D;
+      gqd += j * d.T * d.D;
+    }
+  }
   const int32_t t = idx / N, pos = idx - t * N;
   const int32_t n = __ldg(d.bus_order + pos);
   const int32_t tn = t * N + n;
   const int32_t s0 = __ldg(d.inc_ptr + pos), s1 = __ldg(d.inc_ptr + pos + 1);
-  const double *R = d.S + (int64_t)t * 2 * d.L * kRec;
+  const double *R = prod_rec<MANY>(d, t);
   // va: reference element first, then the incident branches in branch order.
   double ga = 0.0, gv = 0.0;
   bool has_a = false, has_v = false;
   if (n == d.ref) { ga = __ldg(y + t); has_a = true; }
   for (int32_t q = s0; q < s1; ++q) {
-    const double2 r = __ldg(reinterpret_cast<const double2 *>(R + (int64_t)q * kRec));
+    const double2 r = __ldg(reinterpret_cast<const double2 *>(R + (int64_t)q * rec_stride<MANY>()));
     ga = has_a ? ga + r.x : r.x;
     gv = has_v ? gv + r.y : r.y;
     has_a = has_v = true;
@@ -97,10 +128,15 @@ __global__ void __launch_bounds__(kAdjBlock) k_vjp_bus(Dev d, const double *__re
   }
 }
 
+template <bool MANY>
 __global__ void __launch_bounds__(kAdjBlock) k_vjp_gen(Dev d, const double *__restrict__ y, double *__restrict__ gx) {
   const int32_t G = d.G;
   const int32_t tg = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
   if (tg >= d.T * G) return;
+  if (MANY) {
+    y += (int64_t)blockIdx.y * d.m;
+    gx += (int64_t)blockIdx.y * d.n;
+  }
   const int32_t t = tg / G, g = tg - t * G;
   const int64_t tn = (int64_t)t * d.N + __ldg(d.gen_bus + g);
   double a = __ldg(y + d.c_k8 + tn);  // bus element (K8, entry +1)
@@ -120,11 +156,16 @@ __global__ void __launch_bounds__(kAdjBlock) k_vjp_gen(Dev d, const double *__re
 // ---------------------------------------------------------------------------
 // J v (+ load tangents): one row at a time in its J order.
 // ---------------------------------------------------------------------------
+template <bool MANY>
 __global__ void __launch_bounds__(kAdjBlock) k_jvp_branch(Dev d, const double *__restrict__ x,
                                                        const double *__restrict__ v, double *__restrict__ out) {
   const int32_t L = d.L;
   const int32_t tl = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
   if (tl >= d.T * L) return;
+  if (MANY) {
+    v += (int64_t)blockIdx.y * d.n;
+    out += (int64_t)blockIdx.y * d.m;
+  }
   const int32_t t = tl / L, l = tl - t * L;
   const int64_t TL = (int64_t)d.T * L, tN = (int64_t)t * d.N;
   const int64_t pb = d.x_p + 2 * (int64_t)t * L, qb = d.x_q + 2 * (int64_t)t * L;
@@ -148,12 +189,22 @@ __global__ void __launch_bounds__(kAdjBlock) k_jvp_branch(Dev d, const double *_
   out[rk1 + 6 * TL] = fma(twice(qt), vqt, twice(pt) * vpt);
 }
 
+template <bool MANY>
 __global__ void __launch_bounds__(kAdjBlock) k_jvp_bus(Dev d, const double *__restrict__ x,
                                                     const double *__restrict__ v, const double *__restrict__ dpd,
                                                     const double *__restrict__ dqd, double *__restrict__ out) {
   const int32_t N = d.N;
   const int32_t idx = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
   if (idx >= d.T * N) return;
+  if (MANY) {
+    const int64_t j = blockIdx.y;
+    v += j * d.n;
+    out += j * d.m;
+    if (dpd) {
+      dpd += j * d.T * d.D;
+      dqd += j * d.T * d.D;
+    }
+  }
   const int32_t t = idx / N, pos = idx - t * N;
   const int32_t n = __ldg(d.bus_order + pos);
   const int32_t tn = t * N + n;
@@ -185,10 +236,15 @@ __global__ void __launch_bounds__(kAdjBlock) k_jvp_bus(Dev d, const double *__re
   out[d.c_k9 + tn] = aQ;
 }
 
+template <bool MANY>
 __global__ void __launch_bounds__(kAdjBlock) k_jvp_gen(Dev d, const double *__restrict__ v, double *__restrict__ out) {
   const int32_t G = d.G;
   const int32_t tg = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
   if (tg >= (d.T - 1) * G) return;  // ramp rows (t, g), t = 1..T-1, row index (t - 1) G + g
+  if (MANY) {
+    v += (int64_t)blockIdx.y * d.n;
+    out += (int64_t)blockIdx.y * d.m;
+  }
   const int64_t cur = d.x_pg + G + tg;
   out[d.c_k10 + tg] = __ldg(v + cur) - __ldg(v + cur - G);
   if (d.qramp) {
@@ -202,12 +258,17 @@ __global__ void __launch_bounds__(kAdjBlock) k_jvp_gen(Dev d, const double *__re
 // thermal diagonals), each entry (r, c, w) adding fma(w, v[c], .) to r and,
 // off the diagonal, fma(w, v[r], .) to c.
 // ---------------------------------------------------------------------------
+template <bool MANY>
 __global__ void __launch_bounds__(kAdjBlock) k_hvp_branch(Dev d, const double *__restrict__ x,
                                                        const double *__restrict__ lam, const double *__restrict__ v,
                                                        double *__restrict__ hv) {
   const int32_t L = d.L;
   const int32_t tl = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
   if (tl >= d.T * L) return;
+  if (MANY) {
+    v += (int64_t)blockIdx.y * d.n;
+    hv += (int64_t)blockIdx.y * d.n;
+  }
   const int32_t t = tl / L, l = tl - t * L;
   const int64_t TL = (int64_t)d.T * L, tN = (int64_t)t * d.N;
   const int64_t pb = d.x_p + 2 * (int64_t)t * L, qb = d.x_q + 2 * (int64_t)t * L;
@@ -229,24 +290,69 @@ __global__ void __launch_bounds__(kAdjBlock) k_hvp_branch(Dev d, const double *_
   hv[qb + l] = h6 * __ldg(v + qb + l);
   hv[pb + L + l] = h7 * __ldg(v + pb + L + l);
   hv[qb + L + l] = h7 * __ldg(v + qb + L + l);
-  double *R = d.S + (int64_t)t * 2 * L * kRec;
-  *reinterpret_cast<double2 *>(R + (int64_t)__ldg(d.br_slot + l) * kRec) = make_double2(hf, hvf);
-  *reinterpret_cast<double2 *>(R + (int64_t)__ldg(d.br_slot + L + l) * kRec) = make_double2(ht, hvt);
+  double *R = prod_rec<MANY>(d, t);
+  *reinterpret_cast<double2 *>(R + (int64_t)__ldg(d.br_slot + l) * rec_stride<MANY>()) = make_double2(hf, hvf);
+  *reinterpret_cast<double2 *>(R + (int64_t)__ldg(d.br_slot + L + l) * rec_stride<MANY>()) = make_double2(ht, hvt);
 }
 
+// The branch element of W v with its W values as the sweep wrote them at the
+// same (x, lam) (hw [nnz_hess]: the element's ten block entries Wdd, -Wdd,
+// Wdd, Wdvf, -Wdvf, Wvfvf, Wdvt, -Wdvt, -Asum, Wvtvt and the thermal
+// diagonals h6, h6, h7, h7) instead of recomputed: the same operands in the
+// same order as k_hvp_branch, so the same results bit for bit.
+template <bool MANY>
+__global__ void __launch_bounds__(kAdjBlock) k_hvp_branch_hw(Dev d, const double *__restrict__ hw,
+                                                          const double *__restrict__ v, double *__restrict__ hv) {
+  const int32_t L = d.L;
+  const int32_t tl = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+  if (tl >= d.T * L) return;
+  if (MANY) {
+    v += (int64_t)blockIdx.y * d.n;
+    hv += (int64_t)blockIdx.y * d.n;
+  }
+  const int32_t t = tl / L, l = tl - t * L;
+  const int64_t tN = (int64_t)t * d.N;
+  const int64_t pb = d.x_p + 2 * (int64_t)t * L, qb = d.x_q + 2 * (int64_t)t * L;
+  const int32_t f = __ldg(d.br_f + l), to = __ldg(d.br_t + l);
+  const double *hb = hw + d.h_br + (int64_t)tl * 10;
+  const double Wdd = __ldg(hb), nWdd = __ldg(hb + 1), Wdvf = __ldg(hb + 3), nWdvf = __ldg(hb + 4);
+  const double Wvfvf = __ldg(hb + 5), Wdvt = __ldg(hb + 6), nWdvt = __ldg(hb + 7), nAsum = __ldg(hb + 8);
+  const double Wvtvt = __ldg(hb + 9);
+  const double uf = __ldg(v + tN + f), ut = __ldg(v + tN + to);
+  const double wf = __ldg(v + d.x_vm + tN + f), wt = __ldg(v + d.x_vm + tN + to);
+  const double hf = fma(Wdvt, wt, fma(Wdvf, wf, fma(nWdd, ut, Wdd * uf)));
+  const double ht = fma(nWdvt, wt, fma(nWdvf, wf, fma(Wdd, ut, nWdd * uf)));
+  const double hvf = fma(nAsum, wt, fma(Wvfvf, wf, fma(nWdvf, ut, Wdvf * uf)));
+  const double hvt = fma(Wvtvt, wt, fma(nAsum, wf, fma(nWdvt, ut, Wdvt * uf)));
+  const double *th = hw + d.h_th + (int64_t)tl * 4;
+  const double h6 = __ldg(th), h7 = __ldg(th + 2);
+  hv[pb + l] = h6 * __ldg(v + pb + l);
+  hv[qb + l] = h6 * __ldg(v + qb + l);
+  hv[pb + L + l] = h7 * __ldg(v + pb + L + l);
+  hv[qb + L + l] = h7 * __ldg(v + qb + L + l);
+  double *R = prod_rec<MANY>(d, t);
+  *reinterpret_cast<double2 *>(R + (int64_t)__ldg(d.br_slot + l) * rec_stride<MANY>()) = make_double2(hf, hvf);
+  *reinterpret_cast<double2 *>(R + (int64_t)__ldg(d.br_slot + L + l) * rec_stride<MANY>()) = make_double2(ht, hvt);
+}
+
+template <bool MANY>
 __global__ void __launch_bounds__(kAdjBlock) k_hvp_bus(Dev d, const double *__restrict__ lam,
                                                     const double *__restrict__ v, double *__restrict__ hv) {
   const int32_t N = d.N;
   const int32_t idx = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
   if (idx >= d.T * N) return;
+  if (MANY) {
+    v += (int64_t)blockIdx.y * d.n;
+    hv += (int64_t)blockIdx.y * d.n;
+  }
   const int32_t t = idx / N, pos = idx - t * N;
   const int32_t n = __ldg(d.bus_order + pos);
   const int32_t tn = t * N + n;
   const int32_t s0 = __ldg(d.inc_ptr + pos), s1 = __ldg(d.inc_ptr + pos + 1);
-  const double *R = d.S + (int64_t)t * 2 * d.L * kRec;
+  const double *R = prod_rec<MANY>(d, t);
   double ha = 0.0, hm = 0.0;
   for (int32_t q = s0; q < s1; ++q) {
-    const double2 r = __ldg(reinterpret_cast<const double2 *>(R + (int64_t)q * kRec));
+    const double2 r = __ldg(reinterpret_cast<const double2 *>(R + (int64_t)q * rec_stride<MANY>()));
     ha = (q == s0) ? r.x : ha + r.x;
     hm = (q == s0) ? r.y : hm + r.y;
   }
@@ -258,11 +364,16 @@ __global__ void __launch_bounds__(kAdjBlock) k_hvp_bus(Dev d, const double *__re
   hv[d.x_vm + tn] = (s1 > s0) ? hm + Lbus : Lbus;
 }
 
+template <bool MANY>
 __global__ void __launch_bounds__(kAdjBlock) k_hvp_gen(Dev d, double sigma, const double *__restrict__ v,
                                                     double *__restrict__ hv) {
   const int32_t G = d.G;
   const int32_t tg = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
   if (tg >= d.T * G) return;
+  if (MANY) {
+    v += (int64_t)blockIdx.y * d.n;
+    hv += (int64_t)blockIdx.y * d.n;
+  }
   const int32_t g = tg % G;
   hv[d.x_pg + tg] = (sigma * __ldg(d.gen_c2x2 + g)) * __ldg(v + d.x_pg + tg);
   hv[d.x_qg + tg] = 0.0;
@@ -295,11 +406,16 @@ __device__ __forceinline__ StoredJ stored_j(const Dev &d, const double *__restri
   return J;
 }
 
+template <bool MANY>
 __global__ void __launch_bounds__(kAdjBlock) k_vjp_branch_jv(Dev d, const double *__restrict__ jv,
                                                           const double *__restrict__ y, double *__restrict__ gx) {
   const int32_t L = d.L;
   const int32_t tl = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
   if (tl >= d.T * L) return;
+  if (MANY) {
+    y += (int64_t)blockIdx.y * d.m;
+    gx += (int64_t)blockIdx.y * d.n;
+  }
   const int32_t t = tl / L, l = tl - t * L;
   const int64_t TL = (int64_t)d.T * L, tN = (int64_t)t * d.N;
   const int64_t pb = d.x_p + 2 * (int64_t)t * L, qb = d.x_q + 2 * (int64_t)t * L;
@@ -317,16 +433,22 @@ __global__ void __launch_bounds__(kAdjBlock) k_vjp_branch_jv(Dev d, const double
   gx[qb + l] = fma(J.jq6, y6, y2) - __ldg(y + r8f + d89);
   gx[pb + L + l] = fma(J.jp7, y7, y3) - __ldg(y + r8t);
   gx[qb + L + l] = fma(J.jq7, y7, y4) - __ldg(y + r8t + d89);
-  double *R = d.S + (int64_t)t * 2 * L * kRec;
-  *reinterpret_cast<double2 *>(R + (int64_t)__ldg(d.br_slot + l) * kRec) = make_double2(Ld, Lvf);
-  *reinterpret_cast<double2 *>(R + (int64_t)__ldg(d.br_slot + L + l) * kRec) = make_double2(negx(Ld), Lvt);
+  double *R = prod_rec<MANY>(d, t);
+  *reinterpret_cast<double2 *>(R + (int64_t)__ldg(d.br_slot + l) * rec_stride<MANY>()) = make_double2(Ld, Lvf);
+  *reinterpret_cast<double2 *>(R + (int64_t)__ldg(d.br_slot + L + l) * rec_stride<MANY>()) =
+      make_double2(negx(Ld), Lvt);
 }
 
+template <bool MANY>
 __global__ void __launch_bounds__(kAdjBlock) k_jvp_branch_jv(Dev d, const double *__restrict__ jv,
                                                           const double *__restrict__ v, double *__restrict__ out) {
   const int32_t L = d.L;
   const int32_t tl = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
   if (tl >= d.T * L) return;
+  if (MANY) {
+    v += (int64_t)blockIdx.y * d.n;
+    out += (int64_t)blockIdx.y * d.m;
+  }
   const int32_t t = tl / L, l = tl - t * L;
   const int64_t TL = (int64_t)d.T * L, tN = (int64_t)t * d.N;
   const int64_t pb = d.x_p + 2 * (int64_t)t * L, qb = d.x_q + 2 * (int64_t)t * L;
@@ -353,6 +475,65 @@ int fail(int code, const std::string &msg) {
   return code;
 }
 
+// The launches of each product; with MANY, k vectors (grid y) and d.S the
+// packed records of the k vectors.
+template <bool MANY>
+void launch_vjp(const Dev &d, unsigned k, const double *x, const double *jv, const double *y, double *gx,
+                double *gpd, double *gqd, cudaStream_t s) {
+  if (d.L > 0) {
+    const dim3 g(grid_for((int64_t)d.T * d.L), k);
+    if (jv) k_vjp_branch_jv<MANY><<<g, kAdjBlock, 0, s>>>(d, jv, y, gx);
+    else k_vjp_branch<MANY><<<g, kAdjBlock, 0, s>>>(d, x, y, gx);
+  }
+  k_vjp_bus<MANY><<<dim3(grid_for((int64_t)d.T * d.N), k), kAdjBlock, 0, s>>>(d, x, y, gx, gpd,
+                                                                               d.D > 0 ? gqd : nullptr);
+  if (d.G > 0) k_vjp_gen<MANY><<<dim3(grid_for((int64_t)d.T * d.G), k), kAdjBlock, 0, s>>>(d, y, gx);
+}
+
+template <bool MANY>
+void launch_jvp(const Dev &d, unsigned k, const double *x, const double *jv, const double *v, const double *dpd,
+                const double *dqd, double *out, cudaStream_t s) {
+  if (d.L > 0) {
+    const dim3 g(grid_for((int64_t)d.T * d.L), k);
+    if (jv) k_jvp_branch_jv<MANY><<<g, kAdjBlock, 0, s>>>(d, jv, v, out);
+    else k_jvp_branch<MANY><<<g, kAdjBlock, 0, s>>>(d, x, v, out);
+  }
+  k_jvp_bus<MANY><<<dim3(grid_for((int64_t)d.T * d.N), k), kAdjBlock, 0, s>>>(d, x, v, d.D > 0 ? dpd : nullptr,
+                                                                               dqd, out);
+  if (d.G > 0 && d.T > 1)
+    k_jvp_gen<MANY><<<dim3(grid_for((int64_t)(d.T - 1) * d.G), k), kAdjBlock, 0, s>>>(d, v, out);
+}
+
+template <bool MANY>
+void launch_hvp(const Dev &d, unsigned k, const double *x, const double *lam, double sigma, const double *hw,
+                const double *v, double *hv, cudaStream_t s) {
+  if (d.L > 0) {
+    const dim3 g(grid_for((int64_t)d.T * d.L), k);
+    if (hw) k_hvp_branch_hw<MANY><<<g, kAdjBlock, 0, s>>>(d, hw, v, hv);
+    else k_hvp_branch<MANY><<<g, kAdjBlock, 0, s>>>(d, x, lam, v, hv);
+  }
+  k_hvp_bus<MANY><<<dim3(grid_for((int64_t)d.T * d.N), k), kAdjBlock, 0, s>>>(d, lam, v, hv);
+  if (d.G > 0) k_hvp_gen<MANY><<<dim3(grid_for((int64_t)d.T * d.G), k), kAdjBlock, 0, s>>>(d, sigma, v, hv);
+}
+
+// The handle's descriptor with d.S pointing at the packed records of k
+// vectors (2 L T double2 each) in the handle's scratch.
+int many_dev(mpopf_handle *h, int32_t k, const char *who, Dev *out) {
+  if (k < 1 || k > 65535) return fail(MPOPF_ERR_ARG, std::string(who) + ": k outside [1, 65535]");
+  const size_t rec = (size_t)2 * h->d.L * h->d.T * rec_stride<true>();
+  const int rc = grow_points_scratch(h, (size_t)k * rec * sizeof(double), who);
+  if (rc != MPOPF_OK) return rc;
+  *out = h->d;
+  out->S = h->pts;
+  return MPOPF_OK;
+}
+
+int done(const char *who) {
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(MPOPF_ERR_CUDA, std::string(who) + ": " + cudaGetErrorString(e));
+  return MPOPF_OK;
+}
+
 }  // namespace
 }  // namespace mpopf
 
@@ -365,17 +546,8 @@ int mpopf_vjp_jv(mpopf_handle *h, const double *x, const double *jv, const doubl
   if (!h || !x || !y || !gx) return fail(MPOPF_ERR_ARG, "mpopf_vjp: NULL argument");
   if (mpopf::is_shard(h->d)) return fail(MPOPF_ERR_ARG, "mpopf_vjp: not available on a period shard");
   if ((gpd == nullptr) != (gqd == nullptr)) return fail(MPOPF_ERR_ARG, "mpopf_vjp: give both gpd and gqd or neither");
-  const Dev &d = h->d;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (d.L > 0) {
-    if (jv) k_vjp_branch_jv<<<grid_for((int64_t)d.T * d.L), kAdjBlock, 0, s>>>(d, jv, y, gx);
-    else k_vjp_branch<<<grid_for((int64_t)d.T * d.L), kAdjBlock, 0, s>>>(d, x, y, gx);
-  }
-  k_vjp_bus<<<grid_for((int64_t)d.T * d.N), kAdjBlock, 0, s>>>(d, x, y, gx, gpd, d.D > 0 ? gqd : nullptr);
-  if (d.G > 0) k_vjp_gen<<<grid_for((int64_t)d.T * d.G), kAdjBlock, 0, s>>>(d, y, gx);
-  const cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return fail(MPOPF_ERR_CUDA, std::string("mpopf_vjp: ") + cudaGetErrorString(e));
-  return MPOPF_OK;
+  launch_vjp<false>(h->d, 1, x, jv, y, gx, gpd, gqd, static_cast<cudaStream_t>(stream));
+  return done("mpopf_vjp");
 }
 
 int mpopf_vjp(mpopf_handle *h, const double *x, const double *y, double *gx, double *gpd, double *gqd, void *stream) {
@@ -387,17 +559,8 @@ int mpopf_jvp_jv(mpopf_handle *h, const double *x, const double *jv, const doubl
   if (!h || !x || !v || !jv_out) return fail(MPOPF_ERR_ARG, "mpopf_jvp: NULL argument");
   if (mpopf::is_shard(h->d)) return fail(MPOPF_ERR_ARG, "mpopf_jvp: not available on a period shard");
   if ((dpd == nullptr) != (dqd == nullptr)) return fail(MPOPF_ERR_ARG, "mpopf_jvp: give both dpd and dqd or neither");
-  const Dev &d = h->d;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (d.L > 0) {
-    if (jv) k_jvp_branch_jv<<<grid_for((int64_t)d.T * d.L), kAdjBlock, 0, s>>>(d, jv, v, jv_out);
-    else k_jvp_branch<<<grid_for((int64_t)d.T * d.L), kAdjBlock, 0, s>>>(d, x, v, jv_out);
-  }
-  k_jvp_bus<<<grid_for((int64_t)d.T * d.N), kAdjBlock, 0, s>>>(d, x, v, d.D > 0 ? dpd : nullptr, dqd, jv_out);
-  if (d.G > 0 && d.T > 1) k_jvp_gen<<<grid_for((int64_t)(d.T - 1) * d.G), kAdjBlock, 0, s>>>(d, v, jv_out);
-  const cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return fail(MPOPF_ERR_CUDA, std::string("mpopf_jvp: ") + cudaGetErrorString(e));
-  return MPOPF_OK;
+  launch_jvp<false>(h->d, 1, x, jv, v, dpd, dqd, jv_out, static_cast<cudaStream_t>(stream));
+  return done("mpopf_jvp");
 }
 
 int mpopf_jvp(mpopf_handle *h, const double *x, const double *v, const double *dpd, const double *dqd, double *jv_out,
@@ -409,14 +572,43 @@ int mpopf_hvp(mpopf_handle *h, const double *x, const double *lam, double sigma,
               void *stream) {
   if (!h || !x || !lam || !v || !hv) return fail(MPOPF_ERR_ARG, "mpopf_hvp: NULL argument");
   if (mpopf::is_shard(h->d)) return fail(MPOPF_ERR_ARG, "mpopf_hvp: not available on a period shard");
-  const Dev &d = h->d;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (d.L > 0) k_hvp_branch<<<grid_for((int64_t)d.T * d.L), kAdjBlock, 0, s>>>(d, x, lam, v, hv);
-  k_hvp_bus<<<grid_for((int64_t)d.T * d.N), kAdjBlock, 0, s>>>(d, lam, v, hv);
-  if (d.G > 0) k_hvp_gen<<<grid_for((int64_t)d.T * d.G), kAdjBlock, 0, s>>>(d, sigma, v, hv);
-  const cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return fail(MPOPF_ERR_CUDA, std::string("mpopf_hvp: ") + cudaGetErrorString(e));
-  return MPOPF_OK;
+  launch_hvp<false>(h->d, 1, x, lam, sigma, nullptr, v, hv, static_cast<cudaStream_t>(stream));
+  return done("mpopf_hvp");
+}
+
+int mpopf_vjp_many(mpopf_handle *h, int32_t k, const double *x, const double *jv, const double *y, double *gx,
+                   double *gpd, double *gqd, void *stream) {
+  if (!h || !x || !y || !gx) return fail(MPOPF_ERR_ARG, "mpopf_vjp_many: NULL argument");
+  if (mpopf::is_shard(h->d)) return fail(MPOPF_ERR_ARG, "mpopf_vjp_many: not available on a period shard");
+  if ((gpd == nullptr) != (gqd == nullptr))
+    return fail(MPOPF_ERR_ARG, "mpopf_vjp_many: give both gpd and gqd or neither");
+  Dev d;
+  const int rc = many_dev(h, k, "mpopf_vjp_many", &d);
+  if (rc != MPOPF_OK) return rc;
+  launch_vjp<true>(d, (unsigned)k, x, jv, y, gx, gpd, gqd, static_cast<cudaStream_t>(stream));
+  return done("mpopf_vjp_many");
+}
+
+int mpopf_jvp_many(mpopf_handle *h, int32_t k, const double *x, const double *jv, const double *v,
+                   const double *dpd, const double *dqd, double *out, void *stream) {
+  if (!h || !x || !v || !out) return fail(MPOPF_ERR_ARG, "mpopf_jvp_many: NULL argument");
+  if (mpopf::is_shard(h->d)) return fail(MPOPF_ERR_ARG, "mpopf_jvp_many: not available on a period shard");
+  if ((dpd == nullptr) != (dqd == nullptr))
+    return fail(MPOPF_ERR_ARG, "mpopf_jvp_many: give both dpd and dqd or neither");
+  if (k < 1 || k > 65535) return fail(MPOPF_ERR_ARG, "mpopf_jvp_many: k outside [1, 65535]");
+  launch_jvp<true>(h->d, (unsigned)k, x, jv, v, dpd, dqd, out, static_cast<cudaStream_t>(stream));
+  return done("mpopf_jvp_many");
+}
+
+int mpopf_hvp_many(mpopf_handle *h, int32_t k, const double *x, const double *lam, double sigma, const double *hw,
+                   const double *v, double *hv, void *stream) {
+  if (!h || !x || !lam || !v || !hv) return fail(MPOPF_ERR_ARG, "mpopf_hvp_many: NULL argument");
+  if (mpopf::is_shard(h->d)) return fail(MPOPF_ERR_ARG, "mpopf_hvp_many: not available on a period shard");
+  Dev d;
+  const int rc = many_dev(h, k, "mpopf_hvp_many", &d);
+  if (rc != MPOPF_OK) return rc;
+  launch_hvp<true>(d, (unsigned)k, x, lam, sigma, hw, v, hv, static_cast<cudaStream_t>(stream));
+  return done("mpopf_hvp_many");
 }
 
 }  // extern "C"

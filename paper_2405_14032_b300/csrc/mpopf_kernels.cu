@@ -1098,6 +1098,31 @@ cudaError_t fork_bus_stream(Fork *fork, bool high_priority) {
   return e;
 }
 
+int grow_points_scratch(mpopf_handle *h, size_t need, const char *who) {
+  if (need <= h->pts_bytes) return MPOPF_OK;
+  if (h->pts) {
+    // an earlier call's kernels may still use the old scratch
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaFree(h->pts);
+    h->pts = nullptr;
+    h->pts_bytes = 0;
+    if (e != cudaSuccess) {
+      set_error(std::string(who) + ": " + cudaGetErrorString(e));
+      return MPOPF_ERR_CUDA;
+    }
+  }
+  void *p = nullptr;
+  const cudaError_t e = cudaMalloc(&p, need);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error(std::string(who) + ": scratch: " + cudaGetErrorString(e));
+    return MPOPF_ERR_ALLOC;
+  }
+  h->pts = static_cast<double *>(p);
+  h->pts_bytes = need;
+  return MPOPF_OK;
+}
+
 int eval_launch_count(const Dev &d, unsigned mk, const Fork *fork) {
   const unsigned rest = MPOPF_OUT_GRAD | MPOPF_OUT_CONS | MPOPF_OUT_JAC | MPOPF_OUT_HESS | MPOPF_OUT_KKT;
   int32_t P = 0;
@@ -1244,25 +1269,8 @@ int mpopf_sweep_points(mpopf_handle *h, int32_t points, const double *x, const d
   const Dev &d = h->d;
   const size_t rec = (size_t)2 * d.L * d.T * kRec;  // record doubles of one point
   const size_t tiles = grid_for((int64_t)d.T * d.G);
-  const size_t need = (size_t)points * (rec + tiles) * sizeof(double);
-  if (need > h->pts_bytes) {
-    if (h->pts) {
-      // an earlier call's kernels may still read the old scratch
-      cudaError_t e = cudaDeviceSynchronize();
-      if (e == cudaSuccess) e = cudaFree(h->pts);
-      h->pts = nullptr;
-      h->pts_bytes = 0;
-      if (e != cudaSuccess) return fail(MPOPF_ERR_CUDA, std::string("mpopf_sweep_points: ") + cudaGetErrorString(e));
-    }
-    void *p = nullptr;
-    const cudaError_t e = cudaMalloc(&p, need);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      return fail(MPOPF_ERR_ALLOC, std::string("mpopf_sweep_points: scratch: ") + cudaGetErrorString(e));
-    }
-    h->pts = static_cast<double *>(p);
-    h->pts_bytes = need;
-  }
+  const int rc = grow_points_scratch(h, (size_t)points * (rec + tiles) * sizeof(double), "mpopf_sweep_points");
+  if (rc != MPOPF_OK) return rc;
   cudaError_t e = launch_points(d, points, h->pts, h->pts + (size_t)points * rec, x, lam, sigma, sigma_x, dvec,
                                 delta_w, f, grad, c, jv, hv, kv, static_cast<cudaStream_t>(stream), &h->fork);
   const cudaError_t l = cudaGetLastError();

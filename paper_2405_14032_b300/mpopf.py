@@ -126,6 +126,9 @@ def lib():
             "mpopf_ipm_rhs": (ctypes.c_int, [_P] * 10 + [_D] + [_P, _P]),
             "mpopf_ipm_recover": (ctypes.c_int, [_P] * 13 + [_D] * 3 + [_P] * 7),
             "mpopf_vjp_jv": (ctypes.c_int, [_P] * 8),
+            "mpopf_vjp_many": (ctypes.c_int, [_P, _I32] + [_P] * 7),
+            "mpopf_jvp_many": (ctypes.c_int, [_P, _I32] + [_P] * 7),
+            "mpopf_hvp_many": (ctypes.c_int, [_P, _I32, _P, _P, _D, _P, _P, _P, _P]),
             "mpopf_jvp_jv": (ctypes.c_int, [_P] * 8),
             "mpopf_batch_create": (ctypes.c_int, [_P, _I32, ctypes.POINTER(_P)]),
             "mpopf_batch_set_io": (ctypes.c_int, [_P, _P, _P]),
@@ -159,7 +162,7 @@ def exported_symbols():
     return ["mpopf_setup", "mpopf_shard_plan", "mpopf_shard_setup", "mpopf_get_pattern", "mpopf_set_loads", "mpopf_eval", "mpopf_eval_obj",
             "mpopf_eval_grad", "mpopf_eval_cons", "mpopf_eval_jac", "mpopf_eval_hess", "mpopf_assemble_kkt",
             "mpopf_sweep", "mpopf_sweep_host", "mpopf_sweep_points", "mpopf_assemble_kkt_noalloc", "mpopf_vjp", "mpopf_jvp", "mpopf_hvp",
-            "mpopf_vjp_jv", "mpopf_jvp_jv", "mpopf_kkt_factor", "mpopf_kkt_solve", "mpopf_csc_pattern",
+            "mpopf_vjp_jv", "mpopf_jvp_jv", "mpopf_vjp_many", "mpopf_jvp_many", "mpopf_hvp_many", "mpopf_kkt_factor", "mpopf_kkt_solve", "mpopf_csc_pattern",
             "mpopf_coo_to_csc", "mpopf_ipm_prepare", "mpopf_ipm_rhs", "mpopf_ipm_recover", "mpopf_batch_create",
             "mpopf_batch_set_io", "mpopf_batch_sweep", "mpopf_batch_set_schedule", "mpopf_batch_get_schedule",
             "mpopf_batch_tune", "mpopf_batch_status", "mpopf_batch_test_stall", "mpopf_batch_destroy",
@@ -436,6 +439,44 @@ class Handle:
         out = torch.empty(self.n, dtype=torch.float64, device="cuda") if out is None else out
         _check(lib().mpopf_hvp(self.h, _ptr(x), _ptr(lam), float(sigma), _ptr(v), _ptr(out), _stream_ptr(stream)),
                "mpopf_hvp")
+        return out
+
+    def _many(self, name, a, width):
+        if a.dim() != 2 or a.shape[1] != width or not a.is_contiguous():
+            raise ValueError(f"{name}: expected a contiguous [k, {width}] tensor")
+        return int(a.shape[0])
+
+    def vjp_many(self, x, Y, loads=True, jv=None, stream=None):
+        """J^T y for the k rows of Y [k, m] at one point: (GX [k, n], GPD, GQD
+        [k, T D] or None); jv: J values at x (optional)."""
+        import torch
+        k = self._many("vjp_many", Y, self.m)
+        gx = torch.empty(k, self.n, dtype=torch.float64, device="cuda")
+        gpd = gqd = None
+        if loads:
+            gpd = torch.empty(k, self.T * self.n_load, dtype=torch.float64, device="cuda")
+            gqd = torch.empty_like(gpd)
+        _check(lib().mpopf_vjp_many(self.h, k, _ptr(x), _ptr(jv), _ptr(Y), _ptr(gx), _ptr(gpd), _ptr(gqd),
+                                    _stream_ptr(stream)), "mpopf_vjp_many")
+        return gx, gpd, gqd
+
+    def jvp_many(self, x, V, dpd=None, dqd=None, jv=None, stream=None):
+        """J v for the k rows of V [k, n] (load tangents dpd, dqd [k, T D]) -> [k, m]."""
+        import torch
+        k = self._many("jvp_many", V, self.n)
+        out = torch.empty(k, self.m, dtype=torch.float64, device="cuda")
+        _check(lib().mpopf_jvp_many(self.h, k, _ptr(x), _ptr(jv), _ptr(V), _ptr(dpd), _ptr(dqd), _ptr(out),
+                                    _stream_ptr(stream)), "mpopf_jvp_many")
+        return out
+
+    def hvp_many(self, x, lam, sigma, V, hw=None, stream=None):
+        """W v for the k rows of V [k, n] -> [k, n]; hw: W values at (x, lam,
+        sigma) (optional)."""
+        import torch
+        k = self._many("hvp_many", V, self.n)
+        out = torch.empty(k, self.n, dtype=torch.float64, device="cuda")
+        _check(lib().mpopf_hvp_many(self.h, k, _ptr(x), _ptr(lam), float(sigma), _ptr(hw), _ptr(V), _ptr(out),
+                                    _stream_ptr(stream)), "mpopf_hvp_many")
         return out
 
     # -- library factorisation of M ---------------------------------------------
