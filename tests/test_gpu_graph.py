@@ -93,3 +93,42 @@ def test_profiling_times_the_callers_stream_kernels():
     for k in ref:
         assert torch.equal(out[k], ref[k]), k
     h.close()
+
+
+def test_points_and_many_products_in_a_graph():
+    """mpopf_sweep_points and the many-vector products captured after a first
+    call of the same size (their scratch exists, so the captured calls
+    allocate nothing): replays equal the eager results bit for bit."""
+    from paper_2405_14032_b300 import mpopf
+    inst = synth.make_instance(73, 300, 480, 60, 180, 6)
+    h = mpopf.Handle(inst)
+    pts = [synth.make_point(73, inst, stream_offset=100 * j) for j in range(3)]
+    st_ = lambda key: torch.as_tensor(np.stack([getattr(p, key) for p in pts]), dtype=torch.float64,
+                                      device="cuda").contiguous()
+    X, LAM, SX, DV = st_("x"), st_("lam"), st_("sigma_x"), st_("dvec")
+    V = torch.randn(5, h.n, generator=torch.Generator(device="cuda").manual_seed(3), device="cuda",
+                    dtype=torch.float64)
+    ref = h.sweep_points(X, LAM, 1.0, SX, DV, 1e-8)
+    ref_h = h.hvp_many(X[0], LAM[0], 1.0, V)
+    torch.cuda.synchronize()
+    out = h.new_point_outputs(3)
+    st = torch.cuda.Stream()
+    st.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    holder = {}
+    with torch.cuda.stream(st):
+        with torch.cuda.graph(g, stream=st):
+            h.sweep_points(X, LAM, 1.0, SX, DV, 1e-8, out=out, stream=st)
+            holder["hv"] = h.hvp_many(X[0], LAM[0], 1.0, V, stream=st)
+    torch.cuda.synchronize()
+    for _ in range(2):
+        for v in out.values():
+            v.fill_(float("nan"))
+        holder["hv"].fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        for k in ref:
+            assert torch.equal(out[k], ref[k]), k
+        assert torch.equal(holder["hv"], ref_h)
+    del g
+    h.close()
