@@ -568,7 +568,7 @@ def batched_comparison(torch, reps=20, fp64_peak=None):
     res = {"workload": "64 uneven instances (N log-uniform [500, 5000], T in {12, 24, 48, 96}), all six outputs",
            "instances": 64, "component_periods": units,
            "sequential_ms": seq_ms, "batched_ms": bat_ms, "batched_untuned_ms": untuned_ms,
-           "sequential_launches": 64 * hs[0].launch_count(), "batched_launches": 1,
+           "sequential_launches": 64 * hs[0].launch_count(), "batched_graph_launches": 1,
            "speedup": seq_ms / bat_ms, "schedule": b.schedule(),
            "instance_sweeps_per_s_batched": 64 / (bat_ms * 1e-3),
            "instance_sweeps_per_s_sequential": 64 / (seq_ms * 1e-3),
@@ -576,6 +576,8 @@ def batched_comparison(torch, reps=20, fp64_peak=None):
            "fp64_ops_hand_count": fp64_ops,
            "fp64_gops_batched": fp64_ops / (bat_ms * 1e-3) / 1e9}
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    res["schedule_kind"] = ("plain sweeps on parallel graph branches" if res["schedule"]["launches"] == 0 else
+                            f"{res['schedule']['launches']} persistent launch(es)")
     res["fp64_frac_of_issue_peak"] = res["fp64_gops_batched"] / fp64_issue_peak(
         sms, measured_peaks().get("sm_max_mhz") or SM_MAX_MHZ)
     if fp64_peak:

@@ -427,7 +427,9 @@ int mpopf_kkt_factor(mpopf_handle *h, const double *kv, int64_t *zero_pivot, voi
 int mpopf_kkt_solve(mpopf_handle *h, const double *rhs, double *dx, void *stream);
 
 /* Batched full sweeps of many independent instances (uneven sizes and
- * horizons) in one CUDA graph of one or two persistent kernel launches.  The
+ * horizons) in one CUDA graph: one or two persistent kernel launches over a
+ * work list of every instance's tiles, or the instances' plain sweeps on
+ * parallel branches of the graph (the schedule decides).  The
  * paper evaluates one model per solver; this runs many, e.g. scenario or
  * rolling-horizon instances, with the same values as mpopf_sweep on each.
  *
@@ -448,8 +450,12 @@ int mpopf_kkt_solve(mpopf_handle *h, const double *rhs, double *dx, void *stream
  *   with every branch tile (the sweep's 64-thread CTAs), the second with every
  *   generator tile, bus tile and objective (bus tiles do not wait; objectives
  *   wait for their generator tiles; run at the bus work's own occupancy; CTAs
- *   per SM and P are not used); sched[5] = (order, tile, CTAs per SM, P,
- *   launches).
+ *   per SM and P are not used), 0 = no persistent launch: each instance's
+ *   plain sweep (mpopf_sweep's launches, on the handle's own side stream and
+ *   schedule) on one of S parallel branches of the graph, instances dealt
+ *   round-robin in the order, S = the CTAs-per-SM argument (1..64, 0 = 16),
+ *   tile and P not used; the graph is captured again by mpopf_batch_set_io;
+ *   sched[5] = (order, tile, CTAs per SM or S, P, launches).
  * mpopf_batch_tune: times candidate schedules (coordinate search; reps graph
  *   launches each, CUDA events on `stream`) and keeps the fastest; *best_ms its
  *   time per sweep.
@@ -470,8 +476,8 @@ int mpopf_batch_set_schedule(mpopf_batch *b, int32_t order, int32_t tile_chunks,
 int mpopf_batch_get_schedule(const mpopf_batch *b, int32_t *sched /* [5] */, int32_t *grid, int32_t *n_items);
 int mpopf_batch_tune(mpopf_batch *b, void *stream, int32_t reps, double *best_ms);
 int mpopf_batch_status(mpopf_batch *b);
-/* Failure-path test hook (one-launch schedules; with two launches nothing
- * waits and the hook returns MPOPF_ERR_ARG).  on != 0 raises the dependency
+/* Failure-path test hook (one-launch schedules; with two launches or plain
+ * sweeps nothing waits and the hook returns MPOPF_ERR_ARG).  on != 0 raises the dependency
  * target of the first bus tile that waits, so that its wait can never be met: the next sweep waits
  * out the bounded limit (about a second), sets the error flag, computes the
  * tile anyway and finishes; mpopf_batch_status then returns MPOPF_ERR_CUDA.

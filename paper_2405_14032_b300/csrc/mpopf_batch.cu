@@ -13,7 +13,10 @@
 // launch takes the branch tiles (in the sweep kernel's 64-thread CTAs) and the
 // second the generator tiles, the bus tiles and the objective items, so the
 // launch boundary replaces the bus tiles' waits and the bus work runs at its
-// own occupancy.  Results do not depend on the
+// own occupancy.  Or no persistent launch at all: each instance's plain sweep
+// (mpopf_sweep's launches) on one of S parallel branches of the graph
+// (instances dealt round-robin in the schedule's order), so that the plain
+// kernels of several instances share the GPU.  Results do not depend on the
 // schedule: each value is computed by the same sequence of operations
 // whichever CTA runs it.
 #include <algorithm>
@@ -37,7 +40,8 @@ struct mpopf_batch {
   int32_t *d_ctl = nullptr;   // [3 + n_counters]
   int32_t n_items = 0, n_counters = 0, cap_ctl = 0;
   // order (0 given, 1 largest first), tile chunks, CTAs per SM (0 = max),
-  // periods per chunk (0 = all), launches (1 or 2)
+  // periods per chunk (0 = all), launches (1 or 2; 0: plain sweeps on
+  // parallel branches, CTAs per SM then the number of branches, 0 = 16)
   int32_t sched[5] = {0, 1, 0, 0, 1};
   int32_t grid = 0;
   // two-launch schedule: items [0, n_items1) go to the first launch, the rest
@@ -49,6 +53,11 @@ struct mpopf_batch {
   cudaGraphExec_t exec = nullptr;
   void *args[7], *args2[7];
   bool io_set = false;
+  std::vector<BatchIO> io_host;          // the instances' pointers (plain-sweep schedule)
+  std::vector<cudaStream_t> br_streams;  // capture streams of the plain-sweep schedule
+  std::vector<cudaEvent_t> br_join;
+  cudaStream_t cap = nullptr;
+  cudaEvent_t ev_start = nullptr;
   std::vector<int32_t> need_host;  // dependency targets as built (the stall hook restores them)
   int32_t stall_counter = -1;      // counter whose target the stall hook raised, or -1
 };
@@ -176,12 +185,62 @@ cudaError_t build_items(mpopf_batch *b) {
   return e;
 }
 
-// (Re)build the graph: reset the counters, then the persistent kernel.
+std::vector<int32_t> instance_order(const mpopf_batch *b) {
+  std::vector<int32_t> order(b->K);
+  std::iota(order.begin(), order.end(), 0);
+  if (b->sched[0] == 1)
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int32_t a, int32_t c) { return work_of(b->hs[a]->d) > work_of(b->hs[c]->d); });
+  return order;
+}
+
+// The plain-sweep schedule's graph, captured from S streams: a start event
+// forks every stream off the capture stream, instance k of the order runs
+// its sweep (launch_eval, the handle's own side stream and schedule) on
+// stream k mod S, and every stream joins the capture stream at the end.
+cudaError_t capture_plain_sweeps(mpopf_batch *b) {
+  const int32_t S = std::min<int32_t>(b->sched[2] ? b->sched[2] : 16, b->K);
+  cudaError_t e = cudaSuccess;
+  if (!b->cap) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess && !b->ev_start) e = cudaEventCreateWithFlags(&b->ev_start, cudaEventDisableTiming);
+  while (e == cudaSuccess && (int32_t)b->br_streams.size() < S) {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (st) b->br_streams.push_back(st);
+    if (ev) b->br_join.push_back(ev);
+  }
+  if (e != cudaSuccess) return e;
+  const std::vector<int32_t> order = instance_order(b);
+  e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  cudaError_t c = cudaEventRecord(b->ev_start, b->cap);
+  for (int32_t s = 0; s < S && c == cudaSuccess; ++s) c = cudaStreamWaitEvent(b->br_streams[s], b->ev_start, 0);
+  for (int32_t k = 0; k < b->K && c == cudaSuccess; ++k) {
+    const int32_t i = order[k];
+    const BatchIO &io = b->io_host[i];
+    c = launch_eval(b->hs[i]->d, MPOPF_OUT_ALL, io.x, io.lam, io.sigma, io.sx, io.dv, io.dw, io.f, io.grad, io.c,
+                    io.jv, io.hv, io.kv, b->br_streams[k % S], nullptr, &b->hs[i]->fork);
+  }
+  for (int32_t s = 0; s < S && c == cudaSuccess; ++s) {
+    c = cudaEventRecord(b->br_join[s], b->br_streams[s]);
+    if (c == cudaSuccess) c = cudaStreamWaitEvent(b->cap, b->br_join[s], 0);
+  }
+  e = cudaStreamEndCapture(b->cap, &b->graph);  // ends the capture whatever happened inside it
+  if (c != cudaSuccess) e = c;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+  return e;
+}
+
+// (Re)build the graph: reset the counters, then the persistent kernel (or the
+// plain sweeps, once the instances' pointers are known).
 cudaError_t build_graph(mpopf_batch *b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   b->exec = nullptr;
   b->graph = nullptr;
+  if (b->sched[4] == 0) return b->io_set ? capture_plain_sweeps(b) : cudaSuccess;
   cudaError_t e = cudaGraphCreate(&b->graph, 0);
   if (e != cudaSuccess) return e;
   cudaMemsetParams mp = {};
@@ -224,6 +283,10 @@ cudaError_t build_graph(mpopf_batch *b) {
 void release(mpopf_batch *b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
+  for (cudaStream_t st : b->br_streams) cudaStreamDestroy(st);
+  for (cudaEvent_t ev : b->br_join) cudaEventDestroy(ev);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  if (b->ev_start) cudaEventDestroy(b->ev_start);
   cudaFree(b->d_devs);
   cudaFree(b->d_io);
   cudaFree(b->d_items);
@@ -278,7 +341,15 @@ int mpopf_batch_set_io(mpopf_batch *b, const mpopf_batch_io *io, void *stream) {
   cudaError_t e = cudaMemcpyAsync(b->d_io, v.data(), b->K * sizeof(BatchIO), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // v is a host temporary
   if (e != cudaSuccess) return fail(MPOPF_ERR_CUDA, std::string("mpopf_batch_set_io: ") + cudaGetErrorString(e));
+  b->io_host = v;
   b->io_set = true;
+  if (b->sched[4] == 0) {  // the plain sweeps' graph holds the pointers: capture it again
+    e = build_graph(b);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(MPOPF_ERR_CUDA, std::string("mpopf_batch_set_io: ") + cudaGetErrorString(e));
+    }
+  }
   return MPOPF_OK;
 }
 
@@ -308,6 +379,8 @@ int mpopf_batch_test_stall(mpopf_batch *b, int32_t on) {
     e = cudaMemcpy(b->d_need + c, &b->need_host[c], sizeof(int32_t), cudaMemcpyHostToDevice);
     b->stall_counter = -1;
   }
+  if (e == cudaSuccess && on && b->sched[4] == 0)
+    return fail(MPOPF_ERR_ARG, "mpopf_batch_test_stall: no bus tile waits (plain sweeps)");
   if (e == cudaSuccess && on) {
     // the first counter a bus tile waits on (a chunk of some instance's branch tiles)
     int32_t c = -1;
@@ -329,7 +402,7 @@ int mpopf_batch_test_stall(mpopf_batch *b, int32_t on) {
 int mpopf_batch_set_schedule(mpopf_batch *b, int32_t order, int32_t tile_chunks, int32_t ctas_per_sm,
                              int32_t chunk_periods, int32_t launches) {
   if (!b || order < 0 || order > 1 || tile_chunks < 1 || tile_chunks > 64 || ctas_per_sm < 0 || chunk_periods < 0 ||
-      launches < 1 || launches > 2)
+      launches < 0 || launches > 2 || (launches == 0 && ctas_per_sm > 64))
     return fail(MPOPF_ERR_ARG, "mpopf_batch_set_schedule: bad argument");
   b->sched[0] = order;
   b->sched[1] = tile_chunks;
@@ -339,7 +412,10 @@ int mpopf_batch_set_schedule(mpopf_batch *b, int32_t order, int32_t tile_chunks,
   cudaError_t e = cudaDeviceSynchronize();
   if (e == cudaSuccess) e = build_items(b);
   if (e == cudaSuccess) e = build_graph(b);
-  if (e != cudaSuccess) return fail(MPOPF_ERR_CUDA, std::string("mpopf_batch_set_schedule: ") + cudaGetErrorString(e));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(MPOPF_ERR_CUDA, std::string("mpopf_batch_set_schedule: ") + cudaGetErrorString(e));
+  }
   return MPOPF_OK;
 }
 
@@ -393,6 +469,9 @@ int mpopf_batch_tune(mpopf_batch *b, void *stream, int32_t reps, double *best_ms
   for (int32_t tile : {1, 2, 4, 8}) trial(0, tile, 0, 0, 2);
   if (best_s[4] == 1)
     for (int32_t P : chunks) trial(0, best_s[1], best_s[2], P, 1);
+  // plain sweeps on 4 .. 64 parallel branches (largest instances first)
+  for (int32_t S : {4, 8, 16, 32, 64})
+    if (S <= 2 * b->K) trial(1, 1, S, 0, 0);
   trial(1, best_s[1], best_s[2], best_s[3], best_s[4]);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

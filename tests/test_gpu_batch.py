@@ -118,14 +118,16 @@ def test_batch_equals_individual_sweeps_every_schedule():
     for (inst, pt), h, io in zip(kept, hs, ios):  # the batched outputs against the oracle, in full
         _check_oracle(inst, pt, h, io)
     for sched in [(0, 1, 0, 0), (1, 1, 1, 1), (0, 2, 2, 2), (1, 4, 0, 3), (0, 4, 1, 0), (1, 2, 3, 1), (0, 1, 0, 2),
-                  (0, 1, 0, 0, 2), (1, 2, 1, 0, 2), (0, 4, 3, 0, 2)]:
+                  (0, 1, 0, 0, 2), (1, 2, 1, 0, 2), (0, 4, 3, 0, 2), (0, 1, 0, 0, 0), (1, 1, 3, 0, 0),
+                  (0, 1, 64, 0, 0), (1, 1, 1, 0, 0)]:
         b.set_schedule(*sched)
         _check_all(b, ios, refs)
         _check_all(b, ios, refs)  # replay of the same graph
     best = b.tune(reps=2)
     assert best > 0
     _check_all(b, ios, refs)
-    for bad in [(0, 1, 0, 0, 0), (0, 1, 0, 0, 3), (2, 1, 0, 0, 1), (0, 0, 0, 0, 1), (0, 1, -1, 0, 1)]:
+    for bad in [(0, 1, 65, 0, 0), (0, 1, 0, 0, 3), (2, 1, 0, 0, 1), (0, 0, 0, 0, 1), (0, 1, -1, 0, 1),
+                (0, 1, 0, 0, -1)]:
         with pytest.raises(mpopf.MpopfError, match="bad argument"):
             b.set_schedule(*bad)
     _check_all(b, ios, refs)
@@ -186,10 +188,12 @@ def test_dependency_wait_timeout_is_reported_not_hung():
             assert torch.equal(io[k], ref[k]), k
     b.test_stall(False)
     _check_all(b, ios, refs)
-    # with two launches nothing waits: the hook has no wait to hold back
-    b.set_schedule(0, 1, 0, 0, 2)
-    assert b.schedule()["launches"] == 2
-    with pytest.raises(mpopf.MpopfError, match="no bus tile waits"):
-        b.test_stall(True)
-    _check_all(b, ios, refs)
+    # with two launches, or plain sweeps, nothing waits: the hook has no wait
+    # to hold back
+    for sched, launches in (((0, 1, 0, 0, 2), 2), ((1, 1, 4, 0, 0), 0)):
+        b.set_schedule(*sched)
+        assert b.schedule()["launches"] == launches
+        with pytest.raises(mpopf.MpopfError, match="no bus tile waits"):
+            b.test_stall(True)
+        _check_all(b, ios, refs)
     b.close()
