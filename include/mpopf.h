@@ -261,8 +261,9 @@ int mpopf_sweep(mpopf_handle *h, const double *x, const double *lam, double sigm
  * call that needs more than the handle holds (after a device-wide
  * synchronisation when it replaces a smaller one) and kept by the handle;
  * calls on one handle must not overlap.  MPOPF_ERR_ARG for a NULL buffer, k
- * outside the range or a shard handle; MPOPF_ERR_ALLOC when the scratch
- * cannot be allocated. */
+ * outside the range, a shard handle, or a call under stream capture that
+ * would have to grow the scratch (make one call of that size first);
+ * MPOPF_ERR_ALLOC when the scratch cannot be allocated. */
 int mpopf_sweep_points(mpopf_handle *h, int32_t k, const double *x, const double *lam, double sigma,
                        const double *sigma_x, const double *dvec, double delta_w, double *f, double *grad, double *c,
                        double *jv, double *hv, double *kv, void *stream);
@@ -320,8 +321,9 @@ int mpopf_hvp(mpopf_handle *h, const double *x, const double *lam, double sigma,
  * bit for bit.  mpopf_vjp_many and mpopf_hvp_many keep their incidence
  * records (k x 2 L T x 16 bytes) in the handle's scratch, grown like
  * mpopf_sweep_points's (shared with it); calls on one handle must not
- * overlap.  MPOPF_ERR_ARG for a NULL argument, k outside the range or a shard
- * handle; MPOPF_ERR_ALLOC when the scratch cannot be allocated. */
+ * overlap.  MPOPF_ERR_ARG for a NULL argument, k outside the range, a shard
+ * handle or a scratch that would have to grow under stream capture;
+ * MPOPF_ERR_ALLOC when the scratch cannot be allocated. */
 int mpopf_vjp_many(mpopf_handle *h, int32_t k, const double *x, const double *jv, const double *y, double *gx,
                    double *gpd, double *gqd, void *stream);
 int mpopf_jvp_many(mpopf_handle *h, int32_t k, const double *x, const double *jv, const double *v,

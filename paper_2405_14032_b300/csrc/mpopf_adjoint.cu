@@ -873,10 +873,10 @@ void launch_hvp(const Dev &d, int32_t k, const double *x, const double *lam, dou
 
 // The handle's descriptor with d.S pointing at the packed records of k
 // vectors (2 L T double2 each) in the handle's scratch.
-int many_dev(mpopf_handle *h, int32_t k, const char *who, Dev *out) {
+int many_dev(mpopf_handle *h, int32_t k, const char *who, cudaStream_t s, Dev *out) {
   if (k < 1 || k > 65535) return fail(MPOPF_ERR_ARG, std::string(who) + ": k outside [1, 65535]");
   const size_t rec = (size_t)2 * h->d.L * h->d.T * rec_stride<1>();
-  const int rc = grow_points_scratch(h, (size_t)k * rec * sizeof(double), who);
+  const int rc = grow_points_scratch(h, (size_t)k * rec * sizeof(double), who, s);
   if (rc != MPOPF_OK) return rc;
   *out = h->d;
   out->S = h->pts;
@@ -938,7 +938,7 @@ int mpopf_vjp_many(mpopf_handle *h, int32_t k, const double *x, const double *jv
   if ((gpd == nullptr) != (gqd == nullptr))
     return fail(MPOPF_ERR_ARG, "mpopf_vjp_many: give both gpd and gqd or neither");
   Dev d;
-  const int rc = many_dev(h, k, "mpopf_vjp_many", &d);
+  const int rc = many_dev(h, k, "mpopf_vjp_many", static_cast<cudaStream_t>(stream), &d);
   if (rc != MPOPF_OK) return rc;
   launch_vjp<kManyNV>(d, k, x, jv, y, gx, gpd, gqd, static_cast<cudaStream_t>(stream));
   return done("mpopf_vjp_many");
@@ -960,7 +960,7 @@ int mpopf_hvp_many(mpopf_handle *h, int32_t k, const double *x, const double *la
   if (!h || !x || !lam || !v || !hv) return fail(MPOPF_ERR_ARG, "mpopf_hvp_many: NULL argument");
   if (mpopf::is_shard(h->d)) return fail(MPOPF_ERR_ARG, "mpopf_hvp_many: not available on a period shard");
   Dev d;
-  const int rc = many_dev(h, k, "mpopf_hvp_many", &d);
+  const int rc = many_dev(h, k, "mpopf_hvp_many", static_cast<cudaStream_t>(stream), &d);
   if (rc != MPOPF_OK) return rc;
   launch_hvp<kManyNV>(d, k, x, lam, sigma, hw, v, hv, static_cast<cudaStream_t>(stream));
   return done("mpopf_hvp_many");

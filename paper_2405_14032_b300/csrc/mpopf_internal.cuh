@@ -216,8 +216,9 @@ struct mpopf_handle {
 namespace mpopf {
 // Makes the handle's scratch of the many-point / many-vector calls at least
 // `need` bytes (a device-wide synchronisation before a smaller one is
-// replaced); MPOPF_OK or an error code with the message set for `who`.
-int grow_points_scratch(mpopf_handle *h, size_t need, const char *who);
+// replaced); MPOPF_OK or an error code with the message set for `who`
+// (MPOPF_ERR_ARG when it would have to grow while `s` is being captured).
+int grow_points_scratch(mpopf_handle *h, size_t need, const char *who, cudaStream_t s);
 // Branch and bus work of periods [t0, t1) of a full sweep, and the generator
 // work with the objective over the whole horizon; together, over a partition
 // of the horizon, exactly the launches of a full sweep (mpopf_kernels.cu).

@@ -1098,8 +1098,14 @@ cudaError_t fork_bus_stream(Fork *fork, bool high_priority) {
   return e;
 }
 
-int grow_points_scratch(mpopf_handle *h, size_t need, const char *who) {
+int grow_points_scratch(mpopf_handle *h, size_t need, const char *who, cudaStream_t s) {
   if (need <= h->pts_bytes) return MPOPF_OK;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+    set_error(std::string(who) + ": the scratch must grow, which a stream capture does not allow; make a first call "
+              "of this size (or larger) before capturing");
+    return MPOPF_ERR_ARG;
+  }
   if (h->pts) {
     // an earlier call's kernels may still use the old scratch
     cudaError_t e = cudaDeviceSynchronize();
@@ -1269,7 +1275,8 @@ int mpopf_sweep_points(mpopf_handle *h, int32_t points, const double *x, const d
   const Dev &d = h->d;
   const size_t rec = (size_t)2 * d.L * d.T * kRec;  // record doubles of one point
   const size_t tiles = grid_for((int64_t)d.T * d.G);
-  const int rc = grow_points_scratch(h, (size_t)points * (rec + tiles) * sizeof(double), "mpopf_sweep_points");
+  const int rc = grow_points_scratch(h, (size_t)points * (rec + tiles) * sizeof(double), "mpopf_sweep_points",
+                                     static_cast<cudaStream_t>(stream));
   if (rc != MPOPF_OK) return rc;
   cudaError_t e = launch_points(d, points, h->pts, h->pts + (size_t)points * rec, x, lam, sigma, sigma_x, dvec,
                                 delta_w, f, grad, c, jv, hv, kv, static_cast<cudaStream_t>(stream), &h->fork);

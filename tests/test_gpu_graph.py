@@ -132,3 +132,37 @@ def test_points_and_many_products_in_a_graph():
         assert torch.equal(holder["hv"], ref_h)
     del g
     h.close()
+
+
+def test_points_scratch_growth_refused_under_capture():
+    """A captured sweep_points / hvp_many call whose scratch would have to grow
+    returns MPOPF_ERR_ARG (no allocation or device synchronisation inside the
+    capture); after an eager call of that size the same capture works."""
+    from paper_2405_14032_b300 import mpopf
+    inst = synth.make_instance(74, 120, 190, 24, 70, 3)
+    h = mpopf.Handle(inst)
+    pts = [synth.make_point(74, inst, stream_offset=100 * j) for j in range(3)]
+    st_ = lambda key: torch.as_tensor(np.stack([getattr(p, key) for p in pts]), dtype=torch.float64,
+                                      device="cuda").contiguous()
+    X, LAM, SX, DV = st_("x"), st_("lam"), st_("sigma_x"), st_("dvec")
+    out = h.new_point_outputs(3)
+    st = torch.cuda.Stream()
+    st.wait_stream(torch.cuda.current_stream())
+    with pytest.raises(mpopf.MpopfError, match="stream capture"):
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(st):
+            with torch.cuda.graph(g, stream=st):
+                h.sweep_points(X, LAM, 1.0, SX, DV, 1e-8, out=out, stream=st)
+    torch.cuda.synchronize()
+    ref = h.sweep_points(X, LAM, 1.0, SX, DV, 1e-8)  # grows the scratch
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(st):
+        with torch.cuda.graph(g, stream=st):
+            h.sweep_points(X, LAM, 1.0, SX, DV, 1e-8, out=out, stream=st)
+    g.replay()
+    torch.cuda.synchronize()
+    for k in ref:
+        assert torch.equal(out[k], ref[k]), k
+    del g
+    h.close()
