@@ -1,6 +1,6 @@
 """Run one workload of the library a few times, for an external profiler.
 
-    python -m paper_2405_14032_b300.profile_run sweep|ipm|adjoint|csc|batch \
+    python -m paper_2405_14032_b300.profile_run sweep|ipm|adjoint|csc|batch|points \
         [--buses 10000] [--periods 24] [--reps 3]
 
 The network is the seeded synthetic one (L = 1.6 N, G = 0.2 N, D = 0.6 N,
@@ -23,12 +23,15 @@ def _instance(buses: int, periods: int, seed: int = 3):
 
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
-    ap.add_argument("workload", choices=["sweep", "ipm", "adjoint", "csc", "batch"])
+    ap.add_argument("workload", choices=["sweep", "ipm", "adjoint", "csc", "batch", "points"])
     ap.add_argument("--buses", type=int, default=10000)
     ap.add_argument("--periods", type=int, default=24)
     ap.add_argument("--reps", type=int, default=3)
-    ap.add_argument("--launches", type=int, default=1, choices=[1, 2],
-                    help="batch: one persistent launch or two (generator/branch, then bus/objective)")
+    ap.add_argument("--launches", type=int, default=1, choices=[0, 1, 2],
+                    help="batch: one persistent launch or two (generator/branch, then bus/objective), or 0: "
+                         "the plain sweeps on --streams parallel graph branches")
+    ap.add_argument("--streams", type=int, default=32, help="batch --launches 0: parallel graph branches")
+    ap.add_argument("--points", type=int, default=16, help="points: points per mpopf_sweep_points call")
     ap.add_argument("--instances", type=int, default=64,
                     help="batch: the first INSTANCES of the 64 benchmark instances (a smaller capture)")
     a = ap.parse_args(argv)
@@ -50,6 +53,8 @@ def main(argv=None) -> int:
         b.set_io(ios)
         if a.launches == 2:
             b.set_schedule(0, 1, 3, 0, 2)
+        elif a.launches == 0:
+            b.set_schedule(1, 1, a.streams, 0, 0)
         for _ in range(a.reps):
             b.sweep()
         b.status()
@@ -65,6 +70,15 @@ def main(argv=None) -> int:
     if a.workload == "sweep":
         for _ in range(a.reps):
             h.sweep(x, lam, pt.sigma, sx, dv, pt.delta_w, out=out)
+    elif a.workload == "points":
+        k = max(1, a.points)
+        X = dev(pt.x).unsqueeze(0) + 1e-3 * torch.randn(k, h.n, dtype=torch.float64, device="cuda",
+                                                        generator=torch.Generator(device="cuda").manual_seed(3))
+        rep = lambda t: t.unsqueeze(0).repeat(k, 1).contiguous()
+        LAM, SX, DV = rep(lam), rep(sx), rep(dv)
+        outs = h.new_point_outputs(k)
+        for _ in range(a.reps):
+            h.sweep_points(X, LAM, pt.sigma, SX, DV, pt.delta_w, out=outs)
     elif a.workload == "adjoint":
         y = dev(synth.uniform(3, 5000, h.m, -1.0, 1.0))
         v = dev(synth.normal(3, 9000, h.n))
