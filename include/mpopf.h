@@ -435,9 +435,10 @@ int mpopf_kkt_solve(mpopf_handle *h, const double *rhs, double *dx, void *stream
  * paper evaluates one model per solver; this runs many, e.g. scenario or
  * rolling-horizon instances, with the same values as mpopf_sweep on each.
  *
- * mpopf_batch_create: the handles (same device, kept alive by the caller until
- *   mpopf_batch_destroy) become one batch; allocates the work list and the
- *   graph (setup time).
+ * mpopf_batch_create: the handles (same device, each at most once, kept alive
+ *   by the caller until mpopf_batch_destroy) become one batch; allocates the
+ *   work list and the graph (setup time); MPOPF_ERR_ARG for a NULL, repeated
+ *   or shard handle.
  * mpopf_batch_set_io: per-instance DEVICE pointers (host array of k
  *   descriptors, copied; synchronises `stream`).
  * mpopf_batch_sweep: one graph launch on `stream`: every instance's f, grad, c,

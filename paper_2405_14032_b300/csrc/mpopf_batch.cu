@@ -305,6 +305,14 @@ int mpopf_batch_create(mpopf_handle *const *hs, int32_t k, mpopf_batch **out) {
     if (!hs[i]) return fail(MPOPF_ERR_ARG, "mpopf_batch_create: NULL handle");
   for (int32_t i = 0; i < k; ++i)
     if (mpopf::is_shard(hs[i]->d)) return fail(MPOPF_ERR_ARG, "mpopf_batch_create: not available on a period shard");
+  {
+    // an instance's scratch (incidence records, objective partials) belongs to
+    // its handle, so a handle may appear only once
+    std::vector<mpopf_handle *> sorted(hs, hs + k);
+    std::sort(sorted.begin(), sorted.end());
+    if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end())
+      return fail(MPOPF_ERR_ARG, "mpopf_batch_create: a handle appears twice");
+  }
   mpopf_batch *b = new mpopf_batch();
   b->K = k;
   b->hs.assign(hs, hs + k);

@@ -197,3 +197,16 @@ def test_dependency_wait_timeout_is_reported_not_hung():
             b.test_stall(True)
         _check_all(b, ios, refs)
     b.close()
+
+
+def test_batch_refuses_a_repeated_handle():
+    """Each instance's scratch belongs to its handle, so a batch holding the
+    same handle twice is refused at creation."""
+    from paper_2405_14032_b300 import mpopf
+    hs, ios, refs = _setup(SMALL[:2])
+    with pytest.raises(mpopf.MpopfError, match="appears twice"):
+        mpopf.Batch([hs[0], hs[1], hs[0]])
+    b = mpopf.Batch(hs)
+    b.set_io(ios)
+    _check_all(b, ios, refs)
+    b.close()
