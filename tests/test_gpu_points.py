@@ -115,3 +115,41 @@ def test_points_single_point_and_errors():
     hs = mp.Handle(inst, shard=(0, T // 2))
     assert lib.mpopf_sweep_points(hs.h, 1, *args) == -1  # not on a period shard
     hs.close()
+
+
+NEED_POINTS_BYTES = 100 * 2**30
+
+
+def test_points_offsets_beyond_2_31():
+    """The 10k-bus network at T = 168 (nnz of M 96.1M) at 24 points in one
+    call: the later points' J, W and M start past 2^31 entries of their
+    arrays (point 23's M at 2.2e9), so the kernels' point offsets are 64-bit
+    wherever they must be.  The first and last points against single sweeps
+    at the same points, on the device.  About 75 GB of device memory: skipped
+    when less than 100 GB is free."""
+    free, _ = torch.cuda.mem_get_info()
+    if free < NEED_POINTS_BYTES:
+        pytest.skip(f"needs {NEED_POINTS_BYTES / 2**30:.0f} GB free on the device, {free / 2**30:.0f} GB free")
+    from paper_2405_14032_b300 import mpopf
+    inst = synth.config_instance("cfg3")
+    pt = synth.make_point(3, inst)
+    h = mpopf.Handle(inst)
+    k = 24
+    assert (k - 1) * h.nnz_kkt > 2**31
+    dev = lambda a: torch.as_tensor(a, dtype=torch.float64, device="cuda")
+    gen = torch.Generator(device="cuda").manual_seed(24)
+    X = dev(pt.x).unsqueeze(0) + 1e-3 * torch.randn(k, h.n, generator=gen, device="cuda", dtype=torch.float64)
+    rep = lambda a: dev(a).unsqueeze(0).expand(k, -1).contiguous()
+    LAM, SX, DV = rep(pt.lam), rep(pt.sigma_x), rep(pt.dvec)
+    out = h.sweep_points(X, LAM, pt.sigma, SX, DV, pt.delta_w)
+    torch.cuda.synchronize()
+    del LAM, SX, DV
+    for j in (0, k - 1):
+        one = h.sweep(X[j], dev(pt.lam), pt.sigma, dev(pt.sigma_x), dev(pt.dvec), pt.delta_w)
+        torch.cuda.synchronize()
+        for key, v in one.items():
+            assert torch.equal(out[key][j], v.reshape(out[key][j].shape)), (j, key)
+        del one
+    del out, X
+    h.close()
+    torch.cuda.empty_cache()
