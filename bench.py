@@ -56,6 +56,17 @@ def fp64_issue_peak(sms, sm_max_mhz):
 
 FP64_OPS_PER_BUS_PERIOD = 33   # hand counts of the bus and generator kernels (their
 FP64_OPS_PER_GEN_PERIOD = 17   # loops vary with the degree; these are averages)
+# With the bus-term launch in the schedule (MPOPF_SCHED_BUS_TERMS), the branch
+# kernel reads the products D8 (m2gs vm) and D9 (p2bs vm) at both ends of its
+# branch (8 operations fewer per element) and k_bw forms them once per bus and
+# period (4 operations).
+FP64_OPS_BUS_TERMS_PER_BRANCH_PERIOD = 8
+FP64_OPS_BUS_TERMS_PER_BUS_PERIOD = 4
+SCHED_BUS_TERMS = 16
+
+
+def branch_ops_per_element(bus_terms):
+    return FP64_OPS_PER_BRANCH_PERIOD - (FP64_OPS_BUS_TERMS_PER_BRANCH_PERIOD if bus_terms else 0)
 
 
 def parse():
@@ -538,8 +549,8 @@ def batched_comparison(torch, reps=20, fp64_peak=None):
         ios.append(io)
         units += s["T"] * (s["n_bus"] + s["n_branch"] + s["n_gen"])
         alg_bytes += algorithmic_bytes(h.n, h.m, h.nnz_jac, h.nnz_hess, h.nnz_kkt, s["n_load"], s["T"])
-        fp64_ops += s["T"] * (FP64_OPS_PER_BRANCH_PERIOD * s["n_branch"] + FP64_OPS_PER_BUS_PERIOD * s["n_bus"]
-                              + FP64_OPS_PER_GEN_PERIOD * s["n_gen"])
+        fp64_ops += fp64_ops_per_sweep(s["n_bus"], s["n_branch"], s["n_gen"], s["T"],
+                                       bool(h.sweep_schedule()[1] & SCHED_BUS_TERMS))
 
     def sequential():
         for h, io in zip(hs, ios):
@@ -1048,9 +1059,11 @@ def run_reference(args, world, rank):
     return 0
 
 
-def fp64_ops_per_sweep(N, L, G, T):
-    """Hand count of the FP64 operations of one full sweep over T periods."""
-    return FP64_OPS_PER_BRANCH_PERIOD * T * L + FP64_OPS_PER_BUS_PERIOD * T * N + FP64_OPS_PER_GEN_PERIOD * T * G
+def fp64_ops_per_sweep(N, L, G, T, bus_terms=False):
+    """Hand count of the FP64 operations of one full sweep over T periods
+    (bus_terms: the schedule forms the bus-end products in their own launch)."""
+    bus = FP64_OPS_PER_BUS_PERIOD + (FP64_OPS_BUS_TERMS_PER_BUS_PERIOD if bus_terms else 0)
+    return branch_ops_per_element(bus_terms) * T * L + bus * T * N + FP64_OPS_PER_GEN_PERIOD * T * G
 
 
 def run_ours(args, world, rank, local):
@@ -1159,8 +1172,9 @@ def run_ours(args, world, rank, local):
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     derived = fp64_issue_peak(sms, measured_peaks().get("sm_max_mhz") or SM_MAX_MHZ)
     peak = probe_rate / 1e9
+    bus_terms = bool(h.sweep_schedule()[1] & SCHED_BUS_TERMS)
     if top == "branch":
-        ops = FP64_OPS_PER_BRANCH_PERIOD * W * inst.net.n_branch
+        ops = branch_ops_per_element(bus_terms) * W * inst.net.n_branch
         achieved = ops / (top_ms * 1e-3) / 1e9
         roof = {"bound": "alu", "kernel": "k_branch (branch x period)", "achieved": achieved, "peak": peak,
                 "unit": "Gop/s (FP64 fma/add/mul)", "frac": achieved / peak,
@@ -1175,14 +1189,15 @@ def run_ours(args, world, rank, local):
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs")
     gbs = alg_whole / (ms_step * 1e-3) / 1e9 * (world if mode == "replicas" else 1)
-    floor_ms = fp64_ops_per_sweep(inst.net.n_bus, inst.net.n_branch, inst.net.n_gen, W) / probe_rate * 1e3
+    floor_ms = fp64_ops_per_sweep(inst.net.n_bus, inst.net.n_branch, inst.net.n_gen, W, bus_terms) / probe_rate * 1e3
     hbm = {"algorithmic_bytes_per_sweep": alg_whole, "gbs": gbs, "peak_gbs": hbm_peak,
            "frac": gbs / hbm_peak if hbm_peak else None, "peak_source": "MEASURED_PEAKS.json",
            "nominal_gbs": 7700.0, "frac_nominal": gbs / 7700.0}
     if mode != "shards":
         # the FP64 work alone bounds the sweep from below; at that floor the
         # algorithmic bytes would move at this fraction of the HBM peak
-        hbm.update({"fp64_ops_per_sweep": fp64_ops_per_sweep(inst.net.n_bus, inst.net.n_branch, inst.net.n_gen, T),
+        hbm.update({"fp64_ops_per_sweep": fp64_ops_per_sweep(inst.net.n_bus, inst.net.n_branch, inst.net.n_gen, T,
+                                                             bus_terms),
                     "fp64_floor_ms": floor_ms,
                     "attainable_frac": (alg_whole / (floor_ms * 1e-3) / 1e9) / hbm_peak if hbm_peak else None,
                     "frac_of_fp64_floor": floor_ms / ms_step})

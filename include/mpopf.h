@@ -507,7 +507,7 @@ int mpopf_launch_count(const mpopf_handle *h, unsigned outputs);
  * before the first branch chunk instead of after the last.  Both streams join
  * `stream` before the call returns, so work enqueued on `stream` afterwards
  * sees every output (under stream capture they are parallel graph branches).
- * MPOPF_SCHED_PDL (with P = 0; the default schedule is P = 0 with this flag):
+ * MPOPF_SCHED_PDL (with P = 0; every default schedule is P = 0 with this flag):
  * the bus kernel is launched with programmatic stream serialization, so its
  * CTAs may be scheduled while the branch kernel's last CTAs run; it waits
  * (griddepcontrol.wait) for the branch kernel's completion before reading its
@@ -516,10 +516,20 @@ int mpopf_launch_count(const mpopf_handle *h, unsigned outputs);
  * branch kernel, side by side: the balance rows with their J rows, the shunt W
  * entries, the gradient zeros and the reference row on the internal second
  * stream, the va / vm rows of M on `stream`.
+ * MPOPF_SCHED_BUS_TERMS (with P = 0; full sweeps): the products D8 (m2gs vm)
+ * and D9 (p2bs vm) of the condensed matrix's arc rows, which the branch kernel
+ * would form at both ends of every branch, are formed once per bus and period
+ * by a small kernel launched before it (into a 2 T N-double scratch of the
+ * handle; the same operations, so the same values); with MPOPF_SCHED_PDL the
+ * branch kernel is its programmatic dependent launch.  A new handle starts
+ * with MPOPF_SCHED_PDL, plus MPOPF_SCHED_BUS_TERMS when its branch x period
+ * launch has at least twice as many elements as the device holds resident
+ * (2 x SMs x 768); mpopf_get_sweep_schedule reports it.
  * Per-kernel profiling (mpopf_profile_start) times unchunked, unsplit launches
  * without programmatic dependencies.
  * MPOPF_ERR_ARG for P < 0 or unknown flags. */
-enum { MPOPF_SCHED_BUS_PRIORITY = 1, MPOPF_SCHED_GEN_FIRST = 2, MPOPF_SCHED_PDL = 4, MPOPF_SCHED_SPLIT_BUS = 8 };
+enum { MPOPF_SCHED_BUS_PRIORITY = 1, MPOPF_SCHED_GEN_FIRST = 2, MPOPF_SCHED_PDL = 4, MPOPF_SCHED_SPLIT_BUS = 8,
+       MPOPF_SCHED_BUS_TERMS = 16 };
 int mpopf_set_sweep_schedule(mpopf_handle *h, int32_t chunk_periods, int32_t flags);
 
 /* An extra dependency of the generator work (generator x period kernel and

@@ -85,6 +85,10 @@ struct Dev {
   // shift asymmetry); the branch kernel then runs an instantiation without the
   // per-branch test
   int32_t all_sym;
+  // [2][T][N]: w8 = D8 (m2gs vm) and w9 = D9 (p2bs vm) of every bus and
+  // period, formed by k_bw before the branch kernel reads them at both ends
+  // of each branch (SCHED_BUS_TERMS)
+  double *bw;
 };
 
 // A period shard's handle evaluates only the periods it owns.
@@ -117,7 +121,8 @@ struct Prof {
 // incidence records are still in L2.
 constexpr int kMaxChunks = 64;
 enum { SCHED_BUS_PRIORITY = MPOPF_SCHED_BUS_PRIORITY, SCHED_GEN_FIRST = MPOPF_SCHED_GEN_FIRST,
-       SCHED_PDL = MPOPF_SCHED_PDL, SCHED_SPLIT_BUS = MPOPF_SCHED_SPLIT_BUS };
+       SCHED_PDL = MPOPF_SCHED_PDL, SCHED_SPLIT_BUS = MPOPF_SCHED_SPLIT_BUS,
+       SCHED_BUS_TERMS = MPOPF_SCHED_BUS_TERMS };
 struct Fork {
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -128,6 +133,10 @@ struct Fork {
   int32_t flags = 0;                   // SCHED_*: bus stream at the highest priority; generator work forked first
   cudaEvent_t gen_after = nullptr;     // the caller's event the generator work also waits for (or none)
 };
+
+// The launch schedule (SCHED_* flags) a new handle starts with, from its
+// branch launch's size on `device` (mpopf_kernels.cu).
+int32_t default_schedule_flags(const Dev &d, int device);
 
 // Kernel launchers (mpopf_kernels.cu).  With fork == nullptr every launch goes
 // to s in order.

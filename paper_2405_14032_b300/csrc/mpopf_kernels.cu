@@ -57,6 +57,28 @@ __device__ __forceinline__ double ld_part(const double *p) {
   return COH ? __ldcg(p) : *p;
 }
 
+// Waits (griddepcontrol.wait) until the grids this launch depends on
+// programmatically have completed and their writes are visible; returns at
+// once for a launch without such a dependency.
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Records a CUDA event pair around one launch when profiling is on.
+struct Timed {
+  Prof *p;
+  cudaStream_t s;
+  int slot;
+  Timed(Prof *prof, cudaStream_t st, int kind) : p(prof), s(st), slot(-1) {
+    if (p && p->next < p->cap) {
+      slot = p->next++;
+      p->kind[slot] = kind;
+      cudaEventRecord(p->ev[2 * slot], s);
+    }
+  }
+  ~Timed() {
+    if (slot >= 0) cudaEventRecord(p->ev[2 * slot + 1], s);
+  }
+};
+
 // Output staging of one warp (k_branch, k_batch).  The J rows of the four
 // flow constraints and the W blocks of 32 consecutive branch elements are
 // contiguous ranges of the outputs, but each lane writes its own short piece
@@ -99,7 +121,10 @@ __device__ __forceinline__ void bulk_done(int lane) {
 // SYM: every branch of the model is symmetric (the per-branch test is known).
 // PTS: the element belongs to point blockIdx.y of a sweep over several points,
 // whose incidence records follow the earlier points' (T periods each).
-template <unsigned MASK, bool BULK = false, bool SYM = false, bool PTS = false>
+// BW: the bus-end products D8 (m2gs vm) and D9 (p2bs vm) come from d.bw,
+// formed by k_bw with the same operations (the element waits for that grid
+// before its first read of them).
+template <unsigned MASK, bool BULK = false, bool SYM = false, bool PTS = false, bool BW = false>
 __device__ __forceinline__ void branch_body(const Dev &d, int32_t tl, unsigned rt, const double *__restrict__ x,
                                             const double *__restrict__ lam, const double *__restrict__ sx,
                                             const double *__restrict__ dv, double dw, double *__restrict__ grad,
@@ -282,8 +307,20 @@ __device__ __forceinline__ void branch_body(const Dev &d, int32_t tl, unsigned r
   const int64_t r8f = d.c_k8 + tN + f, r8t = d.c_k8 + tN + to;
   const double D8f = __ldg(dv + r8f), D9f = __ldg(dv + r8f + (d.c_k9 - d.c_k8));
   const double D8t = __ldg(dv + r8t), D9t = __ldg(dv + r8t + (d.c_k9 - d.c_k8));
-  const double w8f = D8f * (__ldg(d.bus_m2gs + f) * vf), w9f = D9f * (__ldg(d.bus_p2bs + f) * vf);
-  const double w8t = D8t * (__ldg(d.bus_m2gs + to) * vt), w9t = D9t * (__ldg(d.bus_p2bs + to) * vt);
+  double w8f, w9f, w8t, w9t;
+  if (BW) {
+    grid_dependency_wait();
+    const int64_t TN = (int64_t)d.T * d.N;
+    w8f = __ldcg(d.bw + tN + f);
+    w9f = __ldcg(d.bw + TN + tN + f);
+    w8t = __ldcg(d.bw + tN + to);
+    w9t = __ldcg(d.bw + TN + tN + to);
+  } else {
+    w8f = D8f * (__ldg(d.bus_m2gs + f) * vf);
+    w9f = D9f * (__ldg(d.bus_p2bs + f) * vf);
+    w8t = D8t * (__ldg(d.bus_m2gs + to) * vt);
+    w9t = D9t * (__ldg(d.bus_p2bs + to) * vt);
+  }
   const double sxpf = __ldg(sx + pb + l), sxpt = __ldg(sx + pb + L + l);
   const double sxqf = __ldg(sx + qb + l), sxqt = __ldg(sx + qb + L + l);
   const bool flo = f < to;
@@ -334,7 +371,7 @@ __device__ __forceinline__ void branch_body(const Dev &d, int32_t tl, unsigned r
     kv += j_ * (d).nnz_kkt;                                           \
   } while (0)
 
-template <unsigned MASK, bool SYM, bool PTS = false>
+template <unsigned MASK, bool SYM, bool PTS = false, bool BW = false>
 __global__ void __launch_bounds__(MPOPF_BRANCH_BLOCK, MPOPF_BRANCH_MINB)
     k_branch(Dev d, unsigned rt, const double *__restrict__ x, const double *__restrict__ lam,
              const double *__restrict__ sx, const double *__restrict__ dv, double dw, double *__restrict__ grad,
@@ -352,8 +389,58 @@ __global__ void __launch_bounds__(MPOPF_BRANCH_BLOCK, MPOPF_BRANCH_MINB)
   }
   __shared__ __align__(16) double s_stage[MPOPF_BRANCH_BLOCK / 32][kStagePitch];
   const bool full = tl - (int32_t)(threadIdx.x & 31) + 31 < end;  // uniform over the warp
-  branch_body<MASK, false, SYM, PTS>(d, tl, rt, x, lam, sx, dv, dw, grad, c, jv, hv, kv,
-                                     full ? s_stage[threadIdx.x >> 5] : nullptr);
+  branch_body<MASK, false, SYM, PTS, BW>(d, tl, rt, x, lam, sx, dv, dw, grad, c, jv, hv, kv,
+                                         full ? s_stage[threadIdx.x >> 5] : nullptr);
+}
+
+// The bus-end products of the arc rows of M, once per bus and period of
+// [first, end) (t N + n): w8 = D8 (m2gs vm) and w9 = D9 (p2bs vm), the
+// operations the branch kernel would otherwise do at each end of each
+// branch.  A grid-stride loop over a grid of at most a few CTAs per SM, so
+// that every CTA is resident at once and the branch kernel behind it (a
+// programmatic dependent launch) starts at once.
+__global__ void __launch_bounds__(kBlock) k_bw(Dev d, const double *__restrict__ x, const double *__restrict__ dv,
+                                               int32_t first, int32_t end) {
+  asm volatile("griddepcontrol.launch_dependents;");
+  const int64_t TN = (int64_t)d.T * d.N;
+  for (int32_t i = first + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x); i < end;
+       i += (int32_t)(gridDim.x * blockDim.x)) {
+    const int32_t n = i % d.N;
+    const double vm = __ldg(x + d.x_vm + i);
+    d.bw[i] = __ldg(dv + d.c_k8 + i) * (__ldg(d.bus_m2gs + n) * vm);
+    d.bw[TN + i] = __ldg(dv + d.c_k9 + i) * (__ldg(d.bus_p2bs + n) * vm);
+  }
+}
+
+// The bus-end products, then the branch kernel reading them (a programmatic
+// dependent launch when `pdl`), for a full sweep over elements [first, end).
+template <unsigned MASK>
+cudaError_t launch_branch_bw(const Dev &d, unsigned rt, const double *x, const double *lam, const double *sx,
+                             const double *dv, double dw, double *grad, double *c, double *jv, double *hv,
+                             double *kv, cudaStream_t s, bool pdl, Prof *prof) {
+  const int32_t bf = d.w0 * d.N, be = d.w1 * d.N;
+  const unsigned g = (unsigned)std::min<int64_t>(((int64_t)be - bf + kBlock - 1) / kBlock, 148 * 4);
+  k_bw<<<g, kBlock, 0, s>>>(d, x, dv, bf, be);
+  Timed tm(prof, s, KIND_BRANCH);
+  const int32_t first = d.w0 * d.L, end = d.w1 * d.L;
+  const unsigned grid = (unsigned)(((int64_t)end - first + MPOPF_BRANCH_BLOCK - 1) / MPOPF_BRANCH_BLOCK);
+  void (*kern)(Dev, unsigned, const double *, const double *, const double *, const double *, double, double *,
+               double *, double *, double *, double *, int32_t, int32_t) =
+      d.all_sym ? k_branch<MASK, true, false, true> : k_branch<MASK, false, false, true>;
+  if (!pdl) {
+    kern<<<grid, MPOPF_BRANCH_BLOCK, 0, s>>>(d, rt, x, lam, sx, dv, dw, grad, c, jv, hv, kv, first, end);
+    return cudaSuccess;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(MPOPF_BRANCH_BLOCK);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, d, rt, x, lam, sx, dv, dw, grad, c, jv, hv, kv, first, end);
 }
 
 // The branch kernel over elements [first, end) on stream s; the instantiation
@@ -376,10 +463,6 @@ void launch_branch(const Dev &d, unsigned rt, const double *x, const double *lam
 // ---------------------------------------------------------------------------
 // Bus x period.
 // ---------------------------------------------------------------------------
-// Waits (griddepcontrol.wait) until the grids this launch depends on
-// programmatically have completed and their writes are visible; returns at
-// once for a launch without such a dependency.
-__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 // PART: 0 everything; 1 the balance rows, their J rows, the shunt W entries,
 // the gradient zeros and the reference row; 2 the va / vm rows of M (the two
@@ -672,22 +755,6 @@ __global__ void __launch_bounds__(kBlock) k_fsum_points(const double *__restrict
 
 unsigned grid_for(int64_t count) { return (unsigned)((count + kBlock - 1) / kBlock); }
 
-// Records a CUDA event pair around one launch when profiling is on.
-struct Timed {
-  Prof *p;
-  cudaStream_t s;
-  int slot;
-  Timed(Prof *prof, cudaStream_t st, int kind) : p(prof), s(st), slot(-1) {
-    if (p && p->next < p->cap) {
-      slot = p->next++;
-      p->kind[slot] = kind;
-      cudaEventRecord(p->ev[2 * slot], s);
-    }
-  }
-  ~Timed() {
-    if (slot >= 0) cudaEventRecord(p->ev[2 * slot + 1], s);
-  }
-};
 
 // The generator kernel (and the objective sum after it) on stream g, which is
 // the caller's stream s or the handle's side stream.
@@ -805,7 +872,14 @@ cudaError_t launch_all(const Dev &d, unsigned rt, const double *x, const double 
                           fork->gen_after);
     return cudaSuccess;
   };
-  if ((mk & rest) && d.L > 0) {
+  // SCHED_BUS_TERMS (full sweeps): the bus-end products in a launch of
+  // their own before the branch kernel
+  const bool bwp = MASK == MPOPF_OUT_ALL && fork && (fork->flags & SCHED_BUS_TERMS) && d.L > 0 && d.N > 0;
+  if (bwp) {
+    const cudaError_t e = launch_branch_bw<MASK>(d, rt, x, lam, sx, dv, dw, grad, c, jv, hv, kv, s,
+                                                 (fork->flags & SCHED_PDL) && !prof, prof);
+    if (e != cudaSuccess) return e;
+  } else if ((mk & rest) && d.L > 0) {
     Timed tm(prof, s, KIND_BRANCH);
     (void)W;
     launch_branch<MASK>(d, rt, x, lam, sx, dv, dw, grad, c, jv, hv, kv, d.w0 * d.L, d.w1 * d.L, s);
@@ -1129,6 +1203,23 @@ int grow_points_scratch(mpopf_handle *h, size_t need, const char *who, cudaStrea
   return MPOPF_OK;
 }
 
+// The default launch schedule of a new handle: the bus kernel as a
+// programmatic dependent launch; the bus-end products in a launch of their own
+// once the branch launch spans at least two waves of resident CTAs (measured,
+// plain launches: 10k buses x 24 / 48 / 168 periods 2.7 / 2.8 / 1.1% faster,
+// 2,000 x 96 / 192 2.5 / 2.0%, 118 x 10,080 2.5%; 2,000 x 48 and 10k x 12,
+// under two waves, within 1.3%; 2,000 x 24, under one wave, a third slower).
+int32_t default_schedule_flags(const Dev &d, int device) {
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || sms < 1) {
+    cudaGetLastError();
+    sms = 148;
+  }
+  const int64_t wave = (int64_t)sms * MPOPF_BRANCH_BLOCK * MPOPF_BRANCH_MINB;  // resident branch elements
+  const int64_t elements = (int64_t)(d.w1 - d.w0) * d.L;
+  return SCHED_PDL | (elements >= 2 * wave ? SCHED_BUS_TERMS : 0);
+}
+
 int eval_launch_count(const Dev &d, unsigned mk, const Fork *fork) {
   const unsigned rest = MPOPF_OUT_GRAD | MPOPF_OUT_CONS | MPOPF_OUT_JAC | MPOPF_OUT_HESS | MPOPF_OUT_KKT;
   int32_t P = 0;
@@ -1138,6 +1229,7 @@ int eval_launch_count(const Dev &d, unsigned mk, const Fork *fork) {
   else {
     if ((mk & rest) && d.L > 0) ++k;
     if (mk & rest) ++k;
+    if (mk == MPOPF_OUT_ALL && (fork->flags & SCHED_BUS_TERMS) && d.L > 0 && d.N > 0) ++k;  // k_bw
   }
   if (mk && d.G > 0) ++k;
   if (mk & MPOPF_OUT_OBJ) ++k;
@@ -1184,7 +1276,8 @@ int mpopf_launch_count(const mpopf_handle *h, unsigned outputs) {
 
 int mpopf_set_sweep_schedule(mpopf_handle *h, int32_t chunk_periods, int32_t flags) {
   if (!h) return fail(MPOPF_ERR_ARG, "mpopf_set_sweep_schedule: NULL handle");
-  if (chunk_periods < 0 || (flags & ~(SCHED_BUS_PRIORITY | SCHED_GEN_FIRST | SCHED_PDL | SCHED_SPLIT_BUS)))
+  if (chunk_periods < 0 ||
+      (flags & ~(SCHED_BUS_PRIORITY | SCHED_GEN_FIRST | SCHED_PDL | SCHED_SPLIT_BUS | SCHED_BUS_TERMS)))
     return fail(MPOPF_ERR_ARG, "mpopf_set_sweep_schedule: bad argument");
   if ((flags ^ h->fork.flags) & SCHED_BUS_PRIORITY) {
     const cudaError_t e = fork_bus_stream(&h->fork, flags & SCHED_BUS_PRIORITY);

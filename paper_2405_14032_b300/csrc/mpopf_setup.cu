@@ -661,6 +661,7 @@ int setup_model(const mpopf_network *net, int32_t n_periods, const double *pd, c
     d.brp = reinterpret_cast<const int4 *>(dev_upload(h, brp, &err));
   }
   d.S = dev_alloc<double>(h, T * 2 * L * kRec, &err);
+  d.bw = dev_alloc<double>(h, 2 * T * N, &err);
   d.fpart_n = (int32_t)std::max<int64_t>(1, (T * G + kBlock - 1) / kBlock);
   d.fpart = dev_alloc<double>(h, d.fpart_n, &err);
   // patterns and bounds
@@ -706,7 +707,7 @@ int setup_model(const mpopf_network *net, int32_t n_periods, const double *pd, c
   if (err == cudaSuccess) err = cudaEventCreateWithFlags(&h->fork.ev_fork, cudaEventDisableTiming);
   if (err == cudaSuccess) err = cudaEventCreateWithFlags(&h->fork.ev_join, cudaEventDisableTiming);
   if (err == cudaSuccess) err = fork_bus_stream(&h->fork, false);
-  h->fork.flags = SCHED_PDL;  // the default launch schedule
+  h->fork.flags = default_schedule_flags(d, h->device);  // the default launch schedule
   if (err != cudaSuccess) {
     std::string msg = std::string(who) + ": side stream: " + cudaGetErrorString(err);
     fork_destroy(h);
@@ -837,6 +838,7 @@ int mpopf_shard_setup(const mpopf_network *net, int32_t n_periods, int32_t t0, i
   if (rc != MPOPF_OK) return rc;
   (*out)->d.w0 = plan.own0;
   (*out)->d.w1 = plan.own1;
+  (*out)->fork.flags = default_schedule_flags((*out)->d, (*out)->device);  // sized by the owned periods
   return MPOPF_OK;
 }
 

@@ -311,11 +311,12 @@ class Handle:
         return int(lib().mpopf_launch_count(self.h, outputs))
 
     SCHED_BUS_PRIORITY, SCHED_GEN_FIRST, SCHED_PDL, SCHED_SPLIT_BUS = 1, 2, 4, 8
+    SCHED_BUS_TERMS = 16
 
     def set_sweep_schedule(self, chunk_periods, flags=0):
         """Period chunks of the evaluation launches (0: one launch per kernel);
-        flags SCHED_BUS_PRIORITY, SCHED_GEN_FIRST, SCHED_PDL, SCHED_SPLIT_BUS (see
-        mpopf_set_sweep_schedule)."""
+        flags SCHED_BUS_PRIORITY, SCHED_GEN_FIRST, SCHED_PDL, SCHED_SPLIT_BUS,
+        SCHED_BUS_TERMS (see mpopf_set_sweep_schedule)."""
         _check(lib().mpopf_set_sweep_schedule(self.h, int(chunk_periods), int(flags)), "mpopf_set_sweep_schedule")
 
     def set_gen_dependency(self, event):

@@ -41,6 +41,24 @@ def full():
     h.close()
 
 
+def test_default_schedule_has_the_bus_term_launch(full):
+    """The benchmark-size handle starts with the bus-end products in a launch
+    of their own (its branch launch spans far more than two waves), so the
+    parity tests of this file check that schedule; a sweep with it turned off
+    gives the same outputs bit for bit."""
+    from paper_2405_14032_b300 import mpopf
+    inst, pt, h, d, host, pat, o = full
+    assert h.sweep_schedule() == (0, mpopf.Handle.SCHED_PDL | mpopf.Handle.SCHED_BUS_TERMS)
+    h.set_sweep_schedule(0, mpopf.Handle.SCHED_PDL)
+    try:
+        out = h.sweep(d["x"], d["lam"], pt.sigma, d["sx"], d["dv"], pt.delta_w)
+        torch.cuda.synchronize()
+        for k, v in out.items():
+            assert np.array_equal(_np(v), host[k]), k
+    finally:
+        h.set_sweep_schedule(0, mpopf.Handle.SCHED_PDL | mpopf.Handle.SCHED_BUS_TERMS)
+
+
 @pytest.mark.parametrize("t", PERIODS)
 def test_sampled_period_bitwise(full, t):
     inst, pt, h, d, host, pat, o = full

@@ -17,13 +17,13 @@ def _dev(a):
     return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
 
 
-@pytest.mark.parametrize("sched", [(0, 4), (0, 0), (2, 1), (1, 2), (0, 8)])
+@pytest.mark.parametrize("sched", [(0, 4), (0, 0), (2, 1), (1, 2), (0, 8), (0, 20), (0, 16)])
 @pytest.mark.parametrize("shape", [(300, 480, 60, 180, 6), (57, 91, 11, 30, 3), (40, 64, 0, 20, 4)])
 def test_graph_replay_equals_plain(shape, sched):
     """sched: the launch schedule (period chunks with the bus kernels on a
     second stream, itself a parallel branch of the captured graph; the bus
     kernel as a programmatic dependent launch, a programmatic edge of the
-    graph)."""
+    graph; the bus-end products' launch before the branch kernel)."""
     from paper_2405_14032_b300 import mpopf
     N, L, G, D, T = shape
     inst = synth.make_instance(71, N, L, G, D, T)

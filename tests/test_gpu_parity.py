@@ -205,20 +205,25 @@ def test_sweep_host_matches_device(name):
             assert np.array_equal(out[k], dev[k]), (name, k)
 
 
-SCHEDULES = [(1, 0), (2, 1), (3, 2), (4, 3), (5, 0), (0, 0), (0, 2), (0, 6), (0, 8), (0, 12)]
+SCHEDULES = [(1, 0), (2, 1), (3, 2), (4, 3), (5, 0), (0, 0), (0, 2), (0, 6), (0, 8), (0, 12), (0, 16), (0, 20),
+             (0, 24), (2, 16)]
 
 
 def test_chunked_schedules_equal_plain(case):
     """Every launch schedule (period chunks, the bus kernel of each chunk on a
     second stream, with and without its priority raised, the generator work
     forked first or last; the bus kernel as a programmatic dependent launch;
-    the bus work split in two kernels side by side) gives the plain sweep's
+    the bus work split in two kernels side by side; the bus-end products of
+    M in a launch of their own before the branch kernel, with and without the
+    programmatic dependency) gives the plain sweep's
     outputs bit for bit, for
     every output and for the callbacks alone; the plain sweep matches the
     oracle (test_values_match_oracle), so these do too."""
     name, cs = case
     default = cs.h.sweep_schedule()
-    assert default == (0, 4)  # one launch per kernel, the bus kernel a programmatic dependent launch
+    # one launch per kernel, the bus kernel a programmatic dependent launch
+    # (these networks' branch launches fit one wave: no bus-term launch)
+    assert default == (0, 4)
     full = cs.run()
     try:
         for P, flags in SCHEDULES:
@@ -252,5 +257,5 @@ def test_chunked_schedule_cfg2_and_launch_count():
     with pytest.raises(mp.MpopfError, match="bad argument"):
         cs.h.set_sweep_schedule(-1, 0)
     with pytest.raises(mp.MpopfError, match="bad argument"):
-        cs.h.set_sweep_schedule(4, 16)
+        cs.h.set_sweep_schedule(4, 1 << 10)  # a bit no schedule defines
     cs.h.close()

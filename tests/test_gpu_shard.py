@@ -87,7 +87,10 @@ def test_shards_stitch_to_the_unsharded_sweep(name):
     pat = {k: v.cpu().numpy() for k, v in h.pattern().items()}
     torch.cuda.synchronize()
     for parts in parts_list:
-        plans, hs, outs = run_shards(inst, pt, parts, schedule=(2, 0) if parts == 2 else (0, 0))
+        # period chunks for two shards, the bus-end products' own launch (with the
+        # programmatic dependencies) for three, the plain launches otherwise
+        plans, hs, outs = run_shards(inst, pt, parts, schedule=(2, 0) if parts == 2 else (0, 20) if parts == 3
+                                     else (0, 0))
         for key, what in KEYS:
             whole = torch.full_like(ref[key], float("nan"))
             for p, out in zip(plans, outs):

@@ -26,13 +26,14 @@ def test_branch_kernel_register_and_spill_budget(tmp_path):
     cmd = [NVCC, *flags, "-Xptxas", "-v", "-I", os.path.join(build.ROOT, "include"), "-c", src,
            "-o", str(tmp_path / "k.o")]
     out = subprocess.run(cmd, capture_output=True, text=True, check=True).stderr
-    # the report blocks of the full-sweep instantiations k_branch<63, SYM, PTS>
+    # the report blocks of the full-sweep instantiations k_branch<63, SYM, PTS, BW>
     # (with and without the per-branch symmetry test; one point, or several
-    # points with their pointer offsets, which hold more values live)
-    for pts, budget in (("0", (136, 176)), ("1", (184, 224))):
-        blocks = list(re.finditer(r"Compiling entry function '[^']*k_branchILj63ELb[01]ELb" + pts +
+    # points with their pointer offsets, which hold more values live; the
+    # bus-end products computed, or read from the pre-pass)
+    for pts, bw, budget in (("0", "0", (136, 176)), ("1", "0", (184, 224)), ("0", "1", (136, 176))):
+        blocks = list(re.finditer(r"Compiling entry function '[^']*k_branchILj63ELb[01]ELb" + pts + "ELb" + bw +
                                   r"E[^']*'.*?Used (\d+) registers", out, re.S))
-        assert len(blocks) == 2, f"no resource report for both k_branch<63, SYM, {pts}> instantiations"
+        assert len(blocks) == 2, f"no resource report for both k_branch<63, SYM, {pts}, {bw}> instantiations"
         for m in blocks:
             block = out[m.start():m.end()]
             regs = int(m.group(1))
