@@ -132,11 +132,14 @@ struct Fork {
   int32_t chunk = 0;                   // periods per chunk; 0: one launch per kernel
   int32_t flags = 0;                   // SCHED_*: bus stream at the highest priority; generator work forked first
   cudaEvent_t gen_after = nullptr;     // the caller's event the generator work also waits for (or none)
+  int32_t sms = 148;                   // SMs of the handle's device (launch shapes)
 };
 
-// The launch schedule (SCHED_* flags) a new handle starts with, from its
-// branch launch's size on `device` (mpopf_kernels.cu).
-int32_t default_schedule_flags(const Dev &d, int device);
+// The number of SMs of `device` (148 if the query fails), and the launch
+// schedule (SCHED_* flags) a new handle starts with, from its branch launch's
+// size on a device of `sms` SMs (mpopf_kernels.cu).
+int32_t device_sms(int device);
+int32_t default_schedule_flags(const Dev &d, int32_t sms);
 
 // Kernel launchers (mpopf_kernels.cu).  With fork == nullptr every launch goes
 // to s in order.

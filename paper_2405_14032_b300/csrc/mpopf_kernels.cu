@@ -393,6 +393,23 @@ __global__ void __launch_bounds__(MPOPF_BRANCH_BLOCK, MPOPF_BRANCH_MINB)
                                          full ? s_stage[threadIdx.x >> 5] : nullptr);
 }
 
+// The branch kernel over elements [first, end) on stream s; the instantiation
+// without the per-branch symmetry test when every branch is symmetric
+// (measured 0.798 against 0.810 ms at 10k buses x 168; the same values).
+// With PTS, `points` points (grid y).
+template <unsigned MASK, bool PTS = false>
+void launch_branch(const Dev &d, unsigned rt, const double *x, const double *lam, const double *sx,
+                   const double *dv, double dw, double *grad, double *c, double *jv, double *hv, double *kv,
+                   int32_t first, int32_t end, cudaStream_t s, unsigned points = 1) {
+  const dim3 grid((unsigned)(((int64_t)end - first + MPOPF_BRANCH_BLOCK - 1) / MPOPF_BRANCH_BLOCK), PTS ? points : 1);
+  if (d.all_sym)
+    k_branch<MASK, true, PTS><<<grid, MPOPF_BRANCH_BLOCK, 0, s>>>(d, rt, x, lam, sx, dv, dw, grad, c, jv, hv, kv,
+                                                                   first, end);
+  else
+    k_branch<MASK, false, PTS><<<grid, MPOPF_BRANCH_BLOCK, 0, s>>>(d, rt, x, lam, sx, dv, dw, grad, c, jv, hv, kv,
+                                                                    first, end);
+}
+
 // The bus-end products of the arc rows of M, once per bus and period of
 // [first, end) (t N + n): w8 = D8 (m2gs vm) and w9 = D9 (p2bs vm), the
 // operations the branch kernel would otherwise do at each end of each
@@ -417,9 +434,9 @@ __global__ void __launch_bounds__(kBlock) k_bw(Dev d, const double *__restrict__
 template <unsigned MASK>
 cudaError_t launch_branch_bw(const Dev &d, unsigned rt, const double *x, const double *lam, const double *sx,
                              const double *dv, double dw, double *grad, double *c, double *jv, double *hv,
-                             double *kv, cudaStream_t s, bool pdl, Prof *prof) {
+                             double *kv, cudaStream_t s, bool pdl, Prof *prof, int32_t sms) {
   const int32_t bf = d.w0 * d.N, be = d.w1 * d.N;
-  const unsigned g = (unsigned)std::min<int64_t>(((int64_t)be - bf + kBlock - 1) / kBlock, 148 * 4);
+  const unsigned g = (unsigned)std::min<int64_t>(((int64_t)be - bf + kBlock - 1) / kBlock, 4 * (int64_t)sms);
   k_bw<<<g, kBlock, 0, s>>>(d, x, dv, bf, be);
   Timed tm(prof, s, KIND_BRANCH);
   const int32_t first = d.w0 * d.L, end = d.w1 * d.L;
@@ -441,23 +458,6 @@ cudaError_t launch_branch_bw(const Dev &d, unsigned rt, const double *x, const d
   cfg.attrs = at;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, kern, d, rt, x, lam, sx, dv, dw, grad, c, jv, hv, kv, first, end);
-}
-
-// The branch kernel over elements [first, end) on stream s; the instantiation
-// without the per-branch symmetry test when every branch is symmetric
-// (measured 0.798 against 0.810 ms at 10k buses x 168; the same values).
-// With PTS, `points` points (grid y).
-template <unsigned MASK, bool PTS = false>
-void launch_branch(const Dev &d, unsigned rt, const double *x, const double *lam, const double *sx,
-                   const double *dv, double dw, double *grad, double *c, double *jv, double *hv, double *kv,
-                   int32_t first, int32_t end, cudaStream_t s, unsigned points = 1) {
-  const dim3 grid((unsigned)(((int64_t)end - first + MPOPF_BRANCH_BLOCK - 1) / MPOPF_BRANCH_BLOCK), PTS ? points : 1);
-  if (d.all_sym)
-    k_branch<MASK, true, PTS><<<grid, MPOPF_BRANCH_BLOCK, 0, s>>>(d, rt, x, lam, sx, dv, dw, grad, c, jv, hv, kv,
-                                                                   first, end);
-  else
-    k_branch<MASK, false, PTS><<<grid, MPOPF_BRANCH_BLOCK, 0, s>>>(d, rt, x, lam, sx, dv, dw, grad, c, jv, hv, kv,
-                                                                    first, end);
 }
 
 // ---------------------------------------------------------------------------
@@ -877,7 +877,7 @@ cudaError_t launch_all(const Dev &d, unsigned rt, const double *x, const double 
   const bool bwp = MASK == MPOPF_OUT_ALL && fork && (fork->flags & SCHED_BUS_TERMS) && d.L > 0 && d.N > 0;
   if (bwp) {
     const cudaError_t e = launch_branch_bw<MASK>(d, rt, x, lam, sx, dv, dw, grad, c, jv, hv, kv, s,
-                                                 (fork->flags & SCHED_PDL) && !prof, prof);
+                                                 (fork->flags & SCHED_PDL) && !prof, prof, fork->sms);
     if (e != cudaSuccess) return e;
   } else if ((mk & rest) && d.L > 0) {
     Timed tm(prof, s, KIND_BRANCH);
@@ -1209,12 +1209,16 @@ int grow_points_scratch(mpopf_handle *h, size_t need, const char *who, cudaStrea
 // plain launches: 10k buses x 24 / 48 / 168 periods 2.7 / 2.8 / 1.1% faster,
 // 2,000 x 96 / 192 2.5 / 2.0%, 118 x 10,080 2.5%; 2,000 x 48 and 10k x 12,
 // under two waves, within 1.3%; 2,000 x 24, under one wave, a third slower).
-int32_t default_schedule_flags(const Dev &d, int device) {
+int32_t device_sms(int device) {
   int sms = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || sms < 1) {
     cudaGetLastError();
-    sms = 148;
+    sms = 148;  // B300
   }
+  return sms;
+}
+
+int32_t default_schedule_flags(const Dev &d, int32_t sms) {
   const int64_t wave = (int64_t)sms * MPOPF_BRANCH_BLOCK * MPOPF_BRANCH_MINB;  // resident branch elements
   const int64_t elements = (int64_t)(d.w1 - d.w0) * d.L;
   return SCHED_PDL | (elements >= 2 * wave ? SCHED_BUS_TERMS : 0);

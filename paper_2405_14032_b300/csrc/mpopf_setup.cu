@@ -707,7 +707,8 @@ int setup_model(const mpopf_network *net, int32_t n_periods, const double *pd, c
   if (err == cudaSuccess) err = cudaEventCreateWithFlags(&h->fork.ev_fork, cudaEventDisableTiming);
   if (err == cudaSuccess) err = cudaEventCreateWithFlags(&h->fork.ev_join, cudaEventDisableTiming);
   if (err == cudaSuccess) err = fork_bus_stream(&h->fork, false);
-  h->fork.flags = default_schedule_flags(d, h->device);  // the default launch schedule
+  h->fork.sms = device_sms(h->device);
+  h->fork.flags = default_schedule_flags(d, h->fork.sms);  // the default launch schedule
   if (err != cudaSuccess) {
     std::string msg = std::string(who) + ": side stream: " + cudaGetErrorString(err);
     fork_destroy(h);
@@ -838,7 +839,7 @@ int mpopf_shard_setup(const mpopf_network *net, int32_t n_periods, int32_t t0, i
   if (rc != MPOPF_OK) return rc;
   (*out)->d.w0 = plan.own0;
   (*out)->d.w1 = plan.own1;
-  (*out)->fork.flags = default_schedule_flags((*out)->d, (*out)->device);  // sized by the owned periods
+  (*out)->fork.flags = default_schedule_flags((*out)->d, (*out)->fork.sms);  // sized by the owned periods
   return MPOPF_OK;
 }
 
