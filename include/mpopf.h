@@ -489,7 +489,9 @@ int mpopf_batch_status(mpopf_batch *b);
 int mpopf_batch_test_stall(mpopf_batch *b, int32_t on);
 void mpopf_batch_destroy(mpopf_batch *b);
 
-/* Number of kernel launches one mpopf_eval call with these output bits makes. */
+/* Number of kernel launches one mpopf_eval call with these output bits makes
+ * under the handle's current schedule (outside per-kernel profiling, which
+ * runs the unsplit launches without the programmatic dependencies). */
 int mpopf_launch_count(const mpopf_handle *h, unsigned outputs);
 
 /* Launch schedule of the evaluation calls of a handle (a performance setting;

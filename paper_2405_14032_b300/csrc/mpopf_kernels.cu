@@ -1234,6 +1234,9 @@ int eval_launch_count(const Dev &d, unsigned mk, const Fork *fork) {
     if ((mk & rest) && d.L > 0) ++k;
     if (mk & rest) ++k;
     if (mk == MPOPF_OUT_ALL && (fork->flags & SCHED_BUS_TERMS) && d.L > 0 && d.N > 0) ++k;  // k_bw
+    if ((fork->flags & SCHED_SPLIT_BUS) && (mk & MPOPF_OUT_KKT) &&
+        (mk & (MPOPF_OUT_GRAD | MPOPF_OUT_CONS | MPOPF_OUT_JAC | MPOPF_OUT_HESS)))
+      ++k;  // the bus work as two kernels
   }
   if (mk && d.G > 0) ++k;
   if (mk & MPOPF_OUT_OBJ) ++k;

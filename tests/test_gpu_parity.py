@@ -245,6 +245,11 @@ def test_chunked_schedule_cfg2_and_launch_count():
     import paper_2405_14032_b300.mpopf as mp
     cs = Case(synth.config_instance("cfg2"), 2)
     plain = cs.h.launch_count()
+    assert plain == 4  # branch, bus, generator, objective
+    cs.h.set_sweep_schedule(0, mp.Handle.SCHED_PDL | mp.Handle.SCHED_BUS_TERMS)
+    assert cs.h.launch_count() == plain + 1  # and the bus-end products
+    cs.h.set_sweep_schedule(0, mp.Handle.SCHED_SPLIT_BUS)
+    assert cs.h.launch_count() == plain + 1  # the bus work as two kernels
     cs.h.set_sweep_schedule(5, mp.Handle.SCHED_BUS_PRIORITY)
     assert cs.h.launch_count() == plain - 2 + 2 * 5
     pt, o = cs.pt, cs.o
