@@ -256,8 +256,12 @@ int mpopf_sweep(mpopf_handle *h, const double *x, const double *lam, double sigm
  * f [k], grad [k][n], c [k][m], jv [k][nnz_jac], hv [k][nnz_hess],
  * kv [k][nnz_kkt]; sigma and delta_w are shared by the k points.  Each point's
  * outputs equal mpopf_sweep's at that point bit for bit.  1 <= k <= 65535.
- * Scratch for the points' incidence records and objective partials
- * (k x (2 L T x 48 + 8 ceil(T G / 256)) bytes) is allocated by the first
+ * When the k points' branch elements span at least two waves of the device
+ * (k T L >= 2 x SMs x 768), the bus-end products D8 (m2gs vm), D9 (p2bs vm)
+ * are formed in a launch of their own first, as MPOPF_SCHED_BUS_TERMS does
+ * for a single sweep.  Scratch for the points' incidence records, objective
+ * partials and those products (k x (2 L T x 48 + 8 ceil(T G / 256)
+ * [+ 16 T N]) bytes) is allocated by the first
  * call that needs more than the handle holds (after a device-wide
  * synchronisation when it replaces a smaller one) and kept by the handle;
  * calls on one handle must not overlap.  MPOPF_ERR_ARG for a NULL buffer, k

@@ -311,10 +311,12 @@ __device__ __forceinline__ void branch_body(const Dev &d, int32_t tl, unsigned r
   if (BW) {
     grid_dependency_wait();
     const int64_t TN = (int64_t)d.T * d.N;
-    w8f = __ldcg(d.bw + tN + f);
-    w9f = __ldcg(d.bw + TN + tN + f);
-    w8t = __ldcg(d.bw + tN + to);
-    w9t = __ldcg(d.bw + TN + tN + to);
+    const double *bw = d.bw;
+    if (PTS) bw += (int64_t)blockIdx.y * 2 * TN;
+    w8f = __ldcg(bw + tN + f);
+    w9f = __ldcg(bw + TN + tN + f);
+    w8t = __ldcg(bw + tN + to);
+    w9t = __ldcg(bw + TN + tN + to);
   } else {
     w8f = D8f * (__ldg(d.bus_m2gs + f) * vf);
     w9f = D9f * (__ldg(d.bus_p2bs + f) * vf);
@@ -416,10 +418,18 @@ void launch_branch(const Dev &d, unsigned rt, const double *x, const double *lam
 // branch.  A grid-stride loop over a grid of at most a few CTAs per SM, so
 // that every CTA is resident at once and the branch kernel behind it (a
 // programmatic dependent launch) starts at once.
+// With PTS, point blockIdx.y of a sweep over several points (its x, D and
+// products follow the earlier points').
+template <bool PTS = false>
 __global__ void __launch_bounds__(kBlock) k_bw(Dev d, const double *__restrict__ x, const double *__restrict__ dv,
                                                int32_t first, int32_t end) {
   asm volatile("griddepcontrol.launch_dependents;");
   const int64_t TN = (int64_t)d.T * d.N;
+  if (PTS) {
+    x += (int64_t)blockIdx.y * d.n;
+    dv += (int64_t)blockIdx.y * d.m;
+    d.bw += (int64_t)blockIdx.y * 2 * TN;
+  }
   for (int32_t i = first + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x); i < end;
        i += (int32_t)(gridDim.x * blockDim.x)) {
     const int32_t n = i % d.N;
@@ -934,6 +944,14 @@ cudaError_t launch_all(const Dev &d, unsigned rt, const double *x, const double 
   return cudaSuccess;
 }
 
+// Whether a sweep over `points` points forms the bus-end products in a launch
+// of their own: the same rule as a single sweep's default schedule, applied
+// to all points' branch elements.
+bool points_bus_terms(const Dev &d, int32_t points, const Fork *fork) {
+  const int64_t wave = (int64_t)fork->sms * MPOPF_BRANCH_BLOCK * MPOPF_BRANCH_MINB;
+  return d.N > 0 && (int64_t)points * d.T * d.L >= 2 * wave;
+}
+
 // A full sweep at `points` points of one network (the sweep's kernels once
 // each, over every point: grid y): the branch kernel on s, the generator work
 // and the objectives forked onto the side stream after it, the bus kernel as
@@ -941,7 +959,7 @@ cudaError_t launch_all(const Dev &d, unsigned rt, const double *x, const double 
 // fpart hold the points' incidence records (points x 2 L T kRec doubles) and
 // objective partials (points x tiles).  A point's elements run the code of a
 // single sweep's, so its outputs are launch_all's at that point bit for bit.
-cudaError_t launch_points(const Dev &d0, int32_t points, double *S, double *fpart, const double *x,
+cudaError_t launch_points(const Dev &d0, int32_t points, double *S, double *fpart, double *bw, const double *x,
                           const double *lam, double sigma, const double *sx, const double *dv, double dw, double *f,
                           double *grad, double *c, double *jv, double *hv, double *kv, cudaStream_t s,
                           const Fork *fork) {
@@ -949,8 +967,38 @@ cudaError_t launch_points(const Dev &d0, int32_t points, double *S, double *fpar
   Dev d = d0;
   d.S = S;
   d.fpart = fpart;
+  d.bw = bw;
   const unsigned P = (unsigned)points;
-  if (d.L > 0) launch_branch<A, true>(d, A, x, lam, sx, dv, dw, grad, c, jv, hv, kv, 0, d.T * d.L, s, P);
+  if (d.L > 0 && points_bus_terms(d, points, fork)) {
+    // the points' bus-end products first (grid y = point), then the branch
+    // kernel reading them, its programmatic dependent launch
+    const int32_t be = d.T * d.N;
+    const unsigned gx = (unsigned)std::max<int64_t>(
+        1, std::min<int64_t>(((int64_t)be + kBlock - 1) / kBlock, (4 * (int64_t)fork->sms + P - 1) / P));
+    k_bw<true><<<dim3(gx, P), kBlock, 0, s>>>(d, x, dv, 0, be);
+    const int32_t end = d.T * d.L;
+    const dim3 grid((unsigned)(((int64_t)end + MPOPF_BRANCH_BLOCK - 1) / MPOPF_BRANCH_BLOCK), P);
+    void (*kern)(Dev, unsigned, const double *, const double *, const double *, const double *, double, double *,
+                 double *, double *, double *, double *, int32_t, int32_t) =
+        d.all_sym ? k_branch<A, true, true, true> : k_branch<A, false, true, true>;
+    if (fork->flags & SCHED_PDL) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = grid;
+      cfg.blockDim = dim3(MPOPF_BRANCH_BLOCK);
+      cfg.stream = s;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      at[0].val.programmaticStreamSerializationAllowed = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, d, A, x, lam, sx, dv, dw, grad, c, jv, hv, kv, 0, end);
+      if (e != cudaSuccess) return e;
+    } else {
+      kern<<<grid, MPOPF_BRANCH_BLOCK, 0, s>>>(d, A, x, lam, sx, dv, dw, grad, c, jv, hv, kv, 0, end);
+    }
+  } else if (d.L > 0) {
+    launch_branch<A, true>(d, A, x, lam, sx, dv, dw, grad, c, jv, hv, kv, 0, d.T * d.L, s, P);
+  }
   cudaError_t e = cudaEventRecord(fork->ev_fork, s);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(fork->side, fork->ev_fork, 0);
   if (e != cudaSuccess) return e;
@@ -1375,11 +1423,13 @@ int mpopf_sweep_points(mpopf_handle *h, int32_t points, const double *x, const d
   const Dev &d = h->d;
   const size_t rec = (size_t)2 * d.L * d.T * kRec;  // record doubles of one point
   const size_t tiles = grid_for((int64_t)d.T * d.G);
-  const int rc = grow_points_scratch(h, (size_t)points * (rec + tiles) * sizeof(double), "mpopf_sweep_points",
+  const size_t bwn = points_bus_terms(d, points, &h->fork) ? (size_t)2 * d.T * d.N : 0;  // bus-end products
+  const int rc = grow_points_scratch(h, (size_t)points * (rec + tiles + bwn) * sizeof(double), "mpopf_sweep_points",
                                      static_cast<cudaStream_t>(stream));
   if (rc != MPOPF_OK) return rc;
-  cudaError_t e = launch_points(d, points, h->pts, h->pts + (size_t)points * rec, x, lam, sigma, sigma_x, dvec,
-                                delta_w, f, grad, c, jv, hv, kv, static_cast<cudaStream_t>(stream), &h->fork);
+  cudaError_t e = launch_points(d, points, h->pts, h->pts + (size_t)points * rec,
+                                h->pts + (size_t)points * (rec + tiles), x, lam, sigma, sigma_x, dvec, delta_w, f,
+                                grad, c, jv, hv, kv, static_cast<cudaStream_t>(stream), &h->fork);
   const cudaError_t l = cudaGetLastError();
   if (e == cudaSuccess) e = l;
   if (e != cudaSuccess) return fail(MPOPF_ERR_CUDA, std::string("mpopf_sweep_points: ") + cudaGetErrorString(e));

@@ -30,7 +30,8 @@ def test_branch_kernel_register_and_spill_budget(tmp_path):
     # (with and without the per-branch symmetry test; one point, or several
     # points with their pointer offsets, which hold more values live; the
     # bus-end products computed, or read from the pre-pass)
-    for pts, bw, budget in (("0", "0", (136, 176)), ("1", "0", (184, 224)), ("0", "1", (136, 176))):
+    for pts, bw, budget in (("0", "0", (136, 176)), ("1", "0", (184, 224)), ("0", "1", (136, 176)),
+                            ("1", "1", (136, 176))):
         blocks = list(re.finditer(r"Compiling entry function '[^']*k_branchILj63ELb[01]ELb" + pts + "ELb" + bw +
                                   r"E[^']*'.*?Used (\d+) registers", out, re.S))
         assert len(blocks) == 2, f"no resource report for both k_branch<63, SYM, {pts}, {bw}> instantiations"
